@@ -1,0 +1,63 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the bench.
+
+This module draws random numbers and nothing else: it holds none of the
+method's arithmetic (no viscosity formula, no operator, no solver step).
+
+The multi-sinker benchmark of Sec. 2.1 places n sinkers at "precomputed random
+points" that the paper does not publish, so seeded stand-ins are drawn here:
+SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014) turned into 53-bit uniforms u in [0, 1), mapped to
+c = lo + (hi - lo) * u, drawn in the order sinker i, then x, y, z.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_MASK64 = (1 << 64) - 1
+_GOLDEN = 0x9E3779B97F4A7C15
+
+
+def splitmix64_stream(seed: int, count: int) -> list[int]:
+    """Return the first `count` 64-bit outputs of SplitMix64 seeded with `seed`."""
+    state = seed & _MASK64
+    out = []
+    for _ in range(count):
+        state = (state + _GOLDEN) & _MASK64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+        out.append(z ^ (z >> 31))
+    return out
+
+
+def uniform01(seed: int, count: int) -> np.ndarray:
+    """`count` doubles in [0, 1) from the top 53 bits of SplitMix64 outputs."""
+    vals = splitmix64_stream(seed, count)
+    return np.array([(v >> 11) * (1.0 / (1 << 53)) for v in vals], dtype=np.float64)
+
+
+def sinker_centres(seed: int, n_sinkers: int, lo: float = 0.1, hi: float = 0.9) -> np.ndarray:
+    """Sinker centres c_i, shape (n_sinkers, 3), uniform in [lo, hi]^3 (Sec. 2.1 stand-in)."""
+    u = uniform01(seed, 3 * n_sinkers).reshape(n_sinkers, 3)
+    return lo + (hi - lo) * u
+
+
+def normal_vector(seed: int, size: int) -> np.ndarray:
+    """Standard-normal float64 vector of length `size` (a seeded numpy Generator)."""
+    return np.random.default_rng(seed).standard_normal(size)
+
+
+def uniform_vector(seed: int, size: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """Uniform float64 vector of length `size` in [lo, hi) (a seeded numpy Generator)."""
+    return np.random.default_rng(seed).uniform(lo, hi, size)
+
+
+# Workload definitions: the multi-sinker problems of Sec. 2.1 at the sizes the
+# tests and the bench run.  omega is the sinker diameter, delta the Gaussian
+# decay, dr the dynamic ratio max(mu)/min(mu).
+WORKLOADS = {
+    "8^3-Q2-S4-DR1e4": dict(n=8, k=2, n_sinkers=4, omega=0.1, delta=200.0, dr=1e4, seed=0),
+    "32^3-Q2-S24-DR1e6": dict(n=32, k=2, n_sinkers=24, omega=0.05, delta=200.0, dr=1e6, seed=0),
+    "24^3-Q3-S32-DR1e8": dict(n=24, k=3, n_sinkers=32, omega=0.1, delta=200.0, dr=1e8, seed=0),
+    "64^3-Q2-S64-DR1e10": dict(n=64, k=2, n_sinkers=64, omega=0.04, delta=400.0, dr=1e10, seed=0),
+}

@@ -1,0 +1,205 @@
+"""Pins for the oracle's FGMRES, w-BFBT and Stokes solve (Sec. 1.3, Eq. wbfbt, Sec. 3, Sec. 1.2)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+import sympy as sy
+
+from oracle import krylov
+from oracle import mesh as M
+from oracle import operators as op
+from oracle import sinker
+from oracle import wbfbt as W
+from paper_1607_03936_gb300 import inputs
+
+
+# ----------------------------------------------------------------- FGMRES
+
+def test_fgmres_iterates_minimise_residual_over_krylov_space():
+    rng = np.random.default_rng(0)
+    n = 30
+    A = np.eye(n) * 3 + rng.standard_normal((n, n)) / np.sqrt(n)
+    P = np.diag(1 + rng.random(n))
+    b = rng.standard_normal(n)
+    hist = []
+    krylov.fgmres(lambda v: A @ v, lambda v: P @ v, b, rtol=1e-14, restart=n, maxit=12, history=hist)
+    # brute force: min ||b - A P y|| over y in K_j(A P, b)
+    AP = A @ P
+    kv = [b / np.linalg.norm(b)]
+    for j in range(1, 13):
+        Q, _ = np.linalg.qr(np.stack(kv, axis=1))
+        y, *_ = np.linalg.lstsq(AP @ Q, b, rcond=None)
+        best = np.linalg.norm(b - AP @ Q @ y) / np.linalg.norm(b)
+        assert abs(hist[j - 1] - best) < 1e-10
+        kv.append(AP @ kv[-1] / np.linalg.norm(AP @ kv[-1]))
+
+
+def test_fgmres_restarted_reaches_solution():
+    rng = np.random.default_rng(1)
+    n = 60
+    A = np.eye(n) * 4 + rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    x, its, rel = krylov.fgmres(lambda v: A @ v, lambda v: v, b, rtol=1e-12, restart=7, maxit=500)
+    assert rel <= 1e-12
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), atol=1e-10)
+
+
+# ----------------------------------------------------------------- problem helpers
+
+def _problem(n, k, dr, ns, seed=0, omega=0.1, delta=200.0):
+    m = M.Mesh(n, n, n, k)
+    c = inputs.sinker_centres(seed, ns)
+    mu, f = W.sinker_problem(m, c, omega, delta, dr)
+    return m, mu, f
+
+
+def _dense_schur(prob):
+    m = prob.mesh
+    free = np.flatnonzero(m.interior_dof_mask())
+    Bf = prob.B[:, free].toarray()
+    return Bf @ np.linalg.solve(prob.A[free][:, free].toarray(), Bf.T)
+
+
+def test_default_boundary_amplification_rule():
+    assert W.default_a_r(M.Mesh(32, 32, 32, 2)) == 2.0
+    assert W.default_a_r(M.Mesh(64, 64, 64, 2)) == 4.0
+    assert W.default_a_r(M.Mesh(24, 24, 24, 3)) == 3.0
+    assert W.default_a_r(M.Mesh(8, 8, 8, 2)) == 1.0
+    assert W.default_a_r(M.Mesh(32, 32, 32, 3)) == 4.0   # Table 3b, k = 3
+
+
+@pytest.mark.parametrize("sign", [-1.0, 1.0])
+def test_two_iterations_with_exact_blocks(sign):
+    """Exact A^-1 and S^-1 in the block preconditioner: GMRES converges in 2 iterations (Sec. 1.3)."""
+    m, mu, f = _problem(4, 2, 1e4, 4)
+    prob = W.StokesProblem(m, mu)
+    S = _dense_schur(prob)
+    Sp = np.linalg.pinv(S, rcond=1e-12, hermitian=True)
+    pc = W.BlockPreconditioner(prob, mode="exact", schur_sign=sign,
+                               schur_inv=lambda r: op.project_pressure(m, Sp @ op.project_pressure(m, r)))
+    F = np.concatenate([op.load_vector(m, f), np.zeros(m.n_p)])
+    hist = []
+    x, its, rel = krylov.fgmres(prob.apply_K, pc.apply, F, rtol=1e-11, restart=50, history=hist)
+    assert its == 2 and rel < 1e-10
+
+
+@pytest.mark.parametrize("dr", [1e4, 1e6])
+def test_wbfbt_lower_spectral_bound(dr):
+    """With C = D the w-BFBT S~ satisfies q.S~q <= q.Sq, so lambda(S~^-1 S) >= 1 (Sec. 3, lower bound)."""
+    m, mu, _ = _problem(4, 2, dr, 4)
+    prob = W.StokesProblem(m, mu, a_l=1.0, a_r=1.0)
+    S = _dense_schur(prob)
+    wb = W.WBFBT(prob, mode="exact")
+    npr = m.n_p
+    Sinv = np.stack([wb.apply(e) for e in np.eye(npr)], axis=1)
+    one = op.constant_pressure(m) / np.sqrt(m.n_elem)
+    Q, _ = np.linalg.qr(np.column_stack([one, np.eye(npr)[:, : npr - 1]]))
+    Q = Q[:, 1:]                                   # orthonormal basis of the mean-zero space
+    ev = np.sort(np.linalg.eigvals(Q.T @ Sinv @ Q @ Q.T @ S @ Q).real)
+    assert ev[0] >= 1.0 - 1e-9
+    assert ev[-1] < 1e4                            # bounded; its value is reported, not pinned
+
+
+def test_wbfbt_lower_bound_fails_for_a_wrong_weight_order():
+    """Control for the bound test: swapping the roles of C^-1 inside the middle factor breaks it."""
+    m, mu, _ = _problem(4, 2, 1e6, 4)
+    prob = W.StokesProblem(m, mu, a_l=1.0, a_r=1.0)
+    S = _dense_schur(prob)
+    wb = W.WBFBT(prob, mode="exact")
+    # a plausible bug: the middle factor without the weights, B A B^T
+    def wrong(r):
+        r = op.project_pressure(m, r)
+        y = wb.Kr_inv(r)
+        z = prob.B @ (prob.A @ (prob.BT @ y))
+        return op.project_pressure(m, wb.Kl_inv(z))
+    npr = m.n_p
+    Sinv = np.stack([wrong(e) for e in np.eye(npr)], axis=1)
+    one = op.constant_pressure(m) / np.sqrt(m.n_elem)
+    Q, _ = np.linalg.qr(np.column_stack([one, np.eye(npr)[:, : npr - 1]]))
+    Q = Q[:, 1:]
+    ev = np.sort(np.linalg.eigvals(Q.T @ Sinv @ Q @ Q.T @ S @ Q).real)
+    assert ev[0] < 1.0 - 1e-3
+
+
+def test_scale_invariance_of_the_solve():
+    """mu -> 100 mu, f -> 100 f: u unchanged, p x 100, same iterations (weights scale out of S~, Sec. 3)."""
+    m, mu, f = _problem(8, 2, 1e4, 4)
+    u1, p1, it1, _, _ = W.solve(m, mu, f, rtol=1e-10)
+    u2, p2, it2, _, _ = W.solve(m, 100 * mu, 100 * f, rtol=1e-10)
+    assert abs(it1 - it2) <= 1
+    np.testing.assert_allclose(u2, u1, atol=1e-8 * np.abs(u1).max())
+    np.testing.assert_allclose(p2, 100 * p1, atol=1e-8 * np.abs(100 * p1).max())
+
+
+def test_vcycle_and_exact_modes_converge_to_the_same_solution():
+    m, mu, f = _problem(8, 2, 1e4, 4)
+    ue, pe, ite, rele, _ = W.solve(m, mu, f, W.Options(mode="exact"), rtol=1e-10)
+    uv, pv, itv, relv, _ = W.solve(m, mu, f, W.Options(mode="vcycle"), rtol=1e-10)
+    assert rele <= 1e-10 and relv <= 1e-10
+    assert ite < itv
+    np.testing.assert_allclose(uv, ue, atol=1e-7 * np.abs(ue).max())
+    np.testing.assert_allclose(pv, pe, atol=1e-7 * np.abs(pe).max())
+
+
+# ----------------------------------------------------------------- manufactured solution
+
+def _mms_errors(N, k):
+    X, Y, Z = sy.symbols("x y z")
+    s = X * (1 - X) * Y * (1 - Y) * Z * (1 - Z)
+    psi = s ** 2
+    u = [sy.diff(psi, Y), -sy.diff(psi, X), sy.Integer(0)]
+    p = sy.cos(sy.pi * X) * sy.cos(sy.pi * Y) * sy.cos(sy.pi * Z)
+    # constant mu = 1, div u = 0: f = -lap u + grad p
+    f = [-(sy.diff(u[c], X, 2) + sy.diff(u[c], Y, 2) + sy.diff(u[c], Z, 2)) + sy.diff(p, v)
+         for c, v in enumerate((X, Y, Z))]
+    fl = sy.lambdify((X, Y, Z), f, "numpy")
+    ul = sy.lambdify((X, Y, Z), u, "numpy")
+    pl = sy.lambdify((X, Y, Z), p, "numpy")
+    m = M.Mesh(N, N, N, k)
+    P = m.node_coords()
+    fn = np.stack([np.broadcast_to(np.asarray(v, float), (m.n_nodes,)) for v in fl(P[:, 0], P[:, 1], P[:, 2])], -1)
+    A = op.assemble_A(m, op.point_values(m, np.ones(m.n_nodes)))
+    B = op.assemble_B(m)
+    free = np.flatnonzero(m.interior_dof_mask())
+    one = op.constant_pressure(m)
+    Kf = sp.bmat([[A[free][:, free], B[:, free].T, None],
+                  [B[:, free], None, sp.csr_matrix(one[:, None])],
+                  [None, sp.csr_matrix(one[None, :]), None]]).tocsc()
+    F = op.load_vector(m, fn)
+    rhs = np.concatenate([F[free], np.zeros(m.n_p), [0.0]])
+    sol = spla.spsolve(Kf, rhs)
+    uh = np.zeros(m.n_u)
+    uh[free] = sol[: free.size]
+    ph = sol[free.size: free.size + m.n_p].reshape(m.n_elem, m.Np)
+    # L2 errors with 6-point Gauss-Legendre per axis
+    from numpy.polynomial.legendre import leggauss
+    from oracle import gll
+    g, gw = leggauss(6)
+    Lg = gll.lagrange_eval(m.xi, g)                      # (6, n)
+    Wg = np.einsum("a,b,c->abc", gw, gw, gw).ravel() * m.detJ
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)[:, ::-1]   # (l, j, i) order -> xyz
+    psi_g = gll.pressure_basis_at_points(k, pts)
+    p2n = m.point_to_node()
+    ec = m.element_coords()
+    eu = ep = 0.0
+    n = m.n
+    for e in range(m.n_elem):
+        x0 = ec[e] * m.h
+        xp = x0[None, :] + (pts + 1) * m.h[None, :] / 2
+        ue_ex = np.stack([np.broadcast_to(np.asarray(v, float), (xp.shape[0],)) for v in ul(xp[:, 0], xp[:, 1], xp[:, 2])], -1)
+        for c in range(3):
+            loc = uh[c * m.n_nodes + p2n[e]].reshape(n, n, n)   # (l, j, i)
+            val = np.einsum("al,bj,ci,lji->abc", Lg, Lg, Lg, loc).ravel()
+            eu += Wg @ (val - ue_ex[:, c]) ** 2
+        ep += Wg @ (psi_g @ ph[e] - pl(xp[:, 0], xp[:, 1], xp[:, 2])) ** 2
+    return np.sqrt(eu), np.sqrt(ep)
+
+
+@pytest.mark.slow
+def test_manufactured_solution_rates_q2():
+    """Optimal rates for Q2 x P1disc at constant viscosity: O(h^3) velocity, O(h^2) pressure (Sec. 1.2)."""
+    e = [_mms_errors(N, 2) for N in (2, 4, 8)]
+    ru = np.log2(e[1][0] / e[2][0])
+    rp = np.log2(e[1][1] / e[2][1])
+    assert ru > 2.7, e
+    assert rp > 1.8, e
