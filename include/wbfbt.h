@@ -1,0 +1,143 @@
+/*
+ * wbfbt.h -- C ABI of the GB300 w-BFBT Stokes solver.
+ *
+ * Discretisation (Sec. 1.2): a structured brick of nx x ny x nz affine
+ * hexahedra on [0,lx] x [0,ly] x [0,lz]; continuous nodal Q_k velocity on
+ * Gauss-Lobatto-Legendre (GLL) nodes and discontinuous modal P_{k-1}
+ * pressure (monomials xi^a eta^b zeta^c, a+b+c <= k-1, ordered by total
+ * degree then lexicographically descending), k in {2, 3, 4}; (k+1)^3-point
+ * GLL collocated quadrature.
+ *
+ * Vector layouts (all arrays contiguous, no padding):
+ *   node index      n = ix + NX*(iy + NY*iz),  NX = k*nx+1, NY = k*ny+1, NZ = k*nz+1
+ *   velocity  u     component-major [3][NX*NY*NZ]  (u_x of all nodes, then u_y, u_z)
+ *   pressure  p     element-major   [nx*ny*nz][Np], element e = ex + nx*(ey + ny*ez),
+ *                   Np = k(k+1)(k+2)/6
+ *   viscosity mu    per node        [NX*NY*NZ]
+ * Dirichlet velocity DOFs (every node on the boundary, Eq. dir-bc) stay in
+ * storage: operator inputs there are ignored and outputs there are zero.
+ *
+ * Ownership: the caller owns every input and output buffer; the context owns
+ * the multigrid hierarchy and all workspaces, allocated in wbfbt_create and
+ * freed in wbfbt_destroy.  No other call allocates device memory.  All work
+ * is issued on the stream given to wbfbt_create, in the order of the calls;
+ * "device" pointers must be valid on that stream.  Calls that return results
+ * to the host (wbfbt_solve) synchronise that stream.
+ *
+ * Errors: every call returns an int status, 0 on success, a negative
+ * WBFBT_ERR_* code otherwise (see wbfbt_status_string).  No call aborts the
+ * process, and no kernel waits on a flag or spins: every device loop is
+ * bounded by its problem size.
+ */
+#ifndef WBFBT_H
+#define WBFBT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WBFBT_OK               0
+#define WBFBT_ERR_INVALID     -1   /* bad argument: null pointer, size, order, dtype       */
+#define WBFBT_ERR_CUDA        -2   /* a CUDA runtime call failed                            */
+#define WBFBT_ERR_NONFINITE   -3   /* NaN or Inf met in a residual or a Krylov coefficient  */
+#define WBFBT_ERR_BREAKDOWN   -4   /* Krylov breakdown (zero or negative pivot / norm)      */
+#define WBFBT_ERR_MAXIT       -5   /* iteration limit reached before the tolerance          */
+#define WBFBT_ERR_SETUP       -6   /* coarse factorisation failed (matrix not SPD)          */
+
+#define WBFBT_F64 0                /* dtype / precision codes */
+#define WBFBT_F32 1
+#define WBFBT_MIXED 1              /* preconditioner in FP32, Krylov and coarse solve FP64 */
+
+typedef struct {
+    int nx, ny, nz;                /* elements per direction, >= 1                         */
+    double lx, ly, lz;             /* brick extents, > 0                                   */
+} wbfbt_mesh;
+
+typedef struct {
+    double a_l, a_r;               /* boundary amplification of Eq. bdramp (>= 1); a_r <= 0
+                                      selects max(1, (N/16) 2^(k-2)), the Table 3 setting  */
+    int restart;                   /* FGMRES restart length m (default 50)                 */
+    int cheb_degree;               /* Chebyshev steps per smoothing (default 3, Sec. 6)    */
+    int mg_min_n;                  /* coarsen while all counts are even and min > this (4) */
+    int precision;                 /* WBFBT_F64 or WBFBT_MIXED                              */
+    int schur_sign;                /* -1 (default): [A B^T; 0 -S~]; +1: printed block      */
+} wbfbt_opts;
+
+typedef struct wbfbt_ctx wbfbt_ctx;
+
+/* Fill *opts with the defaults listed above. */
+void wbfbt_default_opts(wbfbt_opts* opts);
+
+/* Multi-sinker viscosity and body force of Sec. 2.1 at every velocity node.
+ *   mu(x) = (DR^1/2 - DR^-1/2)(1 - chi(x)) + DR^-1/2,
+ *   chi(x) = prod_i [1 - exp(-delta max(0, |x - c_i| - omega/2)^2)],
+ *   f(x) = (0, 0, beta (chi(x) - 1)).
+ * centres: HOST array [n_sinkers][3]; mu_out: device [nodes]; f_out: device
+ * [3][nodes] (may be NULL).  FP64.  stream: a cudaStream_t (NULL = default). */
+int wbfbt_sinker_setup(const wbfbt_mesh* mesh, int k, const double* centres, int n_sinkers,
+                       double omega, double delta, double dr, double beta,
+                       double* mu_out, double* f_out, void* stream);
+
+/* Build a solver context: the fine operators, the sqrt(mu) lumped weights
+ * C = M~_u(w_l), D = M~_u(w_r) (Eq. wbfbt, Eq. bdramp), and three multigrid
+ * hierarchies (A; continuous Q_k Poisson for K_l and K_r, Sec. 6) with
+ * coarsened coefficients, Jacobi diagonals, Chebyshev bounds and the FP64
+ * coarsest inverses.  mu_nodes: device or host pointer [nodes], FP64, every
+ * entry > 0 and finite.  opts may be NULL (defaults).  On success *out owns
+ * all device memory of the solver. */
+int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wbfbt_opts* opts,
+                 void* stream, wbfbt_ctx** out);
+
+/* Operator applies on the fine mesh, device pointers, dtype WBFBT_F64 or WBFBT_F32.
+ *   apply_A  : y = A u                 (viscous stress, Sec. 1.2)          u, y [3][nodes]
+ *   apply_B  : p = B u                 (divergence, b(v,q) = -int q div v) u [3][nodes], p [E][Np]
+ *   apply_BT : u = B^T p               (gradient)                          p [E][Np], u [3][nodes]
+ *   apply_K  : [yu; yp] = [A u + B^T p; B u]  (Eq. discrete-stokes; x = [u; p] contiguous)
+ * Outputs are overwritten.  In and out must not alias. */
+int wbfbt_apply_A(wbfbt_ctx* ctx, const void* u, void* y, int dtype);
+int wbfbt_apply_B(wbfbt_ctx* ctx, const void* u, void* p, int dtype);
+int wbfbt_apply_BT(wbfbt_ctx* ctx, const void* p, void* u, int dtype);
+int wbfbt_apply_K(wbfbt_ctx* ctx, const void* x, void* y, int dtype);
+
+/* Building blocks of the preconditioner, in the context's preconditioner precision
+ * (dtype must equal WBFBT_F64 for an FP64 context, WBFBT_F32 for a mixed one):
+ *   apply_Kw    : y = B C_w^-1 B^T p, which = 0 for C (w_l), 1 for D (w_r)        (Sec. 6)
+ *   apply_Ainv  : y = one V-cycle for A from a zero guess                           (Sec. 6)
+ *   apply_Kinv  : y = one pressure-Poisson V-cycle for K_w, which as above          (Sec. 6)
+ *   apply_schur_inv : y = S~^-1 r, the w-BFBT approximation (Eq. wbfbt) with V-cycles;
+ *                 r and y are projected against the constant pressure mode
+ *   apply_precond   : y = [A~ B^T; 0 s S~]^-1 x  (Eq. precond-stokes), x, y = [u; p] */
+int wbfbt_apply_Kw(wbfbt_ctx* ctx, int which, const void* p, void* y, int dtype);
+int wbfbt_apply_Ainv(wbfbt_ctx* ctx, const void* r, void* y, int dtype);
+int wbfbt_apply_Kinv(wbfbt_ctx* ctx, int which, const void* r, void* y, int dtype);
+int wbfbt_apply_schur_inv(wbfbt_ctx* ctx, const void* r_p, void* y_p, int dtype);
+int wbfbt_apply_precond(wbfbt_ctx* ctx, const void* x, void* y, int dtype);
+
+/* Solve [A B^T; B 0][u; p] = [F; 0] with right-preconditioned FGMRES(m),
+ * x0 = 0, until ||r|| <= rtol ||r_0|| (Euclidean, all DOFs; Sec. 1.3, Sec. 7).
+ * f_nodes: body force at the nodes [3][nodes]; the load vector is
+ * F_c(n) = sum_{(e,q) at n} W_q |J| f_c(x_n) (GLL quadrature), zero on the
+ * Dirichlet boundary.  u [3][nodes], p [E][Np] receive the solution, p with
+ * zero constant-mode mean.  f_nodes, u, p: all device or all host pointers
+ * (host pointers are staged through context buffers, copies included).
+ * iters / final_rel_res (may be NULL): total inner iterations and the true
+ * relative residual ||F - K x|| / ||F|| in FP64 at exit.  Returns
+ * WBFBT_ERR_MAXIT if maxit iterations did not reach rtol (the iterate is
+ * still written). */
+int wbfbt_solve(wbfbt_ctx* ctx, const double* f_nodes, double* u, double* p, double rtol, int maxit,
+                int* iters, double* final_rel_res);
+
+/* Sizes of the context's vectors. */
+int wbfbt_sizes(const wbfbt_ctx* ctx, long long* n_nodes, long long* n_elem, int* np_per_elem,
+                int* n_levels);
+
+/* Total device bytes owned by the context. */
+long long wbfbt_device_bytes(const wbfbt_ctx* ctx);
+
+void wbfbt_destroy(wbfbt_ctx* ctx);
+const char* wbfbt_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WBFBT_H */

@@ -261,7 +261,9 @@ class PressurePoissonMG:
         self.mesh = mesh
         self.K = op.assemble_Kw(B, cdiag, mesh)
         diag = self.K.diagonal()
-        self.dinv = 1.0 / diag
+        # a zero diagonal (the constant mode of a mesh whose only element has all faces on the
+        # Dirichlet boundary) is skipped by the smoother, as Dirichlet rows are
+        self.dinv = np.where(diag > 0.0, 1.0 / np.where(diag > 0.0, diag, 1.0), 0.0)
         self.lam = power_lambda(self.K, self.dinv, splitmix64_uniform(START_SEED, self.K.shape[0]))
         amp = op.boundary_amplification(mesh, a)
         c_pts = 1.0 / (amp[:, None] * np.sqrt(op.point_values(mesh, mu_nodes)))

@@ -1,0 +1,57 @@
+// Shared device-side definitions: mesh geometry, index maps, error checks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "tables.h"
+
+// Structured brick of nx x ny x nz affine hexahedra carrying Q_k nodes.
+struct Grid {
+  int nx, ny, nz;       // elements per axis
+  int NX, NY, NZ;       // nodes per axis, k * n + 1
+  int nn;               // nodes
+  int ne;               // elements
+  double h[3];          // element sizes
+  double detJ;          // hx hy hz / 8
+};
+
+inline Grid make_grid(int nx, int ny, int nz, int k, double lx, double ly, double lz) {
+  Grid g;
+  g.nx = nx; g.ny = ny; g.nz = nz;
+  g.NX = k * nx + 1; g.NY = k * ny + 1; g.NZ = k * nz + 1;
+  g.nn = g.NX * g.NY * g.NZ;
+  g.ne = nx * ny * nz;
+  g.h[0] = lx / nx; g.h[1] = ly / ny; g.h[2] = lz / nz;
+  g.detJ = g.h[0] * g.h[1] * g.h[2] / 8.0;
+  return g;
+}
+
+__host__ __device__ inline bool on_boundary(const Grid& g, int ix, int iy, int iz) {
+  return ix == 0 || iy == 0 || iz == 0 || ix == g.NX - 1 || iy == g.NY - 1 || iz == g.NZ - 1;
+}
+
+// Elements of one of the 8 parity colours (ex % 2, ey % 2, ez % 2) = (c & 1, (c >> 1) & 1, c >> 2).
+// Two elements of the same colour share no node, so scatter-adds within one colour never collide.
+__host__ __device__ inline int colour_count(const Grid& g, int c) {
+  int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+  return ((g.nx - cx + 1) / 2) * ((g.ny - cy + 1) / 2) * ((g.nz - cz + 1) / 2);
+}
+
+__device__ inline void colour_element(const Grid& g, int c, int t, int& ex, int& ey, int& ez) {
+  if (c < 0) {
+    ex = t % g.nx; t /= g.nx; ey = t % g.ny; ez = t / g.ny;
+    return;
+  }
+  int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+  int ncx = (g.nx - cx + 1) / 2, ncy = (g.ny - cy + 1) / 2;
+  int ix = t % ncx; t /= ncx;
+  int iy = t % ncy; int iz = t / ncy;
+  ex = 2 * ix + cx; ey = 2 * iy + cy; ez = 2 * iz + cz;
+}
+
+#define WB_CUDA_TRY(expr)                                  \
+  do {                                                     \
+    cudaError_t _e = (expr);                               \
+    if (_e != cudaSuccess) return WBFBT_ERR_CUDA;          \
+  } while (0)

@@ -1,0 +1,428 @@
+// Vector kernels of the solver: deterministic reductions, Chebyshev-Jacobi updates,
+// projections, casts, FGMRES Gram-Schmidt kernels, and the FP64 dense coarsest
+// solve (right-looking Cholesky, explicit inverse, GEMV).
+//
+// Reductions are two-stage with a grid that depends only on the vector length and
+// a fixed tree inside each block, so repeated runs give bitwise-identical sums.
+#include "vec_ops.h"
+
+namespace {
+
+constexpr int RB = 256;          // reduction block size
+constexpr int RMAX = 592;        // max partial blocks (4 x 148-SM-multiple, also 152 x 4 = 608 is close)
+
+inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+__device__ inline double block_sum(double v) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+  if (wid == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  __syncthreads();
+  return v;  // valid in thread 0
+}
+
+template <typename A, typename B>
+__global__ void k_dot_partial(const A* __restrict__ x, const B* __restrict__ y, long long n, long long stride,
+                              double* __restrict__ part) {
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double a = (double)x[i * stride];
+    acc += y ? a * (double)y[i * stride] : a;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_final(const double* __restrict__ part, int np, int ncols, double* __restrict__ out, int sqrt_out) {
+  // one block per column; partials of column c at part[c * np + b]
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < np; b += blockDim.x) acc += part[(size_t)blockIdx.x * np + b];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[blockIdx.x] = sqrt_out ? sqrt(acc) : acc;
+}
+
+int partial_blocks(long long n) {
+  long long b = (n + RB - 1) / RB;
+  return (int)(b < 1 ? 1 : (b > RMAX ? RMAX : b));
+}
+
+template <typename T>
+__global__ void k_cheb_init0(long long n, const T* __restrict__ b, const T* __restrict__ dinv, T inv_theta,
+                             T* __restrict__ r, T* __restrict__ d, T* __restrict__ x) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T rv = b[i];
+  const T dv = dinv[i] * rv * inv_theta;
+  r[i] = rv;
+  d[i] = dv;
+  x[i] = dv;
+}
+
+template <typename T>
+__global__ void k_cheb_init1(long long n, const T* __restrict__ b, const T* __restrict__ mx, const T* __restrict__ dinv,
+                             T inv_theta, T* __restrict__ r, T* __restrict__ d, T* __restrict__ x) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T rv = b[i] - mx[i];
+  const T dv = dinv[i] * rv * inv_theta;
+  r[i] = rv;
+  d[i] = dv;
+  x[i] += dv;
+}
+
+template <typename T>
+__global__ void k_cheb_step(long long n, const T* __restrict__ md, const T* __restrict__ dinv, T a, T bc,
+                            T* __restrict__ r, T* __restrict__ d, T* __restrict__ x) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T rv = r[i] - md[i];
+  const T dv = a * d[i] + bc * (dinv[i] * rv);
+  r[i] = rv;
+  d[i] = dv;
+  x[i] += dv;
+}
+
+template <typename T>
+__global__ void k_sub(long long n, const T* __restrict__ a, T* __restrict__ r) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] -= a[i];
+}
+
+template <typename T>
+__global__ void k_axpby(long long n, T a, const T* __restrict__ x, T b, const T* __restrict__ y, T* __restrict__ z) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = a * x[i] + b * y[i];
+}
+
+template <typename T>
+__global__ void k_mul(long long n, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ z) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = a[i] * b[i];
+}
+
+template <typename T>
+__global__ void k_scale(long long n, T s, const T* __restrict__ x, T* __restrict__ z) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = x[i] * s;
+}
+
+template <typename A, typename B>
+__global__ void k_cast(long long n, const A* __restrict__ x, B* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (B)x[i];
+}
+
+// p[e * np] -= sum / count, sum from device memory (the constant-mode total)
+template <typename T>
+__global__ void k_sub_const_mode(long long count, int np, const double* __restrict__ sum, T* __restrict__ p) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) p[e * np] = T((double)p[e * np] - sum[0] / (double)count);
+}
+
+template <typename T>
+__global__ void k_copy_proj(long long count, int np, const double* __restrict__ sum, const T* __restrict__ src,
+                            T* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count * np) return;
+  T v = src[i];
+  if (i % np == 0) v = T((double)v - sum[0] / (double)count);
+  dst[i] = v;
+}
+
+// ---------------------------------------------------------------- coarse dense solve
+
+template <typename T>
+__global__ void k_coarse_gather(int nn, int ncomp, const int* __restrict__ map, int nfree, const T* __restrict__ b,
+                                double* __restrict__ bf, int pin0) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const int m = map[n];
+  if (m < 0) return;
+  for (int c = 0; c < ncomp; ++c) {
+    const int idx = c * nfree + m;
+    bf[idx] = (pin0 && idx == 0) ? 0.0 : (double)b[(size_t)c * nn + n];
+  }
+}
+
+// xf = Ainv bf, one warp per row
+__global__ void k_gemv_rows(const double* __restrict__ Ainv, int n, const double* __restrict__ bf,
+                            double* __restrict__ xf) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* a = Ainv + (size_t)row * n;
+  double acc = 0.0;
+  for (int c = lane; c < n; c += 32) acc += a[c] * bf[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) xf[row] = acc;
+}
+
+// single block: xf -= mean(xf)
+__global__ void k_sub_mean_small(int n, double* __restrict__ xf) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += xf[i];
+  acc = block_sum(acc);
+  __shared__ double mean;
+  if (threadIdx.x == 0) mean = acc / n;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xf[i] -= mean;
+}
+
+template <typename T>
+__global__ void k_coarse_scatter(int nn, int ncomp, const int* __restrict__ map, int nfree, const double* __restrict__ xf,
+                                 T* __restrict__ x) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const int m = map[n];
+  for (int c = 0; c < ncomp; ++c) x[(size_t)c * nn + n] = m < 0 ? T(0) : T(xf[c * nfree + m]);
+}
+
+__global__ void k_pin_first(double* M, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  M[t] = t == 0 ? 1.0 : 0.0;            // row 0
+  M[(size_t)t * n] = t == 0 ? 1.0 : 0.0; // column 0
+}
+
+// Right-looking Cholesky, lazy scaling: step j subtracts the rank-one term of the
+// unscaled column j from the trailing lower triangle; column j is never written
+// again, and k_chol_scale divides by sqrt(pivot) at the end.
+__global__ void k_chol_update(double* __restrict__ A, int n, int j, int* __restrict__ flag) {
+  const double piv = A[(size_t)j * n + j];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    if (!(piv > 0.0) || !isfinite(piv)) flag[0] = j + 1;
+  }
+  if (!(piv > 0.0)) return;
+  const int kk = j + 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = j + 1 + blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || kk >= n || kk > i) return;
+  A[(size_t)i * n + kk] -= A[(size_t)i * n + j] * A[(size_t)kk * n + j] / piv;
+}
+
+__global__ void k_chol_scale_offdiag(double* __restrict__ A, int n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || c >= i) return;
+  A[(size_t)i * n + c] /= sqrt(A[(size_t)c * n + c]);
+}
+
+__global__ void k_chol_scale_diag(double* __restrict__ A, int n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) A[(size_t)c * n + c] = sqrt(A[(size_t)c * n + c]);
+}
+
+// Y = L^-1 column by column (thread per column), Y pre-zeroed; L lower, row-major.
+__global__ void k_trinv_cols(const double* __restrict__ L, int n, double* __restrict__ Y) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  for (int i = 0; i < n; ++i) {
+    if (i < c) continue;
+    double s = (i == c) ? 1.0 : 0.0;
+    const double* Li = L + (size_t)i * n;
+    for (int k = c; k < i; ++k) s -= Li[k] * Y[(size_t)k * n + c];
+    Y[(size_t)i * n + c] = s / Li[i];
+  }
+}
+
+// Ainv = Y^T Y, 16 x 16 tiles
+__global__ void k_ytY(const double* __restrict__ Y, int n, double* __restrict__ Ainv) {
+  __shared__ double ta[16][17], tb[16][17];
+  const int a = blockIdx.y * 16 + threadIdx.y, b = blockIdx.x * 16 + threadIdx.x;
+  double acc = 0.0;
+  for (int i0 = 0; i0 < n; i0 += 16) {
+    const int ia = i0 + threadIdx.x;  // row of Y loaded for column a-tile
+    ta[threadIdx.y][threadIdx.x] = (ia < n && blockIdx.y * 16 + threadIdx.y < n) ? Y[(size_t)ia * n + blockIdx.y * 16 + threadIdx.y] : 0.0;
+    const int ib = i0 + threadIdx.y;
+    tb[threadIdx.y][threadIdx.x] = (ib < n && b < n) ? Y[(size_t)ib * n + b] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) acc += ta[threadIdx.y][t] * tb[t][threadIdx.x];
+    __syncthreads();
+  }
+  if (a < n && b < n) Ainv[(size_t)a * n + b] = acc;
+}
+
+// ---------------------------------------------------------------- FGMRES (FP64)
+
+__global__ void k_mdot_partial(const double* __restrict__ V, long long ld, const double* __restrict__ w, long long n,
+                               int np, double* __restrict__ part) {
+  const double* v = V + (size_t)blockIdx.y * ld;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)np * blockDim.x)
+    acc += v[i] * w[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[(size_t)blockIdx.y * np + blockIdx.x] = acc;
+}
+
+__global__ void k_gemv_sub(const double* __restrict__ V, long long ld, int ncols, const double* __restrict__ h,
+                           double* __restrict__ w, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = w[i];
+  for (int c = 0; c < ncols; ++c) acc -= h[c] * V[(size_t)c * ld + i];
+  w[i] = acc;
+}
+
+__global__ void k_gemv_add(const double* __restrict__ Z, long long ld, int ncols, const double* __restrict__ y,
+                           double* __restrict__ x, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = x[i];
+  for (int c = 0; c < ncols; ++c) acc += y[c] * Z[(size_t)c * ld + i];
+  x[i] = acc;
+}
+
+__global__ void k_add2(long long n, const double* __restrict__ a, double* __restrict__ h) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) h[i] += a[i];
+}
+
+}  // namespace
+
+// ================================================================== launchers
+
+template <typename A, typename B>
+cudaError_t launch_dot(const A* x, const B* y, long long n, long long stride, double* part, double* out, int sqrt_out,
+                       cudaStream_t st) {
+  const int np = partial_blocks(n);
+  k_dot_partial<A, B><<<np, RB, 0, st>>>(x, y, n, stride, part);
+  k_final<<<1, RB, 0, st>>>(part, np, 1, out, sqrt_out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cheb_init0(long long n, const T* b, const T* dinv, T inv_theta, T* r, T* d, T* x, cudaStream_t st) {
+  k_cheb_init0<T><<<nblk(n, 256), 256, 0, st>>>(n, b, dinv, inv_theta, r, d, x);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_cheb_init1(long long n, const T* b, const T* mx, const T* dinv, T inv_theta, T* r, T* d, T* x,
+                              cudaStream_t st) {
+  k_cheb_init1<T><<<nblk(n, 256), 256, 0, st>>>(n, b, mx, dinv, inv_theta, r, d, x);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_cheb_step(long long n, const T* md, const T* dinv, T a, T bc, T* r, T* d, T* x, cudaStream_t st) {
+  k_cheb_step<T><<<nblk(n, 256), 256, 0, st>>>(n, md, dinv, a, bc, r, d, x);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_sub(long long n, const T* a, T* r, cudaStream_t st) {
+  k_sub<T><<<nblk(n, 256), 256, 0, st>>>(n, a, r);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_axpby(long long n, T a, const T* x, T b, const T* y, T* z, cudaStream_t st) {
+  k_axpby<T><<<nblk(n, 256), 256, 0, st>>>(n, a, x, b, y, z);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_mul(long long n, const T* a, const T* b, T* z, cudaStream_t st) {
+  k_mul<T><<<nblk(n, 256), 256, 0, st>>>(n, a, b, z);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_scale(long long n, T s, const T* x, T* z, cudaStream_t st) {
+  k_scale<T><<<nblk(n, 256), 256, 0, st>>>(n, s, x, z);
+  return cudaGetLastError();
+}
+template <typename A, typename B>
+cudaError_t launch_cast(long long n, const A* x, B* y, cudaStream_t st) {
+  k_cast<A, B><<<nblk(n, 256), 256, 0, st>>>(n, x, y);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_project_pressure(long long ne, int np, const T* src, T* dst, double* part, double* sum,
+                                    cudaStream_t st) {
+  cudaError_t e = launch_dot<T, T>(src, (const T*)nullptr, ne, np, part, sum, 0, st);
+  if (e != cudaSuccess) return e;
+  k_copy_proj<T><<<nblk(ne * np, 256), 256, 0, st>>>(ne, np, sum, src, dst);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coarse_solve(int nn, int ncomp, const int* map, int nfree_nodes, int ndense, const double* Ainv,
+                                int neumann, const T* b, T* x, double* bf, double* xf, cudaStream_t st) {
+  k_coarse_gather<T><<<nblk(nn, 256), 256, 0, st>>>(nn, ncomp, map, nfree_nodes, b, bf, neumann);
+  k_gemv_rows<<<nblk((long long)ndense * 32, 256), 256, 0, st>>>(Ainv, ndense, bf, xf);
+  if (neumann) k_sub_mean_small<<<1, 1024, 0, st>>>(ndense, xf);
+  k_coarse_scatter<T><<<nblk(nn, 256), 256, 0, st>>>(nn, ncomp, map, nfree_nodes, xf, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_inverse(double* M, int n, int pin_first, double* Y, double* Ainv, int* flag, cudaStream_t st) {
+  cudaError_t e;
+  if (pin_first) k_pin_first<<<nblk(n, 256), 256, 0, st>>>(M, n);
+  for (int j = 0; j < n; ++j) {
+    const int m = n - j - 1;
+    dim3 blk(16, 16), grd(m > 0 ? (m + 15) / 16 : 1, m > 0 ? (m + 15) / 16 : 1);
+    k_chol_update<<<grd, blk, 0, st>>>(M, n, j, flag);
+  }
+  {
+    dim3 blk(16, 16), grd((n + 15) / 16, (n + 15) / 16);
+    k_chol_scale_offdiag<<<grd, blk, 0, st>>>(M, n);
+    k_chol_scale_diag<<<nblk(n, 256), 256, 0, st>>>(M, n);
+  }
+  e = cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)n * n, st);
+  if (e != cudaSuccess) return e;
+  k_trinv_cols<<<nblk(n, 64), 64, 0, st>>>(M, n, Y);
+  {
+    dim3 blk(16, 16), grd((n + 15) / 16, (n + 15) / 16);
+    k_ytY<<<grd, blk, 0, st>>>(Y, n, Ainv);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mdot(const double* V, long long ld, int ncols, const double* w, long long n, double* part,
+                        double* out, cudaStream_t st) {
+  const int np = partial_blocks(n);
+  k_mdot_partial<<<dim3(np, ncols), RB, 0, st>>>(V, ld, w, n, np, part);
+  k_final<<<ncols, RB, 0, st>>>(part, np, ncols, out, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_sub(const double* V, long long ld, int ncols, const double* h, double* w, long long n,
+                            cudaStream_t st) {
+  k_gemv_sub<<<nblk(n, 256), 256, 0, st>>>(V, ld, ncols, h, w, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_add(const double* Z, long long ld, int ncols, const double* y, double* x, long long n,
+                            cudaStream_t st) {
+  k_gemv_add<<<nblk(n, 256), 256, 0, st>>>(Z, ld, ncols, y, x, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_vec(long long n, const double* a, double* h, cudaStream_t st) {
+  k_add2<<<nblk(n, 256), 256, 0, st>>>(n, a, h);
+  return cudaGetLastError();
+}
+
+#define WB_VINST(T)                                                                                                   \
+  template cudaError_t launch_cheb_init0<T>(long long, const T*, const T*, T, T*, T*, T*, cudaStream_t);              \
+  template cudaError_t launch_cheb_init1<T>(long long, const T*, const T*, const T*, T, T*, T*, T*, cudaStream_t);    \
+  template cudaError_t launch_cheb_step<T>(long long, const T*, const T*, T, T, T*, T*, T*, cudaStream_t);            \
+  template cudaError_t launch_sub<T>(long long, const T*, T*, cudaStream_t);                                          \
+  template cudaError_t launch_axpby<T>(long long, T, const T*, T, const T*, T*, cudaStream_t);                        \
+  template cudaError_t launch_mul<T>(long long, const T*, const T*, T*, cudaStream_t);                                \
+  template cudaError_t launch_scale<T>(long long, T, const T*, T*, cudaStream_t);                                     \
+  template cudaError_t launch_project_pressure<T>(long long, int, const T*, T*, double*, double*, cudaStream_t);      \
+  template cudaError_t launch_coarse_solve<T>(int, int, const int*, int, int, const double*, int, const T*, T*,       \
+                                              double*, double*, cudaStream_t);                                        \
+  template cudaError_t launch_dot<T, T>(const T*, const T*, long long, long long, double*, double*, int, cudaStream_t);
+WB_VINST(double)
+WB_VINST(float)
+template cudaError_t launch_cast<double, float>(long long, const double*, float*, cudaStream_t);
+template cudaError_t launch_cast<float, double>(long long, const float*, double*, cudaStream_t);
+template cudaError_t launch_cast<double, double>(long long, const double*, double*, cudaStream_t);

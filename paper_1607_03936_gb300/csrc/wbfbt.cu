@@ -1,0 +1,830 @@
+// Solver context, multigrid hierarchies, w-BFBT, block preconditioner and FGMRES
+// behind the C ABI of include/wbfbt.h.
+//
+//  w-BFBT (Eq. wbfbt):   S~^-1 = (B C^-1 B^T)^-1 (B C^-1 A D^-1 B^T) (B D^-1 B^T)^-1,
+//                        C = M~_u(w_l), D = M~_u(w_r), w = a(e) sqrt(mu) (Eq. bdramp)
+//  block preconditioner (Eq. precond-stokes): y_p = s S~^-1 r_p, y_u = A~^-1 (r_u - B^T y_p)
+//  inner inverses (Sec. 6): geometric V-cycles with Chebyshev(3)-Jacobi smoothing, nested
+//                        Q_k transfers, re-discretised coarse operators, FP64 dense coarsest
+//                        solve; the pressure-Poisson cycle smooths on P_{k-1}^disc and
+//                        corrects with a continuous Q_k Poisson V-cycle.
+//  Krylov (Sec. 1.3):    right-preconditioned FGMRES(m), FP64, CGS2, Givens on the host.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "kernels.h"
+#include "vec_ops.h"
+#include "wbfbt.h"
+
+namespace {
+
+struct WbErr {
+  int code;
+};
+
+#define CK(...)                                           \
+  do {                                                    \
+    cudaError_t _e = (__VA_ARGS__);                       \
+    if (_e != cudaSuccess) throw WbErr{WBFBT_ERR_CUDA};   \
+  } while (0)
+
+constexpr double CHEB_LO = 0.1, CHEB_HI = 1.1;
+constexpr int POWER_ITERS = 10;
+constexpr unsigned long long START_SEED = 0x5EED;
+constexpr int MAX_DENSE = 12000;   // coarsest dense matrices are n x n FP64 (three copies during setup)
+
+// Device allocations owned by a context, freed together.
+struct Pool {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  template <typename T>
+  T* get(size_t n) {
+    void* p = nullptr;
+    size_t b = (n ? n : 1) * sizeof(T);
+    if (cudaMalloc(&p, b) != cudaSuccess) throw WbErr{WBFBT_ERR_CUDA};
+    ptrs.push_back(p);
+    bytes += b;
+    return static_cast<T*>(p);
+  }
+  ~Pool() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+template <typename T>
+struct Level {
+  Grid g;
+  const T* coef = nullptr;     // level 0 of A: nodal viscosity; otherwise per element point
+  int coef_nodal = 0;
+  double* coef64 = nullptr;    // FP64 copy used by the setup (per point; nodal on A level 0)
+  T* dinv = nullptr;
+  double lam = 0.0;
+  T *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *tmp = nullptr;
+  T *w1 = nullptr, *w2 = nullptr;  // transfer workspaces towards the next coarser level
+  bool coarsest = false;
+  int* map = nullptr;              // node -> dense index (coarsest)
+  int nfree_nodes = 0, ndense = 0;
+  double *Ainv = nullptr, *bf = nullptr, *xf = nullptr;
+};
+
+template <typename T>
+struct Hier {
+  bool vec = true;
+  int ncomp = 3;
+  std::vector<Level<T>> lv;
+};
+
+template <typename T>
+struct Precond {
+  T *mu = nullptr, *cinv = nullptr, *dinvw = nullptr;   // fine nodal viscosity, C^-1, D^-1
+  Hier<T> HA, HL[2];
+  T* dKw[2] = {nullptr, nullptr};
+  double lamKw[2] = {0, 0};
+  T *pb, *px, *pr, *pd, *ptmp, *vtmp;                   // disc-level pressure / velocity workspaces
+  T *sr, *sy, *sz, *sy2, *sv1, *sv2, *urhs, *utmp;      // Schur / block workspaces
+  T *vin, *vout;                                        // mixed-precision Krylov <-> preconditioner
+};
+
+}  // namespace
+
+struct wbfbt_ctx {
+  cudaStream_t st = nullptr;
+  int k = 2, N = 3, N3 = 27, NP = 4;
+  Grid g;
+  wbfbt_opts opt;
+  int nlev = 1;
+  RefTables htab;
+  RefTables* dtab = nullptr;
+  Pool pool;
+  // FP64 fine data
+  double *mu64 = nullptr, *lm = nullptr, *C = nullptr, *D = nullptr, *cinv64 = nullptr, *dinv64 = nullptr;
+  float* mu32 = nullptr;
+  double* part = nullptr;   // reduction partials
+  double* dsc = nullptr;    // device scalars (64)
+  int* dflag = nullptr;
+  Precond<double> P64;
+  Precond<float> P32;
+  bool mixed = false;
+  // FGMRES
+  long long ntot = 0;
+  int m = 50;
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *x = nullptr, *r = nullptr, *F = nullptr, *hdev = nullptr;
+  double *stage_f = nullptr, *stage_u = nullptr, *stage_p = nullptr;
+};
+
+namespace {
+
+template <typename T>
+Precond<T>& prec(wbfbt_ctx* c);
+template <>
+Precond<double>& prec<double>(wbfbt_ctx* c) { return c->P64; }
+template <>
+Precond<float>& prec<float>(wbfbt_ctx* c) { return c->P32; }
+
+double read_scalar(wbfbt_ctx* c, const double* dptr) {
+  double v = 0.0;
+  CK(cudaMemcpyAsync(&v, dptr, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return v;
+}
+
+template <typename T>
+double norm(wbfbt_ctx* c, const T* v, long long n) {
+  CK(launch_dot<T, T>(v, v, n, 1, c->part, c->dsc, 1, c->st));
+  return read_scalar(c, c->dsc);
+}
+
+// ------------------------------------------------------------------ operators in precision T
+
+template <typename T>
+void op_A(wbfbt_ctx* c, const Level<T>& L, const T* u, T* y) {
+  CK(launch_stokes<T>(L.g, c->k, c->dtab, OP_A, u, nullptr, nullptr, L.coef, L.coef_nodal, y, nullptr, c->st));
+}
+
+template <typename T>
+void op_L(wbfbt_ctx* c, const Level<T>& L, const T* u, T* y) {
+  CK(launch_poisson<T>(L.g, c->k, c->dtab, u, L.coef, y, c->st));
+}
+
+// y = B C_w^-1 B^T p  (which: 0 -> C (w_l), 1 -> D (w_r))
+template <typename T>
+void op_Kw(wbfbt_ctx* c, int which, const T* p, T* y) {
+  Precond<T>& P = prec<T>(c);
+  const T* winv = which == 0 ? P.cinv : P.dinvw;
+  CK(launch_stokes<T>(c->g, c->k, c->dtab, OP_BT, nullptr, nullptr, p, nullptr, 0, P.vtmp, nullptr, c->st));
+  CK(launch_stokes<T>(c->g, c->k, c->dtab, OP_B, P.vtmp, winv, nullptr, nullptr, 0, nullptr, y, c->st));
+}
+
+template <typename T, class Op>
+void chebyshev(wbfbt_ctx* c, Op M, long long n, const T* dinv, double lam, const T* b, T* x, bool zero_guess,
+               bool want_res, T* r, T* d, T* tmp) {
+  const double lmin = CHEB_LO * lam, lmax = CHEB_HI * lam;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  const int steps = c->opt.cheb_degree;
+  if (zero_guess) {
+    CK(launch_cheb_init0<T>(n, b, dinv, T(1.0 / theta), r, d, x, c->st));
+  } else {
+    M(x, tmp);
+    CK(launch_cheb_init1<T>(n, b, tmp, dinv, T(1.0 / theta), r, d, x, c->st));
+  }
+  for (int s = 0; s < steps; ++s) {
+    if (s == steps - 1 && !want_res) break;
+    M(d, tmp);
+    if (s == steps - 1) {
+      CK(launch_sub<T>(n, tmp, r, c->st));
+      break;
+    }
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    CK(launch_cheb_step<T>(n, tmp, dinv, T(rho_new * rho), T(2.0 * rho_new / delta), r, d, x, c->st));
+    rho = rho_new;
+  }
+}
+
+template <typename T>
+void level_apply(wbfbt_ctx* c, const Hier<T>& H, const Level<T>& L, const T* u, T* y) {
+  if (H.vec)
+    op_A<T>(c, L, u, y);
+  else
+    op_L<T>(c, L, u, y);
+}
+
+template <typename T>
+void vcycle(wbfbt_ctx* c, Hier<T>& H, int l, const T* b, T* x) {
+  Level<T>& L = H.lv[l];
+  if (L.coarsest) {
+    CK(launch_coarse_solve<T>(L.g.nn, H.ncomp, L.map, L.nfree_nodes, L.ndense, L.Ainv, H.vec ? 0 : 1, b, x, L.bf,
+                              L.xf, c->st));
+    return;
+  }
+  const long long n = (long long)H.ncomp * L.g.nn;
+  auto M = [&](const T* u, T* y) { level_apply<T>(c, H, L, u, y); };
+  chebyshev<T>(c, M, n, L.dinv, L.lam, b, x, true, true, L.r, L.d, L.tmp);
+  Level<T>& Lc = H.lv[l + 1];
+  CK(launch_restrict<T>(Lc.g, c->k, c->dtab, H.ncomp, L.r, Lc.b, H.vec ? 1 : 0, L.w1, L.w2, c->st));
+  vcycle<T>(c, H, l + 1, Lc.b, Lc.x);
+  CK(launch_prolong<T>(Lc.g, c->k, c->dtab, H.ncomp, Lc.x, x, 1, L.w1, L.w2, c->st));
+  chebyshev<T>(c, M, n, L.dinv, L.lam, b, x, false, false, L.r, L.d, L.tmp);
+}
+
+// Two-space pressure-Poisson V-cycle for K_w (Sec. 6): disc smoothing, Q_k correction, disc smoothing.
+template <typename T>
+void kinv(wbfbt_ctx* c, int which, const T* bd, T* xd) {
+  Precond<T>& P = prec<T>(c);
+  const long long n = (long long)c->g.ne * c->NP;
+  auto M = [&](const T* p, T* y) { op_Kw<T>(c, which, p, y); };
+  chebyshev<T>(c, M, n, P.dKw[which], P.lamKw[which], bd, xd, true, true, P.pr, P.pd, P.ptmp);
+  Level<T>& L0 = P.HL[which].lv[0];
+  CK(launch_disc_to_cont<T>(c->g, c->k, c->dtab, P.pr, L0.b, c->st));
+  vcycle<T>(c, P.HL[which], 0, L0.b, L0.x);
+  CK(launch_cont_to_disc<T>(c->g, c->k, c->dtab, L0.x, xd, 1, c->st));
+  chebyshev<T>(c, M, n, P.dKw[which], P.lamKw[which], bd, xd, false, false, P.pr, P.pd, P.ptmp);
+}
+
+template <typename T>
+void project(wbfbt_ctx* c, const T* src, T* dst) {
+  CK(launch_project_pressure<T>(c->g.ne, c->NP, src, dst, c->part, c->dsc + 1, c->st));
+}
+
+// y = S~^-1 r (Eq. wbfbt), r and y pressure vectors.
+template <typename T>
+void schur_inv(wbfbt_ctx* c, const T* r, T* y) {
+  Precond<T>& P = prec<T>(c);
+  project<T>(c, r, P.sr);
+  kinv<T>(c, 1, P.sr, P.sy);
+  CK(launch_stokes<T>(c->g, c->k, c->dtab, OP_BT, nullptr, nullptr, P.sy, nullptr, 0, P.sv1, nullptr, c->st));
+  CK(launch_stokes<T>(c->g, c->k, c->dtab, OP_A, P.sv1, P.dinvw, nullptr, P.mu, 1, P.sv2, nullptr, c->st));
+  CK(launch_stokes<T>(c->g, c->k, c->dtab, OP_B, P.sv2, P.cinv, nullptr, nullptr, 0, nullptr, P.sz, c->st));
+  kinv<T>(c, 0, P.sz, P.sy2);
+  project<T>(c, P.sy2, y);
+}
+
+// y = [A~ B^T; 0 s S~]^-1 x (Eq. precond-stokes)
+template <typename T>
+void precond(wbfbt_ctx* c, const T* x, T* y) {
+  Precond<T>& P = prec<T>(c);
+  const long long nu = 3LL * c->g.nn;
+  const T* xu = x;
+  const T* xp = x + nu;
+  T* yu = y;
+  T* yp = y + nu;
+  schur_inv<T>(c, xp, yp);
+  if (c->opt.schur_sign < 0) CK(launch_scale<T>((long long)c->g.ne * c->NP, T(-1), yp, yp, c->st));
+  CK(launch_stokes<T>(c->g, c->k, c->dtab, OP_BT, nullptr, nullptr, yp, nullptr, 0, P.utmp, nullptr, c->st));
+  CK(launch_axpby<T>(nu, T(1), xu, T(-1), P.utmp, P.urhs, c->st));
+  vcycle<T>(c, P.HA, 0, P.urhs, yu);
+}
+
+// ------------------------------------------------------------------ setup
+
+template <typename T, class Op>
+double power_lambda(wbfbt_ctx* c, Op M, long long n, const T* dinv, T* v, T* w, T* tmp, const Grid* mask_grid) {
+  CK(launch_splitmix_start<T>(n, START_SEED, v, c->st));
+  if (mask_grid) CK(launch_mask_boundary<T>(*mask_grid, 3, v, c->st));
+  double nv = norm<T>(c, v, n);
+  CK(launch_scale<T>(n, T(1.0 / nv), v, v, c->st));
+  double lam = 0.0;
+  for (int it = 0; it < POWER_ITERS; ++it) {
+    M(v, tmp);
+    CK(launch_mul<T>(n, dinv, tmp, w, c->st));
+    lam = norm<T>(c, w, n);
+    if (!(lam > 0.0) || !std::isfinite(lam)) throw WbErr{WBFBT_ERR_SETUP};
+    CK(launch_scale<T>(n, T(1.0 / lam), w, v, c->st));
+  }
+  return lam;
+}
+
+Grid coarser(const Grid& g, int k) {
+  return make_grid(g.nx / 2, g.ny / 2, g.nz / 2, k, g.h[0] * g.nx, g.h[1] * g.ny, g.h[2] * g.nz);
+}
+
+template <typename T>
+void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int coef0_nodal) {
+  H.vec = vec;
+  H.ncomp = vec ? 3 : 1;
+  H.lv.resize(c->nlev);
+  Grid g = c->g;
+  const double* prev_pts = nullptr;   // FP64 per-point coefficient of the previous level
+  for (int l = 0; l < c->nlev; ++l) {
+    Level<T>& L = H.lv[l];
+    L.g = g;
+    L.coarsest = (l == c->nlev - 1);
+    const size_t npts = (size_t)g.ne * c->N3;
+    const size_t nv = (size_t)H.ncomp * g.nn;
+    if (l == 0) {
+      L.coef64 = const_cast<double*>(coef0_64);
+      L.coef_nodal = coef0_nodal;
+      if (coef0_nodal) {
+        // per-point FP64 copy for coarsening
+        double* pts = c->pool.get<double>(npts);
+        CK(launch_nodal_to_points<double>(g, c->k, coef0_64, pts, c->st));
+        prev_pts = pts;
+      } else {
+        prev_pts = coef0_64;
+      }
+    } else {
+      double* pts = c->pool.get<double>(npts);
+      Grid gf = H.lv[l - 1].g;
+      CK(launch_coarsen_coef<double>(gf, c->k, c->dtab, prev_pts, pts, c->st));
+      L.coef64 = pts;
+      L.coef_nodal = 0;
+      prev_pts = pts;
+    }
+    // coefficient in T
+    if (std::is_same<T, double>::value) {
+      L.coef = reinterpret_cast<const T*>(L.coef64);
+    } else {
+      size_t nc = L.coef_nodal ? (size_t)g.nn : npts;
+      T* cT = c->pool.get<T>(nc);
+      CK((launch_cast<double, T>((long long)nc, L.coef64, cT, c->st)));
+      L.coef = cT;
+    }
+    L.b = c->pool.get<T>(nv);
+    L.x = c->pool.get<T>(nv);
+    if (!L.coarsest) {
+      L.r = c->pool.get<T>(nv);
+      L.d = c->pool.get<T>(nv);
+      L.tmp = c->pool.get<T>(nv);
+      L.dinv = c->pool.get<T>(nv);
+      double* d64 = c->pool.get<double>(nv);
+      if (vec)
+        CK(launch_dinv_A<double>(g, c->k, c->dtab, L.coef64, L.coef_nodal, d64, c->st));
+      else
+        CK(launch_dinv_L<double>(g, c->k, c->dtab, L.coef64, d64, c->st));
+      CK((launch_cast<double, T>((long long)nv, d64, L.dinv, c->st)));
+      Grid gc = coarser(g, c->k);
+      size_t ws = transfer_work_size(gc, c->k);
+      L.w1 = c->pool.get<T>(ws);
+      L.w2 = c->pool.get<T>(ws);
+      T* v = c->pool.get<T>(nv);
+      T* w = c->pool.get<T>(nv);
+      auto M = [&](const T* u, T* y) { level_apply<T>(c, H, L, u, y); };
+      L.lam = power_lambda<T>(c, M, (long long)nv, L.dinv, v, w, L.tmp, vec ? &L.g : nullptr);
+      g = gc;
+    } else {
+      // coarsest: dense FP64 matrix over the free DOFs, explicit inverse
+      std::vector<int> hmap(g.nn);
+      int nfree = 0;
+      for (int n = 0; n < g.nn; ++n) {
+        int ix = n % g.NX, iy = (n / g.NX) % g.NY, iz = n / (g.NX * g.NY);
+        hmap[n] = (vec && on_boundary(g, ix, iy, iz)) ? -1 : nfree++;
+      }
+      const int nd = H.ncomp * nfree;
+      if (nd > MAX_DENSE) throw WbErr{WBFBT_ERR_INVALID};
+      L.nfree_nodes = nfree;
+      L.ndense = nd;
+      L.map = c->pool.get<int>(g.nn);
+      CK(cudaMemcpyAsync(L.map, hmap.data(), sizeof(int) * g.nn, cudaMemcpyHostToDevice, c->st));
+      double* M = c->pool.get<double>((size_t)nd * nd);
+      double* Y = c->pool.get<double>((size_t)nd * nd);
+      L.Ainv = c->pool.get<double>((size_t)nd * nd);
+      L.bf = c->pool.get<double>(nd);
+      L.xf = c->pool.get<double>(nd);
+      CK(cudaMemsetAsync(M, 0, sizeof(double) * (size_t)nd * nd, c->st));
+      if (vec)
+        CK(launch_assemble_dense_A(g, c->k, c->dtab, L.coef64, L.coef_nodal, L.map, nfree, M, nd, c->st));
+      else
+        CK(launch_assemble_dense_L_mapped(g, c->k, c->dtab, L.coef64, L.map, M, nd, c->st));
+      CK(cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
+      CK(launch_dense_inverse(M, nd, vec ? 0 : 1, Y, L.Ainv, c->dflag, c->st));
+      int flag = 0;
+      CK(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      if (flag) throw WbErr{WBFBT_ERR_SETUP};
+    }
+  }
+}
+
+template <typename T>
+void build_precond(wbfbt_ctx* c) {
+  Precond<T>& P = prec<T>(c);
+  const Grid& g = c->g;
+  const size_t nn = g.nn, nu = 3 * nn, np = (size_t)g.ne * c->NP, npts = (size_t)g.ne * c->N3;
+  if (std::is_same<T, double>::value) {
+    P.mu = reinterpret_cast<T*>(c->mu64);
+    P.cinv = reinterpret_cast<T*>(c->cinv64);
+    P.dinvw = reinterpret_cast<T*>(c->dinv64);
+  } else {
+    P.mu = reinterpret_cast<T*>(c->mu32);
+    P.cinv = c->pool.get<T>(nn);
+    P.dinvw = c->pool.get<T>(nn);
+    CK((launch_cast<double, T>((long long)nn, c->cinv64, P.cinv, c->st)));
+    CK((launch_cast<double, T>((long long)nn, c->dinv64, P.dinvw, c->st)));
+  }
+  P.pb = c->pool.get<T>(np);
+  P.px = c->pool.get<T>(np);
+  P.pr = c->pool.get<T>(np);
+  P.pd = c->pool.get<T>(np);
+  P.ptmp = c->pool.get<T>(np);
+  P.vtmp = c->pool.get<T>(nu);
+  P.sr = c->pool.get<T>(np);
+  P.sy = c->pool.get<T>(np);
+  P.sz = c->pool.get<T>(np);
+  P.sy2 = c->pool.get<T>(np);
+  P.sv1 = c->pool.get<T>(nu);
+  P.sv2 = c->pool.get<T>(nu);
+  P.urhs = c->pool.get<T>(nu);
+  P.utmp = c->pool.get<T>(nu);
+  P.vin = c->pool.get<T>(c->ntot);
+  P.vout = c->pool.get<T>(c->ntot);
+  // A hierarchy: viscosity per node on the fine level
+  build_hier<T>(c, P.HA, true, c->mu64, 1);
+  // Poisson hierarchies: c = 1 / (a(e) sqrt(mu)) per point
+  const double amp[2] = {c->opt.a_l, c->opt.a_r};
+  for (int wi = 0; wi < 2; ++wi) {
+    double* c0 = c->pool.get<double>(npts);
+    CK(launch_poisson_coef0<double>(g, c->k, c->mu64, amp[wi], c0, c->st));
+    build_hier<T>(c, P.HL[wi], false, c0, 0);
+    // disc level: Jacobi diagonal of K_w and lambda_hat
+    double* d64 = c->pool.get<double>(np);
+    CK(launch_dinv_Kw<double>(g, c->k, c->dtab, wi == 0 ? c->cinv64 : c->dinv64, d64, c->st));
+    P.dKw[wi] = c->pool.get<T>(np);
+    CK((launch_cast<double, T>((long long)np, d64, P.dKw[wi], c->st)));
+    auto M = [&](const T* p, T* y) { op_Kw<T>(c, wi, p, y); };
+    P.lamKw[wi] = power_lambda<T>(c, M, (long long)np, P.dKw[wi], P.px, P.pd, P.ptmp, nullptr);
+  }
+}
+
+__global__ void k_inv_masked(Grid g, const double* __restrict__ w, double* __restrict__ inv) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nn) return;
+  const int ix = n % g.NX, iy = (n / g.NX) % g.NY, iz = n / (g.NX * g.NY);
+  inv[n] = on_boundary(g, ix, iy, iz) ? 0.0 : 1.0 / w[n];
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int n_levels(int nx, int ny, int nz, int min_n) {
+  int L = 1;
+  while (nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0 && std::min(nx, std::min(ny, nz)) > min_n) {
+    nx /= 2; ny /= 2; nz /= 2;
+    ++L;
+  }
+  return L;
+}
+
+template <class F>
+int guarded(F f) {
+  try {
+    f();
+    return WBFBT_OK;
+  } catch (const WbErr& e) {
+    return e.code;
+  } catch (...) {
+    return WBFBT_ERR_CUDA;
+  }
+}
+
+// ------------------------------------------------------------------ FGMRES
+
+void apply_K64(wbfbt_ctx* c, const double* x, double* y) {
+  const long long nu = 3LL * c->g.nn;
+  CK(launch_stokes<double>(c->g, c->k, c->dtab, OP_A | OP_BT | OP_B, x, nullptr, x + nu, c->mu64, 1, y, y + nu,
+                           c->st));
+}
+
+void precond_any(wbfbt_ctx* c, const double* v, double* z) {
+  if (!c->mixed) {
+    precond<double>(c, v, z);
+  } else {
+    CK((launch_cast<double, float>(c->ntot, v, c->P32.vin, c->st)));
+    precond<float>(c, c->P32.vin, c->P32.vout);
+    CK((launch_cast<float, double>(c->ntot, c->P32.vout, z, c->st)));
+  }
+}
+
+int fgmres(wbfbt_ctx* c, double rtol, int maxit, int* iters, double* relres) {
+  const long long n = c->ntot;
+  const int m = c->m;
+  double* x = c->x;
+  double* r = c->r;
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, c->st));
+  CK(cudaMemcpyAsync(r, c->F, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+  const double beta0 = norm<double>(c, r, n);
+  if (!std::isfinite(beta0)) return WBFBT_ERR_NONFINITE;
+  if (beta0 == 0.0) {
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return WBFBT_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m), hcol(2 * (m + 1) + 1);
+  int its = 0;
+  double rel = 1.0;
+  bool done = false;
+  int status = WBFBT_OK;
+  while (!done) {
+    const double beta = norm<double>(c, r, n);
+    CK(launch_scale<double>(n, 1.0 / beta, r, c->V, c->st));
+    std::fill(gv.begin(), gv.end(), 0.0);
+    std::fill(H.begin(), H.end(), 0.0);
+    gv[0] = beta;
+    int jdone = 0;
+    bool converged = false;
+    for (int j = 0; j < m; ++j) {
+      double* vj = c->V + (size_t)j * n;
+      double* zj = c->Z + (size_t)j * n;
+      precond_any(c, vj, zj);
+      apply_K64(c, zj, c->w);
+      // CGS2: h = V^T w, w -= V h, twice
+      double* h1 = c->hdev;
+      double* h2 = c->hdev + (m + 1);
+      double* hn = c->hdev + 2 * (m + 1);
+      CK(launch_mdot(c->V, n, j + 1, c->w, n, c->part, h1, c->st));
+      CK(launch_gemv_sub(c->V, n, j + 1, h1, c->w, n, c->st));
+      CK(launch_mdot(c->V, n, j + 1, c->w, n, c->part, h2, c->st));
+      CK(launch_gemv_sub(c->V, n, j + 1, h2, c->w, n, c->st));
+      CK(launch_dot<double, double>(c->w, c->w, n, 1, c->part, hn, 1, c->st));
+      CK(cudaMemcpyAsync(hcol.data(), c->hdev, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      const double hnrm = hcol[2 * (m + 1)];
+      for (int i = 0; i <= j; ++i) {
+        const double hv = hcol[i] + hcol[(m + 1) + i];
+        if (!std::isfinite(hv)) return WBFBT_ERR_NONFINITE;
+        H[(size_t)i * m + j] = hv;
+      }
+      if (!std::isfinite(hnrm)) return WBFBT_ERR_NONFINITE;
+      H[(size_t)(j + 1) * m + j] = hnrm;
+      if (hnrm > 0.0) CK(launch_scale<double>(n, 1.0 / hnrm, c->w, c->V + (size_t)(j + 1) * n, c->st));
+      for (int i = 0; i < j; ++i) {
+        const double a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+      }
+      const double a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+      const double den = std::hypot(a, b);
+      if (!(den > 0.0)) return WBFBT_ERR_BREAKDOWN;
+      cs[j] = a / den;
+      sn[j] = b / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++its;
+      jdone = j + 1;
+      if (std::fabs(gv[j + 1]) <= rtol * beta0 || its >= maxit || hnrm == 0.0) {
+        converged = std::fabs(gv[j + 1]) <= rtol * beta0;
+        break;
+      }
+    }
+    for (int i = jdone - 1; i >= 0; --i) {
+      double s = gv[i];
+      for (int k2 = i + 1; k2 < jdone; ++k2) s -= H[(size_t)i * m + k2] * y[k2];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    CK(cudaMemcpyAsync(c->hdev, y.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, c->st));
+    CK(launch_gemv_add(c->Z, n, jdone, c->hdev, x, n, c->st));
+    apply_K64(c, x, c->w);
+    CK(launch_axpby<double>(n, 1.0, c->F, -1.0, c->w, r, c->st));
+    rel = norm<double>(c, r, n) / beta0;
+    if (!std::isfinite(rel)) return WBFBT_ERR_NONFINITE;
+    if ((converged && rel <= rtol) || its >= maxit) done = true;
+  }
+  if (rel > rtol) status = WBFBT_ERR_MAXIT;
+  if (iters) *iters = its;
+  if (relres) *relres = rel;
+  return status;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+
+extern "C" {
+
+void wbfbt_default_opts(wbfbt_opts* o) {
+  if (!o) return;
+  o->a_l = 1.0;
+  o->a_r = 0.0;
+  o->restart = 50;
+  o->cheb_degree = 3;
+  o->mg_min_n = 4;
+  o->precision = WBFBT_F64;
+  o->schur_sign = -1;
+}
+
+const char* wbfbt_status_string(int s) {
+  switch (s) {
+    case WBFBT_OK: return "ok";
+    case WBFBT_ERR_INVALID: return "invalid argument";
+    case WBFBT_ERR_CUDA: return "CUDA runtime error";
+    case WBFBT_ERR_NONFINITE: return "non-finite value in a residual or Krylov coefficient";
+    case WBFBT_ERR_BREAKDOWN: return "Krylov breakdown";
+    case WBFBT_ERR_MAXIT: return "iteration limit reached before the tolerance";
+    case WBFBT_ERR_SETUP: return "setup failed (coarse matrix not SPD or bad eigenvalue estimate)";
+    default: return "unknown status";
+  }
+}
+
+static bool mesh_ok(const wbfbt_mesh* m, int k) {
+  return m && k >= 2 && k <= 4 && m->nx >= 1 && m->ny >= 1 && m->nz >= 1 && m->lx > 0 && m->ly > 0 && m->lz > 0 &&
+         (long long)(k * m->nx + 1) * (k * m->ny + 1) * (k * m->nz + 1) < (1LL << 30);
+}
+
+int wbfbt_sinker_setup(const wbfbt_mesh* mesh, int k, const double* centres, int ns, double omega, double delta,
+                       double dr, double beta, double* mu_out, double* f_out, void* stream) {
+  if (!mesh_ok(mesh, k) || (!centres && ns > 0) || ns < 0 || ns > 128 || !mu_out || !(dr >= 1.0)) return WBFBT_ERR_INVALID;
+  RefTables t;
+  if (!build_ref_tables(k, &t)) return WBFBT_ERR_INVALID;
+  Grid g = make_grid(mesh->nx, mesh->ny, mesh->nz, k, mesh->lx, mesh->ly, mesh->lz);
+  cudaError_t e = launch_sinker(g, k, t, centres, ns, omega, delta, dr, beta, mu_out, f_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? WBFBT_OK : WBFBT_ERR_CUDA;
+}
+
+int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wbfbt_opts* opts, void* stream,
+                 wbfbt_ctx** out) {
+  if (!out || !mu_nodes || !mesh_ok(mesh, k)) return WBFBT_ERR_INVALID;
+  *out = nullptr;
+  auto c = std::make_unique<wbfbt_ctx>();
+  wbfbt_default_opts(&c->opt);
+  if (opts) c->opt = *opts;
+  if (c->opt.restart < 1 || c->opt.restart > 1000 || c->opt.cheb_degree < 1 || c->opt.cheb_degree > 16 ||
+      c->opt.a_l < 1.0 || (c->opt.a_r > 0 && c->opt.a_r < 1.0) ||
+      (c->opt.precision != WBFBT_F64 && c->opt.precision != WBFBT_MIXED) || c->opt.mg_min_n < 1)
+    return WBFBT_ERR_INVALID;
+  if (c->opt.schur_sign >= 0) c->opt.schur_sign = 1; else c->opt.schur_sign = -1;
+  c->st = (cudaStream_t)stream;
+  c->k = k;
+  c->N = k + 1;
+  c->N3 = c->N * c->N * c->N;
+  c->NP = k * (k + 1) * (k + 2) / 6;
+  c->g = make_grid(mesh->nx, mesh->ny, mesh->nz, k, mesh->lx, mesh->ly, mesh->lz);
+  if (c->opt.a_r <= 0) {
+    const int N = std::max(mesh->nx, std::max(mesh->ny, mesh->nz));
+    c->opt.a_r = std::max(1.0, (N / 16.0) * std::pow(2.0, k - 2));
+  }
+  c->nlev = n_levels(mesh->nx, mesh->ny, mesh->nz, c->opt.mg_min_n);
+  c->mixed = c->opt.precision == WBFBT_MIXED;
+  c->m = c->opt.restart;
+  if (!build_ref_tables(k, &c->htab)) return WBFBT_ERR_INVALID;
+  wbfbt_ctx* cp = c.get();
+  int status = guarded([&]() {
+    const Grid& g = cp->g;
+    const size_t nn = g.nn;
+    cp->dtab = cp->pool.get<RefTables>(1);
+    CK(cudaMemcpyAsync(cp->dtab, &cp->htab, sizeof(RefTables), cudaMemcpyHostToDevice, cp->st));
+    cp->part = cp->pool.get<double>((size_t)592 * (1001));
+    cp->dsc = cp->pool.get<double>(64);
+    cp->dflag = cp->pool.get<int>(4);
+    cp->mu64 = cp->pool.get<double>(nn);
+    CK(cudaMemcpyAsync(cp->mu64, mu_nodes, sizeof(double) * nn, cudaMemcpyDefault, cp->st));
+    // validate mu: positive and finite
+    {
+      std::vector<double> hmu(nn);
+      CK(cudaMemcpyAsync(hmu.data(), cp->mu64, sizeof(double) * nn, cudaMemcpyDeviceToHost, cp->st));
+      CK(cudaStreamSynchronize(cp->st));
+      for (double v : hmu)
+        if (!(v > 0.0) || !std::isfinite(v)) throw WbErr{WBFBT_ERR_INVALID};
+    }
+    cp->mu32 = cp->pool.get<float>(nn);
+    CK((launch_cast<double, float>((long long)nn, cp->mu64, cp->mu32, cp->st)));
+    cp->lm = cp->pool.get<double>(nn);
+    CK(launch_lumped_mass(g, cp->k, cp->dtab, cp->lm, cp->st));
+    cp->C = cp->pool.get<double>(nn);
+    cp->D = cp->pool.get<double>(nn);
+    CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_l, cp->C, cp->st));
+    CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_r, cp->D, cp->st));
+    cp->cinv64 = cp->pool.get<double>(nn);
+    cp->dinv64 = cp->pool.get<double>(nn);
+    k_inv_masked<<<(nn + 255) / 256, 256, 0, cp->st>>>(g, cp->C, cp->cinv64);
+    k_inv_masked<<<(nn + 255) / 256, 256, 0, cp->st>>>(g, cp->D, cp->dinv64);
+    CK(cudaGetLastError());
+    cp->ntot = 3LL * nn + (long long)g.ne * cp->NP;
+    if (cp->mixed)
+      build_precond<float>(cp);
+    else
+      build_precond<double>(cp);
+    const long long n = cp->ntot;
+    cp->V = cp->pool.get<double>((size_t)(cp->m + 1) * n);
+    cp->Z = cp->pool.get<double>((size_t)cp->m * n);
+    cp->w = cp->pool.get<double>(n);
+    cp->x = cp->pool.get<double>(n);
+    cp->r = cp->pool.get<double>(n);
+    cp->F = cp->pool.get<double>(n);
+    cp->hdev = cp->pool.get<double>(2 * (cp->m + 1) + 1);
+    cp->stage_f = cp->pool.get<double>(3 * nn);
+    cp->stage_u = cp->pool.get<double>(3 * nn);
+    cp->stage_p = cp->pool.get<double>((size_t)g.ne * cp->NP);
+    CK(cudaStreamSynchronize(cp->st));
+  });
+  if (status != WBFBT_OK) return status;
+  *out = c.release();
+  return WBFBT_OK;
+}
+
+void wbfbt_destroy(wbfbt_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  delete c;
+}
+
+int wbfbt_sizes(const wbfbt_ctx* c, long long* nn, long long* ne, int* np, int* nl) {
+  if (!c) return WBFBT_ERR_INVALID;
+  if (nn) *nn = c->g.nn;
+  if (ne) *ne = c->g.ne;
+  if (np) *np = c->NP;
+  if (nl) *nl = c->nlev;
+  return WBFBT_OK;
+}
+
+long long wbfbt_device_bytes(const wbfbt_ctx* c) { return c ? (long long)c->pool.bytes : 0; }
+
+static int stokes_apply(wbfbt_ctx* c, int ops, const void* u, const void* p, void* yu, void* yp, int dtype) {
+  if (!c || (dtype != WBFBT_F64 && dtype != WBFBT_F32)) return WBFBT_ERR_INVALID;
+  return guarded([&]() {
+    if (dtype == WBFBT_F64)
+      CK(launch_stokes<double>(c->g, c->k, c->dtab, ops, (const double*)u, nullptr, (const double*)p, c->mu64, 1,
+                               (double*)yu, (double*)yp, c->st));
+    else
+      CK(launch_stokes<float>(c->g, c->k, c->dtab, ops, (const float*)u, nullptr, (const float*)p, c->mu32, 1,
+                              (float*)yu, (float*)yp, c->st));
+  });
+}
+
+int wbfbt_apply_A(wbfbt_ctx* c, const void* u, void* y, int dtype) {
+  if (!u || !y) return WBFBT_ERR_INVALID;
+  return stokes_apply(c, OP_A, u, nullptr, y, nullptr, dtype);
+}
+
+int wbfbt_apply_B(wbfbt_ctx* c, const void* u, void* p, int dtype) {
+  if (!u || !p) return WBFBT_ERR_INVALID;
+  return stokes_apply(c, OP_B, u, nullptr, nullptr, p, dtype);
+}
+
+int wbfbt_apply_BT(wbfbt_ctx* c, const void* p, void* u, int dtype) {
+  if (!u || !p) return WBFBT_ERR_INVALID;
+  return stokes_apply(c, OP_BT, nullptr, p, u, nullptr, dtype);
+}
+
+int wbfbt_apply_K(wbfbt_ctx* c, const void* x, void* y, int dtype) {
+  if (!c || !x || !y) return WBFBT_ERR_INVALID;
+  const size_t es = dtype == WBFBT_F64 ? 8 : 4;
+  const size_t nu = 3 * (size_t)c->g.nn;
+  return stokes_apply(c, OP_A | OP_BT | OP_B, x, (const char*)x + nu * es, y, (char*)y + nu * es, dtype);
+}
+
+static bool prec_dtype_ok(wbfbt_ctx* c, int dtype) {
+  return c && ((dtype == WBFBT_F64 && !c->mixed) || (dtype == WBFBT_F32 && c->mixed));
+}
+
+int wbfbt_apply_Kw(wbfbt_ctx* c, int which, const void* p, void* y, int dtype) {
+  if (!prec_dtype_ok(c, dtype) || !p || !y || (which != 0 && which != 1)) return WBFBT_ERR_INVALID;
+  return guarded([&]() {
+    if (dtype == WBFBT_F64) op_Kw<double>(c, which, (const double*)p, (double*)y);
+    else op_Kw<float>(c, which, (const float*)p, (float*)y);
+  });
+}
+
+int wbfbt_apply_Ainv(wbfbt_ctx* c, const void* r, void* y, int dtype) {
+  if (!prec_dtype_ok(c, dtype) || !r || !y) return WBFBT_ERR_INVALID;
+  return guarded([&]() {
+    if (dtype == WBFBT_F64) vcycle<double>(c, c->P64.HA, 0, (const double*)r, (double*)y);
+    else vcycle<float>(c, c->P32.HA, 0, (const float*)r, (float*)y);
+  });
+}
+
+int wbfbt_apply_Kinv(wbfbt_ctx* c, int which, const void* r, void* y, int dtype) {
+  if (!prec_dtype_ok(c, dtype) || !r || !y || (which != 0 && which != 1)) return WBFBT_ERR_INVALID;
+  return guarded([&]() {
+    if (dtype == WBFBT_F64) kinv<double>(c, which, (const double*)r, (double*)y);
+    else kinv<float>(c, which, (const float*)r, (float*)y);
+  });
+}
+
+int wbfbt_apply_schur_inv(wbfbt_ctx* c, const void* r, void* y, int dtype) {
+  if (!prec_dtype_ok(c, dtype) || !r || !y) return WBFBT_ERR_INVALID;
+  return guarded([&]() {
+    if (dtype == WBFBT_F64) schur_inv<double>(c, (const double*)r, (double*)y);
+    else schur_inv<float>(c, (const float*)r, (float*)y);
+  });
+}
+
+int wbfbt_apply_precond(wbfbt_ctx* c, const void* x, void* y, int dtype) {
+  if (!prec_dtype_ok(c, dtype) || !x || !y) return WBFBT_ERR_INVALID;
+  return guarded([&]() {
+    if (dtype == WBFBT_F64) precond<double>(c, (const double*)x, (double*)y);
+    else precond<float>(c, (const float*)x, (float*)y);
+  });
+}
+
+int wbfbt_solve(wbfbt_ctx* c, const double* f_nodes, double* u, double* p, double rtol, int maxit, int* iters,
+                double* final_rel_res) {
+  if (!c || !f_nodes || !u || !p || !(rtol > 0.0) || maxit < 1) return WBFBT_ERR_INVALID;
+  const bool dev_f = is_device_ptr(f_nodes), dev_u = is_device_ptr(u), dev_p = is_device_ptr(p);
+  if (dev_f != dev_u || dev_u != dev_p) return WBFBT_ERR_INVALID;
+  int status = WBFBT_OK;
+  int g = guarded([&]() {
+    const size_t nn = c->g.nn, nu = 3 * nn, np = (size_t)c->g.ne * c->NP;
+    const double* fd = f_nodes;
+    if (!dev_f) {
+      CK(cudaMemcpyAsync(c->stage_f, f_nodes, sizeof(double) * nu, cudaMemcpyHostToDevice, c->st));
+      fd = c->stage_f;
+    }
+    CK(cudaMemsetAsync(c->F + nu, 0, sizeof(double) * np, c->st));
+    CK(launch_load_vector(c->g, c->lm, fd, c->F, c->st));
+    status = fgmres(c, rtol, maxit, iters, final_rel_res);
+    if (status != WBFBT_OK && status != WBFBT_ERR_MAXIT) return;
+    double* ud = dev_u ? u : c->stage_u;
+    double* pd = dev_p ? p : c->stage_p;
+    CK(cudaMemcpyAsync(ud, c->x, sizeof(double) * nu, cudaMemcpyDeviceToDevice, c->st));
+    project<double>(c, c->x + nu, pd);
+    if (!dev_u) {
+      CK(cudaMemcpyAsync(u, c->stage_u, sizeof(double) * nu, cudaMemcpyDeviceToHost, c->st));
+      CK(cudaMemcpyAsync(p, c->stage_p, sizeof(double) * np, cudaMemcpyDeviceToHost, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+  });
+  return g != WBFBT_OK ? g : status;
+}
+
+}  // extern "C"

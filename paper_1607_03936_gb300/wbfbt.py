@@ -1,0 +1,222 @@
+"""ctypes binding of libwbfbt.so (include/wbfbt.h): argument marshalling only.
+
+Every numerical step runs inside the CUDA library; this module turns torch
+tensors into raw pointers and the current CUDA stream into a cudaStream_t.
+Importing it loads the library and raises if it is missing: there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+F64, F32 = 0, 1
+MIXED = 1
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "non-finite value", -4: "Krylov breakdown",
+          -5: "iteration limit reached", -6: "setup failed"}
+
+SYMBOLS = ["wbfbt_default_opts", "wbfbt_sinker_setup", "wbfbt_create", "wbfbt_apply_A", "wbfbt_apply_B",
+           "wbfbt_apply_BT", "wbfbt_apply_K", "wbfbt_apply_Kw", "wbfbt_apply_Ainv", "wbfbt_apply_Kinv",
+           "wbfbt_apply_schur_inv", "wbfbt_apply_precond", "wbfbt_solve", "wbfbt_sizes", "wbfbt_device_bytes",
+           "wbfbt_destroy", "wbfbt_status_string"]
+
+
+class WbfbtError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("a_l", ctypes.c_double), ("a_r", ctypes.c_double), ("restart", ctypes.c_int),
+                ("cheb_degree", ctypes.c_int), ("mg_min_n", ctypes.c_int), ("precision", ctypes.c_int),
+                ("schur_sign", ctypes.c_int)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing: build it with paper_1607_03936_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.wbfbt_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.wbfbt_default_opts.restype = None
+    lib.wbfbt_sinker_setup.argtypes = [ctypes.POINTER(Mesh), i, vp, i, d, d, d, d, vp, vp, vp]
+    lib.wbfbt_create.argtypes = [ctypes.POINTER(Mesh), i, vp, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    for name in ("wbfbt_apply_A", "wbfbt_apply_B", "wbfbt_apply_BT", "wbfbt_apply_K", "wbfbt_apply_Ainv",
+                 "wbfbt_apply_schur_inv", "wbfbt_apply_precond"):
+        getattr(lib, name).argtypes = [vp, vp, vp, i]
+    lib.wbfbt_apply_Kw.argtypes = [vp, i, vp, vp, i]
+    lib.wbfbt_apply_Kinv.argtypes = [vp, i, vp, vp, i]
+    lib.wbfbt_solve.argtypes = [vp, vp, vp, vp, d, i, ctypes.POINTER(i), ctypes.POINTER(d)]
+    lib.wbfbt_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.wbfbt_device_bytes.argtypes = [vp]
+    lib.wbfbt_device_bytes.restype = ctypes.c_longlong
+    lib.wbfbt_destroy.argtypes = [vp]
+    lib.wbfbt_destroy.restype = None
+    lib.wbfbt_status_string.argtypes = [i]
+    lib.wbfbt_status_string.restype = ctypes.c_char_p
+    return lib   # every other entry point returns int, ctypes' default
+
+
+_LIB: ctypes.CDLL | None = None
+
+
+def lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise WbfbtError(status, what)
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    lib().wbfbt_default_opts(ctypes.byref(o))
+    return o
+
+
+def sinker_setup(nx: int, k: int, centres, omega: float, delta: float, dr: float, beta: float = 10.0,
+                 ny: int | None = None, nz: int | None = None, lengths=(1.0, 1.0, 1.0), device="cuda"):
+    """Multi-sinker viscosity and forcing of Sec. 2.1 at every node; returns (mu, f) device tensors."""
+    ny, nz = ny or nx, nz or nx
+    mesh = Mesh(nx, ny, nz, *lengths)
+    nn = (k * nx + 1) * (k * ny + 1) * (k * nz + 1)
+    mu = torch.empty(nn, dtype=torch.float64, device=device)
+    f = torch.empty(3 * nn, dtype=torch.float64, device=device)
+    c = torch.as_tensor(centres, dtype=torch.float64).contiguous().cpu()
+    _check(lib().wbfbt_sinker_setup(ctypes.byref(mesh), k, ctypes.c_void_p(c.data_ptr()), int(c.shape[0]), omega,
+                                    delta, dr, beta, _ptr(mu), _ptr(f), _stream()), "wbfbt_sinker_setup")
+    return mu, f
+
+
+@dataclass
+class SolveResult:
+    iters: int
+    rel_res: float
+    status: int
+
+
+class Solver:
+    """Owns one wbfbt_ctx.  All tensors are device tensors on the current stream unless noted."""
+
+    def __init__(self, nx: int, k: int, mu: torch.Tensor, ny: int | None = None, nz: int | None = None,
+                 lengths=(1.0, 1.0, 1.0), a_l: float = 1.0, a_r: float = 0.0, restart: int = 50,
+                 cheb_degree: int = 3, mg_min_n: int = 4, precision: int = F64, schur_sign: int = -1):
+        self.nx, self.ny, self.nz, self.k = nx, ny or nx, nz or nx, k
+        self.mesh = Mesh(self.nx, self.ny, self.nz, *lengths)
+        o = default_opts()
+        o.a_l, o.a_r, o.restart, o.cheb_degree = a_l, a_r, restart, cheb_degree
+        o.mg_min_n, o.precision, o.schur_sign = mg_min_n, precision, schur_sign
+        self.opts = o
+        self.precision = precision
+        self._mu = mu.contiguous()
+        h = ctypes.c_void_p()
+        _check(lib().wbfbt_create(ctypes.byref(self.mesh), k, _ptr(self._mu), ctypes.byref(o), _stream(),
+                                  ctypes.byref(h)), "wbfbt_create")
+        self.h = h
+        nn, ne = ctypes.c_longlong(), ctypes.c_longlong()
+        npe, nl = ctypes.c_int(), ctypes.c_int()
+        _check(lib().wbfbt_sizes(h, ctypes.byref(nn), ctypes.byref(ne), ctypes.byref(npe), ctypes.byref(nl)),
+               "wbfbt_sizes")
+        self.n_nodes, self.n_elem, self.np, self.n_levels = nn.value, ne.value, npe.value, nl.value
+        self.n_u, self.n_p = 3 * self.n_nodes, self.n_elem * self.np
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().wbfbt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def device_bytes(self) -> int:
+        return lib().wbfbt_device_bytes(self.h)
+
+    @property
+    def pdtype(self) -> torch.dtype:
+        return torch.float64 if self.precision == F64 else torch.float32
+
+    def _apply(self, name, x, nout, *extra):
+        y = torch.empty(nout, dtype=x.dtype, device=x.device)
+        _check(getattr(lib(), name)(self.h, *extra, _ptr(x), _ptr(y), _dtype_code(x)), name)
+        return y
+
+    def apply_A(self, u):
+        return self._apply("wbfbt_apply_A", u, self.n_u)
+
+    def apply_B(self, u):
+        return self._apply("wbfbt_apply_B", u, self.n_p)
+
+    def apply_BT(self, p):
+        return self._apply("wbfbt_apply_BT", p, self.n_u)
+
+    def apply_K(self, x):
+        return self._apply("wbfbt_apply_K", x, self.n_u + self.n_p)
+
+    def apply_Kw(self, which: int, p):
+        return self._apply("wbfbt_apply_Kw", p, self.n_p, which)
+
+    def apply_Ainv(self, r):
+        return self._apply("wbfbt_apply_Ainv", r, self.n_u)
+
+    def apply_Kinv(self, which: int, r):
+        return self._apply("wbfbt_apply_Kinv", r, self.n_p, which)
+
+    def apply_schur_inv(self, r):
+        return self._apply("wbfbt_apply_schur_inv", r, self.n_p)
+
+    def apply_precond(self, x):
+        return self._apply("wbfbt_apply_precond", x, self.n_u + self.n_p)
+
+    def solve(self, f: torch.Tensor, rtol: float = 1e-6, maxit: int = 1000, u=None, p=None, check=True):
+        """Solve with body force f [3][nodes] (device or pinned/pageable host float64 tensor)."""
+        dev = f.device
+        u = torch.empty(self.n_u, dtype=torch.float64, device=dev) if u is None else u
+        p = torch.empty(self.n_p, dtype=torch.float64, device=dev) if p is None else p
+        its, rel = ctypes.c_int(), ctypes.c_double()
+        st = lib().wbfbt_solve(self.h, _ptr(f), _ptr(u), _ptr(p), rtol, maxit, ctypes.byref(its), ctypes.byref(rel))
+        if check and st not in (0, -5):
+            _check(st, "wbfbt_solve")
+        return u, p, SolveResult(its.value, rel.value, st)

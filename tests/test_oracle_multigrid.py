@@ -172,3 +172,14 @@ def test_pressure_poisson_vcycle_symmetric():
     y = op.project_pressure(m, rng.standard_normal(m.n_p))
     a, b = y @ op.project_pressure(m, pp.apply(x)), x @ op.project_pressure(m, pp.apply(y))
     assert abs(a - b) < 1e-10 * abs(a)
+
+
+def test_single_element_mesh_pressure_poisson_is_finite():
+    """Degenerate case: one element, every face Dirichlet; the constant mode has a zero K_w diagonal."""
+    m = M.Mesh(1, 1, 1, 2)
+    mu = np.ones(m.n_nodes)
+    B = op.assemble_B(m)
+    pp = mg.PressurePoissonMG(m, B, op.lumped_weight_diag(m, mu, 1.0), mu, 1.0)
+    assert pp.dinv[0] == 0.0 and np.all(pp.dinv[1:] > 0)
+    y = pp.apply(op.project_pressure(m, np.arange(m.n_p, dtype=float)))
+    assert np.all(np.isfinite(y))
