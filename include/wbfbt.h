@@ -88,6 +88,13 @@ int wbfbt_sinker_setup(const wbfbt_mesh* mesh, int k, const double* centres, int
 int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wbfbt_opts* opts,
                  void* stream, wbfbt_ctx** out);
 
+/* Recompute everything that depends on the viscosity (weights, hierarchies, Jacobi
+ * diagonals, Chebyshev bounds, coarsest inverses) for a new mu_nodes (device or
+ * host pointer, same layout and rules as in wbfbt_create), reusing the context's
+ * memory: no allocation.  This is the per-nonlinear-step setup of a Picard or
+ * Newton loop, whose linearised Stokes systems share the mesh but not mu (Sec. 2). */
+int wbfbt_setup(wbfbt_ctx* ctx, const double* mu_nodes);
+
 /* Operator applies on the fine mesh, device pointers, dtype WBFBT_F64 or WBFBT_F32.
  *   apply_A  : y = A u                 (viscous stress, Sec. 1.2)          u, y [3][nodes]
  *   apply_B  : p = B u                 (divergence, b(v,q) = -int q div v) u [3][nodes], p [E][Np]
@@ -133,6 +140,9 @@ int wbfbt_sizes(const wbfbt_ctx* ctx, long long* n_nodes, long long* n_elem, int
 
 /* Total device bytes owned by the context. */
 long long wbfbt_device_bytes(const wbfbt_ctx* ctx);
+
+/* Number of CUDA kernels this library has launched in the process so far (all contexts). */
+long long wbfbt_launch_count(void);
 
 void wbfbt_destroy(wbfbt_ctx* ctx);
 const char* wbfbt_status_string(int status);

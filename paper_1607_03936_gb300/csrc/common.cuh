@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 
 #include "tables.h"
@@ -49,6 +50,14 @@ __device__ inline void colour_element(const Grid& g, int c, int t, int& ex, int&
   int iy = t % ncy; int iz = t / ncy;
   ex = 2 * ix + cx; ey = 2 * iy + cy; ez = 2 * iz + cz;
 }
+
+// Process-wide count of kernel launches issued by this library (one shared instance:
+// inline-function statics are merged across translation units).
+inline std::atomic<long long>& wb_launch_counter() {
+  static std::atomic<long long> n{0};
+  return n;
+}
+inline void wb_count_launch() { wb_launch_counter().fetch_add(1, std::memory_order_relaxed); }
 
 #define WB_CUDA_TRY(expr)                                  \
   do {                                                     \

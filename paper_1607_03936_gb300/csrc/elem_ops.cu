@@ -175,10 +175,10 @@ cudaError_t run_stokes(const Grid& g, const RefTables* tab, const T* u, const T*
     for (int c = 0; c < 8; ++c) {
       int cnt = colour_count(g, c);
       if (cnt == 0) continue;
-      k_stokes<T, N, OPS><<<(cnt + EPB - 1) / EPB, TH, 0, st>>>(g, tab, c, cnt, u, us, p, coef, coef_nodal, yu, yp);
+      wb_count_launch(), k_stokes<T, N, OPS><<<(cnt + EPB - 1) / EPB, TH, 0, st>>>(g, tab, c, cnt, u, us, p, coef, coef_nodal, yu, yp);
     }
   } else {
-    k_stokes<T, N, OPS><<<(g.ne + EPB - 1) / EPB, TH, 0, st>>>(g, tab, -1, g.ne, u, us, p, coef, coef_nodal, yu, yp);
+    wb_count_launch(), k_stokes<T, N, OPS><<<(g.ne + EPB - 1) / EPB, TH, 0, st>>>(g, tab, -1, g.ne, u, us, p, coef, coef_nodal, yu, yp);
   }
   return cudaGetLastError();
 }
@@ -254,7 +254,7 @@ cudaError_t run_poisson(const Grid& g, const RefTables* tab, const T* u, const T
   for (int c = 0; c < 8; ++c) {
     int cnt = colour_count(g, c);
     if (cnt == 0) continue;
-    k_poisson<T, N><<<(cnt + EPB - 1) / EPB, TH, 0, st>>>(g, tab, c, cnt, u, coef, y);
+    wb_count_launch(), k_poisson<T, N><<<(cnt + EPB - 1) / EPB, TH, 0, st>>>(g, tab, c, cnt, u, coef, y);
   }
   return cudaGetLastError();
 }
@@ -654,7 +654,7 @@ cudaError_t run_dense(const Grid& g, const RefTables* tab, const double* coef, i
     int cnt = colour_count(g, c);
     if (cnt == 0) continue;
     dim3 grid(cnt, (VEC ? 3 : 1) * N3);
-    k_dense_assemble<N, VEC><<<grid, N3, 0, st>>>(g, tab, c, coef, cn, map, nfree, M, ld);
+    wb_count_launch(), k_dense_assemble<N, VEC><<<grid, N3, 0, st>>>(g, tab, c, coef, cn, map, nfree, M, ld);
   }
   return cudaGetLastError();
 }
@@ -678,67 +678,67 @@ cudaError_t launch_assemble_dense_L_mapped(const Grid& g, int k, const RefTables
 }
 
 cudaError_t launch_identity_map(int n, int* m, cudaStream_t st) {
-  k_iota<<<blocks_for(n, 256), 256, 0, st>>>(n, m);
+  wb_count_launch(), k_iota<<<blocks_for(n, 256), 256, 0, st>>>(n, m);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_dinv_A(const Grid& g, int k, const RefTables* dtab, const T* coef, int cn, T* dinv,
                           cudaStream_t st) {
-  WB_DISPATCH_N(k, ((k_dinv_stiff<T, N, true><<<blocks_for(g.nn, 128), 128, 0, st>>>(g, dtab, coef, cn, dinv)),
+  WB_DISPATCH_N(k, ((wb_count_launch(), k_dinv_stiff<T, N, true><<<blocks_for(g.nn, 128), 128, 0, st>>>(g, dtab, coef, cn, dinv)),
                     cudaGetLastError()));
 }
 
 template <typename T>
 cudaError_t launch_dinv_L(const Grid& g, int k, const RefTables* dtab, const T* coef, T* dinv, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((k_dinv_stiff<T, N, false><<<blocks_for(g.nn, 128), 128, 0, st>>>(g, dtab, coef, 0, dinv)),
+  WB_DISPATCH_N(k, ((wb_count_launch(), k_dinv_stiff<T, N, false><<<blocks_for(g.nn, 128), 128, 0, st>>>(g, dtab, coef, 0, dinv)),
                     cudaGetLastError()));
 }
 
 template <typename T>
 cudaError_t launch_dinv_Kw(const Grid& g, int k, const RefTables* dtab, const T* cinv, T* dinv, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((k_dinv_Kw<T, N><<<blocks_for((long long)g.ne * Cfg<N>::NP, 128), 128, 0, st>>>(g, dtab, cinv, dinv)),
+  WB_DISPATCH_N(k, ((wb_count_launch(), k_dinv_Kw<T, N><<<blocks_for((long long)g.ne * Cfg<N>::NP, 128), 128, 0, st>>>(g, dtab, cinv, dinv)),
                     cudaGetLastError()));
 }
 
 cudaError_t launch_lumped_weight(const Grid& g, int k, const RefTables* dtab, const double* mu, double a, double* out,
                                  cudaStream_t st) {
-  k_lumped<<<blocks_for(g.nn, 128), 128, 0, st>>>(g, k, dtab, mu, a, out);
+  wb_count_launch(), k_lumped<<<blocks_for(g.nn, 128), 128, 0, st>>>(g, k, dtab, mu, a, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lumped_mass(const Grid& g, int k, const RefTables* dtab, double* out, cudaStream_t st) {
-  k_lumped<<<blocks_for(g.nn, 128), 128, 0, st>>>(g, k, dtab, nullptr, 1.0, out);
+  wb_count_launch(), k_lumped<<<blocks_for(g.nn, 128), 128, 0, st>>>(g, k, dtab, nullptr, 1.0, out);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_poisson_coef0(const Grid& g, int k, const double* mu, double a, T* c, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((k_poisson_coef0<T, N><<<blocks_for((long long)g.ne * Cfg<N>::N3, 128), 128, 0, st>>>(g, mu, a, 0, c)),
+  WB_DISPATCH_N(k, ((wb_count_launch(), k_poisson_coef0<T, N><<<blocks_for((long long)g.ne * Cfg<N>::N3, 128), 128, 0, st>>>(g, mu, a, 0, c)),
                     cudaGetLastError()));
 }
 
 template <typename T>
 cudaError_t launch_nodal_to_points(const Grid& g, int k, const double* mu, T* c, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((k_poisson_coef0<T, N><<<blocks_for((long long)g.ne * Cfg<N>::N3, 128), 128, 0, st>>>(g, mu, 1.0, 1, c)),
+  WB_DISPATCH_N(k, ((wb_count_launch(), k_poisson_coef0<T, N><<<blocks_for((long long)g.ne * Cfg<N>::N3, 128), 128, 0, st>>>(g, mu, 1.0, 1, c)),
                     cudaGetLastError()));
 }
 
 template <typename T>
 cudaError_t launch_coarsen_coef(const Grid& gf, int k, const RefTables* dtab, const T* cf, T* cc, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((k_coarsen_coef<T, N><<<blocks_for((long long)(gf.ne / 8) * Cfg<N>::N3, 128), 128, 0, st>>>(gf, dtab, cf, cc)),
+  WB_DISPATCH_N(k, ((wb_count_launch(), k_coarsen_coef<T, N><<<blocks_for((long long)(gf.ne / 8) * Cfg<N>::N3, 128), 128, 0, st>>>(gf, dtab, cf, cc)),
                     cudaGetLastError()));
 }
 
 template <typename T>
 cudaError_t launch_disc_to_cont(const Grid& g, int k, const RefTables* dtab, const T* rd, T* rc, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((k_disc_to_cont<T, N><<<blocks_for(g.nn, 128), 128, 0, st>>>(g, dtab, rd, rc)), cudaGetLastError()));
+  WB_DISPATCH_N(k, ((wb_count_launch(), k_disc_to_cont<T, N><<<blocks_for(g.nn, 128), 128, 0, st>>>(g, dtab, rd, rc)), cudaGetLastError()));
 }
 
 template <typename T>
 cudaError_t launch_cont_to_disc(const Grid& g, int k, const RefTables* dtab, const T* ec, T* ed, int add,
                                 cudaStream_t st) {
-  WB_DISPATCH_N(k, ((k_cont_to_disc<T, N><<<blocks_for(g.ne, 128), 128, 0, st>>>(g, dtab, ec, ed, add)), cudaGetLastError()));
+  WB_DISPATCH_N(k, ((wb_count_launch(), k_cont_to_disc<T, N><<<blocks_for(g.ne, 128), 128, 0, st>>>(g, dtab, ec, ed, add)), cudaGetLastError()));
 }
 
 size_t transfer_work_size(const Grid& gc, int k) {
@@ -760,9 +760,9 @@ cudaError_t launch_prolong(const Grid& gc, int k, const RefTables* dtab, int nco
   for (int c = 0; c < ncomp; ++c) {
     const T* in = in_c + c * nc;
     T* out = out_f + c * nf;
-    k_pass<T><<<blocks_for((long long)nfx * ncy * ncz, bs), bs, 0, st>>>(dtab, k, 0, ncx, ncy, ncz, gc.nx, 1, in, w1, 0);
-    k_pass<T><<<blocks_for((long long)nfx * nfy * ncz, bs), bs, 0, st>>>(dtab, k, 1, nfx, ncy, ncz, gc.ny, 1, w1, w2, 0);
-    k_pass<T><<<blocks_for((long long)nfx * nfy * nfz, bs), bs, 0, st>>>(dtab, k, 2, nfx, nfy, ncz, gc.nz, 1, w2, out, add);
+    wb_count_launch(), k_pass<T><<<blocks_for((long long)nfx * ncy * ncz, bs), bs, 0, st>>>(dtab, k, 0, ncx, ncy, ncz, gc.nx, 1, in, w1, 0);
+    wb_count_launch(), k_pass<T><<<blocks_for((long long)nfx * nfy * ncz, bs), bs, 0, st>>>(dtab, k, 1, nfx, ncy, ncz, gc.ny, 1, w1, w2, 0);
+    wb_count_launch(), k_pass<T><<<blocks_for((long long)nfx * nfy * nfz, bs), bs, 0, st>>>(dtab, k, 2, nfx, nfy, ncz, gc.nz, 1, w2, out, add);
   }
   return cudaGetLastError();
 }
@@ -777,11 +777,11 @@ cudaError_t launch_restrict(const Grid& gc, int k, const RefTables* dtab, int nc
   for (int c = 0; c < ncomp; ++c) {
     const T* in = in_f + c * nf;
     T* out = out_c + c * nc;
-    k_pass<T><<<blocks_for((long long)ncx * nfy * nfz, bs), bs, 0, st>>>(dtab, k, 0, nfx, nfy, nfz, gc.nx, 0, in, w1, 0);
-    k_pass<T><<<blocks_for((long long)ncx * ncy * nfz, bs), bs, 0, st>>>(dtab, k, 1, ncx, nfy, nfz, gc.ny, 0, w1, w2, 0);
-    k_pass<T><<<blocks_for((long long)ncx * ncy * ncz, bs), bs, 0, st>>>(dtab, k, 2, ncx, ncy, nfz, gc.nz, 0, w2, out, 0);
+    wb_count_launch(), k_pass<T><<<blocks_for((long long)ncx * nfy * nfz, bs), bs, 0, st>>>(dtab, k, 0, nfx, nfy, nfz, gc.nx, 0, in, w1, 0);
+    wb_count_launch(), k_pass<T><<<blocks_for((long long)ncx * ncy * nfz, bs), bs, 0, st>>>(dtab, k, 1, ncx, nfy, nfz, gc.ny, 0, w1, w2, 0);
+    wb_count_launch(), k_pass<T><<<blocks_for((long long)ncx * ncy * ncz, bs), bs, 0, st>>>(dtab, k, 2, ncx, ncy, nfz, gc.nz, 0, w2, out, 0);
   }
-  if (mask) k_mask_boundary<T><<<blocks_for(gc.nn, 256), 256, 0, st>>>(gc, ncomp, out_c);
+  if (mask) wb_count_launch(), k_mask_boundary<T><<<blocks_for(gc.nn, 256), 256, 0, st>>>(gc, ncomp, out_c);
   return cudaGetLastError();
 }
 
@@ -792,13 +792,13 @@ cudaError_t launch_sinker(const Grid& g, int k, const RefTables& htab, const dou
   for (int s = 0; s < ns; ++s)
     for (int d = 0; d < 3; ++d) cs.c[s][d] = centres[3 * s + d];
   for (int a = 0; a < WB_MAXN; ++a) cs.x[a] = htab.x[a];
-  k_sinker<<<blocks_for(g.nn, 128), 128, 0, st>>>(g, k, cs, ns, omega, delta, dr, beta, mu, f);
+  wb_count_launch(), k_sinker<<<blocks_for(g.nn, 128), 128, 0, st>>>(g, k, cs, ns, omega, delta, dr, beta, mu, f);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_mask_boundary(const Grid& g, int ncomp, T* v, cudaStream_t st) {
-  k_mask_boundary<T><<<blocks_for(g.nn, 256), 256, 0, st>>>(g, ncomp, v);
+  wb_count_launch(), k_mask_boundary<T><<<blocks_for(g.nn, 256), 256, 0, st>>>(g, ncomp, v);
   return cudaGetLastError();
 }
 
@@ -828,12 +828,12 @@ __global__ void k_load_vector(Grid g, const double* __restrict__ lm, const doubl
 
 template <typename T>
 cudaError_t launch_splitmix_start(long long n, unsigned long long seed, T* v, cudaStream_t st) {
-  k_splitmix_start<T><<<blocks_for(n, 256), 256, 0, st>>>(n, seed, v);
+  wb_count_launch(), k_splitmix_start<T><<<blocks_for(n, 256), 256, 0, st>>>(n, seed, v);
   return cudaGetLastError();
 }
 
 cudaError_t launch_load_vector(const Grid& g, const double* lm, const double* f, double* F, cudaStream_t st) {
-  k_load_vector<<<blocks_for(g.nn, 256), 256, 0, st>>>(g, lm, f, F);
+  wb_count_launch(), k_load_vector<<<blocks_for(g.nn, 256), 256, 0, st>>>(g, lm, f, F);
   return cudaGetLastError();
 }
 

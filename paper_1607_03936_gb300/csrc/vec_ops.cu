@@ -295,50 +295,50 @@ template <typename A, typename B>
 cudaError_t launch_dot(const A* x, const B* y, long long n, long long stride, double* part, double* out, int sqrt_out,
                        cudaStream_t st) {
   const int np = partial_blocks(n);
-  k_dot_partial<A, B><<<np, RB, 0, st>>>(x, y, n, stride, part);
-  k_final<<<1, RB, 0, st>>>(part, np, 1, out, sqrt_out);
+  wb_count_launch(), k_dot_partial<A, B><<<np, RB, 0, st>>>(x, y, n, stride, part);
+  wb_count_launch(), k_final<<<1, RB, 0, st>>>(part, np, 1, out, sqrt_out);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_cheb_init0(long long n, const T* b, const T* dinv, T inv_theta, T* r, T* d, T* x, cudaStream_t st) {
-  k_cheb_init0<T><<<nblk(n, 256), 256, 0, st>>>(n, b, dinv, inv_theta, r, d, x);
+  wb_count_launch(), k_cheb_init0<T><<<nblk(n, 256), 256, 0, st>>>(n, b, dinv, inv_theta, r, d, x);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_cheb_init1(long long n, const T* b, const T* mx, const T* dinv, T inv_theta, T* r, T* d, T* x,
                               cudaStream_t st) {
-  k_cheb_init1<T><<<nblk(n, 256), 256, 0, st>>>(n, b, mx, dinv, inv_theta, r, d, x);
+  wb_count_launch(), k_cheb_init1<T><<<nblk(n, 256), 256, 0, st>>>(n, b, mx, dinv, inv_theta, r, d, x);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_cheb_step(long long n, const T* md, const T* dinv, T a, T bc, T* r, T* d, T* x, cudaStream_t st) {
-  k_cheb_step<T><<<nblk(n, 256), 256, 0, st>>>(n, md, dinv, a, bc, r, d, x);
+  wb_count_launch(), k_cheb_step<T><<<nblk(n, 256), 256, 0, st>>>(n, md, dinv, a, bc, r, d, x);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_sub(long long n, const T* a, T* r, cudaStream_t st) {
-  k_sub<T><<<nblk(n, 256), 256, 0, st>>>(n, a, r);
+  wb_count_launch(), k_sub<T><<<nblk(n, 256), 256, 0, st>>>(n, a, r);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_axpby(long long n, T a, const T* x, T b, const T* y, T* z, cudaStream_t st) {
-  k_axpby<T><<<nblk(n, 256), 256, 0, st>>>(n, a, x, b, y, z);
+  wb_count_launch(), k_axpby<T><<<nblk(n, 256), 256, 0, st>>>(n, a, x, b, y, z);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_mul(long long n, const T* a, const T* b, T* z, cudaStream_t st) {
-  k_mul<T><<<nblk(n, 256), 256, 0, st>>>(n, a, b, z);
+  wb_count_launch(), k_mul<T><<<nblk(n, 256), 256, 0, st>>>(n, a, b, z);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_scale(long long n, T s, const T* x, T* z, cudaStream_t st) {
-  k_scale<T><<<nblk(n, 256), 256, 0, st>>>(n, s, x, z);
+  wb_count_launch(), k_scale<T><<<nblk(n, 256), 256, 0, st>>>(n, s, x, z);
   return cudaGetLastError();
 }
 template <typename A, typename B>
 cudaError_t launch_cast(long long n, const A* x, B* y, cudaStream_t st) {
-  k_cast<A, B><<<nblk(n, 256), 256, 0, st>>>(n, x, y);
+  wb_count_launch(), k_cast<A, B><<<nblk(n, 256), 256, 0, st>>>(n, x, y);
   return cudaGetLastError();
 }
 
@@ -347,39 +347,39 @@ cudaError_t launch_project_pressure(long long ne, int np, const T* src, T* dst, 
                                     cudaStream_t st) {
   cudaError_t e = launch_dot<T, T>(src, (const T*)nullptr, ne, np, part, sum, 0, st);
   if (e != cudaSuccess) return e;
-  k_copy_proj<T><<<nblk(ne * np, 256), 256, 0, st>>>(ne, np, sum, src, dst);
+  wb_count_launch(), k_copy_proj<T><<<nblk(ne * np, 256), 256, 0, st>>>(ne, np, sum, src, dst);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_coarse_solve(int nn, int ncomp, const int* map, int nfree_nodes, int ndense, const double* Ainv,
                                 int neumann, const T* b, T* x, double* bf, double* xf, cudaStream_t st) {
-  k_coarse_gather<T><<<nblk(nn, 256), 256, 0, st>>>(nn, ncomp, map, nfree_nodes, b, bf, neumann);
-  k_gemv_rows<<<nblk((long long)ndense * 32, 256), 256, 0, st>>>(Ainv, ndense, bf, xf);
-  if (neumann) k_sub_mean_small<<<1, 1024, 0, st>>>(ndense, xf);
-  k_coarse_scatter<T><<<nblk(nn, 256), 256, 0, st>>>(nn, ncomp, map, nfree_nodes, xf, x);
+  wb_count_launch(), k_coarse_gather<T><<<nblk(nn, 256), 256, 0, st>>>(nn, ncomp, map, nfree_nodes, b, bf, neumann);
+  wb_count_launch(), k_gemv_rows<<<nblk((long long)ndense * 32, 256), 256, 0, st>>>(Ainv, ndense, bf, xf);
+  if (neumann) wb_count_launch(), k_sub_mean_small<<<1, 1024, 0, st>>>(ndense, xf);
+  wb_count_launch(), k_coarse_scatter<T><<<nblk(nn, 256), 256, 0, st>>>(nn, ncomp, map, nfree_nodes, xf, x);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dense_inverse(double* M, int n, int pin_first, double* Y, double* Ainv, int* flag, cudaStream_t st) {
   cudaError_t e;
-  if (pin_first) k_pin_first<<<nblk(n, 256), 256, 0, st>>>(M, n);
+  if (pin_first) wb_count_launch(), k_pin_first<<<nblk(n, 256), 256, 0, st>>>(M, n);
   for (int j = 0; j < n; ++j) {
     const int m = n - j - 1;
     dim3 blk(16, 16), grd(m > 0 ? (m + 15) / 16 : 1, m > 0 ? (m + 15) / 16 : 1);
-    k_chol_update<<<grd, blk, 0, st>>>(M, n, j, flag);
+    wb_count_launch(), k_chol_update<<<grd, blk, 0, st>>>(M, n, j, flag);
   }
   {
     dim3 blk(16, 16), grd((n + 15) / 16, (n + 15) / 16);
-    k_chol_scale_offdiag<<<grd, blk, 0, st>>>(M, n);
-    k_chol_scale_diag<<<nblk(n, 256), 256, 0, st>>>(M, n);
+    wb_count_launch(), k_chol_scale_offdiag<<<grd, blk, 0, st>>>(M, n);
+    wb_count_launch(), k_chol_scale_diag<<<nblk(n, 256), 256, 0, st>>>(M, n);
   }
   e = cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)n * n, st);
   if (e != cudaSuccess) return e;
-  k_trinv_cols<<<nblk(n, 64), 64, 0, st>>>(M, n, Y);
+  wb_count_launch(), k_trinv_cols<<<nblk(n, 64), 64, 0, st>>>(M, n, Y);
   {
     dim3 blk(16, 16), grd((n + 15) / 16, (n + 15) / 16);
-    k_ytY<<<grd, blk, 0, st>>>(Y, n, Ainv);
+    wb_count_launch(), k_ytY<<<grd, blk, 0, st>>>(Y, n, Ainv);
   }
   return cudaGetLastError();
 }
@@ -387,25 +387,25 @@ cudaError_t launch_dense_inverse(double* M, int n, int pin_first, double* Y, dou
 cudaError_t launch_mdot(const double* V, long long ld, int ncols, const double* w, long long n, double* part,
                         double* out, cudaStream_t st) {
   const int np = partial_blocks(n);
-  k_mdot_partial<<<dim3(np, ncols), RB, 0, st>>>(V, ld, w, n, np, part);
-  k_final<<<ncols, RB, 0, st>>>(part, np, ncols, out, 0);
+  wb_count_launch(), k_mdot_partial<<<dim3(np, ncols), RB, 0, st>>>(V, ld, w, n, np, part);
+  wb_count_launch(), k_final<<<ncols, RB, 0, st>>>(part, np, ncols, out, 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemv_sub(const double* V, long long ld, int ncols, const double* h, double* w, long long n,
                             cudaStream_t st) {
-  k_gemv_sub<<<nblk(n, 256), 256, 0, st>>>(V, ld, ncols, h, w, n);
+  wb_count_launch(), k_gemv_sub<<<nblk(n, 256), 256, 0, st>>>(V, ld, ncols, h, w, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemv_add(const double* Z, long long ld, int ncols, const double* y, double* x, long long n,
                             cudaStream_t st) {
-  k_gemv_add<<<nblk(n, 256), 256, 0, st>>>(Z, ld, ncols, y, x, n);
+  wb_count_launch(), k_gemv_add<<<nblk(n, 256), 256, 0, st>>>(Z, ld, ncols, y, x, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_add_vec(long long n, const double* a, double* h, cudaStream_t st) {
-  k_add2<<<nblk(n, 256), 256, 0, st>>>(n, a, h);
+  wb_count_launch(), k_add2<<<nblk(n, 256), 256, 0, st>>>(n, a, h);
   return cudaGetLastError();
 }
 

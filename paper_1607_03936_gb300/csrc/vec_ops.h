@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "common.cuh"
+
 // out[0] = sum_i x[i*stride] * y[i*stride] (y == nullptr: sum of x), deterministic; sqrt_out takes sqrt.
 // part: >= 592 doubles of workspace.
 template <typename A, typename B>

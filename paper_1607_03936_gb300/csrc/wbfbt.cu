@@ -49,6 +49,12 @@ struct Pool {
     bytes += b;
     return static_cast<T*>(p);
   }
+  // Allocate on first use only, so a second setup pass over the same structures allocates nothing.
+  template <typename T>
+  T* ensure(T*& p, size_t n) {
+    if (!p) p = get<T>(n);
+    return p;
+  }
   ~Pool() {
     for (void* p : ptrs) cudaFree(p);
   }
@@ -68,6 +74,9 @@ struct Level {
   int* map = nullptr;              // node -> dense index (coarsest)
   int nfree_nodes = 0, ndense = 0;
   double *Ainv = nullptr, *bf = nullptr, *xf = nullptr;
+  // setup scratch kept for re-setup without allocation
+  double *pts64 = nullptr, *d64 = nullptr, *Md = nullptr, *Yd = nullptr;
+  T *coefT = nullptr, *pv = nullptr, *pw = nullptr;
 };
 
 template <typename T>
@@ -83,9 +92,11 @@ struct Precond {
   Hier<T> HA, HL[2];
   T* dKw[2] = {nullptr, nullptr};
   double lamKw[2] = {0, 0};
-  T *pb, *px, *pr, *pd, *ptmp, *vtmp;                   // disc-level pressure / velocity workspaces
-  T *sr, *sy, *sz, *sy2, *sv1, *sv2, *urhs, *utmp;      // Schur / block workspaces
-  T *vin, *vout;                                        // mixed-precision Krylov <-> preconditioner
+  T *pb = nullptr, *px = nullptr, *pr = nullptr, *pd = nullptr, *ptmp = nullptr, *vtmp = nullptr;
+  T *sr = nullptr, *sy = nullptr, *sz = nullptr, *sy2 = nullptr, *sv1 = nullptr, *sv2 = nullptr;
+  T *urhs = nullptr, *utmp = nullptr;                   // Schur / block workspaces
+  T *vin = nullptr, *vout = nullptr;                    // mixed-precision Krylov <-> preconditioner
+  double *c0[2] = {nullptr, nullptr}, *dK64[2] = {nullptr, nullptr};
 };
 
 }  // namespace
@@ -299,51 +310,49 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
       L.coef64 = const_cast<double*>(coef0_64);
       L.coef_nodal = coef0_nodal;
       if (coef0_nodal) {
-        // per-point FP64 copy for coarsening
-        double* pts = c->pool.get<double>(npts);
-        CK(launch_nodal_to_points<double>(g, c->k, coef0_64, pts, c->st));
-        prev_pts = pts;
+        c->pool.ensure(L.pts64, npts);   // per-point FP64 copy for coarsening
+        CK(launch_nodal_to_points<double>(g, c->k, coef0_64, L.pts64, c->st));
+        prev_pts = L.pts64;
       } else {
         prev_pts = coef0_64;
       }
     } else {
-      double* pts = c->pool.get<double>(npts);
-      Grid gf = H.lv[l - 1].g;
-      CK(launch_coarsen_coef<double>(gf, c->k, c->dtab, prev_pts, pts, c->st));
-      L.coef64 = pts;
+      c->pool.ensure(L.pts64, npts);
+      CK(launch_coarsen_coef<double>(H.lv[l - 1].g, c->k, c->dtab, prev_pts, L.pts64, c->st));
+      L.coef64 = L.pts64;
       L.coef_nodal = 0;
-      prev_pts = pts;
+      prev_pts = L.pts64;
     }
     // coefficient in T
     if (std::is_same<T, double>::value) {
       L.coef = reinterpret_cast<const T*>(L.coef64);
     } else {
       size_t nc = L.coef_nodal ? (size_t)g.nn : npts;
-      T* cT = c->pool.get<T>(nc);
-      CK((launch_cast<double, T>((long long)nc, L.coef64, cT, c->st)));
-      L.coef = cT;
+      c->pool.ensure(L.coefT, nc);
+      CK((launch_cast<double, T>((long long)nc, L.coef64, L.coefT, c->st)));
+      L.coef = L.coefT;
     }
-    L.b = c->pool.get<T>(nv);
-    L.x = c->pool.get<T>(nv);
+    c->pool.ensure(L.b, nv);
+    c->pool.ensure(L.x, nv);
     if (!L.coarsest) {
-      L.r = c->pool.get<T>(nv);
-      L.d = c->pool.get<T>(nv);
-      L.tmp = c->pool.get<T>(nv);
-      L.dinv = c->pool.get<T>(nv);
-      double* d64 = c->pool.get<double>(nv);
+      c->pool.ensure(L.r, nv);
+      c->pool.ensure(L.d, nv);
+      c->pool.ensure(L.tmp, nv);
+      c->pool.ensure(L.dinv, nv);
+      c->pool.ensure(L.d64, nv);
       if (vec)
-        CK(launch_dinv_A<double>(g, c->k, c->dtab, L.coef64, L.coef_nodal, d64, c->st));
+        CK(launch_dinv_A<double>(g, c->k, c->dtab, L.coef64, L.coef_nodal, L.d64, c->st));
       else
-        CK(launch_dinv_L<double>(g, c->k, c->dtab, L.coef64, d64, c->st));
-      CK((launch_cast<double, T>((long long)nv, d64, L.dinv, c->st)));
+        CK(launch_dinv_L<double>(g, c->k, c->dtab, L.coef64, L.d64, c->st));
+      CK((launch_cast<double, T>((long long)nv, L.d64, L.dinv, c->st)));
       Grid gc = coarser(g, c->k);
       size_t ws = transfer_work_size(gc, c->k);
-      L.w1 = c->pool.get<T>(ws);
-      L.w2 = c->pool.get<T>(ws);
-      T* v = c->pool.get<T>(nv);
-      T* w = c->pool.get<T>(nv);
+      c->pool.ensure(L.w1, ws);
+      c->pool.ensure(L.w2, ws);
+      c->pool.ensure(L.pv, nv);
+      c->pool.ensure(L.pw, nv);
       auto M = [&](const T* u, T* y) { level_apply<T>(c, H, L, u, y); };
-      L.lam = power_lambda<T>(c, M, (long long)nv, L.dinv, v, w, L.tmp, vec ? &L.g : nullptr);
+      L.lam = power_lambda<T>(c, M, (long long)nv, L.dinv, L.pv, L.pw, L.tmp, vec ? &L.g : nullptr);
       g = gc;
     } else {
       // coarsest: dense FP64 matrix over the free DOFs, explicit inverse
@@ -357,20 +366,23 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
       if (nd > MAX_DENSE) throw WbErr{WBFBT_ERR_INVALID};
       L.nfree_nodes = nfree;
       L.ndense = nd;
-      L.map = c->pool.get<int>(g.nn);
-      CK(cudaMemcpyAsync(L.map, hmap.data(), sizeof(int) * g.nn, cudaMemcpyHostToDevice, c->st));
-      double* M = c->pool.get<double>((size_t)nd * nd);
-      double* Y = c->pool.get<double>((size_t)nd * nd);
-      L.Ainv = c->pool.get<double>((size_t)nd * nd);
-      L.bf = c->pool.get<double>(nd);
-      L.xf = c->pool.get<double>(nd);
-      CK(cudaMemsetAsync(M, 0, sizeof(double) * (size_t)nd * nd, c->st));
+      if (!L.map) {
+        c->pool.ensure(L.map, g.nn);
+        CK(cudaMemcpyAsync(L.map, hmap.data(), sizeof(int) * g.nn, cudaMemcpyHostToDevice, c->st));
+        CK(cudaStreamSynchronize(c->st));   // hmap is a stack-local host buffer
+      }
+      c->pool.ensure(L.Md, (size_t)nd * nd);
+      c->pool.ensure(L.Yd, (size_t)nd * nd);
+      c->pool.ensure(L.Ainv, (size_t)nd * nd);
+      c->pool.ensure(L.bf, nd);
+      c->pool.ensure(L.xf, nd);
+      CK(cudaMemsetAsync(L.Md, 0, sizeof(double) * (size_t)nd * nd, c->st));
       if (vec)
-        CK(launch_assemble_dense_A(g, c->k, c->dtab, L.coef64, L.coef_nodal, L.map, nfree, M, nd, c->st));
+        CK(launch_assemble_dense_A(g, c->k, c->dtab, L.coef64, L.coef_nodal, L.map, nfree, L.Md, nd, c->st));
       else
-        CK(launch_assemble_dense_L_mapped(g, c->k, c->dtab, L.coef64, L.map, M, nd, c->st));
+        CK(launch_assemble_dense_L_mapped(g, c->k, c->dtab, L.coef64, L.map, L.Md, nd, c->st));
       CK(cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
-      CK(launch_dense_inverse(M, nd, vec ? 0 : 1, Y, L.Ainv, c->dflag, c->st));
+      CK(launch_dense_inverse(L.Md, nd, vec ? 0 : 1, L.Yd, L.Ainv, c->dflag, c->st));
       int flag = 0;
       CK(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
       CK(cudaStreamSynchronize(c->st));
@@ -390,40 +402,30 @@ void build_precond(wbfbt_ctx* c) {
     P.dinvw = reinterpret_cast<T*>(c->dinv64);
   } else {
     P.mu = reinterpret_cast<T*>(c->mu32);
-    P.cinv = c->pool.get<T>(nn);
-    P.dinvw = c->pool.get<T>(nn);
+    c->pool.ensure(P.cinv, nn);
+    c->pool.ensure(P.dinvw, nn);
     CK((launch_cast<double, T>((long long)nn, c->cinv64, P.cinv, c->st)));
     CK((launch_cast<double, T>((long long)nn, c->dinv64, P.dinvw, c->st)));
   }
-  P.pb = c->pool.get<T>(np);
-  P.px = c->pool.get<T>(np);
-  P.pr = c->pool.get<T>(np);
-  P.pd = c->pool.get<T>(np);
-  P.ptmp = c->pool.get<T>(np);
-  P.vtmp = c->pool.get<T>(nu);
-  P.sr = c->pool.get<T>(np);
-  P.sy = c->pool.get<T>(np);
-  P.sz = c->pool.get<T>(np);
-  P.sy2 = c->pool.get<T>(np);
-  P.sv1 = c->pool.get<T>(nu);
-  P.sv2 = c->pool.get<T>(nu);
-  P.urhs = c->pool.get<T>(nu);
-  P.utmp = c->pool.get<T>(nu);
-  P.vin = c->pool.get<T>(c->ntot);
-  P.vout = c->pool.get<T>(c->ntot);
+  for (T** q : {&P.pb, &P.px, &P.pr, &P.pd, &P.ptmp, &P.sr, &P.sy, &P.sz, &P.sy2}) c->pool.ensure(*q, np);
+  for (T** q : {&P.vtmp, &P.sv1, &P.sv2, &P.urhs, &P.utmp}) c->pool.ensure(*q, nu);
+  if (!std::is_same<T, double>::value) {
+    c->pool.ensure(P.vin, c->ntot);
+    c->pool.ensure(P.vout, c->ntot);
+  }
   // A hierarchy: viscosity per node on the fine level
   build_hier<T>(c, P.HA, true, c->mu64, 1);
   // Poisson hierarchies: c = 1 / (a(e) sqrt(mu)) per point
   const double amp[2] = {c->opt.a_l, c->opt.a_r};
   for (int wi = 0; wi < 2; ++wi) {
-    double* c0 = c->pool.get<double>(npts);
-    CK(launch_poisson_coef0<double>(g, c->k, c->mu64, amp[wi], c0, c->st));
-    build_hier<T>(c, P.HL[wi], false, c0, 0);
+    c->pool.ensure(P.c0[wi], npts);
+    CK(launch_poisson_coef0<double>(g, c->k, c->mu64, amp[wi], P.c0[wi], c->st));
+    build_hier<T>(c, P.HL[wi], false, P.c0[wi], 0);
     // disc level: Jacobi diagonal of K_w and lambda_hat
-    double* d64 = c->pool.get<double>(np);
-    CK(launch_dinv_Kw<double>(g, c->k, c->dtab, wi == 0 ? c->cinv64 : c->dinv64, d64, c->st));
-    P.dKw[wi] = c->pool.get<T>(np);
-    CK((launch_cast<double, T>((long long)np, d64, P.dKw[wi], c->st)));
+    c->pool.ensure(P.dK64[wi], np);
+    CK(launch_dinv_Kw<double>(g, c->k, c->dtab, wi == 0 ? c->cinv64 : c->dinv64, P.dK64[wi], c->st));
+    c->pool.ensure(P.dKw[wi], np);
+    CK((launch_cast<double, T>((long long)np, P.dK64[wi], P.dKw[wi], c->st)));
     auto M = [&](const T* p, T* y) { op_Kw<T>(c, wi, p, y); };
     P.lamKw[wi] = power_lambda<T>(c, M, (long long)np, P.dKw[wi], P.px, P.pd, P.ptmp, nullptr);
   }
@@ -578,6 +580,40 @@ int fgmres(wbfbt_ctx* c, double rtol, int maxit, int* iters, double* relres) {
 
 }  // namespace
 
+namespace {
+
+__global__ void k_check_positive(long long n, const double* __restrict__ v, int* __restrict__ flag) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && (!(v[i] > 0.0) || !isfinite(v[i]))) atomicExch(flag, 1);
+}
+
+// Everything that depends on the viscosity: weights, hierarchies, diagonals, eigenvalue
+// estimates, coarsest inverses.  Allocates only on the first call for a context.
+void run_setup(wbfbt_ctx* cp, const double* mu_nodes) {
+  const Grid& g = cp->g;
+  const size_t nn = g.nn;
+  CK(cudaMemcpyAsync(cp->mu64, mu_nodes, sizeof(double) * nn, cudaMemcpyDefault, cp->st));
+  CK(cudaMemsetAsync(cp->dflag, 0, sizeof(int), cp->st));
+  wb_count_launch(), k_check_positive<<<(unsigned)((nn + 255) / 256), 256, 0, cp->st>>>((long long)nn, cp->mu64, cp->dflag);
+  CK(cudaGetLastError());
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, cp->dflag, sizeof(int), cudaMemcpyDeviceToHost, cp->st));
+  CK(cudaStreamSynchronize(cp->st));
+  if (bad) throw WbErr{WBFBT_ERR_INVALID};
+  CK((launch_cast<double, float>((long long)nn, cp->mu64, cp->mu32, cp->st)));
+  CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_l, cp->C, cp->st));
+  CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_r, cp->D, cp->st));
+  wb_count_launch(), k_inv_masked<<<(unsigned)((nn + 255) / 256), 256, 0, cp->st>>>(g, cp->C, cp->cinv64);
+  wb_count_launch(), k_inv_masked<<<(unsigned)((nn + 255) / 256), 256, 0, cp->st>>>(g, cp->D, cp->dinv64);
+  CK(cudaGetLastError());
+  if (cp->mixed)
+    build_precond<float>(cp);
+  else
+    build_precond<double>(cp);
+}
+
+}  // namespace
+
 // ================================================================== C ABI
 
 extern "C" {
@@ -657,33 +693,15 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
     cp->dsc = cp->pool.get<double>(64);
     cp->dflag = cp->pool.get<int>(4);
     cp->mu64 = cp->pool.get<double>(nn);
-    CK(cudaMemcpyAsync(cp->mu64, mu_nodes, sizeof(double) * nn, cudaMemcpyDefault, cp->st));
-    // validate mu: positive and finite
-    {
-      std::vector<double> hmu(nn);
-      CK(cudaMemcpyAsync(hmu.data(), cp->mu64, sizeof(double) * nn, cudaMemcpyDeviceToHost, cp->st));
-      CK(cudaStreamSynchronize(cp->st));
-      for (double v : hmu)
-        if (!(v > 0.0) || !std::isfinite(v)) throw WbErr{WBFBT_ERR_INVALID};
-    }
     cp->mu32 = cp->pool.get<float>(nn);
-    CK((launch_cast<double, float>((long long)nn, cp->mu64, cp->mu32, cp->st)));
     cp->lm = cp->pool.get<double>(nn);
-    CK(launch_lumped_mass(g, cp->k, cp->dtab, cp->lm, cp->st));
     cp->C = cp->pool.get<double>(nn);
     cp->D = cp->pool.get<double>(nn);
-    CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_l, cp->C, cp->st));
-    CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_r, cp->D, cp->st));
     cp->cinv64 = cp->pool.get<double>(nn);
     cp->dinv64 = cp->pool.get<double>(nn);
-    k_inv_masked<<<(nn + 255) / 256, 256, 0, cp->st>>>(g, cp->C, cp->cinv64);
-    k_inv_masked<<<(nn + 255) / 256, 256, 0, cp->st>>>(g, cp->D, cp->dinv64);
-    CK(cudaGetLastError());
     cp->ntot = 3LL * nn + (long long)g.ne * cp->NP;
-    if (cp->mixed)
-      build_precond<float>(cp);
-    else
-      build_precond<double>(cp);
+    CK(launch_lumped_mass(g, cp->k, cp->dtab, cp->lm, cp->st));
+    run_setup(cp, mu_nodes);
     const long long n = cp->ntot;
     cp->V = cp->pool.get<double>((size_t)(cp->m + 1) * n);
     cp->Z = cp->pool.get<double>((size_t)cp->m * n);
@@ -702,6 +720,11 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
   return WBFBT_OK;
 }
 
+int wbfbt_setup(wbfbt_ctx* c, const double* mu_nodes) {
+  if (!c || !mu_nodes) return WBFBT_ERR_INVALID;
+  return guarded([&]() { run_setup(c, mu_nodes); });
+}
+
 void wbfbt_destroy(wbfbt_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
@@ -718,6 +741,8 @@ int wbfbt_sizes(const wbfbt_ctx* c, long long* nn, long long* ne, int* np, int* 
 }
 
 long long wbfbt_device_bytes(const wbfbt_ctx* c) { return c ? (long long)c->pool.bytes : 0; }
+
+long long wbfbt_launch_count(void) { return wb_launch_counter().load(); }
 
 static int stokes_apply(wbfbt_ctx* c, int ops, const void* u, const void* p, void* yu, void* yp, int dtype) {
   if (!c || (dtype != WBFBT_F64 && dtype != WBFBT_F32)) return WBFBT_ERR_INVALID;

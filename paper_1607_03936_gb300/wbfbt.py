@@ -20,9 +20,9 @@ MIXED = 1
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "non-finite value", -4: "Krylov breakdown",
           -5: "iteration limit reached", -6: "setup failed"}
 
-SYMBOLS = ["wbfbt_default_opts", "wbfbt_sinker_setup", "wbfbt_create", "wbfbt_apply_A", "wbfbt_apply_B",
+SYMBOLS = ["wbfbt_default_opts", "wbfbt_sinker_setup", "wbfbt_create", "wbfbt_setup", "wbfbt_apply_A", "wbfbt_apply_B",
            "wbfbt_apply_BT", "wbfbt_apply_K", "wbfbt_apply_Kw", "wbfbt_apply_Ainv", "wbfbt_apply_Kinv",
-           "wbfbt_apply_schur_inv", "wbfbt_apply_precond", "wbfbt_solve", "wbfbt_sizes", "wbfbt_device_bytes",
+           "wbfbt_apply_schur_inv", "wbfbt_apply_precond", "wbfbt_solve", "wbfbt_sizes", "wbfbt_device_bytes", "wbfbt_launch_count",
            "wbfbt_destroy", "wbfbt_status_string"]
 
 
@@ -57,6 +57,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.wbfbt_default_opts.restype = None
     lib.wbfbt_sinker_setup.argtypes = [ctypes.POINTER(Mesh), i, vp, i, d, d, d, d, vp, vp, vp]
     lib.wbfbt_create.argtypes = [ctypes.POINTER(Mesh), i, vp, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    lib.wbfbt_setup.argtypes = [vp, vp]
     for name in ("wbfbt_apply_A", "wbfbt_apply_B", "wbfbt_apply_BT", "wbfbt_apply_K", "wbfbt_apply_Ainv",
                  "wbfbt_apply_schur_inv", "wbfbt_apply_precond"):
         getattr(lib, name).argtypes = [vp, vp, vp, i]
@@ -67,6 +68,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                                 ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.wbfbt_device_bytes.argtypes = [vp]
     lib.wbfbt_device_bytes.restype = ctypes.c_longlong
+    lib.wbfbt_launch_count.argtypes = []
+    lib.wbfbt_launch_count.restype = ctypes.c_longlong
     lib.wbfbt_destroy.argtypes = [vp]
     lib.wbfbt_destroy.restype = None
     lib.wbfbt_status_string.argtypes = [i]
@@ -127,6 +130,11 @@ def sinker_setup(nx: int, k: int, centres, omega: float, delta: float, dr: float
     return mu, f
 
 
+def launch_count() -> int:
+    """Kernels launched by libwbfbt.so so far in this process."""
+    return lib().wbfbt_launch_count()
+
+
 @dataclass
 class SolveResult:
     iters: int
@@ -158,6 +166,11 @@ class Solver:
                "wbfbt_sizes")
         self.n_nodes, self.n_elem, self.np, self.n_levels = nn.value, ne.value, npe.value, nl.value
         self.n_u, self.n_p = 3 * self.n_nodes, self.n_elem * self.np
+
+    def setup(self, mu: torch.Tensor):
+        """Re-run the viscosity-dependent setup for a new mu (no allocation)."""
+        self._mu = mu.contiguous()
+        _check(lib().wbfbt_setup(self.h, _ptr(self._mu)), "wbfbt_setup")
 
     def close(self):
         if getattr(self, "h", None):
