@@ -19,10 +19,12 @@
  *
  * Ownership: the caller owns every input and output buffer; the context owns
  * the multigrid hierarchy and all workspaces, allocated in wbfbt_create and
- * freed in wbfbt_destroy.  No other call allocates device memory.  All work
- * is issued on the stream given to wbfbt_create, in the order of the calls;
- * "device" pointers must be valid on that stream.  Calls that return results
- * to the host (wbfbt_solve) synchronise that stream.
+ * freed in wbfbt_destroy.  No other call allocates device memory.  Work is
+ * stream-ordered with the stream given to wbfbt_create: each call runs after
+ * all work issued on that stream before it, on an internal stream of the
+ * context, and work issued on the caller's stream after the call runs after
+ * it.  "device" pointers must be valid for that order.  Calls that return
+ * results to the host (wbfbt_solve) synchronise.
  *
  * Errors: every call returns an int status, 0 on success, a negative
  * WBFBT_ERR_* code otherwise (see wbfbt_status_string).  No call aborts the
@@ -61,6 +63,7 @@ typedef struct {
     int mg_min_n;                  /* coarsen while all counts are even and min > this (4) */
     int precision;                 /* WBFBT_F64 or WBFBT_MIXED                              */
     int schur_sign;                /* -1 (default): [A B^T; 0 -S~]; +1: printed block      */
+    int use_graphs;                /* 1 (default): replay the preconditioner as a CUDA graph */
 } wbfbt_opts;
 
 typedef struct wbfbt_ctx wbfbt_ctx;

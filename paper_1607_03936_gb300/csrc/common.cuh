@@ -14,6 +14,7 @@ struct Grid {
   int nn;               // nodes
   int ne;               // elements
   double h[3];          // element sizes
+  double s[3];          // 2 / h: reference-to-physical derivative scale per axis
   double detJ;          // hx hy hz / 8
 };
 
@@ -24,6 +25,7 @@ inline Grid make_grid(int nx, int ny, int nz, int k, double lx, double ly, doubl
   g.nn = g.NX * g.NY * g.NZ;
   g.ne = nx * ny * nz;
   g.h[0] = lx / nx; g.h[1] = ly / ny; g.h[2] = lz / nz;
+  g.s[0] = 2.0 / g.h[0]; g.s[1] = 2.0 / g.h[1]; g.s[2] = 2.0 / g.h[2];
   g.detJ = g.h[0] * g.h[1] * g.h[2] / 8.0;
   return g;
 }

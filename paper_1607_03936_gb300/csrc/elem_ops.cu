@@ -51,6 +51,32 @@ __device__ inline int sym_index(int c, int d) {
   return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
 }
 
+// Operator tables in shared memory for the hot kernels: derivative matrices pre-scaled by
+// 2/h per axis, tensor quadrature weights times |J|, and the pressure basis at the points,
+// so that the per-point work is only the sum-factorisation FMAs and the pointwise physics.
+template <typename T, int N>
+struct OpTab {
+  T Ds[3][N][N];             // Ds[d][i][a] = (2 / h_d) l_a'(x_i)
+  T W3[Cfg<N>::N3];          // W_q |J|
+  T Psi[Cfg<N>::N3][Cfg<N>::NP];
+};
+
+template <typename T, int N>
+__device__ inline void load_optab(OpTab<T, N>& s, const RefTables* __restrict__ tab, const Grid& g, bool need_psi) {
+  constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP;
+  for (int t = threadIdx.x; t < 3 * N * N; t += blockDim.x) {
+    const int d = t / (N * N), r = t % (N * N);
+    s.Ds[d][r / N][r % N] = T(g.s[d] * tab->D[r / N][r % N]);
+  }
+  for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+    const int i = q % N, j = (q / N) % N, l = q / (N * N);
+    s.W3[q] = T(tab->w[i] * tab->w[j] * tab->w[l] * g.detJ);
+    if (need_psi)
+      for (int m = 0; m < NP; ++m)
+        s.Psi[q][m] = T(tab->pw[i][tab->ex[m][0]] * tab->pw[j][tab->ex[m][1]] * tab->pw[l][tab->ex[m][2]]);
+  }
+}
+
 // ------------------------------------------------------------------ Stokes family
 
 template <typename T, int N, int OPS>
@@ -61,80 +87,82 @@ k_stokes(Grid g, const RefTables* __restrict__ tab, int colour, int count, const
   constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, EPB = Cfg<N>::EPB, K = N - 1;
   constexpr bool DA = OPS & OP_A, DBT = OPS & OP_BT, DB = OPS & OP_B;
   constexpr bool SCAT = DA || DBT, GRAD = DA || DB;
-  __shared__ SmTab<T, N> st;
+  constexpr int NS = DA ? 6 : 1;      // stored stress components (B^T alone needs only -W p)
+  __shared__ OpTab<T, N> st;
   __shared__ T su[GRAD ? EPB : 1][3][N3];
-  __shared__ T sS[SCAT ? EPB : 1][6][N3];
+  __shared__ T sS[SCAT ? EPB : 1][NS][N3];
   __shared__ T sdiv[DB ? EPB : 1][N3];
-  load_tab(st, tab);
+  load_optab(st, tab, g, DB || DBT);
 
   const int tid = threadIdx.x;
   const int le = tid / N3, q = tid - le * N3;
   const int i = q % N, j = (q / N) % N, l = q / (N * N);
   const int eidx = blockIdx.x * EPB + le;
   const bool act = eidx < count;
-  int ex = 0, ey = 0, ez = 0, e = 0, node = 0;
+  int e = 0, node = 0;
   bool interior = false;
   if (act) {
+    int ex, ey, ez;
     colour_element(g, colour, eidx, ex, ey, ez);
     e = ex + g.nx * (ey + g.ny * ez);
-    int ix = K * ex + i, iy = K * ey + j, iz = K * ez + l;
+    const int ix = K * ex + i, iy = K * ey + j, iz = K * ez + l;
     node = ix + g.NX * (iy + g.NY * iz);
     interior = !on_boundary(g, ix, iy, iz);
   }
   T mu = 0, pq = 0;
-  __syncthreads();
   if (act) {
     if (GRAD) {
-      T sc = (us != nullptr && interior) ? us[node] : T(1);
+      const T sc = (us != nullptr && interior) ? us[node] : T(1);
 #pragma unroll
       for (int c = 0; c < 3; ++c) su[GRAD ? le : 0][c][q] = interior ? u[(size_t)c * g.nn + node] * sc : T(0);
     }
     if (DA) mu = coef_nodal ? coef[node] : coef[(size_t)e * N3 + q];
-    if (DBT) {
-#pragma unroll
-      for (int m = 0; m < NP; ++m) pq += psi(st, m, i, j, l) * p[(size_t)e * NP + m];
-    }
   }
-  __syncthreads();
-  const T s0 = T(2.0 / g.h[0]), s1 = T(2.0 / g.h[1]), s2 = T(2.0 / g.h[2]);
-  const T Wq = st.w[i] * st.w[j] * st.w[l] * T(g.detJ);
+  __syncthreads();   // tables and tile loaded
+  if (act && DBT) {
+#pragma unroll
+    for (int m = 0; m < NP; ++m) pq += st.Psi[q][m] * p[(size_t)e * NP + m];
+  }
   if (act) {
-    T G[3][3];
-    if (GRAD) {
+    const T Wq = st.W3[q];
+    if (DA) {
+      T G[3][3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
         for (int a = 0; a < N; ++a) {
-          a0 += st.D[i][a] * su[GRAD ? le : 0][c][a + N * (j + N * l)];
-          a1 += st.D[j][a] * su[GRAD ? le : 0][c][i + N * (a + N * l)];
-          a2 += st.D[l][a] * su[GRAD ? le : 0][c][i + N * (j + N * a)];
+          a0 += st.Ds[0][i][a] * su[GRAD ? le : 0][c][a + N * (j + N * l)];
+          a1 += st.Ds[1][j][a] * su[GRAD ? le : 0][c][i + N * (a + N * l)];
+          a2 += st.Ds[2][l][a] * su[GRAD ? le : 0][c][i + N * (j + N * a)];
         }
-        G[c][0] = s0 * a0;
-        G[c][1] = s1 * a1;
-        G[c][2] = s2 * a2;
+        G[c][0] = a0;
+        G[c][1] = a1;
+        G[c][2] = a2;
       }
-    }
-    if (DB) sdiv[DB ? le : 0][q] = Wq * (G[0][0] + G[1][1] + G[2][2]);
-    if (SCAT) {
-      T S[6] = {0, 0, 0, 0, 0, 0};
-      if (DA) {
-        T f = Wq * T(2) * mu;
-        S[0] = f * G[0][0];
-        S[1] = f * G[1][1];
-        S[2] = f * G[2][2];
-        S[3] = f * T(0.5) * (G[0][1] + G[1][0]);
-        S[4] = f * T(0.5) * (G[0][2] + G[2][0]);
-        S[5] = f * T(0.5) * (G[1][2] + G[2][1]);
-      }
-      if (DBT) {
-        T t = Wq * pq;
-        S[0] -= t;
-        S[1] -= t;
-        S[2] -= t;
-      }
+      if (DB) sdiv[DB ? le : 0][q] = Wq * (G[0][0] + G[1][1] + G[2][2]);
+      const T f = Wq * T(2) * mu, hf = Wq * mu;
+      const T t = DBT ? Wq * pq : T(0);
+      T* S = &sS[SCAT ? le : 0][0][0];
+      S[0 * N3 + q] = f * G[0][0] - t;
+      S[(NS > 1 ? 1 : 0) * N3 + q] = f * G[1][1] - t;
+      S[(NS > 2 ? 2 : 0) * N3 + q] = f * G[2][2] - t;
+      S[(NS > 3 ? 3 : 0) * N3 + q] = hf * (G[0][1] + G[1][0]);
+      S[(NS > 4 ? 4 : 0) * N3 + q] = hf * (G[0][2] + G[2][0]);
+      S[(NS > 5 ? 5 : 0) * N3 + q] = hf * (G[1][2] + G[2][1]);
+    } else {
+      if (DB) {
+        // divergence only: the three diagonal derivatives
+        T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
-      for (int s = 0; s < 6; ++s) sS[SCAT ? le : 0][s][q] = S[s];
+        for (int a = 0; a < N; ++a) {
+          a0 += st.Ds[0][i][a] * su[GRAD ? le : 0][0][a + N * (j + N * l)];
+          a1 += st.Ds[1][j][a] * su[GRAD ? le : 0][1][i + N * (a + N * l)];
+          a2 += st.Ds[2][l][a] * su[GRAD ? le : 0][2][i + N * (j + N * a)];
+        }
+        sdiv[DB ? le : 0][q] = Wq * (a0 + a1 + a2);
+      }
+      if (DBT) sS[SCAT ? le : 0][0][q] = -Wq * pq;
     }
   }
   __syncthreads();
@@ -142,24 +170,33 @@ k_stokes(Grid g, const RefTables* __restrict__ tab, int colour, int count, const
   if (DB && q < NP) {
     const int m = q;
     T acc = 0;
-    for (int qq = 0; qq < N3; ++qq) {
-      int ii = qq % N, jj = (qq / N) % N, ll = qq / (N * N);
-      acc += psi(st, m, ii, jj, ll) * sdiv[DB ? le : 0][qq];
-    }
+#pragma unroll
+    for (int qq = 0; qq < N3; ++qq) acc += st.Psi[qq][m] * sdiv[DB ? le : 0][qq];
     yp[(size_t)e * NP + m] = -acc;
   }
   if (SCAT && interior) {
+    const T* S = &sS[SCAT ? le : 0][0][0];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const int i0 = sym_index(c, 0), i1 = sym_index(c, 1), i2 = sym_index(c, 2);
-      T a0 = 0, a1 = 0, a2 = 0;
+      T acc = 0;
+      if (DA) {
+        const int i0 = sym_index(c, 0), i1 = sym_index(c, 1), i2 = sym_index(c, 2);
 #pragma unroll
-      for (int a = 0; a < N; ++a) {
-        a0 += st.D[a][i] * sS[SCAT ? le : 0][i0][a + N * (j + N * l)];
-        a1 += st.D[a][j] * sS[SCAT ? le : 0][i1][i + N * (a + N * l)];
-        a2 += st.D[a][l] * sS[SCAT ? le : 0][i2][i + N * (j + N * a)];
+        for (int a = 0; a < N; ++a) {
+          acc += st.Ds[0][a][i] * S[i0 * N3 + a + N * (j + N * l)];
+          acc += st.Ds[1][a][j] * S[i1 * N3 + i + N * (a + N * l)];
+          acc += st.Ds[2][a][l] * S[i2 * N3 + i + N * (j + N * a)];
+        }
+      } else {
+        // B^T alone: y_c = sum_a Ds[c][a][q_c] (-W p)(q with axis c -> a)
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+          const int qa = c == 0 ? a + N * (j + N * l) : (c == 1 ? i + N * (a + N * l) : i + N * (j + N * a));
+          const int qc = c == 0 ? i : (c == 1 ? j : l);
+          acc += st.Ds[c][a][qc] * S[qa];
+        }
       }
-      yu[(size_t)c * g.nn + node] += s0 * a0 + s1 * a1 + s2 * a2;
+      yu[(size_t)c * g.nn + node] += acc;
     }
   }
 }
@@ -202,10 +239,10 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_poisson(Grid g, const RefTables* __restrict__ tab, int colour, int count, const T* __restrict__ u,
           const T* __restrict__ coef, T* __restrict__ y) {
   constexpr int N3 = Cfg<N>::N3, EPB = Cfg<N>::EPB, K = N - 1;
-  __shared__ SmTab<T, N> st;
+  __shared__ OpTab<T, N> st;
   __shared__ T su[EPB][N3];
   __shared__ T sF[EPB][3][N3];
-  load_tab(st, tab);
+  load_optab(st, tab, g, false);
   const int tid = threadIdx.x;
   const int le = tid / N3, q = tid - le * N3;
   const int i = q % N, j = (q / N) % N, l = q / (N * N);
@@ -220,30 +257,29 @@ k_poisson(Grid g, const RefTables* __restrict__ tab, int colour, int count, cons
     su[le][q] = u[node];
   }
   __syncthreads();
-  const T s[3] = {T(2.0 / g.h[0]), T(2.0 / g.h[1]), T(2.0 / g.h[2])};
   if (act) {
     T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
     for (int a = 0; a < N; ++a) {
-      a0 += st.D[i][a] * su[le][a + N * (j + N * l)];
-      a1 += st.D[j][a] * su[le][i + N * (a + N * l)];
-      a2 += st.D[l][a] * su[le][i + N * (j + N * a)];
+      a0 += st.Ds[0][i][a] * su[le][a + N * (j + N * l)];
+      a1 += st.Ds[1][j][a] * su[le][i + N * (a + N * l)];
+      a2 += st.Ds[2][l][a] * su[le][i + N * (j + N * a)];
     }
-    T f = st.w[i] * st.w[j] * st.w[l] * T(g.detJ) * coef[(size_t)e * N3 + q];
-    sF[le][0][q] = f * s[0] * a0;
-    sF[le][1][q] = f * s[1] * a1;
-    sF[le][2][q] = f * s[2] * a2;
+    const T f = st.W3[q] * coef[(size_t)e * N3 + q];
+    sF[le][0][q] = f * a0;
+    sF[le][1][q] = f * a1;
+    sF[le][2][q] = f * a2;
   }
   __syncthreads();
   if (!act) return;
-  T a0 = 0, a1 = 0, a2 = 0;
+  T acc = 0;
 #pragma unroll
   for (int a = 0; a < N; ++a) {
-    a0 += st.D[a][i] * sF[le][0][a + N * (j + N * l)];
-    a1 += st.D[a][j] * sF[le][1][i + N * (a + N * l)];
-    a2 += st.D[a][l] * sF[le][2][i + N * (j + N * a)];
+    acc += st.Ds[0][a][i] * sF[le][0][a + N * (j + N * l)];
+    acc += st.Ds[1][a][j] * sF[le][1][i + N * (a + N * l)];
+    acc += st.Ds[2][a][l] * sF[le][2][i + N * (j + N * a)];
   }
-  y[node] += s[0] * a0 + s[1] * a1 + s[2] * a2;
+  y[node] += acc;
 }
 
 template <typename T, int N>
@@ -287,7 +323,7 @@ k_dense_assemble(Grid g, const RefTables* __restrict__ tab, int colour, const do
   const int node = node_of(q);
   for (int c = 0; c < NC; ++c) su[c][q] = (c == cin && q == qin) ? 1.0 : 0.0;
   __syncthreads();
-  const double s[3] = {2.0 / g.h[0], 2.0 / g.h[1], 2.0 / g.h[2]};
+  const double* s = g.s;
   const double Wq = st.w[i] * st.w[j] * st.w[l] * g.detJ;
   const double cq = coef_nodal ? coef[node] : coef[(size_t)e * N3 + q];
   double G[NC][3];
@@ -363,7 +399,7 @@ __global__ void k_dinv_stiff(Grid g, const RefTables* __restrict__ tab, const T*
   for_elements_of_node(g, K, ix, iy, iz, [&](int e, int ex, int ey, int ez, int a0, int a1, int a2) {
     const int a[3] = {a0, a1, a2};
     for (int d = 0; d < 3; ++d) {
-      const double sd = 2.0 / g.h[d];
+      const double sd = g.s[d];
       for (int ii = 0; ii < N; ++ii) {
         int qq[3] = {a0, a1, a2};
         qq[d] = ii;
@@ -413,7 +449,7 @@ __global__ void k_dinv_Kw(Grid g, const RefTables* __restrict__ tab, const T* __
         const double ps = tab->pw[qq[0]][tab->ex[m][0]] * tab->pw[qq[1]][tab->ex[m][1]] * tab->pw[qq[2]][tab->ex[m][2]];
         b += Wq * ps * tab->D[ii][a[c]];
       }
-      b *= -(2.0 / g.h[c]) * g.detJ;
+      b *= -g.s[c] * g.detJ;
       acc += b * b * ci;
     }
   }

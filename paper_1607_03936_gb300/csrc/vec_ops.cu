@@ -194,62 +194,32 @@ __global__ void k_pin_first(double* M, int n) {
   M[(size_t)t * n] = t == 0 ? 1.0 : 0.0; // column 0
 }
 
-// Right-looking Cholesky, lazy scaling: step j subtracts the rank-one term of the
-// unscaled column j from the trailing lower triangle; column j is never written
-// again, and k_chol_scale divides by sqrt(pivot) at the end.
-__global__ void k_chol_update(double* __restrict__ A, int n, int j, int* __restrict__ flag) {
-  const double piv = A[(size_t)j * n + j];
+// In-place Gauss-Jordan inversion of an SPD matrix, one pivot per pair of launches:
+//   a_ik -= a_ij a_jk / a_jj (i, k != j);  a_jk /= a_jj;  a_ij = -a_ij / a_jj;  a_jj = 1 / a_jj.
+// The pivot is saved by the first kernel so the second can overwrite row and column j.
+__global__ void k_gj_update(double* __restrict__ A, int n, int j, double* __restrict__ piv, int* __restrict__ flag) {
+  const double p = A[(size_t)j * n + j];
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
-    if (!(piv > 0.0) || !isfinite(piv)) flag[0] = j + 1;
+    piv[j] = p;
+    if (!(p > 0.0) || !isfinite(p)) flag[0] = j + 1;
   }
-  if (!(piv > 0.0)) return;
-  const int kk = j + 1 + blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = j + 1 + blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= n || kk >= n || kk > i) return;
-  A[(size_t)i * n + kk] -= A[(size_t)i * n + j] * A[(size_t)kk * n + j] / piv;
-}
-
-__global__ void k_chol_scale_offdiag(double* __restrict__ A, int n) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!(p > 0.0)) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= n || c >= i) return;
-  A[(size_t)i * n + c] /= sqrt(A[(size_t)c * n + c]);
+  if (i >= n || k >= n || i == j || k == j) return;
+  A[(size_t)i * n + k] -= A[(size_t)i * n + j] * A[(size_t)j * n + k] / p;
 }
 
-__global__ void k_chol_scale_diag(double* __restrict__ A, int n) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < n) A[(size_t)c * n + c] = sqrt(A[(size_t)c * n + c]);
-}
-
-// Y = L^-1 column by column (thread per column), Y pre-zeroed; L lower, row-major.
-__global__ void k_trinv_cols(const double* __restrict__ L, int n, double* __restrict__ Y) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
-  for (int i = 0; i < n; ++i) {
-    if (i < c) continue;
-    double s = (i == c) ? 1.0 : 0.0;
-    const double* Li = L + (size_t)i * n;
-    for (int k = c; k < i; ++k) s -= Li[k] * Y[(size_t)k * n + c];
-    Y[(size_t)i * n + c] = s / Li[i];
+__global__ void k_gj_pivot(double* __restrict__ A, int n, int j, const double* __restrict__ piv) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const double p = piv[j];
+  if (!(p > 0.0) || t >= n) return;
+  if (t == j) {
+    A[(size_t)j * n + j] = 1.0 / p;
+  } else {
+    A[(size_t)j * n + t] /= p;
+    A[(size_t)t * n + j] = -A[(size_t)t * n + j] / p;
   }
-}
-
-// Ainv = Y^T Y, 16 x 16 tiles
-__global__ void k_ytY(const double* __restrict__ Y, int n, double* __restrict__ Ainv) {
-  __shared__ double ta[16][17], tb[16][17];
-  const int a = blockIdx.y * 16 + threadIdx.y, b = blockIdx.x * 16 + threadIdx.x;
-  double acc = 0.0;
-  for (int i0 = 0; i0 < n; i0 += 16) {
-    const int ia = i0 + threadIdx.x;  // row of Y loaded for column a-tile
-    ta[threadIdx.y][threadIdx.x] = (ia < n && blockIdx.y * 16 + threadIdx.y < n) ? Y[(size_t)ia * n + blockIdx.y * 16 + threadIdx.y] : 0.0;
-    const int ib = i0 + threadIdx.y;
-    tb[threadIdx.y][threadIdx.x] = (ib < n && b < n) ? Y[(size_t)ib * n + b] : 0.0;
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < 16; ++t) acc += ta[threadIdx.y][t] * tb[t][threadIdx.x];
-    __syncthreads();
-  }
-  if (a < n && b < n) Ainv[(size_t)a * n + b] = acc;
 }
 
 // ---------------------------------------------------------------- FGMRES (FP64)
@@ -361,26 +331,16 @@ cudaError_t launch_coarse_solve(int nn, int ncomp, const int* map, int nfree_nod
   return cudaGetLastError();
 }
 
-cudaError_t launch_dense_inverse(double* M, int n, int pin_first, double* Y, double* Ainv, int* flag, cudaStream_t st) {
-  cudaError_t e;
+cudaError_t launch_dense_inverse(double* M, int n, int pin_first, double* piv, double* Ainv, int* flag,
+                                 cudaStream_t st) {
   if (pin_first) wb_count_launch(), k_pin_first<<<nblk(n, 256), 256, 0, st>>>(M, n);
+  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
   for (int j = 0; j < n; ++j) {
-    const int m = n - j - 1;
-    dim3 blk(16, 16), grd(m > 0 ? (m + 15) / 16 : 1, m > 0 ? (m + 15) / 16 : 1);
-    wb_count_launch(), k_chol_update<<<grd, blk, 0, st>>>(M, n, j, flag);
+    wb_count_launch(), k_gj_update<<<grd, blk, 0, st>>>(M, n, j, piv, flag);
+    wb_count_launch(), k_gj_pivot<<<nblk(n, 256), 256, 0, st>>>(M, n, j, piv);
   }
-  {
-    dim3 blk(16, 16), grd((n + 15) / 16, (n + 15) / 16);
-    wb_count_launch(), k_chol_scale_offdiag<<<grd, blk, 0, st>>>(M, n);
-    wb_count_launch(), k_chol_scale_diag<<<nblk(n, 256), 256, 0, st>>>(M, n);
-  }
-  e = cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)n * n, st);
+  cudaError_t e = cudaMemcpyAsync(Ainv, M, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
-  wb_count_launch(), k_trinv_cols<<<nblk(n, 64), 64, 0, st>>>(M, n, Y);
-  {
-    dim3 blk(16, 16), grd((n + 15) / 16, (n + 15) / 16);
-    wb_count_launch(), k_ytY<<<grd, blk, 0, st>>>(Y, n, Ainv);
-  }
   return cudaGetLastError();
 }
 

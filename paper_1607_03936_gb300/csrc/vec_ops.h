@@ -44,9 +44,11 @@ template <typename T>
 cudaError_t launch_coarse_solve(int nn, int ncomp, const int* map, int nfree_nodes, int ndense, const double* Ainv,
                                 int neumann, const T* b, T* x, double* bf, double* xf, cudaStream_t st);
 
-// Dense SPD inverse: Cholesky of M in place (pin_first: row/col 0 replaced by the identity first),
-// Y = L^-1, Ainv = Y^T Y.  flag[0] != 0 afterwards if a pivot was not positive.
-cudaError_t launch_dense_inverse(double* M, int n, int pin_first, double* Y, double* Ainv, int* flag, cudaStream_t st);
+// Dense SPD inverse by in-place Gauss-Jordan on M (pin_first: row/col 0 replaced by the identity
+// first), copied to Ainv; piv: n doubles of workspace.  flag[0] != 0 afterwards if a pivot was not
+// positive (the matrix is not SPD).
+cudaError_t launch_dense_inverse(double* M, int n, int pin_first, double* piv, double* Ainv, int* flag,
+                                 cudaStream_t st);
 
 // FGMRES: out[c] = V[c] . w for c < ncols (deterministic); w -= V^T-weighted sum; x += Z y.
 cudaError_t launch_mdot(const double* V, long long ld, int ncols, const double* w, long long n, double* part,

@@ -75,7 +75,7 @@ struct Level {
   int nfree_nodes = 0, ndense = 0;
   double *Ainv = nullptr, *bf = nullptr, *xf = nullptr;
   // setup scratch kept for re-setup without allocation
-  double *pts64 = nullptr, *d64 = nullptr, *Md = nullptr, *Yd = nullptr;
+  double *pts64 = nullptr, *d64 = nullptr, *Md = nullptr, *Yd = nullptr;   // Yd: pivots
   T *coefT = nullptr, *pv = nullptr, *pw = nullptr;
 };
 
@@ -102,7 +102,19 @@ struct Precond {
 }  // namespace
 
 struct wbfbt_ctx {
-  cudaStream_t st = nullptr;
+  ~wbfbt_ctx() {
+    if (st) cudaStreamSynchronize(st);
+    if (pgraph) cudaGraphExecDestroy(pgraph);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (st) cudaStreamDestroy(st);
+  }
+  cudaStream_t st = nullptr;    // internal stream: every kernel of the context runs here
+  cudaStream_t ust = nullptr;   // the caller's stream, fenced against st at every entry point
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t pgraph = nullptr;   // captured preconditioner application (FGMRES hot loop)
+  bool graph_dirty = true;
+  long long graph_kernels = 0;
   int k = 2, N = 3, N3 = 27, NP = 4;
   Grid g;
   wbfbt_opts opt;
@@ -372,7 +384,7 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
         CK(cudaStreamSynchronize(c->st));   // hmap is a stack-local host buffer
       }
       c->pool.ensure(L.Md, (size_t)nd * nd);
-      c->pool.ensure(L.Yd, (size_t)nd * nd);
+      c->pool.ensure(L.Yd, (size_t)nd);
       c->pool.ensure(L.Ainv, (size_t)nd * nd);
       c->pool.ensure(L.bf, nd);
       c->pool.ensure(L.xf, nd);
@@ -409,10 +421,8 @@ void build_precond(wbfbt_ctx* c) {
   }
   for (T** q : {&P.pb, &P.px, &P.pr, &P.pd, &P.ptmp, &P.sr, &P.sy, &P.sz, &P.sy2}) c->pool.ensure(*q, np);
   for (T** q : {&P.vtmp, &P.sv1, &P.sv2, &P.urhs, &P.utmp}) c->pool.ensure(*q, nu);
-  if (!std::is_same<T, double>::value) {
-    c->pool.ensure(P.vin, c->ntot);
-    c->pool.ensure(P.vout, c->ntot);
-  }
+  c->pool.ensure(P.vin, c->ntot);
+  c->pool.ensure(P.vout, c->ntot);
   // A hierarchy: viscosity per node on the fine level
   build_hier<T>(c, P.HA, true, c->mu64, 1);
   // Poisson hierarchies: c = 1 / (a(e) sqrt(mu)) per point
@@ -468,6 +478,18 @@ int guarded(F f) {
   }
 }
 
+// Runs f on the context's internal stream, ordered after all prior work on the caller's stream,
+// and makes the caller's stream wait for it.
+template <class F>
+int guarded_ctx(wbfbt_ctx* c, F f) {
+  if (cudaEventRecord(c->ev_in, c->ust) != cudaSuccess || cudaStreamWaitEvent(c->st, c->ev_in, 0) != cudaSuccess)
+    return WBFBT_ERR_CUDA;
+  int r = guarded(f);
+  if (cudaEventRecord(c->ev_out, c->st) != cudaSuccess || cudaStreamWaitEvent(c->ust, c->ev_out, 0) != cudaSuccess)
+    return r != WBFBT_OK ? r : WBFBT_ERR_CUDA;
+  return r;
+}
+
 // ------------------------------------------------------------------ FGMRES
 
 void apply_K64(wbfbt_ctx* c, const double* x, double* y) {
@@ -476,8 +498,45 @@ void apply_K64(wbfbt_ctx* c, const double* x, double* y) {
                            c->st));
 }
 
+template <typename T>
+void precond_graphed(wbfbt_ctx* c, const double* v, double* z) {
+  Precond<T>& P = prec<T>(c);
+  if (c->pgraph == nullptr || c->graph_dirty) {
+    if (c->pgraph) {
+      cudaGraphExecDestroy(c->pgraph);
+      c->pgraph = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    const long long n0 = wb_launch_counter().load();
+    CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    try {
+      precond<T>(c, P.vin, P.vout);
+    } catch (...) {
+      cudaStreamEndCapture(c->st, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    CK(cudaStreamEndCapture(c->st, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&c->pgraph, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    c->graph_kernels = wb_launch_counter().load() - n0;
+    wb_launch_counter().fetch_sub(c->graph_kernels);   // captured, not run
+    c->graph_dirty = false;
+  }
+  CK((launch_cast<double, T>(c->ntot, v, P.vin, c->st)));
+  CK(cudaGraphLaunch(c->pgraph, c->st));
+  wb_launch_counter().fetch_add(c->graph_kernels);
+  CK((launch_cast<T, double>(c->ntot, P.vout, z, c->st)));
+}
+
 void precond_any(wbfbt_ctx* c, const double* v, double* z) {
-  if (!c->mixed) {
+  if (c->opt.use_graphs) {
+    if (c->mixed)
+      precond_graphed<float>(c, v, z);
+    else
+      precond_graphed<double>(c, v, z);
+  } else if (!c->mixed) {
     precond<double>(c, v, z);
   } else {
     CK((launch_cast<double, float>(c->ntot, v, c->P32.vin, c->st)));
@@ -610,6 +669,7 @@ void run_setup(wbfbt_ctx* cp, const double* mu_nodes) {
     build_precond<float>(cp);
   else
     build_precond<double>(cp);
+  cp->graph_dirty = true;   // Chebyshev coefficients are baked into the captured launches
 }
 
 }  // namespace
@@ -627,6 +687,7 @@ void wbfbt_default_opts(wbfbt_opts* o) {
   o->mg_min_n = 4;
   o->precision = WBFBT_F64;
   o->schur_sign = -1;
+  o->use_graphs = 1;
 }
 
 const char* wbfbt_status_string(int s) {
@@ -669,7 +730,11 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
       (c->opt.precision != WBFBT_F64 && c->opt.precision != WBFBT_MIXED) || c->opt.mg_min_n < 1)
     return WBFBT_ERR_INVALID;
   if (c->opt.schur_sign >= 0) c->opt.schur_sign = 1; else c->opt.schur_sign = -1;
-  c->st = (cudaStream_t)stream;
+  c->ust = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return WBFBT_ERR_CUDA;
   c->k = k;
   c->N = k + 1;
   c->N3 = c->N * c->N * c->N;
@@ -684,7 +749,7 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
   c->m = c->opt.restart;
   if (!build_ref_tables(k, &c->htab)) return WBFBT_ERR_INVALID;
   wbfbt_ctx* cp = c.get();
-  int status = guarded([&]() {
+  int status = guarded_ctx(cp, [&]() {
     const Grid& g = cp->g;
     const size_t nn = g.nn;
     cp->dtab = cp->pool.get<RefTables>(1);
@@ -722,12 +787,11 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
 
 int wbfbt_setup(wbfbt_ctx* c, const double* mu_nodes) {
   if (!c || !mu_nodes) return WBFBT_ERR_INVALID;
-  return guarded([&]() { run_setup(c, mu_nodes); });
+  return guarded_ctx(c, [&]() { run_setup(c, mu_nodes); });
 }
 
 void wbfbt_destroy(wbfbt_ctx* c) {
   if (!c) return;
-  cudaStreamSynchronize(c->st);
   delete c;
 }
 
@@ -746,7 +810,7 @@ long long wbfbt_launch_count(void) { return wb_launch_counter().load(); }
 
 static int stokes_apply(wbfbt_ctx* c, int ops, const void* u, const void* p, void* yu, void* yp, int dtype) {
   if (!c || (dtype != WBFBT_F64 && dtype != WBFBT_F32)) return WBFBT_ERR_INVALID;
-  return guarded([&]() {
+  return guarded_ctx(c, [&]() {
     if (dtype == WBFBT_F64)
       CK(launch_stokes<double>(c->g, c->k, c->dtab, ops, (const double*)u, nullptr, (const double*)p, c->mu64, 1,
                                (double*)yu, (double*)yp, c->st));
@@ -784,7 +848,7 @@ static bool prec_dtype_ok(wbfbt_ctx* c, int dtype) {
 
 int wbfbt_apply_Kw(wbfbt_ctx* c, int which, const void* p, void* y, int dtype) {
   if (!prec_dtype_ok(c, dtype) || !p || !y || (which != 0 && which != 1)) return WBFBT_ERR_INVALID;
-  return guarded([&]() {
+  return guarded_ctx(c, [&]() {
     if (dtype == WBFBT_F64) op_Kw<double>(c, which, (const double*)p, (double*)y);
     else op_Kw<float>(c, which, (const float*)p, (float*)y);
   });
@@ -792,7 +856,7 @@ int wbfbt_apply_Kw(wbfbt_ctx* c, int which, const void* p, void* y, int dtype) {
 
 int wbfbt_apply_Ainv(wbfbt_ctx* c, const void* r, void* y, int dtype) {
   if (!prec_dtype_ok(c, dtype) || !r || !y) return WBFBT_ERR_INVALID;
-  return guarded([&]() {
+  return guarded_ctx(c, [&]() {
     if (dtype == WBFBT_F64) vcycle<double>(c, c->P64.HA, 0, (const double*)r, (double*)y);
     else vcycle<float>(c, c->P32.HA, 0, (const float*)r, (float*)y);
   });
@@ -800,7 +864,7 @@ int wbfbt_apply_Ainv(wbfbt_ctx* c, const void* r, void* y, int dtype) {
 
 int wbfbt_apply_Kinv(wbfbt_ctx* c, int which, const void* r, void* y, int dtype) {
   if (!prec_dtype_ok(c, dtype) || !r || !y || (which != 0 && which != 1)) return WBFBT_ERR_INVALID;
-  return guarded([&]() {
+  return guarded_ctx(c, [&]() {
     if (dtype == WBFBT_F64) kinv<double>(c, which, (const double*)r, (double*)y);
     else kinv<float>(c, which, (const float*)r, (float*)y);
   });
@@ -808,7 +872,7 @@ int wbfbt_apply_Kinv(wbfbt_ctx* c, int which, const void* r, void* y, int dtype)
 
 int wbfbt_apply_schur_inv(wbfbt_ctx* c, const void* r, void* y, int dtype) {
   if (!prec_dtype_ok(c, dtype) || !r || !y) return WBFBT_ERR_INVALID;
-  return guarded([&]() {
+  return guarded_ctx(c, [&]() {
     if (dtype == WBFBT_F64) schur_inv<double>(c, (const double*)r, (double*)y);
     else schur_inv<float>(c, (const float*)r, (float*)y);
   });
@@ -816,7 +880,7 @@ int wbfbt_apply_schur_inv(wbfbt_ctx* c, const void* r, void* y, int dtype) {
 
 int wbfbt_apply_precond(wbfbt_ctx* c, const void* x, void* y, int dtype) {
   if (!prec_dtype_ok(c, dtype) || !x || !y) return WBFBT_ERR_INVALID;
-  return guarded([&]() {
+  return guarded_ctx(c, [&]() {
     if (dtype == WBFBT_F64) precond<double>(c, (const double*)x, (double*)y);
     else precond<float>(c, (const float*)x, (float*)y);
   });
@@ -828,7 +892,7 @@ int wbfbt_solve(wbfbt_ctx* c, const double* f_nodes, double* u, double* p, doubl
   const bool dev_f = is_device_ptr(f_nodes), dev_u = is_device_ptr(u), dev_p = is_device_ptr(p);
   if (dev_f != dev_u || dev_u != dev_p) return WBFBT_ERR_INVALID;
   int status = WBFBT_OK;
-  int g = guarded([&]() {
+  int g = guarded_ctx(c, [&]() {
     const size_t nn = c->g.nn, nu = 3 * nn, np = (size_t)c->g.ne * c->NP;
     const double* fd = f_nodes;
     if (!dev_f) {

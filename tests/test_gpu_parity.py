@@ -221,3 +221,26 @@ def test_full_size_sampled_A_apply(wb):
     ref = op.sampled_apply_A(m, mu, u, nodes)
     err = np.abs(y[:, nodes].T - ref).max() / np.abs(ref).max()
     assert err < 1e-12
+
+
+def test_graph_replay_matches_direct_launches(wb):
+    """The CUDA-graph preconditioner replays exactly the launches of the direct path."""
+    m, mu, f, _ = problem(8, 8, 8, 2, dr=1e6, ns=8)
+    fg = T(f.T.ravel())
+    u1, p1, r1 = gpu_solver(wb, m, mu, use_graphs=True).solve(fg)
+    u2, p2, r2 = gpu_solver(wb, m, mu, use_graphs=False).solve(fg)
+    assert r1.iters == r2.iters
+    assert torch.equal(u1, u2) and torch.equal(p1, p2)
+
+
+def test_resetup_reuses_memory_and_matches_fresh_context(wb):
+    m, mu, f, _ = problem(8, 8, 8, 2, dr=1e4)
+    _, mu2, _, _ = problem(8, 8, 8, 2, dr=1e6, ns=8, seed=3)
+    s = gpu_solver(wb, m, mu)
+    before = s.device_bytes
+    s.setup(T(mu2))
+    assert s.device_bytes == before
+    u1, p1, r1 = s.solve(T(f.T.ravel()))
+    u2, p2, r2 = gpu_solver(wb, m, mu2).solve(T(f.T.ravel()))
+    assert r1.iters == r2.iters
+    assert torch.equal(u1, u2) and torch.equal(p1, p2)
