@@ -144,6 +144,28 @@ int wbfbt_sizes(const wbfbt_ctx* ctx, long long* n_nodes, long long* n_elem, int
 /* Total device bytes owned by the context. */
 long long wbfbt_device_bytes(const wbfbt_ctx* ctx);
 
+/* Allocation-free form of the weighted pressure-Poisson apply, without a context:
+ *   y = B C^-1 B^T p,  C = M~_u(w), w = a(e) sqrt(mu)  (a on boundary elements, 1 elsewhere).
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc -- code running under another framework's memory pool or
+ * allocator hooks, real-time or embedded hosts that forbid device allocation
+ * after start-up (it may synchronise the device and fragment memory), and
+ * library code that may only touch caller-provided buffers.  Its temporaries
+ * (C^-1 and the intermediate B^T p) live in a file-scope device array of
+ * 4 * WBFBT_NOALLOC_MAX_NODES doubles (16 MiB) that every GPU loading this
+ * library holds until the process exits; meshes with more than
+ * WBFBT_NOALLOC_MAX_NODES velocity nodes are rejected with WBFBT_ERR_INVALID.
+ * mu_nodes [nodes], p [E][Np], y [E][Np]: FP64 device pointers; y is overwritten.
+ * The first call on a device, with that device current, resolves the array's
+ * device address and fills the reference tables (a synchronous copy), so make
+ * that first call before any stream capture.  All calls on a device share the
+ * one array and leave their intermediates in it: calls that overlap on the GPU
+ * (different streams, or different host threads) race and must be serialised
+ * by the caller.  Returns 0 or a WBFBT_ERR_* code; never allocates. */
+#define WBFBT_NOALLOC_MAX_NODES (1 << 19)
+int wbfbt_apply_Kw_noalloc(const wbfbt_mesh* mesh, int k, const double* mu_nodes, double a,
+                           const double* p, double* y, void* stream);
+
 /* Number of CUDA kernels this library has launched in the process so far (all contexts). */
 long long wbfbt_launch_count(void);
 

@@ -23,7 +23,8 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "non-finite val
 SYMBOLS = ["wbfbt_default_opts", "wbfbt_sinker_setup", "wbfbt_create", "wbfbt_setup", "wbfbt_apply_A", "wbfbt_apply_B",
            "wbfbt_apply_BT", "wbfbt_apply_K", "wbfbt_apply_Kw", "wbfbt_apply_Ainv", "wbfbt_apply_Kinv",
            "wbfbt_apply_schur_inv", "wbfbt_apply_precond", "wbfbt_solve", "wbfbt_sizes", "wbfbt_device_bytes", "wbfbt_launch_count",
-           "wbfbt_destroy", "wbfbt_status_string"]
+           "wbfbt_destroy", "wbfbt_status_string", "wbfbt_apply_Kw_noalloc"]
+NOALLOC_MAX_NODES = 1 << 19
 
 
 class WbfbtError(RuntimeError):
@@ -72,6 +73,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.wbfbt_launch_count.restype = ctypes.c_longlong
     lib.wbfbt_destroy.argtypes = [vp]
     lib.wbfbt_destroy.restype = None
+    lib.wbfbt_apply_Kw_noalloc.argtypes = [ctypes.POINTER(Mesh), i, vp, d, vp, vp, vp]
     lib.wbfbt_status_string.argtypes = [i]
     lib.wbfbt_status_string.restype = ctypes.c_char_p
     return lib   # every other entry point returns int, ctypes' default
@@ -133,6 +135,20 @@ def sinker_setup(nx: int, k: int, centres, omega: float, delta: float, dr: float
 def launch_count() -> int:
     """Kernels launched by libwbfbt.so so far in this process."""
     return lib().wbfbt_launch_count()
+
+
+def apply_Kw_noalloc(nx: int, k: int, mu: torch.Tensor, a: float, p: torch.Tensor, y: torch.Tensor,
+                     ny: int | None = None, nz: int | None = None, lengths=(1.0, 1.0, 1.0)) -> torch.Tensor:
+    """y = B C^-1 B^T p without a context and without any device allocation (FP64 device tensors).
+
+    For callers that cannot allocate device memory; the temporaries live in a static device
+    array of the library (meshes up to NOALLOC_MAX_NODES velocity nodes).  Concurrent calls
+    on one device race on that array.
+    """
+    mesh = Mesh(nx, ny or nx, nz or nx, *lengths)
+    _check(lib().wbfbt_apply_Kw_noalloc(ctypes.byref(mesh), k, _ptr(mu), a, _ptr(p), _ptr(y), _stream()),
+           "wbfbt_apply_Kw_noalloc")
+    return y
 
 
 @dataclass
