@@ -1,0 +1,65 @@
+// Two-pass element operators with fused vector epilogues, and fused grid transfers.
+//
+// An operator apply y = M u runs as an element pass, which writes every element's
+// local output (its contribution to each of its n^3 nodes) to a scratch array Ye,
+// and a node pass, which sums the contributions of the (up to 8) elements around
+// each node in a fixed order -- deterministic, with no atomics and no colouring --
+// and hands the sum to an epilogue (store, Chebyshev step, residual update, ...).
+// Element-local outputs (B u, per element and pressure mode) take the epilogue
+// directly in the element pass.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+enum : int {
+  EPI_STORE = 0,       // y = v
+  EPI_CHEB_STEP = 1,   // r -= v; d = a d + bc dinv r; x += d
+  EPI_SUB = 2,         // r -= v
+  EPI_CHEB_INIT1 = 3,  // r = b - v; d = dinv r inv_theta; x += d
+  EPI_SCALE = 4,       // y = v * sc[node]            (nodal scale shared by the components)
+  EPI_DINV = 5,        // y = dinv * v
+  EPI_BMINUS = 6,      // y = b - v
+};
+
+template <typename T>
+struct Epi {
+  int mode = EPI_STORE;
+  T* y = nullptr;
+  T* r = nullptr;
+  T* d = nullptr;
+  T* x = nullptr;
+  const T* b = nullptr;
+  const T* dinv = nullptr;
+  const T* sc = nullptr;
+  T a = 0, bc = 0, inv_theta = 0;
+};
+
+// Element pass of the Stokes family (ops: OP_A | OP_BT | OP_B as in kernels.h).  Velocity
+// contributions go to Ye [ne][3][n^3]; the B output (if OP_B) goes through `pe` per (e, m).
+template <typename T>
+cudaError_t launch_elem_stokes(const Grid& g, int k, const RefTables* dtab, int ops, const T* u, const T* us,
+                               const T* p, const T* coef, int coef_nodal, T* Ye, const Epi<T>& pe, cudaStream_t st);
+
+// Element pass of the scalar Q_k Poisson operator: Ye [ne][n^3].
+template <typename T>
+cudaError_t launch_elem_poisson(const Grid& g, int k, const RefTables* dtab, const T* u, const T* coef, T* Ye,
+                                cudaStream_t st);
+
+// Node pass: v = sum of element contributions (0 on boundary nodes when mask_boundary), then the
+// epilogue on entry c * nn + node for each of ncomp components.
+template <typename T>
+cudaError_t launch_gather(const Grid& g, int k, int ncomp, int mask_boundary, const T* Ye, const Epi<T>& e,
+                          cudaStream_t st);
+
+// Fused transfers between coarse grid gc and its refinement, ncomp components.
+//   prolong : out_f (+)= P in_c in one pass (N^3 coarse values per fine node)
+//   restrict: out_c = P^T in_f in three separable passes, all components per launch
+//             (w1, w2: transfer_work_size(gc, k) * ncomp entries each)
+template <typename T>
+cudaError_t launch_prolong_fused(const Grid& gc, int k, const RefTables* dtab, int ncomp, const T* in_c, T* out_f,
+                                 int add, cudaStream_t st);
+template <typename T>
+cudaError_t launch_restrict_batched(const Grid& gc, int k, const RefTables* dtab, int ncomp, const T* in_f, T* out_c,
+                                    int mask_dirichlet, T* w1, T* w2, cudaStream_t st);

@@ -1,0 +1,404 @@
+// Two-pass element operators with fused epilogues and fused grid transfers (see fused.h).
+//
+// Element pass: one thread per element point, EPB elements per block; the element's
+// velocity tile is gathered into shared memory, the gradient is formed by 1-D
+// derivative sums along each axis (sum factorisation, n FMAs per entry), the
+// quadrature-weighted stress 2 mu W eps(u) - W p I is stored back, and the transposed
+// derivative sums give the element's contribution to each of its nodes (Sec. 1.2:
+// a(u,v) = int 2 mu eps(u):eps(v), b(v,q) = -int q div v).
+// Node pass: each node adds the contributions of its elements in the order
+// (ez, ey, ex) ascending, so results are bitwise reproducible.
+#include "elem_common.cuh"
+#include "fused.h"
+#include "kernels.h"
+
+namespace {
+
+using namespace wb;
+
+template <typename T>
+__device__ inline void epi_apply(const Epi<T>& E, size_t i, int node, T v) {
+  switch (E.mode) {
+    case EPI_STORE: E.y[i] = v; break;
+    case EPI_SCALE: E.y[i] = v * E.sc[node]; break;
+    case EPI_DINV: E.y[i] = E.dinv[i] * v; break;
+    case EPI_BMINUS: E.y[i] = E.b[i] - v; break;
+    case EPI_SUB: E.r[i] -= v; break;
+    case EPI_CHEB_INIT1: {
+      const T rv = E.b[i] - v;
+      const T dv = E.dinv[i] * rv * E.inv_theta;
+      E.r[i] = rv;
+      E.d[i] = dv;
+      E.x[i] += dv;
+    } break;
+    case EPI_CHEB_STEP: {
+      const T rv = E.r[i] - v;
+      const T dv = E.a * E.d[i] + E.bc * (E.dinv[i] * rv);
+      E.r[i] = rv;
+      E.d[i] = dv;
+      E.x[i] += dv;
+    } break;
+    default: break;
+  }
+}
+
+template <typename T, int N, int OPS>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_elem(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ u, const T* __restrict__ us,
+       const T* __restrict__ p, const T* __restrict__ coef, int coef_nodal, T* __restrict__ Ye, Epi<T> pe) {
+  constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, EPB = Cfg<N>::EPB, K = N - 1;
+  constexpr bool DA = OPS & OP_A, DBT = OPS & OP_BT, DB = OPS & OP_B;
+  constexpr bool SCAT = DA || DBT, GRAD = DA || DB;
+  constexpr int NS = DA ? 6 : 1;
+  __shared__ OpTab<T, N> st;
+  __shared__ T su[GRAD ? EPB : 1][3][N3];
+  __shared__ T sS[SCAT ? EPB : 1][NS][N3];
+  __shared__ T sdiv[DB ? EPB : 1][N3];
+  load_optab(st, tab, g, DB || DBT);
+
+  const int tid = threadIdx.x;
+  const int le = tid / N3, q = tid - le * N3;
+  const int i = q % N, j = (q / N) % N, l = q / (N * N);
+  const int e = blockIdx.x * EPB + le;
+  const bool act = e < g.ne;
+  int node = 0;
+  bool interior = false;
+  if (act) {
+    const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
+    const int ix = K * ex + i, iy = K * ey + j, iz = K * ez + l;
+    node = ix + g.NX * (iy + g.NY * iz);
+    interior = !on_boundary(g, ix, iy, iz);
+  }
+  T mu = 0, pq = 0;
+  if (act) {
+    if (GRAD) {
+      const T sc = (us != nullptr && interior) ? us[node] : T(1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) su[GRAD ? le : 0][c][q] = interior ? u[(size_t)c * g.nn + node] * sc : T(0);
+    }
+    if (DA) mu = coef_nodal ? coef[node] : coef[(size_t)e * N3 + q];
+  }
+  __syncthreads();
+  if (act && DBT) {
+#pragma unroll
+    for (int m = 0; m < NP; ++m) pq += st.Psi[q][m] * p[(size_t)e * NP + m];
+  }
+  if (act) {
+    const T Wq = st.W3[q];
+    if (DA) {
+      T G[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+          a0 += st.Ds[0][i][a] * su[GRAD ? le : 0][c][a + N * (j + N * l)];
+          a1 += st.Ds[1][j][a] * su[GRAD ? le : 0][c][i + N * (a + N * l)];
+          a2 += st.Ds[2][l][a] * su[GRAD ? le : 0][c][i + N * (j + N * a)];
+        }
+        G[c][0] = a0;
+        G[c][1] = a1;
+        G[c][2] = a2;
+      }
+      if (DB) sdiv[DB ? le : 0][q] = Wq * (G[0][0] + G[1][1] + G[2][2]);
+      const T f = Wq * T(2) * mu, hf = Wq * mu;
+      const T t = DBT ? Wq * pq : T(0);
+      T* S = &sS[SCAT ? le : 0][0][0];
+      S[0 * N3 + q] = f * G[0][0] - t;
+      S[(NS > 1 ? 1 : 0) * N3 + q] = f * G[1][1] - t;
+      S[(NS > 2 ? 2 : 0) * N3 + q] = f * G[2][2] - t;
+      S[(NS > 3 ? 3 : 0) * N3 + q] = hf * (G[0][1] + G[1][0]);
+      S[(NS > 4 ? 4 : 0) * N3 + q] = hf * (G[0][2] + G[2][0]);
+      S[(NS > 5 ? 5 : 0) * N3 + q] = hf * (G[1][2] + G[2][1]);
+    } else {
+      if (DB) {
+        T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+          a0 += st.Ds[0][i][a] * su[GRAD ? le : 0][0][a + N * (j + N * l)];
+          a1 += st.Ds[1][j][a] * su[GRAD ? le : 0][1][i + N * (a + N * l)];
+          a2 += st.Ds[2][l][a] * su[GRAD ? le : 0][2][i + N * (j + N * a)];
+        }
+        sdiv[DB ? le : 0][q] = Wq * (a0 + a1 + a2);
+      }
+      if (DBT) sS[SCAT ? le : 0][0][q] = -Wq * pq;
+    }
+  }
+  __syncthreads();
+  if (!act) return;
+  if (DB && q < NP) {
+    const int m = q;
+    T acc = 0;
+#pragma unroll
+    for (int qq = 0; qq < N3; ++qq) acc += st.Psi[qq][m] * sdiv[DB ? le : 0][qq];
+    epi_apply(pe, (size_t)e * NP + m, 0, -acc);
+  }
+  if (SCAT) {
+    const T* S = &sS[SCAT ? le : 0][0][0];
+    T* out = Ye + (size_t)e * 3 * N3 + q;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T acc = 0;
+      if (DA) {
+        const int i0 = sym_index(c, 0), i1 = sym_index(c, 1), i2 = sym_index(c, 2);
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+          acc += st.Ds[0][a][i] * S[i0 * N3 + a + N * (j + N * l)];
+          acc += st.Ds[1][a][j] * S[i1 * N3 + i + N * (a + N * l)];
+          acc += st.Ds[2][a][l] * S[i2 * N3 + i + N * (j + N * a)];
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+          const int qa = c == 0 ? a + N * (j + N * l) : (c == 1 ? i + N * (a + N * l) : i + N * (j + N * a));
+          const int qc = c == 0 ? i : (c == 1 ? j : l);
+          acc += st.Ds[c][a][qc] * S[qa];
+        }
+      }
+      out[c * N3] = acc;
+    }
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_elem_poisson(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ u, const T* __restrict__ coef,
+               T* __restrict__ Ye) {
+  constexpr int N3 = Cfg<N>::N3, EPB = Cfg<N>::EPB, K = N - 1;
+  __shared__ OpTab<T, N> st;
+  __shared__ T su[EPB][N3];
+  __shared__ T sF[EPB][3][N3];
+  load_optab(st, tab, g, false);
+  const int tid = threadIdx.x;
+  const int le = tid / N3, q = tid - le * N3;
+  const int i = q % N, j = (q / N) % N, l = q / (N * N);
+  const int e = blockIdx.x * EPB + le;
+  const bool act = e < g.ne;
+  if (act) {
+    const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
+    su[le][q] = u[(K * ex + i) + g.NX * ((K * ey + j) + g.NY * (K * ez + l))];
+  }
+  __syncthreads();
+  if (act) {
+    T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      a0 += st.Ds[0][i][a] * su[le][a + N * (j + N * l)];
+      a1 += st.Ds[1][j][a] * su[le][i + N * (a + N * l)];
+      a2 += st.Ds[2][l][a] * su[le][i + N * (j + N * a)];
+    }
+    const T f = st.W3[q] * coef[(size_t)e * N3 + q];
+    sF[le][0][q] = f * a0;
+    sF[le][1][q] = f * a1;
+    sF[le][2][q] = f * a2;
+  }
+  __syncthreads();
+  if (!act) return;
+  T acc = 0;
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    acc += st.Ds[0][a][i] * sF[le][0][a + N * (j + N * l)];
+    acc += st.Ds[1][a][j] * sF[le][1][i + N * (a + N * l)];
+    acc += st.Ds[2][a][l] * sF[le][2][i + N * (j + N * a)];
+  }
+  Ye[(size_t)e * N3 + q] = acc;
+}
+
+// Node pass: thread per node, sum over the elements containing it in (ez, ey, ex) order.
+template <typename T, int N, int NC>
+__global__ void k_gather(Grid g, int mask_boundary, const T* __restrict__ Ye, Epi<T> E) {
+  constexpr int N3 = Cfg<N>::N3, K = N - 1;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nn) return;
+  const int ix = n % g.NX, iy = (n / g.NX) % g.NY, iz = n / (g.NX * g.NY);
+  T v[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) v[c] = T(0);
+  if (!(mask_boundary && on_boundary(g, ix, iy, iz))) {
+    for_elements_of_node(g, K, ix, iy, iz, [&](int e, int, int, int, int a0, int a1, int a2) {
+      const T* src = Ye + (size_t)e * NC * N3 + (a0 + N * (a1 + N * a2));
+#pragma unroll
+      for (int c = 0; c < NC; ++c) v[c] += src[c * N3];
+    });
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) epi_apply(E, (size_t)c * g.nn + n, n, v[c]);
+}
+
+// Fine node value = sum over the N^3 coarse nodes of its coarse element of the tensor weights.
+template <typename T, int N>
+__global__ void k_prolong3d(Grid gc, const RefTables* __restrict__ tab, int ncomp, const T* __restrict__ in_c,
+                            T* __restrict__ out_f, int add) {
+  constexpr int K = N - 1;
+  const int NXf = 2 * K * gc.nx + 1, NYf = 2 * K * gc.ny + 1, NZf = 2 * K * gc.nz + 1;
+  const long long nf = (long long)NXf * NYf * NZf;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nf) return;
+  const int idx[3] = {(int)(t % NXf), (int)((t / NXf) % NYf), (int)(t / ((long long)NXf * NYf))};
+  const int nfe[3] = {2 * gc.nx, 2 * gc.ny, 2 * gc.nz};
+  double w[3][N];
+  int base[3];
+  for (int d = 0; d < 3; ++d) {
+    int ef = idx[d] / K;
+    if (ef > nfe[d] - 1) ef = nfe[d] - 1;
+    const int a = idx[d] - K * ef, s = ef % 2;
+    base[d] = K * (ef / 2);
+#pragma unroll
+    for (int b = 0; b < N; ++b) w[d][b] = tab->P1[s][a][b];
+  }
+  for (int c = 0; c < ncomp; ++c) {
+    const T* src = in_c + (size_t)c * gc.nn;
+    double acc = 0.0;
+#pragma unroll
+    for (int bz = 0; bz < N; ++bz) {
+      if (w[2][bz] == 0.0) continue;
+#pragma unroll
+      for (int by = 0; by < N; ++by) {
+        if (w[1][by] == 0.0) continue;
+        const double wzy = w[2][bz] * w[1][by];
+        const T* row = src + (size_t)(base[0]) + (size_t)gc.NX * ((base[1] + by) + (size_t)gc.NY * (base[2] + bz));
+#pragma unroll
+        for (int bx = 0; bx < N; ++bx) acc += wzy * w[0][bx] * (double)row[bx];
+      }
+    }
+    T* dst = out_f + (size_t)c * nf + t;
+    *dst = add ? T((double)*dst + acc) : T(acc);
+  }
+}
+
+// One axis of P^T for all components (grid.y = component); the last pass may zero boundary nodes.
+template <typename T>
+__global__ void k_rpass(const RefTables* __restrict__ tab, int K, int axis, int d0, int d1, int d2, int nc_el,
+                        long long in_stride, long long out_stride, const T* __restrict__ in, T* __restrict__ out,
+                        int mask_last) {
+  const int nfine = 2 * K * nc_el + 1, ncoarse = K * nc_el + 1;
+  int od[3] = {d0, d1, d2};
+  od[axis] = ncoarse;
+  const long long tot = (long long)od[0] * od[1] * od[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  int o[3];
+  o[0] = (int)(t % od[0]);
+  o[1] = (int)((t / od[0]) % od[1]);
+  o[2] = (int)(t / ((long long)od[0] * od[1]));
+  const T* src = in + blockIdx.y * in_stride;
+  T* dst = out + blockIdx.y * out_stride;
+  if (mask_last && (o[0] == 0 || o[1] == 0 || o[2] == 0 || o[0] == od[0] - 1 || o[1] == od[1] - 1 ||
+                    o[2] == od[2] - 1)) {
+    dst[t] = T(0);
+    return;
+  }
+  const int id[3] = {d0, d1, d2};
+  const int i_c = o[axis];
+  const int nf_el = 2 * nc_el;
+  int lo = 2 * i_c - 2 * K, hi = 2 * i_c + 2 * K;
+  if (lo < 0) lo = 0;
+  if (hi > nfine - 1) hi = nfine - 1;
+  long long stride = axis == 0 ? 1 : (axis == 1 ? id[0] : (long long)id[0] * id[1]);
+  int c3[3] = {o[0], o[1], o[2]};
+  c3[axis] = 0;
+  const long long base = (long long)c3[0] + (long long)id[0] * (c3[1] + (long long)id[1] * c3[2]);
+  double acc = 0.0;
+  for (int i_f = lo; i_f <= hi; ++i_f) {
+    int ef = i_f / K;
+    if (ef > nf_el - 1) ef = nf_el - 1;
+    const int a = i_f - K * ef, ec = ef / 2, s = ef % 2;
+    const int b = i_c - K * ec;
+    if (b < 0 || b > K) continue;
+    acc += tab->P1[s][a][b] * (double)src[base + i_f * stride];
+  }
+  dst[t] = T(acc);
+}
+
+inline unsigned nb(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <typename T, int N>
+cudaError_t run_elem(const Grid& g, const RefTables* tab, int ops, const T* u, const T* us, const T* p, const T* coef,
+                     int cn, T* Ye, const Epi<T>& pe, cudaStream_t st) {
+  constexpr int EPB = Cfg<N>::EPB, TH = Cfg<N>::THREADS;
+  const unsigned blocks = (unsigned)((g.ne + EPB - 1) / EPB);
+  switch (ops) {
+    case OP_A: wb_count_launch(), k_elem<T, N, OP_A><<<blocks, TH, 0, st>>>(g, tab, u, us, p, coef, cn, Ye, pe); break;
+    case OP_BT: wb_count_launch(), k_elem<T, N, OP_BT><<<blocks, TH, 0, st>>>(g, tab, u, us, p, coef, cn, Ye, pe); break;
+    case OP_B: wb_count_launch(), k_elem<T, N, OP_B><<<blocks, TH, 0, st>>>(g, tab, u, us, p, coef, cn, Ye, pe); break;
+    case OP_A | OP_BT | OP_B:
+      wb_count_launch(), k_elem<T, N, OP_A | OP_BT | OP_B><<<blocks, TH, 0, st>>>(g, tab, u, us, p, coef, cn, Ye, pe);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define WB_FUSED_DISPATCH(k, CALL) \
+  switch (k) {                     \
+    case 2: { constexpr int N = 3; return CALL; } \
+    case 3: { constexpr int N = 4; return CALL; } \
+    case 4: { constexpr int N = 5; return CALL; } \
+    default: return cudaErrorInvalidValue; \
+  }
+
+template <typename T>
+cudaError_t launch_elem_stokes(const Grid& g, int k, const RefTables* dtab, int ops, const T* u, const T* us,
+                               const T* p, const T* coef, int cn, T* Ye, const Epi<T>& pe, cudaStream_t st) {
+  WB_FUSED_DISPATCH(k, (run_elem<T, N>(g, dtab, ops, u, us, p, coef, cn, Ye, pe, st)));
+}
+
+template <typename T>
+cudaError_t launch_elem_poisson(const Grid& g, int k, const RefTables* dtab, const T* u, const T* coef, T* Ye,
+                                cudaStream_t st) {
+  WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_elem_poisson<T, N><<<(unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB),
+                                                                Cfg<N>::THREADS, 0, st>>>(g, dtab, u, coef, Ye)),
+                        cudaGetLastError()));
+}
+
+template <typename T>
+cudaError_t launch_gather(const Grid& g, int k, int ncomp, int mask, const T* Ye, const Epi<T>& e, cudaStream_t st) {
+  if (ncomp == 3) {
+    WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_gather<T, N, 3><<<nb(g.nn, 128), 128, 0, st>>>(g, mask, Ye, e)),
+                          cudaGetLastError()));
+  }
+  if (ncomp == 1) {
+    WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_gather<T, N, 1><<<nb(g.nn, 128), 128, 0, st>>>(g, mask, Ye, e)),
+                          cudaGetLastError()));
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_prolong_fused(const Grid& gc, int k, const RefTables* dtab, int ncomp, const T* in_c, T* out_f,
+                                 int add, cudaStream_t st) {
+  const long long nf = (long long)(2 * k * gc.nx + 1) * (2 * k * gc.ny + 1) * (2 * k * gc.nz + 1);
+  WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_prolong3d<T, N><<<nb(nf, 128), 128, 0, st>>>(gc, dtab, ncomp, in_c,
+                                                                                            out_f, add)),
+                        cudaGetLastError()));
+}
+
+template <typename T>
+cudaError_t launch_restrict_batched(const Grid& gc, int k, const RefTables* dtab, int ncomp, const T* in_f, T* out_c,
+                                    int mask, T* w1, T* w2, cudaStream_t st) {
+  const int ncx = gc.NX, ncy = gc.NY, ncz = gc.NZ;
+  const int nfx = 2 * k * gc.nx + 1, nfy = 2 * k * gc.ny + 1, nfz = 2 * k * gc.nz + 1;
+  const long long nf = (long long)nfx * nfy * nfz, n1 = (long long)ncx * nfy * nfz, n2 = (long long)ncx * ncy * nfz;
+  const long long nc = (long long)ncx * ncy * ncz;
+  const int bs = 256;
+  wb_count_launch(), k_rpass<T><<<dim3(nb(n1, bs), ncomp), bs, 0, st>>>(dtab, k, 0, nfx, nfy, nfz, gc.nx, nf, n1, in_f, w1, 0);
+  wb_count_launch(), k_rpass<T><<<dim3(nb(n2, bs), ncomp), bs, 0, st>>>(dtab, k, 1, ncx, nfy, nfz, gc.ny, n1, n2, w1, w2, 0);
+  wb_count_launch(), k_rpass<T><<<dim3(nb(nc, bs), ncomp), bs, 0, st>>>(dtab, k, 2, ncx, ncy, nfz, gc.nz, n2, nc, w2, out_c,
+                                                                        mask);
+  return cudaGetLastError();
+}
+
+#define WB_FUSED_INST(T)                                                                                              \
+  template cudaError_t launch_elem_stokes<T>(const Grid&, int, const RefTables*, int, const T*, const T*, const T*,   \
+                                             const T*, int, T*, const Epi<T>&, cudaStream_t);                         \
+  template cudaError_t launch_elem_poisson<T>(const Grid&, int, const RefTables*, const T*, const T*, T*,             \
+                                              cudaStream_t);                                                          \
+  template cudaError_t launch_gather<T>(const Grid&, int, int, int, const T*, const Epi<T>&, cudaStream_t);           \
+  template cudaError_t launch_prolong_fused<T>(const Grid&, int, const RefTables*, int, const T*, T*, int,            \
+                                               cudaStream_t);                                                         \
+  template cudaError_t launch_restrict_batched<T>(const Grid&, int, const RefTables*, int, const T*, T*, int, T*, T*, \
+                                                  cudaStream_t);
+WB_FUSED_INST(double)
+WB_FUSED_INST(float)

@@ -15,6 +15,7 @@
 #include <memory>
 #include <vector>
 
+#include "fused.h"
 #include "kernels.h"
 #include "vec_ops.h"
 #include "wbfbt.h"
@@ -96,6 +97,7 @@ struct Precond {
   T *sr = nullptr, *sy = nullptr, *sz = nullptr, *sy2 = nullptr, *sv1 = nullptr, *sv2 = nullptr;
   T *urhs = nullptr, *utmp = nullptr;                   // Schur / block workspaces
   T *vin = nullptr, *vout = nullptr;                    // mixed-precision Krylov <-> preconditioner
+  T* Ye = nullptr;                                      // element-pass outputs [ne][3][n^3] (finest level)
   double *c0[2] = {nullptr, nullptr}, *dK64[2] = {nullptr, nullptr};
 };
 
@@ -136,6 +138,8 @@ struct wbfbt_ctx {
   int m = 50;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *x = nullptr, *r = nullptr, *F = nullptr, *hdev = nullptr;
   double *stage_f = nullptr, *stage_u = nullptr, *stage_p = nullptr;
+  double* Ye64 = nullptr;   // element-pass scratch for the FP64 applies
+  float* Ye32 = nullptr;    // element-pass scratch for the FP32 applies
 };
 
 namespace {
@@ -161,59 +165,86 @@ double norm(wbfbt_ctx* c, const T* v, long long n) {
 }
 
 // ------------------------------------------------------------------ operators in precision T
+//
+// Every operator below takes an epilogue: the value M u is never stored on its own but handed to
+// a fused update (store, Chebyshev step, residual update, Jacobi scaling) in the node pass.
 
 template <typename T>
-void op_A(wbfbt_ctx* c, const Level<T>& L, const T* u, T* y) {
-  CK(launch_stokes<T>(L.g, c->k, c->dtab, OP_A, u, nullptr, nullptr, L.coef, L.coef_nodal, y, nullptr, c->st));
+Epi<T> epi_store(T* y) {
+  Epi<T> e;
+  e.mode = EPI_STORE;
+  e.y = y;
+  return e;
 }
 
 template <typename T>
-void op_L(wbfbt_ctx* c, const Level<T>& L, const T* u, T* y) {
-  CK(launch_poisson<T>(L.g, c->k, c->dtab, u, L.coef, y, c->st));
+Epi<T> epi_scale(T* y, const T* sc) {
+  Epi<T> e;
+  e.mode = EPI_SCALE;
+  e.y = y;
+  e.sc = sc;
+  return e;
 }
 
-// y = B C_w^-1 B^T p  (which: 0 -> C (w_l), 1 -> D (w_r))
+// Level operator (A for the vector hierarchy, L_c for the scalar ones) with epilogue.
 template <typename T>
-void op_Kw(wbfbt_ctx* c, int which, const T* p, T* y) {
+void level_apply(wbfbt_ctx* c, const Hier<T>& H, const Level<T>& L, const T* u, const Epi<T>& e) {
+  T* Ye = prec<T>(c).Ye;
+  if (H.vec)
+    CK(launch_elem_stokes<T>(L.g, c->k, c->dtab, OP_A, u, nullptr, nullptr, L.coef, L.coef_nodal, Ye, Epi<T>(),
+                             c->st));
+  else
+    CK(launch_elem_poisson<T>(L.g, c->k, c->dtab, u, L.coef, Ye, c->st));
+  CK(launch_gather<T>(L.g, c->k, H.ncomp, H.vec ? 1 : 0, Ye, e, c->st));
+}
+
+// K_w p = B C_w^-1 B^T p with epilogue on the pressure output (which: 0 -> C (w_l), 1 -> D (w_r)).
+template <typename T>
+void op_Kw(wbfbt_ctx* c, int which, const T* p, const Epi<T>& e) {
   Precond<T>& P = prec<T>(c);
   const T* winv = which == 0 ? P.cinv : P.dinvw;
-  CK(launch_stokes<T>(c->g, c->k, c->dtab, OP_BT, nullptr, nullptr, p, nullptr, 0, P.vtmp, nullptr, c->st));
-  CK(launch_stokes<T>(c->g, c->k, c->dtab, OP_B, P.vtmp, winv, nullptr, nullptr, 0, nullptr, y, c->st));
+  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, OP_BT, nullptr, nullptr, p, nullptr, 0, P.Ye, Epi<T>(), c->st));
+  CK(launch_gather<T>(c->g, c->k, 3, 1, P.Ye, epi_scale<T>(P.vtmp, winv), c->st));
+  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, OP_B, P.vtmp, nullptr, nullptr, nullptr, 0, nullptr, e, c->st));
 }
 
+// Chebyshev-Jacobi (Saad, Alg. 12.1) over [0.1, 1.1] lambda_hat; M(src, epi) applies the operator
+// to src and feeds the result to the epilogue.
 template <typename T, class Op>
 void chebyshev(wbfbt_ctx* c, Op M, long long n, const T* dinv, double lam, const T* b, T* x, bool zero_guess,
-               bool want_res, T* r, T* d, T* tmp) {
+               bool want_res, T* r, T* d) {
   const double lmin = CHEB_LO * lam, lmax = CHEB_HI * lam;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
   const int steps = c->opt.cheb_degree;
+  Epi<T> e;
+  e.r = r;
+  e.d = d;
+  e.x = x;
+  e.b = b;
+  e.dinv = dinv;
+  e.inv_theta = T(1.0 / theta);
   if (zero_guess) {
     CK(launch_cheb_init0<T>(n, b, dinv, T(1.0 / theta), r, d, x, c->st));
   } else {
-    M(x, tmp);
-    CK(launch_cheb_init1<T>(n, b, tmp, dinv, T(1.0 / theta), r, d, x, c->st));
+    e.mode = EPI_CHEB_INIT1;
+    M(x, e);
   }
   for (int s = 0; s < steps; ++s) {
     if (s == steps - 1 && !want_res) break;
-    M(d, tmp);
     if (s == steps - 1) {
-      CK(launch_sub<T>(n, tmp, r, c->st));
+      e.mode = EPI_SUB;
+      M(d, e);
       break;
     }
     const double rho_new = 1.0 / (2.0 * sigma - rho);
-    CK(launch_cheb_step<T>(n, tmp, dinv, T(rho_new * rho), T(2.0 * rho_new / delta), r, d, x, c->st));
+    e.mode = EPI_CHEB_STEP;
+    e.a = T(rho_new * rho);
+    e.bc = T(2.0 * rho_new / delta);
+    M(d, e);
     rho = rho_new;
   }
-}
-
-template <typename T>
-void level_apply(wbfbt_ctx* c, const Hier<T>& H, const Level<T>& L, const T* u, T* y) {
-  if (H.vec)
-    op_A<T>(c, L, u, y);
-  else
-    op_L<T>(c, L, u, y);
 }
 
 template <typename T>
@@ -225,13 +256,13 @@ void vcycle(wbfbt_ctx* c, Hier<T>& H, int l, const T* b, T* x) {
     return;
   }
   const long long n = (long long)H.ncomp * L.g.nn;
-  auto M = [&](const T* u, T* y) { level_apply<T>(c, H, L, u, y); };
-  chebyshev<T>(c, M, n, L.dinv, L.lam, b, x, true, true, L.r, L.d, L.tmp);
+  auto M = [&](const T* u, const Epi<T>& e) { level_apply<T>(c, H, L, u, e); };
+  chebyshev<T>(c, M, n, L.dinv, L.lam, b, x, true, true, L.r, L.d);
   Level<T>& Lc = H.lv[l + 1];
-  CK(launch_restrict<T>(Lc.g, c->k, c->dtab, H.ncomp, L.r, Lc.b, H.vec ? 1 : 0, L.w1, L.w2, c->st));
+  CK(launch_restrict_batched<T>(Lc.g, c->k, c->dtab, H.ncomp, L.r, Lc.b, H.vec ? 1 : 0, L.w1, L.w2, c->st));
   vcycle<T>(c, H, l + 1, Lc.b, Lc.x);
-  CK(launch_prolong<T>(Lc.g, c->k, c->dtab, H.ncomp, Lc.x, x, 1, L.w1, L.w2, c->st));
-  chebyshev<T>(c, M, n, L.dinv, L.lam, b, x, false, false, L.r, L.d, L.tmp);
+  CK(launch_prolong_fused<T>(Lc.g, c->k, c->dtab, H.ncomp, Lc.x, x, 1, c->st));
+  chebyshev<T>(c, M, n, L.dinv, L.lam, b, x, false, false, L.r, L.d);
 }
 
 // Two-space pressure-Poisson V-cycle for K_w (Sec. 6): disc smoothing, Q_k correction, disc smoothing.
@@ -239,13 +270,13 @@ template <typename T>
 void kinv(wbfbt_ctx* c, int which, const T* bd, T* xd) {
   Precond<T>& P = prec<T>(c);
   const long long n = (long long)c->g.ne * c->NP;
-  auto M = [&](const T* p, T* y) { op_Kw<T>(c, which, p, y); };
-  chebyshev<T>(c, M, n, P.dKw[which], P.lamKw[which], bd, xd, true, true, P.pr, P.pd, P.ptmp);
+  auto M = [&](const T* p, const Epi<T>& e) { op_Kw<T>(c, which, p, e); };
+  chebyshev<T>(c, M, n, P.dKw[which], P.lamKw[which], bd, xd, true, true, P.pr, P.pd);
   Level<T>& L0 = P.HL[which].lv[0];
   CK(launch_disc_to_cont<T>(c->g, c->k, c->dtab, P.pr, L0.b, c->st));
   vcycle<T>(c, P.HL[which], 0, L0.b, L0.x);
   CK(launch_cont_to_disc<T>(c->g, c->k, c->dtab, L0.x, xd, 1, c->st));
-  chebyshev<T>(c, M, n, P.dKw[which], P.lamKw[which], bd, xd, false, false, P.pr, P.pd, P.ptmp);
+  chebyshev<T>(c, M, n, P.dKw[which], P.lamKw[which], bd, xd, false, false, P.pr, P.pd);
 }
 
 template <typename T>
@@ -259,9 +290,13 @@ void schur_inv(wbfbt_ctx* c, const T* r, T* y) {
   Precond<T>& P = prec<T>(c);
   project<T>(c, r, P.sr);
   kinv<T>(c, 1, P.sr, P.sy);
-  CK(launch_stokes<T>(c->g, c->k, c->dtab, OP_BT, nullptr, nullptr, P.sy, nullptr, 0, P.sv1, nullptr, c->st));
-  CK(launch_stokes<T>(c->g, c->k, c->dtab, OP_A, P.sv1, P.dinvw, nullptr, P.mu, 1, P.sv2, nullptr, c->st));
-  CK(launch_stokes<T>(c->g, c->k, c->dtab, OP_B, P.sv2, P.cinv, nullptr, nullptr, 0, nullptr, P.sz, c->st));
+  // middle factor B C^-1 A D^-1 B^T y, each diagonal scaling fused into the preceding node pass
+  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, OP_BT, nullptr, nullptr, P.sy, nullptr, 0, P.Ye, Epi<T>(), c->st));
+  CK(launch_gather<T>(c->g, c->k, 3, 1, P.Ye, epi_scale<T>(P.sv1, P.dinvw), c->st));
+  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, OP_A, P.sv1, nullptr, nullptr, P.mu, 1, P.Ye, Epi<T>(), c->st));
+  CK(launch_gather<T>(c->g, c->k, 3, 1, P.Ye, epi_scale<T>(P.sv2, P.cinv), c->st));
+  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, OP_B, P.sv2, nullptr, nullptr, nullptr, 0, nullptr,
+                           epi_store<T>(P.sz), c->st));
   kinv<T>(c, 0, P.sz, P.sy2);
   project<T>(c, P.sy2, y);
 }
@@ -277,23 +312,31 @@ void precond(wbfbt_ctx* c, const T* x, T* y) {
   T* yp = y + nu;
   schur_inv<T>(c, xp, yp);
   if (c->opt.schur_sign < 0) CK(launch_scale<T>((long long)c->g.ne * c->NP, T(-1), yp, yp, c->st));
-  CK(launch_stokes<T>(c->g, c->k, c->dtab, OP_BT, nullptr, nullptr, yp, nullptr, 0, P.utmp, nullptr, c->st));
-  CK(launch_axpby<T>(nu, T(1), xu, T(-1), P.utmp, P.urhs, c->st));
+  // r_u - B^T y_p in one element pass + node pass
+  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, OP_BT, nullptr, nullptr, yp, nullptr, 0, P.Ye, Epi<T>(), c->st));
+  Epi<T> e;
+  e.mode = EPI_BMINUS;
+  e.y = P.urhs;
+  e.b = xu;
+  CK(launch_gather<T>(c->g, c->k, 3, 1, P.Ye, e, c->st));
   vcycle<T>(c, P.HA, 0, P.urhs, yu);
 }
 
 // ------------------------------------------------------------------ setup
 
 template <typename T, class Op>
-double power_lambda(wbfbt_ctx* c, Op M, long long n, const T* dinv, T* v, T* w, T* tmp, const Grid* mask_grid) {
+double power_lambda(wbfbt_ctx* c, Op M, long long n, const T* dinv, T* v, T* w, const Grid* mask_grid) {
   CK(launch_splitmix_start<T>(n, START_SEED, v, c->st));
   if (mask_grid) CK(launch_mask_boundary<T>(*mask_grid, 3, v, c->st));
   double nv = norm<T>(c, v, n);
   CK(launch_scale<T>(n, T(1.0 / nv), v, v, c->st));
   double lam = 0.0;
   for (int it = 0; it < POWER_ITERS; ++it) {
-    M(v, tmp);
-    CK(launch_mul<T>(n, dinv, tmp, w, c->st));
+    Epi<T> e;
+    e.mode = EPI_DINV;
+    e.y = w;
+    e.dinv = dinv;
+    M(v, e);
     lam = norm<T>(c, w, n);
     if (!(lam > 0.0) || !std::isfinite(lam)) throw WbErr{WBFBT_ERR_SETUP};
     CK(launch_scale<T>(n, T(1.0 / lam), w, v, c->st));
@@ -363,8 +406,8 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
       c->pool.ensure(L.w2, ws);
       c->pool.ensure(L.pv, nv);
       c->pool.ensure(L.pw, nv);
-      auto M = [&](const T* u, T* y) { level_apply<T>(c, H, L, u, y); };
-      L.lam = power_lambda<T>(c, M, (long long)nv, L.dinv, L.pv, L.pw, L.tmp, vec ? &L.g : nullptr);
+      auto M = [&](const T* u, const Epi<T>& e) { level_apply<T>(c, H, L, u, e); };
+      L.lam = power_lambda<T>(c, M, (long long)nv, L.dinv, L.pv, L.pw, vec ? &L.g : nullptr);
       g = gc;
     } else {
       // coarsest: dense FP64 matrix over the free DOFs, explicit inverse
@@ -423,6 +466,7 @@ void build_precond(wbfbt_ctx* c) {
   for (T** q : {&P.vtmp, &P.sv1, &P.sv2, &P.urhs, &P.utmp}) c->pool.ensure(*q, nu);
   c->pool.ensure(P.vin, c->ntot);
   c->pool.ensure(P.vout, c->ntot);
+  c->pool.ensure(P.Ye, (size_t)3 * g.ne * c->N3);
   // A hierarchy: viscosity per node on the fine level
   build_hier<T>(c, P.HA, true, c->mu64, 1);
   // Poisson hierarchies: c = 1 / (a(e) sqrt(mu)) per point
@@ -436,8 +480,8 @@ void build_precond(wbfbt_ctx* c) {
     CK(launch_dinv_Kw<double>(g, c->k, c->dtab, wi == 0 ? c->cinv64 : c->dinv64, P.dK64[wi], c->st));
     c->pool.ensure(P.dKw[wi], np);
     CK((launch_cast<double, T>((long long)np, P.dK64[wi], P.dKw[wi], c->st)));
-    auto M = [&](const T* p, T* y) { op_Kw<T>(c, wi, p, y); };
-    P.lamKw[wi] = power_lambda<T>(c, M, (long long)np, P.dKw[wi], P.px, P.pd, P.ptmp, nullptr);
+    auto M = [&](const T* p, const Epi<T>& e) { op_Kw<T>(c, wi, p, e); };
+    P.lamKw[wi] = power_lambda<T>(c, M, (long long)np, P.dKw[wi], P.px, P.pd, nullptr);
   }
 }
 
@@ -494,8 +538,9 @@ int guarded_ctx(wbfbt_ctx* c, F f) {
 
 void apply_K64(wbfbt_ctx* c, const double* x, double* y) {
   const long long nu = 3LL * c->g.nn;
-  CK(launch_stokes<double>(c->g, c->k, c->dtab, OP_A | OP_BT | OP_B, x, nullptr, x + nu, c->mu64, 1, y, y + nu,
-                           c->st));
+  CK(launch_elem_stokes<double>(c->g, c->k, c->dtab, OP_A | OP_BT | OP_B, x, nullptr, x + nu, c->mu64, 1, c->Ye64,
+                                epi_store<double>(y + nu), c->st));
+  CK(launch_gather<double>(c->g, c->k, 3, 1, c->Ye64, epi_store<double>(y), c->st));
 }
 
 template <typename T>
@@ -674,6 +719,17 @@ void run_setup(wbfbt_ctx* cp, const double* mu_nodes) {
 
 }  // namespace
 
+namespace {
+
+template <typename T>
+void stokes_apply_t(wbfbt_ctx* c, int ops, const T* u, const T* p, T* yu, T* yp, const T* mu, T* Ye) {
+  const bool scat = (ops & OP_A) || (ops & OP_BT);
+  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, ops, u, nullptr, p, mu, 1, Ye, epi_store<T>(yp), c->st));
+  if (scat) CK(launch_gather<T>(c->g, c->k, 3, 1, Ye, epi_store<T>(yu), c->st));
+}
+
+}  // namespace
+
 // ================================================================== C ABI
 
 extern "C" {
@@ -765,6 +821,8 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
     cp->cinv64 = cp->pool.get<double>(nn);
     cp->dinv64 = cp->pool.get<double>(nn);
     cp->ntot = 3LL * nn + (long long)g.ne * cp->NP;
+    cp->Ye64 = cp->pool.get<double>((size_t)3 * g.ne * cp->N3);
+    cp->Ye32 = cp->pool.get<float>((size_t)3 * g.ne * cp->N3);
     CK(launch_lumped_mass(g, cp->k, cp->dtab, cp->lm, cp->st));
     run_setup(cp, mu_nodes);
     const long long n = cp->ntot;
@@ -812,11 +870,9 @@ static int stokes_apply(wbfbt_ctx* c, int ops, const void* u, const void* p, voi
   if (!c || (dtype != WBFBT_F64 && dtype != WBFBT_F32)) return WBFBT_ERR_INVALID;
   return guarded_ctx(c, [&]() {
     if (dtype == WBFBT_F64)
-      CK(launch_stokes<double>(c->g, c->k, c->dtab, ops, (const double*)u, nullptr, (const double*)p, c->mu64, 1,
-                               (double*)yu, (double*)yp, c->st));
+      stokes_apply_t<double>(c, ops, (const double*)u, (const double*)p, (double*)yu, (double*)yp, c->mu64, c->Ye64);
     else
-      CK(launch_stokes<float>(c->g, c->k, c->dtab, ops, (const float*)u, nullptr, (const float*)p, c->mu32, 1,
-                              (float*)yu, (float*)yp, c->st));
+      stokes_apply_t<float>(c, ops, (const float*)u, (const float*)p, (float*)yu, (float*)yp, c->mu32, c->Ye32);
   });
 }
 
@@ -849,8 +905,8 @@ static bool prec_dtype_ok(wbfbt_ctx* c, int dtype) {
 int wbfbt_apply_Kw(wbfbt_ctx* c, int which, const void* p, void* y, int dtype) {
   if (!prec_dtype_ok(c, dtype) || !p || !y || (which != 0 && which != 1)) return WBFBT_ERR_INVALID;
   return guarded_ctx(c, [&]() {
-    if (dtype == WBFBT_F64) op_Kw<double>(c, which, (const double*)p, (double*)y);
-    else op_Kw<float>(c, which, (const float*)p, (float*)y);
+    if (dtype == WBFBT_F64) op_Kw<double>(c, which, (const double*)p, epi_store<double>((double*)y));
+    else op_Kw<float>(c, which, (const float*)p, epi_store<float>((float*)y));
   });
 }
 
