@@ -402,8 +402,8 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
       CK((launch_cast<double, T>((long long)nv, L.d64, L.dinv, c->st)));
       Grid gc = coarser(g, c->k);
       size_t ws = transfer_work_size(gc, c->k);
-      c->pool.ensure(L.w1, ws);
-      c->pool.ensure(L.w2, ws);
+      c->pool.ensure(L.w1, ws * H.ncomp);   // restriction passes run all components at once
+      c->pool.ensure(L.w2, ws * H.ncomp);
       c->pool.ensure(L.pv, nv);
       c->pool.ensure(L.pw, nv);
       auto M = [&](const T* u, const Epi<T>& e) { level_apply<T>(c, H, L, u, e); };
