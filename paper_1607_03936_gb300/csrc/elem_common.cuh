@@ -44,29 +44,47 @@ __device__ inline int sym_index(int c, int d) {
 }
 
 // Operator tables in shared memory for the hot kernels: derivative matrices pre-scaled by
-// 2/h per axis, tensor quadrature weights times |J|, and the pressure basis at the points,
-// so that the per-point work is only the sum-factorisation FMAs and the pointwise physics.
+// 2/h per axis, tensor quadrature weights (with and without |J|), the pressure basis at the
+// points, the inverse reference pressure mass and the per-child 1-D interpolation weights.
+// Built once per level on the host (make_optab) in the kernel's precision, so blocks only copy
+// them into shared memory: no per-block arithmetic, and no FP64 arithmetic in FP32 kernels.
 template <typename T, int N>
 struct OpTab {
   T Ds[3][N][N];             // Ds[d][i][a] = (2 / h_d) l_a'(x_i)
   T W3[Cfg<N>::N3];          // W_q |J|
+  T Wref[Cfg<N>::N3];        // W_q (reference element)
   T Psi[Cfg<N>::N3][Cfg<N>::NP];
+  T Minv[Cfg<N>::NP][Cfg<N>::NP];
+  T P1[2][N][N];             // P1[s][a][b] = l_b((x_a + 2s - 1) / 2)
 };
 
 template <typename T, int N>
-__device__ inline void load_optab(OpTab<T, N>& s, const RefTables* __restrict__ tab, const Grid& g, bool need_psi) {
+inline void make_optab(const RefTables& t, const Grid& g, OpTab<T, N>* o) {
   constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP;
-  for (int t = threadIdx.x; t < 3 * N * N; t += blockDim.x) {
-    const int d = t / (N * N), r = t % (N * N);
-    s.Ds[d][r / N][r % N] = T(g.s[d] * tab->D[r / N][r % N]);
-  }
-  for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+  for (int d = 0; d < 3; ++d)
+    for (int i = 0; i < N; ++i)
+      for (int a = 0; a < N; ++a) o->Ds[d][i][a] = T(g.s[d] * t.D[i][a]);
+  for (int q = 0; q < N3; ++q) {
     const int i = q % N, j = (q / N) % N, l = q / (N * N);
-    s.W3[q] = T(tab->w[i] * tab->w[j] * tab->w[l] * g.detJ);
-    if (need_psi)
-      for (int m = 0; m < NP; ++m)
-        s.Psi[q][m] = T(tab->pw[i][tab->ex[m][0]] * tab->pw[j][tab->ex[m][1]] * tab->pw[l][tab->ex[m][2]]);
+    const double w = t.w[i] * t.w[j] * t.w[l];
+    o->W3[q] = T(w * g.detJ);
+    o->Wref[q] = T(w);
+    for (int m = 0; m < NP; ++m) o->Psi[q][m] = T(t.pw[i][t.ex[m][0]] * t.pw[j][t.ex[m][1]] * t.pw[l][t.ex[m][2]]);
   }
+  for (int m = 0; m < NP; ++m)
+    for (int mp = 0; mp < NP; ++mp) o->Minv[m][mp] = T(t.minv[m][mp]);
+  for (int s2 = 0; s2 < 2; ++s2)
+    for (int a = 0; a < N; ++a)
+      for (int b = 0; b < N; ++b) o->P1[s2][a][b] = T(t.P1[s2][a][b]);
+}
+
+// Block-wide copy of a table from global memory into shared memory (32-bit words).
+template <typename Tab>
+__device__ inline void copy_tab(Tab& dst, const Tab* __restrict__ src) {
+  static_assert(sizeof(Tab) % 4 == 0, "table size must be a multiple of 4 bytes");
+  const unsigned* s = reinterpret_cast<const unsigned*>(src);
+  unsigned* d = reinterpret_cast<unsigned*>(&dst);
+  for (int t = threadIdx.x; t < (int)(sizeof(Tab) / 4); t += blockDim.x) d[t] = s[t];
 }
 
 // Calls f(e, ex, ey, ez, a0, a1, a2) for every element containing node (ix, iy, iz), in a fixed order.

@@ -17,6 +17,23 @@ namespace {
 
 using namespace wb;
 
+// Colour-scatter kernels (used by the allocation-free entry point) build their tables in the block.
+template <typename T, int N>
+__device__ inline void load_optab(OpTab<T, N>& s, const RefTables* __restrict__ tab, const Grid& g, bool need_psi) {
+  constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP;
+  for (int t = threadIdx.x; t < 3 * N * N; t += blockDim.x) {
+    const int d = t / (N * N), r = t % (N * N);
+    s.Ds[d][r / N][r % N] = T(g.s[d] * tab->D[r / N][r % N]);
+  }
+  for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+    const int i = q % N, j = (q / N) % N, l = q / (N * N);
+    s.W3[q] = T(tab->w[i] * tab->w[j] * tab->w[l] * g.detJ);
+    if (need_psi)
+      for (int m = 0; m < NP; ++m)
+        s.Psi[q][m] = T(tab->pw[i][tab->ex[m][0]] * tab->pw[j][tab->ex[m][1]] * tab->pw[l][tab->ex[m][2]]);
+  }
+}
+
 // ------------------------------------------------------------------ Stokes family
 
 template <typename T, int N, int OPS>

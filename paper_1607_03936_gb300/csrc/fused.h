@@ -38,14 +38,30 @@ struct Epi {
 
 // Element pass of the Stokes family (ops: OP_A | OP_BT | OP_B as in kernels.h).  Velocity
 // contributions go to Ye [ne][3][n^3]; the B output (if OP_B) goes through `pe` per (e, m).
+// Per-level operator tables (derivatives scaled by 2/h, weights, pressure basis, inverse pressure
+// mass, transfer weights) in precision T, built on the host once per level: size and builder.
 template <typename T>
-cudaError_t launch_elem_stokes(const Grid& g, int k, const RefTables* dtab, int ops, const T* u, const T* us,
-                               const T* p, const T* coef, int coef_nodal, T* Ye, const Epi<T>& pe, cudaStream_t st);
+size_t optab_bytes(int k);
+template <typename T>
+void build_optab_host(const RefTables& t, const Grid& g, int k, void* out);
+
+template <typename T>
+cudaError_t launch_elem_stokes(const Grid& g, int k, const void* optab, int ops, const T* u, const T* us, const T* p,
+                               const T* coef, int coef_nodal, T* Ye, const Epi<T>& pe, cudaStream_t st);
 
 // Element pass of the scalar Q_k Poisson operator: Ye [ne][n^3].
 template <typename T>
-cudaError_t launch_elem_poisson(const Grid& g, int k, const RefTables* dtab, const T* u, const T* coef, T* Ye,
+cudaError_t launch_elem_poisson(const Grid& g, int k, const void* optab, const T* u, const T* coef, T* Ye,
                                 cudaStream_t st);
+
+// Pressure transfers of the two-space Poisson cycle: r_c = M_cd M_d^-1 r_d (element pass into Ye
+// [ne][n^3], then a node pass) and e_d (+)= M_d^-1 M_dc e_c (element pass).
+template <typename T>
+cudaError_t launch_disc_to_cont_fused(const Grid& g, int k, const void* optab, const T* rd, T* rc, T* Ye,
+                                      cudaStream_t st);
+template <typename T>
+cudaError_t launch_cont_to_disc_fused(const Grid& g, int k, const void* optab, const T* ec, T* ed, int add,
+                                      cudaStream_t st);
 
 // Node pass: v = sum of element contributions (0 on boundary nodes when mask_boundary), then the
 // epilogue on entry c * nn + node for each of ncomp components.
@@ -57,9 +73,10 @@ cudaError_t launch_gather(const Grid& g, int k, int ncomp, int mask_boundary, co
 //   prolong : out_f (+)= P in_c in one pass (N^3 coarse values per fine node)
 //   restrict: out_c = P^T in_f in three separable passes, all components per launch
 //             (w1, w2: transfer_work_size(gc, k) * ncomp entries each)
+// (optab: the coarse grid's table; only its transfer weights are used.)
 template <typename T>
-cudaError_t launch_prolong_fused(const Grid& gc, int k, const RefTables* dtab, int ncomp, const T* in_c, T* out_f,
-                                 int add, cudaStream_t st);
+cudaError_t launch_prolong_fused(const Grid& gc, int k, const void* optab, int ncomp, const T* in_c, T* out_f, int add,
+                                 cudaStream_t st);
 template <typename T>
-cudaError_t launch_restrict_batched(const Grid& gc, int k, const RefTables* dtab, int ncomp, const T* in_f, T* out_c,
+cudaError_t launch_restrict_batched(const Grid& gc, int k, const void* optab, int ncomp, const T* in_f, T* out_c,
                                     int mask_dirichlet, T* w1, T* w2, cudaStream_t st);

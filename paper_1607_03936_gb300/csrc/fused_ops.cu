@@ -44,7 +44,7 @@ __device__ inline void epi_apply(const Epi<T>& E, size_t i, int node, T v) {
 
 template <typename T, int N, int OPS>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
-k_elem(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ u, const T* __restrict__ us,
+k_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, const T* __restrict__ us,
        const T* __restrict__ p, const T* __restrict__ coef, int coef_nodal, T* __restrict__ Ye, Epi<T> pe) {
   constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, EPB = Cfg<N>::EPB, K = N - 1;
   constexpr bool DA = OPS & OP_A, DBT = OPS & OP_BT, DB = OPS & OP_B;
@@ -54,7 +54,7 @@ k_elem(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ u, const
   __shared__ T su[GRAD ? EPB : 1][3][N3];
   __shared__ T sS[SCAT ? EPB : 1][NS][N3];
   __shared__ T sdiv[DB ? EPB : 1][N3];
-  load_optab(st, tab, g, DB || DBT);
+  copy_tab(st, otab);
 
   const int tid = threadIdx.x;
   const int le = tid / N3, q = tid - le * N3;
@@ -162,13 +162,13 @@ k_elem(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ u, const
 
 template <typename T, int N>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
-k_elem_poisson(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ u, const T* __restrict__ coef,
+k_elem_poisson(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, const T* __restrict__ coef,
                T* __restrict__ Ye) {
   constexpr int N3 = Cfg<N>::N3, EPB = Cfg<N>::EPB, K = N - 1;
   __shared__ OpTab<T, N> st;
   __shared__ T su[EPB][N3];
   __shared__ T sF[EPB][3][N3];
-  load_optab(st, tab, g, false);
+  copy_tab(st, otab);
   const int tid = threadIdx.x;
   const int le = tid / N3, q = tid - le * N3;
   const int i = q % N, j = (q / N) % N, l = q / (N * N);
@@ -227,50 +227,58 @@ __global__ void k_gather(Grid g, int mask_boundary, const T* __restrict__ Ye, Ep
 
 // Fine node value = sum over the N^3 coarse nodes of its coarse element of the tensor weights.
 template <typename T, int N>
-__global__ void k_prolong3d(Grid gc, const RefTables* __restrict__ tab, int ncomp, const T* __restrict__ in_c,
+__global__ void k_prolong3d(Grid gc, const OpTab<T, N>* __restrict__ otab, int ncomp, const T* __restrict__ in_c,
                             T* __restrict__ out_f, int add) {
   constexpr int K = N - 1;
+  __shared__ T P1[2][N][N];
+  for (int t = threadIdx.x; t < 2 * N * N; t += blockDim.x) (&P1[0][0][0])[t] = (&otab->P1[0][0][0])[t];
+  __syncthreads();
   const int NXf = 2 * K * gc.nx + 1, NYf = 2 * K * gc.ny + 1, NZf = 2 * K * gc.nz + 1;
   const long long nf = (long long)NXf * NYf * NZf;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nf) return;
   const int idx[3] = {(int)(t % NXf), (int)((t / NXf) % NYf), (int)(t / ((long long)NXf * NYf))};
   const int nfe[3] = {2 * gc.nx, 2 * gc.ny, 2 * gc.nz};
-  double w[3][N];
-  int base[3];
+  int base[3], sa[3][2];
   for (int d = 0; d < 3; ++d) {
     int ef = idx[d] / K;
     if (ef > nfe[d] - 1) ef = nfe[d] - 1;
-    const int a = idx[d] - K * ef, s = ef % 2;
+    sa[d][0] = ef % 2;
+    sa[d][1] = idx[d] - K * ef;
     base[d] = K * (ef / 2);
-#pragma unroll
-    for (int b = 0; b < N; ++b) w[d][b] = tab->P1[s][a][b];
   }
+  const T* wx = P1[sa[0][0]][sa[0][1]];
+  const T* wy = P1[sa[1][0]][sa[1][1]];
+  const T* wz = P1[sa[2][0]][sa[2][1]];
   for (int c = 0; c < ncomp; ++c) {
     const T* src = in_c + (size_t)c * gc.nn;
-    double acc = 0.0;
+    T acc = 0;
 #pragma unroll
     for (int bz = 0; bz < N; ++bz) {
-      if (w[2][bz] == 0.0) continue;
 #pragma unroll
       for (int by = 0; by < N; ++by) {
-        if (w[1][by] == 0.0) continue;
-        const double wzy = w[2][bz] * w[1][by];
-        const T* row = src + (size_t)(base[0]) + (size_t)gc.NX * ((base[1] + by) + (size_t)gc.NY * (base[2] + bz));
+        const T wzy = wz[bz] * wy[by];
+        const T* row = src + (size_t)base[0] + (size_t)gc.NX * ((base[1] + by) + (size_t)gc.NY * (base[2] + bz));
+        T r = 0;
 #pragma unroll
-        for (int bx = 0; bx < N; ++bx) acc += wzy * w[0][bx] * (double)row[bx];
+        for (int bx = 0; bx < N; ++bx) r += wx[bx] * row[bx];
+        acc += wzy * r;
       }
     }
     T* dst = out_f + (size_t)c * nf + t;
-    *dst = add ? T((double)*dst + acc) : T(acc);
+    *dst = add ? *dst + acc : acc;
   }
 }
 
 // One axis of P^T for all components (grid.y = component); the last pass may zero boundary nodes.
-template <typename T>
-__global__ void k_rpass(const RefTables* __restrict__ tab, int K, int axis, int d0, int d1, int d2, int nc_el,
+template <typename T, int N>
+__global__ void k_rpass(const OpTab<T, N>* __restrict__ otab, int axis, int d0, int d1, int d2, int nc_el,
                         long long in_stride, long long out_stride, const T* __restrict__ in, T* __restrict__ out,
                         int mask_last) {
+  constexpr int K = N - 1;
+  __shared__ T P1[2][N][N];
+  for (int t = threadIdx.x; t < 2 * N * N; t += blockDim.x) (&P1[0][0][0])[t] = (&otab->P1[0][0][0])[t];
+  __syncthreads();
   const int nfine = 2 * K * nc_el + 1, ncoarse = K * nc_el + 1;
   int od[3] = {d0, d1, d2};
   od[axis] = ncoarse;
@@ -294,28 +302,91 @@ __global__ void k_rpass(const RefTables* __restrict__ tab, int K, int axis, int 
   int lo = 2 * i_c - 2 * K, hi = 2 * i_c + 2 * K;
   if (lo < 0) lo = 0;
   if (hi > nfine - 1) hi = nfine - 1;
-  long long stride = axis == 0 ? 1 : (axis == 1 ? id[0] : (long long)id[0] * id[1]);
+  const long long stride = axis == 0 ? 1 : (axis == 1 ? id[0] : (long long)id[0] * id[1]);
   int c3[3] = {o[0], o[1], o[2]};
   c3[axis] = 0;
   const long long base = (long long)c3[0] + (long long)id[0] * (c3[1] + (long long)id[1] * c3[2]);
-  double acc = 0.0;
+  T acc = 0;
   for (int i_f = lo; i_f <= hi; ++i_f) {
     int ef = i_f / K;
     if (ef > nf_el - 1) ef = nf_el - 1;
     const int a = i_f - K * ef, ec = ef / 2, s = ef % 2;
     const int b = i_c - K * ec;
     if (b < 0 || b > K) continue;
-    acc += tab->P1[s][a][b] * (double)src[base + i_f * stride];
+    acc += P1[s][a][b] * src[base + i_f * stride];
   }
-  dst[t] = T(acc);
+  dst[t] = acc;
+}
+
+// Pressure transfers of the two-space Poisson cycle (|J| cancels between M_d^-1 and the masses):
+//   element pass of r_c = M_cd M_d^-1 r_d: Ye[e][q] = W_q sum_m psi_m(q) (Minv r_e)_m
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_d2c_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ rd, T* __restrict__ Ye) {
+  constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, EPB = Cfg<N>::EPB;
+  __shared__ OpTab<T, N> st;
+  __shared__ T sv[EPB][NP];
+  copy_tab(st, otab);
+  const int le = threadIdx.x / N3, q = threadIdx.x - le * N3;
+  const int e = blockIdx.x * EPB + le;
+  const bool act = e < g.ne;
+  __syncthreads();
+  if (act && q < NP) {
+    T v = 0;
+#pragma unroll
+    for (int mp = 0; mp < NP; ++mp) v += st.Minv[q][mp] * rd[(size_t)e * NP + mp];
+    sv[le][q] = v;
+  }
+  __syncthreads();
+  if (!act) return;
+  T acc = 0;
+#pragma unroll
+  for (int m = 0; m < NP; ++m) acc += st.Psi[q][m] * sv[le][m];
+  Ye[(size_t)e * N3 + q] = st.Wref[q] * acc;
+}
+
+//   e_d[e][m] (+)= sum_m' Minv[m][m'] sum_q W_q psi_m'(q) e_c(node(e, q))
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_c2d_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ ec, T* __restrict__ ed, int add) {
+  constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, EPB = Cfg<N>::EPB, K = N - 1;
+  __shared__ OpTab<T, N> st;
+  __shared__ T sw[EPB][N3];
+  __shared__ T sg[EPB][NP];
+  copy_tab(st, otab);
+  const int le = threadIdx.x / N3, q = threadIdx.x - le * N3;
+  const int i = q % N, j = (q / N) % N, l = q / (N * N);
+  const int e = blockIdx.x * EPB + le;
+  const bool act = e < g.ne;
+  __syncthreads();
+  if (act) {
+    const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
+    sw[le][q] = st.Wref[q] * ec[(K * ex + i) + g.NX * ((K * ey + j) + g.NY * (K * ez + l))];
+  }
+  __syncthreads();
+  if (act && q < NP) {
+    T acc = 0;
+#pragma unroll
+    for (int qq = 0; qq < N3; ++qq) acc += st.Psi[qq][q] * sw[le][qq];
+    sg[le][q] = acc;
+  }
+  __syncthreads();
+  if (act && q < NP) {
+    T v = 0;
+#pragma unroll
+    for (int mp = 0; mp < NP; ++mp) v += st.Minv[q][mp] * sg[le][mp];
+    T* dst = ed + (size_t)e * NP + q;
+    *dst = add ? *dst + v : v;
+  }
 }
 
 inline unsigned nb(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 template <typename T, int N>
-cudaError_t run_elem(const Grid& g, const RefTables* tab, int ops, const T* u, const T* us, const T* p, const T* coef,
+cudaError_t run_elem(const Grid& g, const void* otab_v, int ops, const T* u, const T* us, const T* p, const T* coef,
                      int cn, T* Ye, const Epi<T>& pe, cudaStream_t st) {
   constexpr int EPB = Cfg<N>::EPB, TH = Cfg<N>::THREADS;
+  const OpTab<T, N>* tab = static_cast<const OpTab<T, N>*>(otab_v);
   const unsigned blocks = (unsigned)((g.ne + EPB - 1) / EPB);
   switch (ops) {
     case OP_A: wb_count_launch(), k_elem<T, N, OP_A><<<blocks, TH, 0, st>>>(g, tab, u, us, p, coef, cn, Ye, pe); break;
@@ -339,17 +410,45 @@ cudaError_t run_elem(const Grid& g, const RefTables* tab, int ops, const T* u, c
     default: return cudaErrorInvalidValue; \
   }
 
+#define WB_TAB(T) static_cast<const OpTab<T, N>*>(otab)
+
 template <typename T>
-cudaError_t launch_elem_stokes(const Grid& g, int k, const RefTables* dtab, int ops, const T* u, const T* us,
-                               const T* p, const T* coef, int cn, T* Ye, const Epi<T>& pe, cudaStream_t st) {
-  WB_FUSED_DISPATCH(k, (run_elem<T, N>(g, dtab, ops, u, us, p, coef, cn, Ye, pe, st)));
+cudaError_t launch_elem_stokes(const Grid& g, int k, const void* otab, int ops, const T* u, const T* us, const T* p,
+                               const T* coef, int cn, T* Ye, const Epi<T>& pe, cudaStream_t st) {
+  WB_FUSED_DISPATCH(k, (run_elem<T, N>(g, otab, ops, u, us, p, coef, cn, Ye, pe, st)));
 }
 
 template <typename T>
-cudaError_t launch_elem_poisson(const Grid& g, int k, const RefTables* dtab, const T* u, const T* coef, T* Ye,
+cudaError_t launch_elem_poisson(const Grid& g, int k, const void* otab, const T* u, const T* coef, T* Ye,
                                 cudaStream_t st) {
   WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_elem_poisson<T, N><<<(unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB),
-                                                                Cfg<N>::THREADS, 0, st>>>(g, dtab, u, coef, Ye)),
+                                                                Cfg<N>::THREADS, 0, st>>>(g, WB_TAB(T), u, coef, Ye)),
+                        cudaGetLastError()));
+}
+
+template <typename T>
+cudaError_t launch_disc_to_cont_fused(const Grid& g, int k, const void* otab, const T* rd, T* rc, T* Ye,
+                                      cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  switch (k) {
+    case 2: { constexpr int N = 3; wb_count_launch(), k_d2c_elem<T, N><<<(unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB), Cfg<N>::THREADS, 0, st>>>(g, WB_TAB(T), rd, Ye); break; }
+    case 3: { constexpr int N = 4; wb_count_launch(), k_d2c_elem<T, N><<<(unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB), Cfg<N>::THREADS, 0, st>>>(g, WB_TAB(T), rd, Ye); break; }
+    case 4: { constexpr int N = 5; wb_count_launch(), k_d2c_elem<T, N><<<(unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB), Cfg<N>::THREADS, 0, st>>>(g, WB_TAB(T), rd, Ye); break; }
+    default: return cudaErrorInvalidValue;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  Epi<T> ep;
+  ep.mode = EPI_STORE;
+  ep.y = rc;
+  return launch_gather<T>(g, k, 1, 0, Ye, ep, st);
+}
+
+template <typename T>
+cudaError_t launch_cont_to_disc_fused(const Grid& g, int k, const void* otab, const T* ec, T* ed, int add,
+                                      cudaStream_t st) {
+  WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_c2d_elem<T, N><<<(unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB),
+                                                            Cfg<N>::THREADS, 0, st>>>(g, WB_TAB(T), ec, ed, add)),
                         cudaGetLastError()));
 }
 
@@ -367,38 +466,70 @@ cudaError_t launch_gather(const Grid& g, int k, int ncomp, int mask, const T* Ye
 }
 
 template <typename T>
-cudaError_t launch_prolong_fused(const Grid& gc, int k, const RefTables* dtab, int ncomp, const T* in_c, T* out_f,
-                                 int add, cudaStream_t st) {
+cudaError_t launch_prolong_fused(const Grid& gc, int k, const void* otab, int ncomp, const T* in_c, T* out_f, int add,
+                                 cudaStream_t st) {
   const long long nf = (long long)(2 * k * gc.nx + 1) * (2 * k * gc.ny + 1) * (2 * k * gc.nz + 1);
-  WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_prolong3d<T, N><<<nb(nf, 128), 128, 0, st>>>(gc, dtab, ncomp, in_c,
+  WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_prolong3d<T, N><<<nb(nf, 128), 128, 0, st>>>(gc, WB_TAB(T), ncomp, in_c,
                                                                                             out_f, add)),
                         cudaGetLastError()));
 }
 
-template <typename T>
-cudaError_t launch_restrict_batched(const Grid& gc, int k, const RefTables* dtab, int ncomp, const T* in_f, T* out_c,
-                                    int mask, T* w1, T* w2, cudaStream_t st) {
+namespace {
+template <typename T, int N>
+cudaError_t run_restrict(const Grid& gc, const void* otab, int ncomp, const T* in_f, T* out_c, int mask, T* w1, T* w2,
+                         cudaStream_t st) {
+  constexpr int K = N - 1;
+  const OpTab<T, N>* tab = static_cast<const OpTab<T, N>*>(otab);
   const int ncx = gc.NX, ncy = gc.NY, ncz = gc.NZ;
-  const int nfx = 2 * k * gc.nx + 1, nfy = 2 * k * gc.ny + 1, nfz = 2 * k * gc.nz + 1;
+  const int nfx = 2 * K * gc.nx + 1, nfy = 2 * K * gc.ny + 1, nfz = 2 * K * gc.nz + 1;
   const long long nf = (long long)nfx * nfy * nfz, n1 = (long long)ncx * nfy * nfz, n2 = (long long)ncx * ncy * nfz;
   const long long nc = (long long)ncx * ncy * ncz;
   const int bs = 256;
-  wb_count_launch(), k_rpass<T><<<dim3(nb(n1, bs), ncomp), bs, 0, st>>>(dtab, k, 0, nfx, nfy, nfz, gc.nx, nf, n1, in_f, w1, 0);
-  wb_count_launch(), k_rpass<T><<<dim3(nb(n2, bs), ncomp), bs, 0, st>>>(dtab, k, 1, ncx, nfy, nfz, gc.ny, n1, n2, w1, w2, 0);
-  wb_count_launch(), k_rpass<T><<<dim3(nb(nc, bs), ncomp), bs, 0, st>>>(dtab, k, 2, ncx, ncy, nfz, gc.nz, n2, nc, w2, out_c,
-                                                                        mask);
+  wb_count_launch(), k_rpass<T, N><<<dim3(nb(n1, bs), ncomp), bs, 0, st>>>(tab, 0, nfx, nfy, nfz, gc.nx, nf, n1, in_f, w1, 0);
+  wb_count_launch(), k_rpass<T, N><<<dim3(nb(n2, bs), ncomp), bs, 0, st>>>(tab, 1, ncx, nfy, nfz, gc.ny, n1, n2, w1, w2, 0);
+  wb_count_launch(), k_rpass<T, N><<<dim3(nb(nc, bs), ncomp), bs, 0, st>>>(tab, 2, ncx, ncy, nfz, gc.nz, n2, nc, w2, out_c,
+                                                                           mask);
   return cudaGetLastError();
+}
+}  // namespace
+
+template <typename T>
+cudaError_t launch_restrict_batched(const Grid& gc, int k, const void* otab, int ncomp, const T* in_f, T* out_c,
+                                    int mask, T* w1, T* w2, cudaStream_t st) {
+  WB_FUSED_DISPATCH(k, (run_restrict<T, N>(gc, otab, ncomp, in_f, out_c, mask, w1, w2, st)));
+}
+
+template <typename T>
+size_t optab_bytes(int k) {
+  switch (k) {
+    case 2: return sizeof(OpTab<T, 3>);
+    case 3: return sizeof(OpTab<T, 4>);
+    case 4: return sizeof(OpTab<T, 5>);
+    default: return 0;
+  }
+}
+
+template <typename T>
+void build_optab_host(const RefTables& t, const Grid& g, int k, void* out) {
+  switch (k) {
+    case 2: make_optab<T, 3>(t, g, static_cast<OpTab<T, 3>*>(out)); break;
+    case 3: make_optab<T, 4>(t, g, static_cast<OpTab<T, 4>*>(out)); break;
+    case 4: make_optab<T, 5>(t, g, static_cast<OpTab<T, 5>*>(out)); break;
+    default: break;
+  }
 }
 
 #define WB_FUSED_INST(T)                                                                                              \
-  template cudaError_t launch_elem_stokes<T>(const Grid&, int, const RefTables*, int, const T*, const T*, const T*,   \
+  template cudaError_t launch_elem_stokes<T>(const Grid&, int, const void*, int, const T*, const T*, const T*,        \
                                              const T*, int, T*, const Epi<T>&, cudaStream_t);                         \
-  template cudaError_t launch_elem_poisson<T>(const Grid&, int, const RefTables*, const T*, const T*, T*,             \
-                                              cudaStream_t);                                                          \
+  template cudaError_t launch_elem_poisson<T>(const Grid&, int, const void*, const T*, const T*, T*, cudaStream_t);  \
   template cudaError_t launch_gather<T>(const Grid&, int, int, int, const T*, const Epi<T>&, cudaStream_t);           \
-  template cudaError_t launch_prolong_fused<T>(const Grid&, int, const RefTables*, int, const T*, T*, int,            \
-                                               cudaStream_t);                                                         \
-  template cudaError_t launch_restrict_batched<T>(const Grid&, int, const RefTables*, int, const T*, T*, int, T*, T*, \
-                                                  cudaStream_t);
+  template cudaError_t launch_prolong_fused<T>(const Grid&, int, const void*, int, const T*, T*, int, cudaStream_t);  \
+  template cudaError_t launch_restrict_batched<T>(const Grid&, int, const void*, int, const T*, T*, int, T*, T*,      \
+                                                  cudaStream_t);                                                      \
+  template cudaError_t launch_disc_to_cont_fused<T>(const Grid&, int, const void*, const T*, T*, T*, cudaStream_t);   \
+  template cudaError_t launch_cont_to_disc_fused<T>(const Grid&, int, const void*, const T*, T*, int, cudaStream_t);  \
+  template size_t optab_bytes<T>(int);                                                                                \
+  template void build_optab_host<T>(const RefTables&, const Grid&, int, void*);
 WB_FUSED_INST(double)
 WB_FUSED_INST(float)

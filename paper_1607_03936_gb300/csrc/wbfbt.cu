@@ -78,6 +78,7 @@ struct Level {
   // setup scratch kept for re-setup without allocation
   double *pts64 = nullptr, *d64 = nullptr, *Md = nullptr, *Yd = nullptr;   // Yd: pivots
   T *coefT = nullptr, *pv = nullptr, *pw = nullptr;
+  void* optab = nullptr;           // this level's operator tables in precision T (device)
 };
 
 template <typename T>
@@ -140,6 +141,8 @@ struct wbfbt_ctx {
   double *stage_f = nullptr, *stage_u = nullptr, *stage_p = nullptr;
   double* Ye64 = nullptr;   // element-pass scratch for the FP64 applies
   float* Ye32 = nullptr;    // element-pass scratch for the FP32 applies
+  void* ot64 = nullptr;     // fine-level operator tables, FP64
+  void* ot32 = nullptr;     // fine-level operator tables, FP32
 };
 
 namespace {
@@ -150,6 +153,22 @@ template <>
 Precond<double>& prec<double>(wbfbt_ctx* c) { return c->P64; }
 template <>
 Precond<float>& prec<float>(wbfbt_ctx* c) { return c->P32; }
+
+template <typename T>
+const void* fine_tab(wbfbt_ctx* c) {
+  return std::is_same<T, double>::value ? c->ot64 : c->ot32;
+}
+
+// Device copy of the operator tables of grid g in precision T (built once; tables depend only on g).
+template <typename T>
+void* make_device_optab(wbfbt_ctx* c, const Grid& g) {
+  const size_t nb = optab_bytes<T>(c->k);
+  std::vector<unsigned char> h(nb);
+  build_optab_host<T>(c->htab, g, c->k, h.data());
+  unsigned char* d = c->pool.get<unsigned char>(nb);
+  CK(cudaMemcpy(d, h.data(), nb, cudaMemcpyHostToDevice));
+  return d;
+}
 
 double read_scalar(wbfbt_ctx* c, const double* dptr) {
   double v = 0.0;
@@ -191,10 +210,10 @@ template <typename T>
 void level_apply(wbfbt_ctx* c, const Hier<T>& H, const Level<T>& L, const T* u, const Epi<T>& e) {
   T* Ye = prec<T>(c).Ye;
   if (H.vec)
-    CK(launch_elem_stokes<T>(L.g, c->k, c->dtab, OP_A, u, nullptr, nullptr, L.coef, L.coef_nodal, Ye, Epi<T>(),
+    CK(launch_elem_stokes<T>(L.g, c->k, L.optab, OP_A, u, nullptr, nullptr, L.coef, L.coef_nodal, Ye, Epi<T>(),
                              c->st));
   else
-    CK(launch_elem_poisson<T>(L.g, c->k, c->dtab, u, L.coef, Ye, c->st));
+    CK(launch_elem_poisson<T>(L.g, c->k, L.optab, u, L.coef, Ye, c->st));
   CK(launch_gather<T>(L.g, c->k, H.ncomp, H.vec ? 1 : 0, Ye, e, c->st));
 }
 
@@ -203,9 +222,9 @@ template <typename T>
 void op_Kw(wbfbt_ctx* c, int which, const T* p, const Epi<T>& e) {
   Precond<T>& P = prec<T>(c);
   const T* winv = which == 0 ? P.cinv : P.dinvw;
-  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, OP_BT, nullptr, nullptr, p, nullptr, 0, P.Ye, Epi<T>(), c->st));
+  CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_BT, nullptr, nullptr, p, nullptr, 0, P.Ye, Epi<T>(), c->st));
   CK(launch_gather<T>(c->g, c->k, 3, 1, P.Ye, epi_scale<T>(P.vtmp, winv), c->st));
-  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, OP_B, P.vtmp, nullptr, nullptr, nullptr, 0, nullptr, e, c->st));
+  CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_B, P.vtmp, nullptr, nullptr, nullptr, 0, nullptr, e, c->st));
 }
 
 // Chebyshev-Jacobi (Saad, Alg. 12.1) over [0.1, 1.1] lambda_hat; M(src, epi) applies the operator
@@ -259,9 +278,9 @@ void vcycle(wbfbt_ctx* c, Hier<T>& H, int l, const T* b, T* x) {
   auto M = [&](const T* u, const Epi<T>& e) { level_apply<T>(c, H, L, u, e); };
   chebyshev<T>(c, M, n, L.dinv, L.lam, b, x, true, true, L.r, L.d);
   Level<T>& Lc = H.lv[l + 1];
-  CK(launch_restrict_batched<T>(Lc.g, c->k, c->dtab, H.ncomp, L.r, Lc.b, H.vec ? 1 : 0, L.w1, L.w2, c->st));
+  CK(launch_restrict_batched<T>(Lc.g, c->k, Lc.optab, H.ncomp, L.r, Lc.b, H.vec ? 1 : 0, L.w1, L.w2, c->st));
   vcycle<T>(c, H, l + 1, Lc.b, Lc.x);
-  CK(launch_prolong_fused<T>(Lc.g, c->k, c->dtab, H.ncomp, Lc.x, x, 1, c->st));
+  CK(launch_prolong_fused<T>(Lc.g, c->k, Lc.optab, H.ncomp, Lc.x, x, 1, c->st));
   chebyshev<T>(c, M, n, L.dinv, L.lam, b, x, false, false, L.r, L.d);
 }
 
@@ -273,9 +292,9 @@ void kinv(wbfbt_ctx* c, int which, const T* bd, T* xd) {
   auto M = [&](const T* p, const Epi<T>& e) { op_Kw<T>(c, which, p, e); };
   chebyshev<T>(c, M, n, P.dKw[which], P.lamKw[which], bd, xd, true, true, P.pr, P.pd);
   Level<T>& L0 = P.HL[which].lv[0];
-  CK(launch_disc_to_cont<T>(c->g, c->k, c->dtab, P.pr, L0.b, c->st));
+  CK(launch_disc_to_cont_fused<T>(c->g, c->k, fine_tab<T>(c), P.pr, L0.b, P.Ye, c->st));
   vcycle<T>(c, P.HL[which], 0, L0.b, L0.x);
-  CK(launch_cont_to_disc<T>(c->g, c->k, c->dtab, L0.x, xd, 1, c->st));
+  CK(launch_cont_to_disc_fused<T>(c->g, c->k, fine_tab<T>(c), L0.x, xd, 1, c->st));
   chebyshev<T>(c, M, n, P.dKw[which], P.lamKw[which], bd, xd, false, false, P.pr, P.pd);
 }
 
@@ -291,11 +310,11 @@ void schur_inv(wbfbt_ctx* c, const T* r, T* y) {
   project<T>(c, r, P.sr);
   kinv<T>(c, 1, P.sr, P.sy);
   // middle factor B C^-1 A D^-1 B^T y, each diagonal scaling fused into the preceding node pass
-  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, OP_BT, nullptr, nullptr, P.sy, nullptr, 0, P.Ye, Epi<T>(), c->st));
+  CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_BT, nullptr, nullptr, P.sy, nullptr, 0, P.Ye, Epi<T>(), c->st));
   CK(launch_gather<T>(c->g, c->k, 3, 1, P.Ye, epi_scale<T>(P.sv1, P.dinvw), c->st));
-  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, OP_A, P.sv1, nullptr, nullptr, P.mu, 1, P.Ye, Epi<T>(), c->st));
+  CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_A, P.sv1, nullptr, nullptr, P.mu, 1, P.Ye, Epi<T>(), c->st));
   CK(launch_gather<T>(c->g, c->k, 3, 1, P.Ye, epi_scale<T>(P.sv2, P.cinv), c->st));
-  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, OP_B, P.sv2, nullptr, nullptr, nullptr, 0, nullptr,
+  CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_B, P.sv2, nullptr, nullptr, nullptr, 0, nullptr,
                            epi_store<T>(P.sz), c->st));
   kinv<T>(c, 0, P.sz, P.sy2);
   project<T>(c, P.sy2, y);
@@ -313,7 +332,7 @@ void precond(wbfbt_ctx* c, const T* x, T* y) {
   schur_inv<T>(c, xp, yp);
   if (c->opt.schur_sign < 0) CK(launch_scale<T>((long long)c->g.ne * c->NP, T(-1), yp, yp, c->st));
   // r_u - B^T y_p in one element pass + node pass
-  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, OP_BT, nullptr, nullptr, yp, nullptr, 0, P.Ye, Epi<T>(), c->st));
+  CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_BT, nullptr, nullptr, yp, nullptr, 0, P.Ye, Epi<T>(), c->st));
   Epi<T> e;
   e.mode = EPI_BMINUS;
   e.y = P.urhs;
@@ -389,6 +408,7 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
     }
     c->pool.ensure(L.b, nv);
     c->pool.ensure(L.x, nv);
+    if (!L.optab) L.optab = make_device_optab<T>(c, g);
     if (!L.coarsest) {
       c->pool.ensure(L.r, nv);
       c->pool.ensure(L.d, nv);
@@ -538,7 +558,7 @@ int guarded_ctx(wbfbt_ctx* c, F f) {
 
 void apply_K64(wbfbt_ctx* c, const double* x, double* y) {
   const long long nu = 3LL * c->g.nn;
-  CK(launch_elem_stokes<double>(c->g, c->k, c->dtab, OP_A | OP_BT | OP_B, x, nullptr, x + nu, c->mu64, 1, c->Ye64,
+  CK(launch_elem_stokes<double>(c->g, c->k, c->ot64, OP_A | OP_BT | OP_B, x, nullptr, x + nu, c->mu64, 1, c->Ye64,
                                 epi_store<double>(y + nu), c->st));
   CK(launch_gather<double>(c->g, c->k, 3, 1, c->Ye64, epi_store<double>(y), c->st));
 }
@@ -724,7 +744,7 @@ namespace {
 template <typename T>
 void stokes_apply_t(wbfbt_ctx* c, int ops, const T* u, const T* p, T* yu, T* yp, const T* mu, T* Ye) {
   const bool scat = (ops & OP_A) || (ops & OP_BT);
-  CK(launch_elem_stokes<T>(c->g, c->k, c->dtab, ops, u, nullptr, p, mu, 1, Ye, epi_store<T>(yp), c->st));
+  CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), ops, u, nullptr, p, mu, 1, Ye, epi_store<T>(yp), c->st));
   if (scat) CK(launch_gather<T>(c->g, c->k, 3, 1, Ye, epi_store<T>(yu), c->st));
 }
 
@@ -823,6 +843,8 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
     cp->ntot = 3LL * nn + (long long)g.ne * cp->NP;
     cp->Ye64 = cp->pool.get<double>((size_t)3 * g.ne * cp->N3);
     cp->Ye32 = cp->pool.get<float>((size_t)3 * g.ne * cp->N3);
+    cp->ot64 = make_device_optab<double>(cp, g);
+    cp->ot32 = make_device_optab<float>(cp, g);
     CK(launch_lumped_mass(g, cp->k, cp->dtab, cp->lm, cp->st));
     run_setup(cp, mu_nodes);
     const long long n = cp->ntot;
