@@ -115,6 +115,12 @@ __global__ void k_scale(long long n, T s, const T* __restrict__ x, T* __restrict
   if (i < n) z[i] = x[i] * s;
 }
 
+template <typename T>
+__global__ void k_scale_by_inv(long long n, const double* __restrict__ s, const T* __restrict__ x, T* __restrict__ z) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = T((double)x[i] / s[0]);
+}
+
 template <typename A, typename B>
 __global__ void k_cast(long long n, const A* __restrict__ x, B* __restrict__ y) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -194,31 +200,128 @@ __global__ void k_pin_first(double* M, int n) {
   M[(size_t)t * n] = t == 0 ? 1.0 : 0.0; // column 0
 }
 
-// In-place Gauss-Jordan inversion of an SPD matrix, one pivot per pair of launches:
-//   a_ik -= a_ij a_jk / a_jj (i, k != j);  a_jk /= a_jj;  a_ij = -a_ij / a_jj;  a_jj = 1 / a_jj.
-// The pivot is saved by the first kernel so the second can overwrite row and column j.
-__global__ void k_gj_update(double* __restrict__ A, int n, int j, double* __restrict__ piv, int* __restrict__ flag) {
-  const double p = A[(size_t)j * n + j];
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
-    piv[j] = p;
-    if (!(p > 0.0) || !isfinite(p)) flag[0] = j + 1;
+// Blocked in-place Gauss-Jordan inversion of SPD matrices (no pivoting; every pivot block is a
+// Schur complement of an SPD matrix, hence SPD).  For the pivot block J = [J0, J0 + bb):
+//   P     <- inv(A[J][J])                       (one block per matrix, GJ in shared memory)
+//   A[J][K] <- P A[J][K]              (K not in J)
+//   A[I][K] <- A[I][K] - A[I][J] A[J][K]   (I, K not in J; A[J][K] already updated)
+//   A[I][J] <- -A[I][J] P            (I not in J);   A[J][J] <- P
+// After the last block A holds inv(A).  Several matrices run in one launch (grid.z / grid.x).
+constexpr int GJB = 32;
+
+struct GjJobs {
+  double* A[4];
+  int n[4];
+  double* P[4];   // GJB x GJB workspace per matrix
+};
+
+__global__ void k_bgj_pivot(GjJobs jobs, int J0, int* __restrict__ flag) {
+  const int z = blockIdx.x;
+  const int n = jobs.n[z];
+  if (J0 >= n) return;
+  const int bb = min(GJB, n - J0);
+  double* A = jobs.A[z];
+  __shared__ double S[GJB][GJB + 1];
+  const int r = threadIdx.y, c = threadIdx.x;   // 32 x 32 threads
+  if (r < bb && c < bb) S[r][c] = A[(size_t)(J0 + r) * n + J0 + c];
+  __syncthreads();
+  for (int j = 0; j < bb; ++j) {
+    const double p = S[j][j];
+    if (r == 0 && c == 0 && (!(p > 0.0) || !isfinite(p))) flag[0] = J0 + j + 1;
+    __syncthreads();
+    if (!(p > 0.0)) return;   // uniform across the block
+    const double ip = 1.0 / p;
+    const double rj = S[j][c], ci = S[r][j];
+    __syncthreads();
+    if (r < bb && c < bb) {
+      if (r != j && c != j) S[r][c] -= ci * rj * ip;
+      else if (r == j && c != j) S[r][c] = rj * ip;
+      else if (r != j && c == j) S[r][c] = -ci * ip;
+      else S[r][c] = ip;
+    }
+    __syncthreads();
   }
-  if (!(p > 0.0)) return;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= n || k >= n || i == j || k == j) return;
-  A[(size_t)i * n + k] -= A[(size_t)i * n + j] * A[(size_t)j * n + k] / p;
+  if (r < bb && c < bb) jobs.P[z][r * GJB + c] = S[r][c];
 }
 
-__global__ void k_gj_pivot(double* __restrict__ A, int n, int j, const double* __restrict__ piv) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const double p = piv[j];
-  if (!(p > 0.0) || t >= n) return;
-  if (t == j) {
-    A[(size_t)j * n + j] = 1.0 / p;
-  } else {
-    A[(size_t)j * n + t] /= p;
-    A[(size_t)t * n + j] = -A[(size_t)t * n + j] / p;
+// A[J][k] <- P A[J][k] for k not in J: one thread per column k, in place (only it touches column k of rows J)
+__global__ void k_bgj_rows(GjJobs jobs, int J0) {
+  const int z = blockIdx.y;
+  const int n = jobs.n[z];
+  if (J0 >= n) return;
+  const int bb = min(GJB, n - J0);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double P[GJB * GJB];
+  for (int t = threadIdx.x; t < GJB * GJB; t += blockDim.x) P[t] = jobs.P[z][t];
+  __syncthreads();
+  if (k >= n || (k >= J0 && k < J0 + bb)) return;
+  double* A = jobs.A[z];
+  double col[GJB];
+#pragma unroll
+  for (int s = 0; s < GJB; ++s) col[s] = s < bb ? A[(size_t)(J0 + s) * n + k] : 0.0;
+  for (int r = 0; r < bb; ++r) {
+    double v = 0.0;
+#pragma unroll
+    for (int s = 0; s < GJB; ++s) v += P[r * GJB + s] * col[s];
+    A[(size_t)(J0 + r) * n + k] = v;
+  }
+}
+
+// A[i][k] -= sum_s A[i][J0+s] A[J0+s][k] for i, k not in J (32 x 8 threads, 32 x 32 tile)
+__global__ void k_bgj_update(GjJobs jobs, int J0) {
+  const int z = blockIdx.z;
+  const int n = jobs.n[z];
+  if (J0 >= n) return;
+  const int bb = min(GJB, n - J0);
+  double* A = jobs.A[z];
+  const int k0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+  if (k0 >= n || i0 >= n) return;
+  __shared__ double Rj[GJB][33];   // A[J0+s][k0+x]
+  __shared__ double Ci[32][GJB + 1];   // A[i0+y][J0+s]
+  for (int t = threadIdx.y * 32 + threadIdx.x; t < GJB * 32; t += 256) {
+    const int s = t / 32, x = t % 32;
+    Rj[s][x] = (s < bb && k0 + x < n) ? A[(size_t)(J0 + s) * n + k0 + x] : 0.0;
+    const int y = t / GJB, s2 = t % GJB;
+    Ci[y][s2] = (s2 < bb && i0 + y < n) ? A[(size_t)(i0 + y) * n + J0 + s2] : 0.0;
+  }
+  __syncthreads();
+  const int k = k0 + threadIdx.x;
+  if (k >= n || (k >= J0 && k < J0 + bb)) return;
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int i = i0 + yy;
+    if (i >= n || (i >= J0 && i < J0 + bb)) continue;
+    double acc = 0.0;
+#pragma unroll
+    for (int s = 0; s < GJB; ++s) acc += Ci[yy][s] * Rj[s][threadIdx.x];
+    A[(size_t)i * n + k] -= acc;
+  }
+}
+
+// A[i][J] <- -A[i][J] P for i not in J (thread per row); A[J][J] <- P
+__global__ void k_bgj_cols(GjJobs jobs, int J0) {
+  const int z = blockIdx.y;
+  const int n = jobs.n[z];
+  if (J0 >= n) return;
+  const int bb = min(GJB, n - J0);
+  double* A = jobs.A[z];
+  __shared__ double P[GJB * GJB];
+  for (int t = threadIdx.x; t < GJB * GJB; t += blockDim.x) P[t] = jobs.P[z][t];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double* row = A + (size_t)i * n + J0;
+  if (i >= J0 && i < J0 + bb) {
+    for (int c = 0; c < bb; ++c) row[c] = P[(i - J0) * GJB + c];
+    return;
+  }
+  double a[GJB];
+#pragma unroll
+  for (int s = 0; s < GJB; ++s) a[s] = s < bb ? row[s] : 0.0;
+  for (int c = 0; c < bb; ++c) {
+    double v = 0.0;
+#pragma unroll
+    for (int s = 0; s < GJB; ++s) v += a[s] * P[s * GJB + c];
+    row[c] = -v;
   }
 }
 
@@ -306,6 +409,12 @@ cudaError_t launch_scale(long long n, T s, const T* x, T* z, cudaStream_t st) {
   wb_count_launch(), k_scale<T><<<nblk(n, 256), 256, 0, st>>>(n, s, x, z);
   return cudaGetLastError();
 }
+template <typename T>
+cudaError_t launch_scale_by_inv(long long n, const double* s, const T* x, T* z, cudaStream_t st) {
+  wb_count_launch(), k_scale_by_inv<T><<<nblk(n, 256), 256, 0, st>>>(n, s, x, z);
+  return cudaGetLastError();
+}
+
 template <typename A, typename B>
 cudaError_t launch_cast(long long n, const A* x, B* y, cudaStream_t st) {
   wb_count_launch(), k_cast<A, B><<<nblk(n, 256), 256, 0, st>>>(n, x, y);
@@ -331,16 +440,24 @@ cudaError_t launch_coarse_solve(int nn, int ncomp, const int* map, int nfree_nod
   return cudaGetLastError();
 }
 
-cudaError_t launch_dense_inverse(double* M, int n, int pin_first, double* piv, double* Ainv, int* flag,
-                                 cudaStream_t st) {
-  if (pin_first) wb_count_launch(), k_pin_first<<<nblk(n, 256), 256, 0, st>>>(M, n);
-  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
-  for (int j = 0; j < n; ++j) {
-    wb_count_launch(), k_gj_update<<<grd, blk, 0, st>>>(M, n, j, piv, flag);
-    wb_count_launch(), k_gj_pivot<<<nblk(n, 256), 256, 0, st>>>(M, n, j, piv);
+cudaError_t launch_dense_inverse_batch(int count, double* const* M, const int* n, const int* pin_first,
+                                       double* pwork, int* flag, cudaStream_t st) {
+  if (count < 1 || count > 4) return cudaErrorInvalidValue;
+  GjJobs jobs{};
+  int nmax = 0;
+  for (int z = 0; z < count; ++z) {
+    jobs.A[z] = M[z];
+    jobs.n[z] = n[z];
+    jobs.P[z] = pwork + (size_t)z * GJB * GJB;
+    if (n[z] > nmax) nmax = n[z];
+    if (pin_first[z]) wb_count_launch(), k_pin_first<<<nblk(n[z], 256), 256, 0, st>>>(M[z], n[z]);
   }
-  cudaError_t e = cudaMemcpyAsync(Ainv, M, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, st);
-  if (e != cudaSuccess) return e;
+  for (int J0 = 0; J0 < nmax; J0 += GJB) {
+    wb_count_launch(), k_bgj_pivot<<<count, dim3(32, 32), 0, st>>>(jobs, J0, flag);
+    wb_count_launch(), k_bgj_rows<<<dim3(nblk(nmax, 128), count), 128, 0, st>>>(jobs, J0);
+    wb_count_launch(), k_bgj_update<<<dim3((nmax + 31) / 32, (nmax + 31) / 32, count), dim3(32, 8), 0, st>>>(jobs, J0);
+    wb_count_launch(), k_bgj_cols<<<dim3(nblk(nmax, 128), count), 128, 0, st>>>(jobs, J0);
+  }
   return cudaGetLastError();
 }
 
@@ -377,6 +494,7 @@ cudaError_t launch_add_vec(long long n, const double* a, double* h, cudaStream_t
   template cudaError_t launch_axpby<T>(long long, T, const T*, T, const T*, T*, cudaStream_t);                        \
   template cudaError_t launch_mul<T>(long long, const T*, const T*, T*, cudaStream_t);                                \
   template cudaError_t launch_scale<T>(long long, T, const T*, T*, cudaStream_t);                                     \
+  template cudaError_t launch_scale_by_inv<T>(long long, const double*, const T*, T*, cudaStream_t);                  \
   template cudaError_t launch_project_pressure<T>(long long, int, const T*, T*, double*, double*, cudaStream_t);      \
   template cudaError_t launch_coarse_solve<T>(int, int, const int*, int, int, const double*, int, const T*, T*,       \
                                               double*, double*, cudaStream_t);                                        \

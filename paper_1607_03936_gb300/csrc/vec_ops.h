@@ -30,6 +30,9 @@ template <typename T>
 cudaError_t launch_mul(long long n, const T* a, const T* b, T* z, cudaStream_t st);
 template <typename T>
 cudaError_t launch_scale(long long n, T s, const T* x, T* z, cudaStream_t st);
+// z = x / s[0] with the divisor read from device memory (no host round trip).
+template <typename T>
+cudaError_t launch_scale_by_inv(long long n, const double* s, const T* x, T* z, cudaStream_t st);
 template <typename A, typename B>
 cudaError_t launch_cast(long long n, const A* x, B* y, cudaStream_t st);
 
@@ -44,11 +47,12 @@ template <typename T>
 cudaError_t launch_coarse_solve(int nn, int ncomp, const int* map, int nfree_nodes, int ndense, const double* Ainv,
                                 int neumann, const T* b, T* x, double* bf, double* xf, cudaStream_t st);
 
-// Dense SPD inverse by in-place Gauss-Jordan on M (pin_first: row/col 0 replaced by the identity
-// first), copied to Ainv; piv: n doubles of workspace.  flag[0] != 0 afterwards if a pivot was not
-// positive (the matrix is not SPD).
-cudaError_t launch_dense_inverse(double* M, int n, int pin_first, double* piv, double* Ainv, int* flag,
-                                 cudaStream_t st);
+// In-place inverses of up to 4 SPD matrices M[z] (n[z] x n[z], row-major) by blocked Gauss-Jordan
+// (32-pivot blocks, 4 launches per block for all matrices together); pin_first[z]: replace row and
+// column 0 by the identity first.  pwork: 4 * 32 * 32 doubles.  flag[0] != 0 afterwards if a pivot
+// was not positive (a matrix is not SPD).
+cudaError_t launch_dense_inverse_batch(int count, double* const* M, const int* n, const int* pin_first,
+                                       double* pwork, int* flag, cudaStream_t st);
 
 // FGMRES: out[c] = V[c] . w for c < ncols (deterministic); w -= V^T-weighted sum; x += Z y.
 cudaError_t launch_mdot(const double* V, long long ld, int ncols, const double* w, long long n, double* part,

@@ -76,7 +76,7 @@ struct Level {
   int nfree_nodes = 0, ndense = 0;
   double *Ainv = nullptr, *bf = nullptr, *xf = nullptr;
   // setup scratch kept for re-setup without allocation
-  double *pts64 = nullptr, *d64 = nullptr, *Md = nullptr, *Yd = nullptr;   // Yd: pivots
+  double *pts64 = nullptr, *d64 = nullptr, *Md = nullptr;
   T *coefT = nullptr, *pv = nullptr, *pw = nullptr;
   void* optab = nullptr;           // this level's operator tables in precision T (device)
 };
@@ -143,6 +143,13 @@ struct wbfbt_ctx {
   float* Ye32 = nullptr;    // element-pass scratch for the FP32 applies
   void* ot64 = nullptr;     // fine-level operator tables, FP64
   void* ot32 = nullptr;     // fine-level operator tables, FP32
+  struct DenseJob {
+    double* M;
+    int n;
+    int pin;
+  };
+  std::vector<DenseJob> dense_jobs;   // coarsest matrices awaiting inversion in the current setup
+  double* gj_work = nullptr;          // 4 x 32 x 32 pivot-block workspace
 };
 
 namespace {
@@ -343,23 +350,26 @@ void precond(wbfbt_ctx* c, const T* x, T* y) {
 
 // ------------------------------------------------------------------ setup
 
+// lambda_hat of D^-1 M by 10 power iterations; the normalisation divides by a norm kept in device
+// memory, so the only host round trip is the final read.
 template <typename T, class Op>
 double power_lambda(wbfbt_ctx* c, Op M, long long n, const T* dinv, T* v, T* w, const Grid* mask_grid) {
+  double* nrm = c->dsc + 8;
   CK(launch_splitmix_start<T>(n, START_SEED, v, c->st));
   if (mask_grid) CK(launch_mask_boundary<T>(*mask_grid, 3, v, c->st));
-  double nv = norm<T>(c, v, n);
-  CK(launch_scale<T>(n, T(1.0 / nv), v, v, c->st));
-  double lam = 0.0;
+  CK(launch_dot<T, T>(v, v, n, 1, c->part, nrm, 1, c->st));
+  CK(launch_scale_by_inv<T>(n, nrm, v, v, c->st));
   for (int it = 0; it < POWER_ITERS; ++it) {
     Epi<T> e;
     e.mode = EPI_DINV;
     e.y = w;
     e.dinv = dinv;
     M(v, e);
-    lam = norm<T>(c, w, n);
-    if (!(lam > 0.0) || !std::isfinite(lam)) throw WbErr{WBFBT_ERR_SETUP};
-    CK(launch_scale<T>(n, T(1.0 / lam), w, v, c->st));
+    CK(launch_dot<T, T>(w, w, n, 1, c->part, nrm, 1, c->st));
+    if (it < POWER_ITERS - 1) CK(launch_scale_by_inv<T>(n, nrm, w, v, c->st));
   }
+  const double lam = read_scalar(c, nrm);
+  if (!(lam > 0.0) || !std::isfinite(lam)) throw WbErr{WBFBT_ERR_SETUP};
   return lam;
 }
 
@@ -447,8 +457,6 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
         CK(cudaStreamSynchronize(c->st));   // hmap is a stack-local host buffer
       }
       c->pool.ensure(L.Md, (size_t)nd * nd);
-      c->pool.ensure(L.Yd, (size_t)nd);
-      c->pool.ensure(L.Ainv, (size_t)nd * nd);
       c->pool.ensure(L.bf, nd);
       c->pool.ensure(L.xf, nd);
       CK(cudaMemsetAsync(L.Md, 0, sizeof(double) * (size_t)nd * nd, c->st));
@@ -456,19 +464,38 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
         CK(launch_assemble_dense_A(g, c->k, c->dtab, L.coef64, L.coef_nodal, L.map, nfree, L.Md, nd, c->st));
       else
         CK(launch_assemble_dense_L_mapped(g, c->k, c->dtab, L.coef64, L.map, L.Md, nd, c->st));
-      CK(cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
-      CK(launch_dense_inverse(L.Md, nd, vec ? 0 : 1, L.Yd, L.Ainv, c->dflag, c->st));
-      int flag = 0;
-      CK(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-      CK(cudaStreamSynchronize(c->st));
-      if (flag) throw WbErr{WBFBT_ERR_SETUP};
+      L.Ainv = L.Md;   // inverted in place by run_dense_jobs once every hierarchy is assembled
+      c->dense_jobs.push_back({L.Md, nd, vec ? 0 : 1});
     }
   }
+}
+
+// Invert every coarsest matrix assembled in this setup, all in one blocked Gauss-Jordan sweep.
+void run_dense_jobs(wbfbt_ctx* c) {
+  const int cnt = (int)c->dense_jobs.size();
+  if (cnt == 0) return;
+  if (cnt > 4) throw WbErr{WBFBT_ERR_INVALID};
+  double* M[4];
+  int n[4], pin[4];
+  for (int z = 0; z < cnt; ++z) {
+    M[z] = c->dense_jobs[z].M;
+    n[z] = c->dense_jobs[z].n;
+    pin[z] = c->dense_jobs[z].pin;
+  }
+  c->pool.ensure(c->gj_work, (size_t)4 * 32 * 32);
+  CK(cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
+  CK(launch_dense_inverse_batch(cnt, M, n, pin, c->gj_work, c->dflag, c->st));
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->dense_jobs.clear();
+  if (flag) throw WbErr{WBFBT_ERR_SETUP};
 }
 
 template <typename T>
 void build_precond(wbfbt_ctx* c) {
   Precond<T>& P = prec<T>(c);
+  c->dense_jobs.clear();
   const Grid& g = c->g;
   const size_t nn = g.nn, nu = 3 * nn, np = (size_t)g.ne * c->NP, npts = (size_t)g.ne * c->N3;
   if (std::is_same<T, double>::value) {
@@ -503,6 +530,7 @@ void build_precond(wbfbt_ctx* c) {
     auto M = [&](const T* p, const Epi<T>& e) { op_Kw<T>(c, wi, p, e); };
     P.lamKw[wi] = power_lambda<T>(c, M, (long long)np, P.dKw[wi], P.px, P.pd, nullptr);
   }
+  run_dense_jobs(c);
 }
 
 __global__ void k_inv_masked(Grid g, const double* __restrict__ w, double* __restrict__ inv) {
