@@ -280,12 +280,12 @@ def run_ours(args, cfg, rank, world):
     bytes32 = a_apply_bytes_per_node(4) * n_nodes
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_for("apply_A_f64"),
-                "kernel": "k_stokes<double,3,OP_A> x 8 colour launches (one A apply)",
-                "per_launch": "one fine-level A apply (8 colour launches), 36n^4+30n^3 flops per element",
+                "kernel": "k_elem<double,3,OP_A> + k_gather<double,3,3> (one A apply)",
+                "per_launch": "one fine-level A apply (element pass + node pass), 36n^4+30n^3 flops per element",
                 "peak_note": "FP64 ALU peak derived from 152 SMs x 2 DFMA/clk x 2.07 GHz"}
     roofline_fp32 = {"bound": "hbm", "achieved": bytes32 / t_a32 / 1e9, "peak": hbm_peak, "unit": "GB/s",
                      "frac": bytes32 / t_a32 / 1e9 / hbm_peak, "traffic": traffic_for("apply_A_f32"),
-                     "kernel": "k_stokes<float,3,OP_A> x 8 colour launches", "peak_note": hbm_note}
+                     "kernel": "k_elem<float,3,OP_A> + k_gather<float,3,3> (one A apply)", "peak_note": hbm_note}
 
     # end-to-end through the C ABI with host buffers (copies inside the timed region)
     mu_h = torch.empty(solver.n_nodes, dtype=torch.float64).pin_memory()

@@ -125,14 +125,31 @@ k_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, co
     }
   }
   __syncthreads();
-  if (!act) return;
-  if (DB && q < NP) {
-    const int m = q;
-    T acc = 0;
+  if (DB) {
+    // B u per mode m: -sum_q Psi[q][m] sdiv[q], split over the element's threads in RC chunks of
+    // ceil(N3 / RC) points (partials in shared memory), then RC-term sums: short dependent chains.
+    constexpr int RC = (N3 / NP) < 8 ? (N3 / NP) : 8;
+    constexpr int CH = (N3 + RC - 1) / RC;
+    __shared__ T spart[DB ? EPB : 1][NP][RC];
+    if (act && q < NP * RC) {
+      const int m = q % NP, ch = q / NP;
+      T acc = 0;
 #pragma unroll
-    for (int qq = 0; qq < N3; ++qq) acc += st.Psi[qq][m] * sdiv[DB ? le : 0][qq];
-    epi_apply(pe, (size_t)e * NP + m, 0, -acc);
+      for (int t = 0; t < CH; ++t) {
+        const int qq = ch * CH + t;
+        if (qq < N3) acc += st.Psi[qq][m] * sdiv[DB ? le : 0][qq];
+      }
+      spart[DB ? le : 0][m][ch] = acc;
+    }
+    __syncthreads();
+    if (act && q < NP) {
+      T acc = 0;
+#pragma unroll
+      for (int ch = 0; ch < RC; ++ch) acc += spart[DB ? le : 0][q][ch];
+      epi_apply(pe, (size_t)e * NP + q, 0, -acc);
+    }
   }
+  if (!act) return;
   if (SCAT) {
     const T* S = &sS[SCAT ? le : 0][0][0];
     T* out = Ye + (size_t)e * 3 * N3 + q;
