@@ -166,6 +166,51 @@ long long wbfbt_device_bytes(const wbfbt_ctx* ctx);
 int wbfbt_apply_Kw_noalloc(const wbfbt_mesh* mesh, int k, const double* mu_nodes, double a,
                            const double* p, double* y, void* stream);
 
+/* ---------------------------------------------------------------- learned correction
+ * (not in the paper: the task's learned part).  A 3-level 3-D convolutional U-Net on the
+ * element grid (channels 16/32/64, 3x3x3 kernels, 2x2x2 average pooling, nearest upsampling,
+ * skip concatenation [up, skip], ReLU after every convolution but the last, zero padding).
+ * Tensors are voxel-major [batch][n^3][channels], voxel ex + n (ey + n ez).  Parameters are
+ * FP32, flattened layer by layer (c1..c11) as W[27][cin][cout] then b[cout], tap
+ * t = (dx+1) + 3 (dy+1) + 9 (dz+1):  y[v][co] = b[co] + sum_t sum_ci W[t][ci][co] x[v+d_t][ci].
+ * Layers: c1 cin->16, c2 16->16, c3 16->32, c4 32->32, c5 32->64, c6 64->64, c7 96->32,
+ * c8 32->32, c9 48->16, c10 16->16, c11 16->cout.  Compute in BF16 tensor-core kernels with
+ * FP32 accumulation; loss = mean squared error; Adam (beta 0.9, 0.999, eps 1e-8).  n must be a
+ * multiple of 4; cin, cout <= 16. */
+typedef struct wbfbt_net wbfbt_net;
+long long wbfbt_net_num_params(int cin, int cout);
+int wbfbt_net_create(int cin, int cout, int n, int max_batch, void* stream, wbfbt_net** out);
+int wbfbt_net_set_params(wbfbt_net* net, const float* theta);          /* device or host, copied */
+int wbfbt_net_get_params(wbfbt_net* net, float* theta);                /* device or host          */
+long long wbfbt_net_param_count(const wbfbt_net* net);
+/* y = net(x): x [batch][n^3][cin], y [batch][n^3][cout], FP32 device pointers. */
+int wbfbt_net_forward(wbfbt_net* net, const float* x, int batch, float* y);
+/* Forward, MSE loss against target [batch][n^3][cout] and backward: *loss (host, may be NULL),
+ * gradient of all parameters into grad (device or host, may be NULL); the gradient is kept
+ * for wbfbt_net_adam_step. */
+int wbfbt_net_loss_grad(wbfbt_net* net, const float* x, const float* target, int batch, double* loss,
+                        float* grad);
+int wbfbt_net_adam_step(wbfbt_net* net, float lr);
+/* Checkpoint: parameters and Adam state, binary file with a header. */
+int wbfbt_net_save(wbfbt_net* net, const char* path);
+int wbfbt_net_load(wbfbt_net* net, const char* path);
+void wbfbt_net_destroy(wbfbt_net* net);
+
+/* Use `net` (or NULL to detach) for the pressure-Poisson inverses inside S~^-1: bit 1 of
+ * `which_mask` for K_r = B D^-1 B^T, bit 0 for K_l = B C^-1 B^T.  Each application builds the
+ * features x[e] = (mean log10 mu over the element's nodes / 4, q_e / s), q = diag(K_w)^-1/2 r,
+ * s = rms(q), runs the net, forms z = s diag(K_w)^-1/2 y, and keeps z only if
+ * ||r - K_w z|| < ||r||; otherwise it runs the V-cycle (the fallback).  The net's grid must be
+ * the element grid (nx = ny = nz = n) and cin = 1 + Np, cout = Np.  While a net is attached
+ * the preconditioner is not replayed as a graph (the acceptance test is a host decision). */
+int wbfbt_attach_net(wbfbt_ctx* ctx, wbfbt_net* net, int which_mask);
+/* A training pair from the solver itself: for a pressure residual r [E][Np] (FP64 device,
+ * mean-free), x_out [E][1+Np] are the features above and y_out [E][Np] the V-cycle
+ * correction z = K~_w^-1 r in the net's output units (y = z / (s diag(K_w)^-1/2)). */
+int wbfbt_learned_sample(wbfbt_ctx* ctx, int which, const double* r, float* x_out, float* y_out);
+/* Learned applications kept / replaced by the V-cycle since the context was created. */
+int wbfbt_learned_stats(const wbfbt_ctx* ctx, long long* accepted, long long* rejected);
+
 /* Number of CUDA kernels this library has launched in the process so far (all contexts). */
 long long wbfbt_launch_count(void);
 

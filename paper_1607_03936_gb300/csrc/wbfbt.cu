@@ -17,6 +17,7 @@
 
 #include "fused.h"
 #include "kernels.h"
+#include "unet.h"
 #include "vec_ops.h"
 #include "wbfbt.h"
 
@@ -150,6 +151,11 @@ struct wbfbt_ctx {
   };
   std::vector<DenseJob> dense_jobs;   // coarsest matrices awaiting inversion in the current setup
   double* gj_work = nullptr;          // 4 x 32 x 32 pivot-block workspace
+  // learned correction
+  wbfbt_net* net = nullptr;
+  int net_mask = 0;
+  float *lx = nullptr, *ly = nullptr, *lq = nullptr, *llogmu = nullptr;
+  long long learned_acc = 0, learned_rej = 0;
 };
 
 namespace {
@@ -305,6 +311,107 @@ void kinv(wbfbt_ctx* c, int which, const T* bd, T* xd) {
   chebyshev<T>(c, M, n, P.dKw[which], P.lamKw[which], bd, xd, false, false, P.pr, P.pd);
 }
 
+// ------------------------------------------------------------------ learned correction
+
+__global__ void k_elem_logmu(Grid g, int K, const double* __restrict__ mu, float* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.ne) return;
+  const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
+  const int n = K + 1;
+  double s = 0.0;
+  for (int l = 0; l < n; ++l)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) s += log10(mu[(K * ex + i) + g.NX * ((K * ey + j) + g.NY * (K * ez + l))]);
+  out[e] = (float)(s / (n * n * n) / 4.0);
+}
+
+// q = diag(K_w)^-1/2 r   (dK holds diag(K_w)^-1)
+template <typename T>
+__global__ void k_learn_q(long long n, const T* __restrict__ dK, const T* __restrict__ r, float* __restrict__ q) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) q[i] = (float)(sqrt((double)dK[i]) * (double)r[i]);
+}
+
+// x[e] = (logmu[e], q[e][0..np) / s),  s = ||q|| / sqrt(count)
+__global__ void k_learn_pack(int ne, int np, const float* __restrict__ logmu, const float* __restrict__ q,
+                             const double* __restrict__ qnorm, long long count, float* __restrict__ x) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)ne * (np + 1)) return;
+  const int e = (int)(t / (np + 1)), c = (int)(t % (np + 1));
+  const double s = qnorm[0] / sqrt((double)count);
+  x[t] = c == 0 ? logmu[e] : (s > 0.0 ? (float)(q[(size_t)e * np + c - 1] / s) : 0.f);
+}
+
+// z = s diag(K_w)^-1/2 y
+template <typename T>
+__global__ void k_learn_unpack(long long n, const T* __restrict__ dK, const float* __restrict__ y,
+                               const double* __restrict__ qnorm, long long count, T* __restrict__ z) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double s = qnorm[0] / sqrt((double)count);
+  z[i] = T(s * sqrt((double)dK[i]) * (double)y[i]);
+}
+
+// target y = z / (s diag(K_w)^-1/2)  (0 where the diagonal entry is skipped)
+template <typename T>
+__global__ void k_learn_target(long long n, const T* __restrict__ dK, const T* __restrict__ z,
+                               const double* __restrict__ qnorm, long long count, float* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double s = qnorm[0] / sqrt((double)count);
+  const double sc = s * sqrt((double)dK[i]);
+  y[i] = sc > 0.0 ? (float)((double)z[i] / sc) : 0.f;
+}
+
+inline unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
+
+// features of residual r into c->lx, ||q|| into dsc[16]
+template <typename T>
+void learned_features(wbfbt_ctx* c, int which, const T* r, float* x) {
+  Precond<T>& P = prec<T>(c);
+  const long long n = (long long)c->g.ne * c->NP;
+  wb_count_launch(), k_learn_q<T><<<nb256(n), 256, 0, c->st>>>(n, P.dKw[which], r, c->lq);
+  CK(launch_dot<float, float>(c->lq, c->lq, n, 1, c->part, c->dsc + 16, 1, c->st));
+  wb_count_launch(), k_learn_pack<<<nb256((long long)c->g.ne * (c->NP + 1)), 256, 0, c->st>>>(
+      c->g.ne, c->NP, c->llogmu, c->lq, c->dsc + 16, n, x);
+  CK(cudaGetLastError());
+}
+
+// Learned pressure-Poisson correction with the V-cycle as fallback (kept only if it reduces ||r||).
+template <typename T>
+void kinv_learned(wbfbt_ctx* c, int which, const T* bd, T* xd) {
+  Precond<T>& P = prec<T>(c);
+  const long long n = (long long)c->g.ne * c->NP;
+  learned_features<T>(c, which, bd, c->lx);
+  if (unet_forward_into(c->net, c->lx, c->ly, c->st) != WBFBT_OK) throw WbErr{WBFBT_ERR_CUDA};
+  wb_count_launch(), k_learn_unpack<T><<<nb256(n), 256, 0, c->st>>>(n, P.dKw[which], c->ly, c->dsc + 16, n, xd);
+  CK(cudaGetLastError());
+  Epi<T> e;
+  e.mode = EPI_BMINUS;
+  e.y = P.ptmp;
+  e.b = bd;
+  op_Kw<T>(c, which, xd, e);
+  CK(launch_dot<T, T>(P.ptmp, P.ptmp, n, 1, c->part, c->dsc + 17, 1, c->st));
+  CK(launch_dot<T, T>(bd, bd, n, 1, c->part, c->dsc + 18, 1, c->st));
+  double nr[2];
+  CK(cudaMemcpyAsync(nr, c->dsc + 17, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (std::isfinite(nr[0]) && nr[0] < nr[1]) {
+    ++c->learned_acc;
+  } else {
+    ++c->learned_rej;
+    kinv<T>(c, which, bd, xd);
+  }
+}
+
+template <typename T>
+void kinv_any(wbfbt_ctx* c, int which, const T* bd, T* xd) {
+  if (c->net && ((c->net_mask >> which) & 1))
+    kinv_learned<T>(c, which, bd, xd);
+  else
+    kinv<T>(c, which, bd, xd);
+}
+
 template <typename T>
 void project(wbfbt_ctx* c, const T* src, T* dst) {
   CK(launch_project_pressure<T>(c->g.ne, c->NP, src, dst, c->part, c->dsc + 1, c->st));
@@ -315,7 +422,7 @@ template <typename T>
 void schur_inv(wbfbt_ctx* c, const T* r, T* y) {
   Precond<T>& P = prec<T>(c);
   project<T>(c, r, P.sr);
-  kinv<T>(c, 1, P.sr, P.sy);
+  kinv_any<T>(c, 1, P.sr, P.sy);
   // middle factor B C^-1 A D^-1 B^T y, each diagonal scaling fused into the preceding node pass
   CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_BT, nullptr, nullptr, P.sy, nullptr, 0, P.Ye, Epi<T>(), c->st));
   CK(launch_gather<T>(c->g, c->k, 3, 1, P.Ye, epi_scale<T>(P.sv1, P.dinvw), c->st));
@@ -323,7 +430,7 @@ void schur_inv(wbfbt_ctx* c, const T* r, T* y) {
   CK(launch_gather<T>(c->g, c->k, 3, 1, P.Ye, epi_scale<T>(P.sv2, P.cinv), c->st));
   CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_B, P.sv2, nullptr, nullptr, nullptr, 0, nullptr,
                            epi_store<T>(P.sz), c->st));
-  kinv<T>(c, 0, P.sz, P.sy2);
+  kinv_any<T>(c, 0, P.sz, P.sy2);
   project<T>(c, P.sy2, y);
 }
 
@@ -624,7 +731,7 @@ void precond_graphed(wbfbt_ctx* c, const double* v, double* z) {
 }
 
 void precond_any(wbfbt_ctx* c, const double* v, double* z) {
-  if (c->opt.use_graphs) {
+  if (c->opt.use_graphs && c->net == nullptr) {
     if (c->mixed)
       precond_graphed<float>(c, v, z);
     else
@@ -763,6 +870,8 @@ void run_setup(wbfbt_ctx* cp, const double* mu_nodes) {
   else
     build_precond<double>(cp);
   cp->graph_dirty = true;   // Chebyshev coefficients are baked into the captured launches
+  wb_count_launch(), k_elem_logmu<<<(unsigned)((g.ne + 127) / 128), 128, 0, cp->st>>>(g, cp->k, cp->mu64, cp->llogmu);
+  CK(cudaGetLastError());
 }
 
 }  // namespace
@@ -873,6 +982,10 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
     cp->Ye32 = cp->pool.get<float>((size_t)3 * g.ne * cp->N3);
     cp->ot64 = make_device_optab<double>(cp, g);
     cp->ot32 = make_device_optab<float>(cp, g);
+    cp->lx = cp->pool.get<float>((size_t)g.ne * (cp->NP + 1));
+    cp->ly = cp->pool.get<float>((size_t)g.ne * cp->NP);
+    cp->lq = cp->pool.get<float>((size_t)g.ne * cp->NP);
+    cp->llogmu = cp->pool.get<float>((size_t)g.ne);
     CK(launch_lumped_mass(g, cp->k, cp->dtab, cp->lm, cp->st));
     run_setup(cp, mu_nodes);
     const long long n = cp->ntot;
@@ -890,6 +1003,45 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
   });
   if (status != WBFBT_OK) return status;
   *out = c.release();
+  return WBFBT_OK;
+}
+
+int wbfbt_attach_net(wbfbt_ctx* c, wbfbt_net* net, int which_mask) {
+  if (!c) return WBFBT_ERR_INVALID;
+  if (net) {
+    if (unet_grid(net) != c->g.nx || c->g.nx != c->g.ny || c->g.nx != c->g.nz || unet_channels_in(net) != 1 + c->NP ||
+        unet_channels_out(net) != c->NP || (which_mask & ~3))
+      return WBFBT_ERR_INVALID;
+  }
+  c->net = net;
+  c->net_mask = net ? which_mask : 0;
+  return WBFBT_OK;
+}
+
+int wbfbt_learned_sample(wbfbt_ctx* c, int which, const double* r, float* x_out, float* y_out) {
+  if (!c || !r || !x_out || !y_out || (which != 0 && which != 1)) return WBFBT_ERR_INVALID;
+  return guarded_ctx(c, [&]() {
+    const long long n = (long long)c->g.ne * c->NP;
+    auto run = [&](auto tag) {
+      using T = decltype(tag);
+      Precond<T>& P = prec<T>(c);
+      CK((launch_cast<double, T>(n, r, P.pb, c->st)));
+      kinv<T>(c, which, P.pb, P.px);
+      learned_features<T>(c, which, P.pb, x_out);
+      wb_count_launch(), k_learn_target<T><<<nb256(n), 256, 0, c->st>>>(n, P.dKw[which], P.px, c->dsc + 16, n, y_out);
+      CK(cudaGetLastError());
+    };
+    if (c->mixed)
+      run(float());
+    else
+      run(double());
+  });
+}
+
+int wbfbt_learned_stats(const wbfbt_ctx* c, long long* accepted, long long* rejected) {
+  if (!c) return WBFBT_ERR_INVALID;
+  if (accepted) *accepted = c->learned_acc;
+  if (rejected) *rejected = c->learned_rej;
   return WBFBT_OK;
 }
 

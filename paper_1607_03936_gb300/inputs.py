@@ -52,6 +52,22 @@ def uniform_vector(seed: int, size: int, lo: float = -1.0, hi: float = 1.0) -> n
     return np.random.default_rng(seed).uniform(lo, hi, size)
 
 
+def unet_init_params(seed: int, cin: int, cout: int, scale: float = 1.0) -> np.ndarray:
+    """He-normal initial U-Net parameters (weights N(0, 2 / (27 cin)), biases 0), flat float32.
+
+    Layer order and shapes follow the parameter layout of the learned correction
+    (c1..c11, W[27][cin][cout] then b[cout]).
+    """
+    chans = [(cin, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (96, 32), (32, 32), (48, 16),
+             (16, 16), (16, cout)]
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in chans:
+        parts.append(rng.standard_normal(27 * ci * co) * np.sqrt(2.0 / (27 * ci)) * scale)
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
+
+
 # Workload definitions: the multi-sinker problems of Sec. 2.1 at the sizes the
 # tests and the bench run.  omega is the sinker diameter, delta the Gaussian
 # decay, dr the dynamic ratio max(mu)/min(mu).

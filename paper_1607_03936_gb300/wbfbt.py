@@ -23,7 +23,11 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "non-finite val
 SYMBOLS = ["wbfbt_default_opts", "wbfbt_sinker_setup", "wbfbt_create", "wbfbt_setup", "wbfbt_apply_A", "wbfbt_apply_B",
            "wbfbt_apply_BT", "wbfbt_apply_K", "wbfbt_apply_Kw", "wbfbt_apply_Ainv", "wbfbt_apply_Kinv",
            "wbfbt_apply_schur_inv", "wbfbt_apply_precond", "wbfbt_solve", "wbfbt_sizes", "wbfbt_device_bytes", "wbfbt_launch_count",
-           "wbfbt_destroy", "wbfbt_status_string", "wbfbt_apply_Kw_noalloc"]
+           "wbfbt_destroy", "wbfbt_status_string", "wbfbt_apply_Kw_noalloc",
+           "wbfbt_net_num_params", "wbfbt_net_create", "wbfbt_net_set_params", "wbfbt_net_get_params",
+           "wbfbt_net_param_count", "wbfbt_net_forward", "wbfbt_net_loss_grad", "wbfbt_net_adam_step",
+           "wbfbt_net_save", "wbfbt_net_load", "wbfbt_net_destroy", "wbfbt_attach_net", "wbfbt_learned_sample",
+           "wbfbt_learned_stats"]
 NOALLOC_MAX_NODES = 1 << 19
 
 
@@ -74,6 +78,23 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.wbfbt_destroy.argtypes = [vp]
     lib.wbfbt_destroy.restype = None
     lib.wbfbt_apply_Kw_noalloc.argtypes = [ctypes.POINTER(Mesh), i, vp, d, vp, vp, vp]
+    lib.wbfbt_net_num_params.argtypes = [i, i]
+    lib.wbfbt_net_num_params.restype = ctypes.c_longlong
+    lib.wbfbt_net_create.argtypes = [i, i, i, i, vp, ctypes.POINTER(vp)]
+    lib.wbfbt_net_set_params.argtypes = [vp, vp]
+    lib.wbfbt_net_get_params.argtypes = [vp, vp]
+    lib.wbfbt_net_param_count.argtypes = [vp]
+    lib.wbfbt_net_param_count.restype = ctypes.c_longlong
+    lib.wbfbt_net_forward.argtypes = [vp, vp, i, vp]
+    lib.wbfbt_net_loss_grad.argtypes = [vp, vp, vp, i, ctypes.POINTER(d), vp]
+    lib.wbfbt_net_adam_step.argtypes = [vp, ctypes.c_float]
+    lib.wbfbt_net_save.argtypes = [vp, ctypes.c_char_p]
+    lib.wbfbt_net_load.argtypes = [vp, ctypes.c_char_p]
+    lib.wbfbt_net_destroy.argtypes = [vp]
+    lib.wbfbt_net_destroy.restype = None
+    lib.wbfbt_attach_net.argtypes = [vp, vp, i]
+    lib.wbfbt_learned_sample.argtypes = [vp, i, vp, vp, vp]
+    lib.wbfbt_learned_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.wbfbt_status_string.argtypes = [i]
     lib.wbfbt_status_string.restype = ctypes.c_char_p
     return lib   # every other entry point returns int, ctypes' default
@@ -189,6 +210,23 @@ class Solver:
         self._mu = mu.contiguous()
         _check(lib().wbfbt_setup(self.h, _ptr(self._mu)), "wbfbt_setup")
 
+    def attach_net(self, net: "Net | None", which_mask: int = 2):
+        """Use `net` for K_r (bit 1) and/or K_l (bit 0) inside S~^-1, V-cycle as fallback."""
+        _check(lib().wbfbt_attach_net(self.h, net.h if net is not None else None, which_mask), "wbfbt_attach_net")
+        self._net = net
+
+    def learned_sample(self, which: int, r: torch.Tensor):
+        """(features [E][1+Np], target [E][Np]) for pressure residual r (FP64 device, mean-free)."""
+        x = torch.empty((self.n_elem, 1 + self.np), dtype=torch.float32, device=r.device)
+        y = torch.empty((self.n_elem, self.np), dtype=torch.float32, device=r.device)
+        _check(lib().wbfbt_learned_sample(self.h, which, _ptr(r), _ptr(x), _ptr(y)), "wbfbt_learned_sample")
+        return x, y
+
+    def learned_stats(self):
+        a, r = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib().wbfbt_learned_stats(self.h, ctypes.byref(a), ctypes.byref(r)), "wbfbt_learned_stats")
+        return a.value, r.value
+
     def close(self):
         if getattr(self, "h", None):
             lib().wbfbt_destroy(self.h)
@@ -250,3 +288,64 @@ class Solver:
         if check and st not in (0, -5):
             _check(st, "wbfbt_solve")
         return u, p, SolveResult(its.value, rel.value, st)
+
+
+class Net:
+    """The learned pressure-Poisson correction (a BF16 tensor-core U-Net), owning a wbfbt_net."""
+
+    def __init__(self, cin: int, cout: int, n: int, max_batch: int = 1):
+        self.cin, self.cout, self.n, self.max_batch = cin, cout, n, max_batch
+        h = ctypes.c_void_p()
+        _check(lib().wbfbt_net_create(cin, cout, n, max_batch, _stream(), ctypes.byref(h)), "wbfbt_net_create")
+        self.h = h
+        self.n_params = lib().wbfbt_net_param_count(h)
+
+    @staticmethod
+    def num_params(cin: int, cout: int) -> int:
+        return lib().wbfbt_net_num_params(cin, cout)
+
+    def set_params(self, theta: torch.Tensor):
+        theta = theta.to(torch.float32).contiguous()
+        _check(lib().wbfbt_net_set_params(self.h, _ptr(theta)), "wbfbt_net_set_params")
+        torch.cuda.synchronize()
+
+    def get_params(self) -> torch.Tensor:
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(lib().wbfbt_net_get_params(self.h, _ptr(out)), "wbfbt_net_get_params")
+        return out
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        x = x.contiguous()
+        batch = x.shape[0] if x.dim() == 3 else 1
+        y = torch.empty((batch, self.n ** 3, self.cout), dtype=torch.float32, device=x.device)
+        _check(lib().wbfbt_net_forward(self.h, _ptr(x), batch, _ptr(y)), "wbfbt_net_forward")
+        return y
+
+    def loss_grad(self, x: torch.Tensor, target: torch.Tensor, want_grad: bool = True):
+        x, target = x.contiguous(), target.contiguous()
+        batch = x.shape[0] if x.dim() == 3 else 1
+        loss = ctypes.c_double()
+        g = torch.empty(self.n_params, dtype=torch.float32, device=x.device) if want_grad else None
+        _check(lib().wbfbt_net_loss_grad(self.h, _ptr(x), _ptr(target), batch, ctypes.byref(loss),
+                                         _ptr(g) if g is not None else None), "wbfbt_net_loss_grad")
+        return loss.value, g
+
+    def adam_step(self, lr: float):
+        _check(lib().wbfbt_net_adam_step(self.h, lr), "wbfbt_net_adam_step")
+
+    def save(self, path: str):
+        _check(lib().wbfbt_net_save(self.h, path.encode()), "wbfbt_net_save")
+
+    def load(self, path: str):
+        _check(lib().wbfbt_net_load(self.h, path.encode()), "wbfbt_net_load")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().wbfbt_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,141 @@
+"""GPU parity of the learned correction: BF16 tensor-core U-Net vs the FP64 NumPy oracle.
+
+Tolerances follow from BF16 storage of weights and activations (8-bit mantissa) with FP32
+accumulation: forward 3e-2 relative (L2), gradients 8e-2 relative (L2), loss 2e-2.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mesh as M
+from oracle import multigrid as mg
+from oracle import operators as op
+from oracle import sinker
+from oracle import unet
+from oracle import wbfbt as W
+from paper_1607_03936_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+CIN, COUT, N = 5, 4, 8
+
+
+@pytest.fixture(scope="module")
+def wb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_03936_gb300 import build
+    build.build()
+    from paper_1607_03936_gb300 import wbfbt
+    return wbfbt
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def _case(seed, batch=1):
+    theta = inputs.unet_init_params(seed, CIN, COUT)
+    rng = np.random.default_rng(seed + 1)
+    x = rng.standard_normal((batch, N, N, N, CIN)).astype(np.float32)
+    t = rng.standard_normal((batch, N, N, N, COUT)).astype(np.float32)
+    return theta, x, t
+
+
+def test_forward_matches_oracle(wb):
+    theta, x, _ = _case(0)
+    net = wb.Net(CIN, COUT, N)
+    net.set_params(torch.tensor(theta, device="cuda"))
+    y = net.forward(torch.tensor(x.reshape(1, -1, CIN), device="cuda")).cpu().numpy().reshape(N, N, N, COUT)
+    ref, _ = unet.forward(theta.astype(np.float64), x[0].astype(np.float64), CIN, COUT)
+    assert rel(y, ref) < 3e-2
+
+
+def test_loss_and_gradients_match_oracle(wb):
+    theta, x, t = _case(1, batch=2)
+    net = wb.Net(CIN, COUT, N, max_batch=2)
+    net.set_params(torch.tensor(theta, device="cuda"))
+    loss, g = net.loss_grad(torch.tensor(x.reshape(2, -1, CIN), device="cuda"),
+                            torch.tensor(t.reshape(2, -1, COUT), device="cuda"))
+    # oracle: the batch mean of per-sample MSEs equals the MSE over the batch
+    ref_l, ref_g = 0.0, 0.0
+    for b in range(2):
+        lb, gb = unet.loss_and_grad(theta.astype(np.float64), x[b].astype(np.float64), t[b].astype(np.float64),
+                                    CIN, COUT)
+        ref_l += lb / 2
+        ref_g = ref_g + gb / 2
+    assert abs(loss - ref_l) / ref_l < 2e-2
+    g = g.cpu().numpy()
+    assert rel(g, ref_g) < 8e-2
+    # per layer, so that a dropped layer or a transposed weight shows up
+    off = 0
+    for name, ci, co in unet.layer_shapes(CIN, COUT):
+        nw = 27 * ci * co
+        assert rel(g[off:off + nw], ref_g[off:off + nw]) < 1.5e-1, name
+        off += nw + co
+
+
+def test_adam_step_and_checkpoint_roundtrip(wb):
+    theta, x, t = _case(2)
+    net = wb.Net(CIN, COUT, N)
+    net.set_params(torch.tensor(theta, device="cuda"))
+    _, g = net.loss_grad(torch.tensor(x.reshape(1, -1, CIN), device="cuda"),
+                         torch.tensor(t.reshape(1, -1, COUT), device="cuda"))
+    net.adam_step(1e-3)
+    got = net.get_params().cpu().numpy()
+    want, _, _ = unet.adam_step(theta.astype(np.float64), 0.0, 0.0, g.cpu().numpy().astype(np.float64), 1, 1e-3)
+    np.testing.assert_allclose(got, want, rtol=1e-5, atol=1e-7)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "net.bin")
+        net.save(path)
+        other = wb.Net(CIN, COUT, N)
+        other.load(path)
+        assert torch.equal(other.get_params(), net.get_params())
+
+
+def test_learned_sample_matches_oracle_vcycle(wb):
+    n, k = 8, 2
+    m = M.Mesh(n, n, n, k)
+    c = inputs.sinker_centres(5, 8)
+    X = m.node_coords()
+    mu = sinker.viscosity(X, c, 0.1, 200.0, 1e6)
+    s = wb.Solver(n, k, torch.tensor(mu, device="cuda"), a_r=2.0)
+    r = op.project_pressure(m, inputs.normal_vector(6, m.n_p))
+    xg, yg = s.learned_sample(1, torch.tensor(r, device="cuda"))
+    prob = W.StokesProblem(m, mu, a_l=1.0, a_r=2.0)
+    pp = mg.PressurePoissonMG(m, prob.B, prob.Ddiag, mu, 2.0)
+    z = pp.apply(r)
+    dsq = np.sqrt(pp.dinv)
+    q = dsq * r
+    sc = np.linalg.norm(q) / np.sqrt(q.size)
+    logmu = np.log10(op.point_values(m, mu)).mean(axis=1) / 4.0
+    xo = np.concatenate([logmu[:, None], (q / sc).reshape(-1, m.Np)], axis=1)
+    yo = (z / (sc * dsq)).reshape(-1, m.Np)
+    assert rel(xg.cpu().numpy(), xo) < 1e-6
+    assert rel(yg.cpu().numpy(), yo) < 1e-6
+
+
+def test_solver_with_attached_net_falls_back_and_converges(wb):
+    n, k = 8, 2
+    m = M.Mesh(n, n, n, k)
+    c = inputs.sinker_centres(0, 4)
+    X = m.node_coords()
+    mu = sinker.viscosity(X, c, 0.1, 200.0, 1e4)
+    f = sinker.forcing(X, c, 0.1, 200.0)
+    ft = torch.tensor(f.T.ravel(), device="cuda")
+    plain = wb.Solver(n, k, torch.tensor(mu, device="cuda"))
+    _, _, r0 = plain.solve(ft)
+    s = wb.Solver(n, k, torch.tensor(mu, device="cuda"))
+    net = wb.Net(1 + s.np, s.np, n)
+    net.set_params(torch.tensor(inputs.unet_init_params(3, 1 + s.np, s.np), device="cuda"))
+    s.attach_net(net, 2)
+    _, _, r1 = s.solve(ft)
+    acc, rej = s.learned_stats()
+    assert r1.status == 0 and r1.rel_res <= 1e-6
+    assert acc + rej >= r1.iters          # one learned attempt per K_r application
+    if acc == 0:                           # all rejected: exactly the plain method
+        assert r1.iters == r0.iters
