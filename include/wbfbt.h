@@ -200,10 +200,11 @@ void wbfbt_net_destroy(wbfbt_net* net);
  * `which_mask` for K_r = B D^-1 B^T, bit 0 for K_l = B C^-1 B^T.  Each application builds the
  * features x[e] = (mean log10 mu over the element's nodes / 4, q_e / s), q = diag(K_w)^-1/2 r,
  * s = rms(q), runs the net, forms z = s diag(K_w)^-1/2 y, and keeps z only if
- * ||r - K_w z|| < ||r||; otherwise it runs the V-cycle (the fallback).  The net's grid must be
+ * ||r - K_w z|| < accept_ratio ||r|| (0 < accept_ratio <= 1; 1 keeps every step that reduces
+ * the residual); otherwise it runs the V-cycle (the fallback).  The net's grid must be
  * the element grid (nx = ny = nz = n) and cin = 1 + Np, cout = Np.  While a net is attached
  * the preconditioner is not replayed as a graph (the acceptance test is a host decision). */
-int wbfbt_attach_net(wbfbt_ctx* ctx, wbfbt_net* net, int which_mask);
+int wbfbt_attach_net(wbfbt_ctx* ctx, wbfbt_net* net, int which_mask, double accept_ratio);
 /* A training pair from the solver itself: for a pressure residual r [E][Np] (FP64 device,
  * mean-free), x_out [E][1+Np] are the features above and y_out [E][Np] the V-cycle
  * correction z = K~_w^-1 r in the net's output units (y = z / (s diag(K_w)^-1/2)). */

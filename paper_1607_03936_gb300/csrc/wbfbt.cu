@@ -154,6 +154,7 @@ struct wbfbt_ctx {
   // learned correction
   wbfbt_net* net = nullptr;
   int net_mask = 0;
+  double net_accept = 1.0;
   float *lx = nullptr, *ly = nullptr, *lq = nullptr, *llogmu = nullptr;
   long long learned_acc = 0, learned_rej = 0;
 };
@@ -396,7 +397,7 @@ void kinv_learned(wbfbt_ctx* c, int which, const T* bd, T* xd) {
   double nr[2];
   CK(cudaMemcpyAsync(nr, c->dsc + 17, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  if (std::isfinite(nr[0]) && nr[0] < nr[1]) {
+  if (std::isfinite(nr[0]) && nr[0] < c->net_accept * nr[1]) {
     ++c->learned_acc;
   } else {
     ++c->learned_rej;
@@ -1006,8 +1007,8 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
   return WBFBT_OK;
 }
 
-int wbfbt_attach_net(wbfbt_ctx* c, wbfbt_net* net, int which_mask) {
-  if (!c) return WBFBT_ERR_INVALID;
+int wbfbt_attach_net(wbfbt_ctx* c, wbfbt_net* net, int which_mask, double accept_ratio) {
+  if (!c || !(accept_ratio > 0.0 && accept_ratio <= 1.0)) return WBFBT_ERR_INVALID;
   if (net) {
     if (unet_grid(net) != c->g.nx || c->g.nx != c->g.ny || c->g.nx != c->g.nz || unet_channels_in(net) != 1 + c->NP ||
         unet_channels_out(net) != c->NP || (which_mask & ~3))
@@ -1015,6 +1016,7 @@ int wbfbt_attach_net(wbfbt_ctx* c, wbfbt_net* net, int which_mask) {
   }
   c->net = net;
   c->net_mask = net ? which_mask : 0;
+  c->net_accept = accept_ratio;
   return WBFBT_OK;
 }
 

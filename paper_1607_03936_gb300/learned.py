@@ -86,7 +86,7 @@ def train(n=32, k=2, n_fields=100, per_field=20, epochs=20, batch=4, lr=1e-3, se
     return net, {"pairs": P, "data_s": t_data, "train_s": time.time() - t1, "steps": steps, "loss_hist": hist}
 
 
-def evaluate(net, n=32, k=2, seeds=range(5000, 5020), omega=0.1, delta=200.0, log=print):
+def evaluate(net, n=32, k=2, seeds=range(5000, 5020), omega=0.1, delta=200.0, accept_ratio=1.0, log=print):
     """FGMRES with and without the net on held-out problems (mixed precision)."""
     rows = []
     for s in seeds:
@@ -97,7 +97,7 @@ def evaluate(net, n=32, k=2, seeds=range(5000, 5020), omega=0.1, delta=200.0, lo
         for tag in ("vcycle", "learned"):
             solver = wb.Solver(n, k, mu, precision=wb.MIXED)
             if tag == "learned":
-                solver.attach_net(net, 2)
+                solver.attach_net(net, 2, accept_ratio)
             solver.solve(f)                                    # warm-up
             torch.cuda.synchronize()
             t0 = time.time()
@@ -128,21 +128,23 @@ def main():
     t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--out", required=True)
     t.add_argument("--evaluate", type=int, default=0, help="held-out seeds to evaluate after training")
+    t.add_argument("--accept", type=float, default=1.0, help="keep a learned step if it leaves < accept x ||r||")
     e = sub.add_parser("evaluate")
     e.add_argument("--ckpt", required=True)
     e.add_argument("--n", type=int, default=32)
     e.add_argument("--seeds", type=int, default=20)
+    e.add_argument("--accept", type=float, default=1.0)
     a = ap.parse_args()
     if a.cmd == "train":
         net, info = train(n=a.n, n_fields=a.fields, per_field=a.per_field, epochs=a.epochs, batch=a.batch, lr=a.lr)
         net.save(a.out)
         print(json.dumps({"train": info}))
         if a.evaluate:
-            evaluate(net, n=a.n, seeds=range(5000, 5000 + a.evaluate))
+            evaluate(net, n=a.n, seeds=range(5000, 5000 + a.evaluate), accept_ratio=a.accept)
     else:
         net = wb.Net(5, 4, a.n)
         net.load(a.ckpt)
-        evaluate(net, n=a.n, seeds=range(5000, 5000 + a.seeds))
+        evaluate(net, n=a.n, seeds=range(5000, 5000 + a.seeds), accept_ratio=a.accept)
 
 
 if __name__ == "__main__":

@@ -92,7 +92,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.wbfbt_net_load.argtypes = [vp, ctypes.c_char_p]
     lib.wbfbt_net_destroy.argtypes = [vp]
     lib.wbfbt_net_destroy.restype = None
-    lib.wbfbt_attach_net.argtypes = [vp, vp, i]
+    lib.wbfbt_attach_net.argtypes = [vp, vp, i, d]
     lib.wbfbt_learned_sample.argtypes = [vp, i, vp, vp, vp]
     lib.wbfbt_learned_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.wbfbt_status_string.argtypes = [i]
@@ -210,9 +210,13 @@ class Solver:
         self._mu = mu.contiguous()
         _check(lib().wbfbt_setup(self.h, _ptr(self._mu)), "wbfbt_setup")
 
-    def attach_net(self, net: "Net | None", which_mask: int = 2):
-        """Use `net` for K_r (bit 1) and/or K_l (bit 0) inside S~^-1, V-cycle as fallback."""
-        _check(lib().wbfbt_attach_net(self.h, net.h if net is not None else None, which_mask), "wbfbt_attach_net")
+    def attach_net(self, net: "Net | None", which_mask: int = 2, accept_ratio: float = 1.0):
+        """Use `net` for K_r (bit 1) and/or K_l (bit 0) inside S~^-1, V-cycle as fallback.
+
+        A learned step is kept only if it leaves ||r - K_w z|| < accept_ratio ||r||.
+        """
+        _check(lib().wbfbt_attach_net(self.h, net.h if net is not None else None, which_mask, accept_ratio),
+               "wbfbt_attach_net")
         self._net = net
 
     def learned_sample(self, which: int, r: torch.Tensor):
