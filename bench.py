@@ -164,6 +164,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# --------------------------------------------------------------------------- multi-rank helpers
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Replicas: rank r solves the seeded problem base_seed + r (no data-path collective)."""
+    return base_seed + rank
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Max of a per-rank timing over all ranks (the job's step time); identity for one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def traffic_for(kernel: str):
@@ -193,7 +211,7 @@ def run_ours(args, cfg, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     n, k = cfg["n"], cfg["k"]
-    seed = cfg["seed"] + rank                  # replicas: each rank solves its own seeded problem
+    seed = replica_seed(cfg["seed"], rank)
     centres = inputs.sinker_centres(seed, cfg["n_sinkers"])
     mu, f = wb.sinker_setup(n, k, centres, cfg["omega"], cfg["delta"], cfg["dr"])
     precision = wb.MIXED if args.precision == "mixed" else wb.F64
@@ -245,11 +263,7 @@ def run_ours(args, cfg, rank, world):
         dist.barrier()
     launches = wb.launch_count() - launches0
     clk = clocks.stop() if clocks else None
-    t_step = statistics.mean(times)
-    t = torch.tensor([t_step], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_step = float(t.item())
+    t_step = max_over_ranks(statistics.mean(times), world, dev)
 
     # dominant kernel: the fine-level A apply, timed on the launching stream with CUDA events
     xk = torch.randn(solver.n_u, dtype=torch.float64, device=dev)

@@ -87,14 +87,22 @@ k_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, co
     const T Wq = st.W3[q];
     if (DA) {
       T G[3][3];
+      T rx[N], ry[N], rz[N];   // this point's derivative rows, held in registers
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        rx[a] = st.Ds[0][i][a];
+        ry[a] = st.Ds[1][j][a];
+        rz[a] = st.Ds[2][l][a];
+      }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         T a0 = 0, a1 = 0, a2 = 0;
+        const T* uc = su[GRAD ? le : 0][c];
 #pragma unroll
         for (int a = 0; a < N; ++a) {
-          a0 += st.Ds[0][i][a] * su[GRAD ? le : 0][c][a + N * (j + N * l)];
-          a1 += st.Ds[1][j][a] * su[GRAD ? le : 0][c][i + N * (a + N * l)];
-          a2 += st.Ds[2][l][a] * su[GRAD ? le : 0][c][i + N * (j + N * a)];
+          a0 += rx[a] * uc[a + N * (j + N * l)];
+          a1 += ry[a] * uc[i + N * (a + N * l)];
+          a2 += rz[a] * uc[i + N * (j + N * a)];
         }
         G[c][0] = a0;
         G[c][1] = a1;
@@ -153,6 +161,13 @@ k_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, co
   if (SCAT) {
     const T* S = &sS[SCAT ? le : 0][0][0];
     T* out = Ye + (size_t)e * 3 * N3 + q;
+    T cx[N], cy[N], cz[N];   // this point's derivative columns (transposed apply)
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      cx[a] = st.Ds[0][a][i];
+      cy[a] = st.Ds[1][a][j];
+      cz[a] = st.Ds[2][a][l];
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       T acc = 0;
@@ -160,9 +175,9 @@ k_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, co
         const int i0 = sym_index(c, 0), i1 = sym_index(c, 1), i2 = sym_index(c, 2);
 #pragma unroll
         for (int a = 0; a < N; ++a) {
-          acc += st.Ds[0][a][i] * S[i0 * N3 + a + N * (j + N * l)];
-          acc += st.Ds[1][a][j] * S[i1 * N3 + i + N * (a + N * l)];
-          acc += st.Ds[2][a][l] * S[i2 * N3 + i + N * (j + N * a)];
+          acc += cx[a] * S[i0 * N3 + a + N * (j + N * l)];
+          acc += cy[a] * S[i1 * N3 + i + N * (a + N * l)];
+          acc += cz[a] * S[i2 * N3 + i + N * (j + N * a)];
         }
       } else {
 #pragma unroll
@@ -196,6 +211,7 @@ k_elem_poisson(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict
     su[le][q] = u[(K * ex + i) + g.NX * ((K * ey + j) + g.NY * (K * ez + l))];
   }
   __syncthreads();
+  T cx[N], cy[N], cz[N];
   if (act) {
     T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
@@ -203,6 +219,9 @@ k_elem_poisson(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict
       a0 += st.Ds[0][i][a] * su[le][a + N * (j + N * l)];
       a1 += st.Ds[1][j][a] * su[le][i + N * (a + N * l)];
       a2 += st.Ds[2][l][a] * su[le][i + N * (j + N * a)];
+      cx[a] = st.Ds[0][a][i];
+      cy[a] = st.Ds[1][a][j];
+      cz[a] = st.Ds[2][a][l];
     }
     const T f = st.W3[q] * coef[(size_t)e * N3 + q];
     sF[le][0][q] = f * a0;
@@ -214,9 +233,9 @@ k_elem_poisson(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict
   T acc = 0;
 #pragma unroll
   for (int a = 0; a < N; ++a) {
-    acc += st.Ds[0][a][i] * sF[le][0][a + N * (j + N * l)];
-    acc += st.Ds[1][a][j] * sF[le][1][i + N * (a + N * l)];
-    acc += st.Ds[2][a][l] * sF[le][2][i + N * (j + N * a)];
+    acc += cx[a] * sF[le][0][a + N * (j + N * l)];
+    acc += cy[a] * sF[le][1][i + N * (a + N * l)];
+    acc += cz[a] * sF[le][2][i + N * (j + N * a)];
   }
   Ye[(size_t)e * N3 + q] = acc;
 }

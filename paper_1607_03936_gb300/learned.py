@@ -34,8 +34,41 @@ def problem_draw(seed: int):
     return inputs.sinker_centres(seed, ns), dr
 
 
-def make_pairs(n: int, k: int, n_fields: int, per_field: int, seed0: int, omega=0.1, delta=200.0):
-    """(x [P][n^3][1+Np], y [P][n^3][Np]) device tensors from n_fields viscosity fields."""
+def smooth_pressure(n: int, np_: int, seed: int) -> np.ndarray:
+    """A smooth random pressure field on the element grid as P_{k-1} coefficients [n^3][Np]:
+    a sum of cosines of wave numbers 0..3 per axis, the constant mode taking the value at the
+    element centre and the three linear modes its derivatives times h/2."""
+    rng = np.random.default_rng(seed)
+    c = (np.arange(n) + 0.5) / n
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    val = np.zeros_like(X)
+    gx, gy, gz = np.zeros_like(X), np.zeros_like(X), np.zeros_like(X)
+    for kz in range(4):
+        for ky in range(4):
+            for kx in range(4):
+                if kx + ky + kz == 0:
+                    continue
+                a = rng.standard_normal() / (kx * kx + ky * ky + kz * kz)
+                cx, cy, cz = np.cos(np.pi * kx * X), np.cos(np.pi * ky * Y), np.cos(np.pi * kz * Z)
+                val += a * cx * cy * cz
+                gx += -a * np.pi * kx * np.sin(np.pi * kx * X) * cy * cz
+                gy += -a * np.pi * ky * cx * np.sin(np.pi * ky * Y) * cz
+                gz += -a * np.pi * kz * cx * cy * np.sin(np.pi * kz * Z)
+    out = np.zeros((n ** 3, np_))
+    h = 1.0 / n
+    out[:, 0] = val.ravel()
+    if np_ >= 4:
+        out[:, 1], out[:, 2], out[:, 3] = gx.ravel() * h / 2, gy.ravel() * h / 2, gz.ravel() * h / 2
+    return out.ravel()
+
+
+def make_pairs(n: int, k: int, n_fields: int, per_field: int, seed0: int, omega=0.1, delta=200.0,
+               smooth_fraction: float = 0.0):
+    """(x [P][n^3][1+Np], y [P][n^3][Np]) device tensors from n_fields viscosity fields.
+
+    A fraction of the residuals is r = K_w z for a smooth random pressure z (the low-frequency
+    residuals FGMRES feeds the preconditioner late in a solve), the rest standard normal.
+    """
     xs, ys = [], []
     solver = None
     for f in range(n_fields):
@@ -46,7 +79,13 @@ def make_pairs(n: int, k: int, n_fields: int, per_field: int, seed0: int, omega=
         else:
             solver.setup(mu)
         for j in range(per_field):
-            r = torch.tensor(inputs.normal_vector(1_000_003 * (seed0 + f) + j, solver.n_p), device="cuda")
+            sd = 1_000_003 * (seed0 + f) + j
+            if j < int(round(smooth_fraction * per_field)):
+                z = torch.tensor(smooth_pressure(n, solver.np, sd), device="cuda")
+                r = solver.apply_Kw(1, z) if solver.precision == wb.F64 else \
+                    solver.apply_Kw(1, z.float()).double()
+            else:
+                r = torch.tensor(inputs.normal_vector(sd, solver.n_p), device="cuda")
             r = r.view(-1, solver.np)
             r[:, 0] -= r[:, 0].mean()                         # mean-free (constant mode)
             x, y = solver.learned_sample(1, r.reshape(-1).contiguous())
@@ -57,9 +96,9 @@ def make_pairs(n: int, k: int, n_fields: int, per_field: int, seed0: int, omega=
 
 
 def train(n=32, k=2, n_fields=100, per_field=20, epochs=20, batch=4, lr=1e-3, seed=1000, init_seed=7,
-          log=print):
+          smooth_fraction=0.0, log=print):
     t0 = time.time()
-    x, y = make_pairs(n, k, n_fields, per_field, seed)
+    x, y = make_pairs(n, k, n_fields, per_field, seed, smooth_fraction=smooth_fraction)
     torch.cuda.synchronize()
     t_data = time.time() - t0
     npe = k * (k + 1) * (k + 2) // 6
@@ -129,6 +168,7 @@ def main():
     t.add_argument("--out", required=True)
     t.add_argument("--evaluate", type=int, default=0, help="held-out seeds to evaluate after training")
     t.add_argument("--accept", type=float, default=1.0, help="keep a learned step if it leaves < accept x ||r||")
+    t.add_argument("--smooth", type=float, default=0.0, help="fraction of smooth (K_w z) residuals")
     e = sub.add_parser("evaluate")
     e.add_argument("--ckpt", required=True)
     e.add_argument("--n", type=int, default=32)
@@ -136,7 +176,8 @@ def main():
     e.add_argument("--accept", type=float, default=1.0)
     a = ap.parse_args()
     if a.cmd == "train":
-        net, info = train(n=a.n, n_fields=a.fields, per_field=a.per_field, epochs=a.epochs, batch=a.batch, lr=a.lr)
+        net, info = train(n=a.n, n_fields=a.fields, per_field=a.per_field, epochs=a.epochs, batch=a.batch, lr=a.lr,
+                          smooth_fraction=a.smooth)
         net.save(a.out)
         print(json.dumps({"train": info}))
         if a.evaluate:
