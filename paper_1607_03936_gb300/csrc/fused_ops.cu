@@ -42,24 +42,23 @@ __device__ inline void epi_apply(const Epi<T>& E, size_t i, int node, T v) {
   }
 }
 
+// One batch of EPB elements (eb); every thread of the block reaches every barrier.
 template <typename T, int N, int OPS>
-__global__ void __launch_bounds__(Cfg<N>::THREADS)
-k_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, const T* __restrict__ us,
-       const T* __restrict__ p, const T* __restrict__ coef, int coef_nodal, T* __restrict__ Ye, Epi<T> pe) {
+__device__ inline void elem_batch(const Grid& g, const OpTab<T, N>& st, int eb, const T* __restrict__ u,
+                                  const T* __restrict__ us, const T* __restrict__ p, const T* __restrict__ coef,
+                                  int coef_nodal, T* __restrict__ Ye, const Epi<T>& pe) {
   constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, EPB = Cfg<N>::EPB, K = N - 1;
   constexpr bool DA = OPS & OP_A, DBT = OPS & OP_BT, DB = OPS & OP_B;
   constexpr bool SCAT = DA || DBT, GRAD = DA || DB;
   constexpr int NS = DA ? 6 : 1;
-  __shared__ OpTab<T, N> st;
   __shared__ T su[GRAD ? EPB : 1][3][N3];
   __shared__ T sS[SCAT ? EPB : 1][NS][N3];
   __shared__ T sdiv[DB ? EPB : 1][N3];
-  copy_tab(st, otab);
 
   const int tid = threadIdx.x;
   const int le = tid / N3, q = tid - le * N3;
   const int i = q % N, j = (q / N) % N, l = q / (N * N);
-  const int e = blockIdx.x * EPB + le;
+  const int e = eb * EPB + le;
   const bool act = e < g.ne;
   int node = 0;
   bool interior = false;
@@ -192,19 +191,30 @@ k_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, co
   }
 }
 
-template <typename T, int N>
+// Grid-stride over element batches: the block copies the operator tables once and reuses them.
+template <typename T, int N, int OPS>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
-k_elem_poisson(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, const T* __restrict__ coef,
-               T* __restrict__ Ye) {
-  constexpr int N3 = Cfg<N>::N3, EPB = Cfg<N>::EPB, K = N - 1;
+k_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, const T* __restrict__ us,
+       const T* __restrict__ p, const T* __restrict__ coef, int coef_nodal, T* __restrict__ Ye, Epi<T> pe) {
   __shared__ OpTab<T, N> st;
+  copy_tab(st, otab);
+  const int nbatch = (g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB;
+  for (int eb = blockIdx.x; eb < nbatch; eb += gridDim.x) {
+    __syncthreads();
+    elem_batch<T, N, OPS>(g, st, eb, u, us, p, coef, coef_nodal, Ye, pe);
+  }
+}
+
+template <typename T, int N>
+__device__ inline void poisson_batch(const Grid& g, const OpTab<T, N>& st, int eb, const T* __restrict__ u,
+                                     const T* __restrict__ coef, T* __restrict__ Ye) {
+  constexpr int N3 = Cfg<N>::N3, EPB = Cfg<N>::EPB, K = N - 1;
   __shared__ T su[EPB][N3];
   __shared__ T sF[EPB][3][N3];
-  copy_tab(st, otab);
   const int tid = threadIdx.x;
   const int le = tid / N3, q = tid - le * N3;
   const int i = q % N, j = (q / N) % N, l = q / (N * N);
-  const int e = blockIdx.x * EPB + le;
+  const int e = eb * EPB + le;
   const bool act = e < g.ne;
   if (act) {
     const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
@@ -238,6 +248,19 @@ k_elem_poisson(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict
     acc += cz[a] * sF[le][2][i + N * (j + N * a)];
   }
   Ye[(size_t)e * N3 + q] = acc;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_elem_poisson(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, const T* __restrict__ coef,
+               T* __restrict__ Ye) {
+  __shared__ OpTab<T, N> st;
+  copy_tab(st, otab);
+  const int nbatch = (g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB;
+  for (int eb = blockIdx.x; eb < nbatch; eb += gridDim.x) {
+    __syncthreads();
+    poisson_batch<T, N>(g, st, eb, u, coef, Ye);
+  }
 }
 
 // Node pass: thread per node, sum over the elements containing it in (ez, ey, ex) order.
@@ -418,12 +441,19 @@ k_c2d_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ e
 
 inline unsigned nb(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Element-pass grid: one block per batch up to 12 blocks per SM (152 SMs); beyond that each
+// block loops over batches, so its shared operator tables are loaded once per several batches.
+inline unsigned elem_blocks(int ne, int epb) {
+  const long long nbatch = (ne + epb - 1) / epb;
+  return (unsigned)(nbatch < 152 * 12 ? nbatch : 152 * 12);
+}
+
 template <typename T, int N>
 cudaError_t run_elem(const Grid& g, const void* otab_v, int ops, const T* u, const T* us, const T* p, const T* coef,
                      int cn, T* Ye, const Epi<T>& pe, cudaStream_t st) {
   constexpr int EPB = Cfg<N>::EPB, TH = Cfg<N>::THREADS;
   const OpTab<T, N>* tab = static_cast<const OpTab<T, N>*>(otab_v);
-  const unsigned blocks = (unsigned)((g.ne + EPB - 1) / EPB);
+  const unsigned blocks = elem_blocks(g.ne, EPB);
   switch (ops) {
     case OP_A: wb_count_launch(), k_elem<T, N, OP_A><<<blocks, TH, 0, st>>>(g, tab, u, us, p, coef, cn, Ye, pe); break;
     case OP_BT: wb_count_launch(), k_elem<T, N, OP_BT><<<blocks, TH, 0, st>>>(g, tab, u, us, p, coef, cn, Ye, pe); break;
@@ -457,8 +487,8 @@ cudaError_t launch_elem_stokes(const Grid& g, int k, const void* otab, int ops, 
 template <typename T>
 cudaError_t launch_elem_poisson(const Grid& g, int k, const void* otab, const T* u, const T* coef, T* Ye,
                                 cudaStream_t st) {
-  WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_elem_poisson<T, N><<<(unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB),
-                                                                Cfg<N>::THREADS, 0, st>>>(g, WB_TAB(T), u, coef, Ye)),
+  WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_elem_poisson<T, N><<<elem_blocks(g.ne, Cfg<N>::EPB), Cfg<N>::THREADS, 0,
+                                                                st>>>(g, WB_TAB(T), u, coef, Ye)),
                         cudaGetLastError()));
 }
 
