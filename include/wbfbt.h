@@ -64,7 +64,16 @@ typedef struct {
     int precision;                 /* WBFBT_F64 or WBFBT_MIXED                              */
     int schur_sign;                /* -1 (default): [A B^T; 0 -S~]; +1: printed block      */
     int use_graphs;                /* 1 (default): replay the preconditioner as a CUDA graph */
+    int elem_kernels;              /* single-precision k = 2 element kernels (no counterpart in
+                                      the paper; the results agree to FP32 rounding):
+                                      WBFBT_ELEM_AUTO (default) one thread per element for
+                                      levels of >= 20000 elements, else one thread per point;
+                                      WBFBT_ELEM_POINT / WBFBT_ELEM_ROW force either         */
 } wbfbt_opts;
+
+#define WBFBT_ELEM_AUTO 0
+#define WBFBT_ELEM_POINT 1
+#define WBFBT_ELEM_ROW 2
 
 typedef struct wbfbt_ctx wbfbt_ctx;
 

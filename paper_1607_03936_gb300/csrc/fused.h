@@ -80,3 +80,40 @@ cudaError_t launch_prolong_fused(const Grid& gc, int k, const void* optab, int n
 template <typename T>
 cudaError_t launch_restrict_batched(const Grid& gc, int k, const void* optab, int ncomp, const T* in_f, T* out_c,
                                     int mask_dirichlet, T* w1, T* w2, cudaStream_t st);
+
+// ---- Q2 single-precision path (q2_ops.cu): one thread per element, warps along element rows.
+// A warp owns a row segment of up to 32 consecutive elements along x (fixed ey, ez); its
+// partial node values, summed along x within the segment, are stored per x-line of nodes as
+// [segment][ez][ey][l][j][component][X], X = 0 .. 64 padded to Q2_ROW_LD entries.
+// n / d for 0 <= n < 2^31 as a multiply-high and a shift (Granlund & Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994): m = ceil(2^(31 + L) / d), L = ceil(log2 d).
+struct FastDiv {
+  unsigned d, m, s;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f{d, 0u, 0u};
+  if (d > 1) {
+    unsigned L = 0;
+    while ((1ull << L) < d) ++L;
+    f.m = (unsigned)(((1ull << (31 + L)) + d - 1) / d);
+    f.s = L - 1;
+  }
+  return f;
+}
+#ifdef __CUDACC__
+__device__ inline unsigned fdiv(unsigned n, const FastDiv& f) { return f.d == 1 ? n : __umulhi(n, f.m) >> f.s; }
+#endif
+
+constexpr int Q2_SEG = 32;      // elements per row segment (one warp)
+constexpr int Q2_ROW_LD = 66;   // stored nodes per x-line of a segment (65, padded to even)
+// Scratch entries the row-segment element pass writes for ncomp components.
+size_t q2_row_scratch(const Grid& g, int ncomp);
+// Scratch entries (precision T, order k) an element pass on grid g may write for 3 components.
+template <typename T>
+size_t elem_scratch_size(const Grid& g, int k);
+
+cudaError_t launch_q2_elem(const Grid& g, int ops, const float* u, const float* p, const float* coef, int coef_nodal,
+                           float* R, const Epi<float>& pe, cudaStream_t st);
+cudaError_t launch_q2_poisson(const Grid& g, const float* u, const float* coef, float* R, cudaStream_t st);
+cudaError_t launch_q2_gather(const Grid& g, int ncomp, int mask_boundary, const float* R, const Epi<float>& e,
+                             cudaStream_t st);

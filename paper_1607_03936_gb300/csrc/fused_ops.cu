@@ -8,39 +8,17 @@
 // a(u,v) = int 2 mu eps(u):eps(v), b(v,q) = -int q div v).
 // Node pass: each node adds the contributions of its elements in the order
 // (ez, ey, ex) ascending, so results are bitwise reproducible.
+#include <algorithm>
+#include <type_traits>
+
 #include "elem_common.cuh"
+#include "epi.cuh"
 #include "fused.h"
 #include "kernels.h"
 
 namespace {
 
 using namespace wb;
-
-template <typename T>
-__device__ inline void epi_apply(const Epi<T>& E, size_t i, int node, T v) {
-  switch (E.mode) {
-    case EPI_STORE: E.y[i] = v; break;
-    case EPI_SCALE: E.y[i] = v * E.sc[node]; break;
-    case EPI_DINV: E.y[i] = E.dinv[i] * v; break;
-    case EPI_BMINUS: E.y[i] = E.b[i] - v; break;
-    case EPI_SUB: E.r[i] -= v; break;
-    case EPI_CHEB_INIT1: {
-      const T rv = E.b[i] - v;
-      const T dv = E.dinv[i] * rv * E.inv_theta;
-      E.r[i] = rv;
-      E.d[i] = dv;
-      E.x[i] += dv;
-    } break;
-    case EPI_CHEB_STEP: {
-      const T rv = E.r[i] - v;
-      const T dv = E.a * E.d[i] + E.bc * (E.dinv[i] * rv);
-      E.r[i] = rv;
-      E.d[i] = dv;
-      E.x[i] += dv;
-    } break;
-    default: break;
-  }
-}
 
 // One batch of EPB elements (eb); every thread of the block reaches every barrier.
 template <typename T, int N, int OPS>
@@ -264,12 +242,24 @@ k_elem_poisson(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict
 }
 
 // Node pass: thread per node, sum over the elements containing it in (ez, ey, ex) order.
+// Grid (x blocks, NY, NZ), or a flat grid when NY or NZ exceed the grid-dimension limit.
 template <typename T, int N, int NC>
 __global__ void k_gather(Grid g, int mask_boundary, const T* __restrict__ Ye, Epi<T> E) {
   constexpr int N3 = Cfg<N>::N3, K = N - 1;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= g.nn) return;
-  const int ix = n % g.NX, iy = (n / g.NX) % g.NY, iz = n / (g.NX * g.NY);
+  int ix, iy, iz, n;
+  if (gridDim.y > 1) {   // 3-D grid (NY >= 3 always)
+    ix = blockIdx.x * blockDim.x + threadIdx.x;
+    iy = blockIdx.y;
+    iz = blockIdx.z;
+    if (ix >= g.NX) return;
+    n = ix + g.NX * (iy + g.NY * iz);
+  } else {
+    n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.nn) return;
+    ix = n % g.NX;
+    iy = (n / g.NX) % g.NY;
+    iz = n / (g.NX * g.NY);
+  }
   T v[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) v[c] = T(0);
@@ -478,19 +468,46 @@ cudaError_t run_elem(const Grid& g, const void* otab_v, int ops, const T* u, con
 
 #define WB_TAB(T) static_cast<const OpTab<T, N>*>(otab)
 
+// Single precision at k = 2 on grids flagged `rowk` takes the thread-per-element row-segment
+// kernels (q2_ops.cu); their scratch layout is the row one, which the matching launch_gather reads.
+template <typename T>
+bool row_path(const Grid& g, int k) {
+  return std::is_same<T, float>::value && k == 2 && g.rowk;
+}
+
+template <typename T>
+size_t elem_scratch_size(const Grid& g, int k) {
+  const size_t n = (size_t)(k + 1);
+  const size_t elem = 3 * (size_t)g.ne * n * n * n;
+  return row_path<T>(g, k) ? std::max(elem, q2_row_scratch(g, 3)) : elem;
+}
+
 template <typename T>
 cudaError_t launch_elem_stokes(const Grid& g, int k, const void* otab, int ops, const T* u, const T* us, const T* p,
                                const T* coef, int cn, T* Ye, const Epi<T>& pe, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (row_path<T>(g, k)) {
+      if (us != nullptr) return cudaErrorInvalidValue;   // input scaling is not part of the row kernels
+      return launch_q2_elem(g, ops, u, p, coef, cn, Ye, pe, st);
+    }
+  }
   WB_FUSED_DISPATCH(k, (run_elem<T, N>(g, otab, ops, u, us, p, coef, cn, Ye, pe, st)));
 }
 
 template <typename T>
 cudaError_t launch_elem_poisson(const Grid& g, int k, const void* otab, const T* u, const T* coef, T* Ye,
                                 cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (row_path<T>(g, k)) return launch_q2_poisson(g, u, coef, Ye, st);
+  }
   WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_elem_poisson<T, N><<<elem_blocks(g.ne, Cfg<N>::EPB), Cfg<N>::THREADS, 0,
                                                                 st>>>(g, WB_TAB(T), u, coef, Ye)),
                         cudaGetLastError()));
 }
+
+template <typename T>
+cudaError_t launch_gather_elem(const Grid& g, int k, int ncomp, int mask, const T* Ye, const Epi<T>& e,
+                               cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_disc_to_cont_fused(const Grid& g, int k, const void* otab, const T* rd, T* rc, T* Ye,
@@ -507,7 +524,7 @@ cudaError_t launch_disc_to_cont_fused(const Grid& g, int k, const void* otab, co
   Epi<T> ep;
   ep.mode = EPI_STORE;
   ep.y = rc;
-  return launch_gather<T>(g, k, 1, 0, Ye, ep, st);
+  return launch_gather_elem<T>(g, k, 1, 0, Ye, ep, st);
 }
 
 template <typename T>
@@ -518,17 +535,30 @@ cudaError_t launch_cont_to_disc_fused(const Grid& g, int k, const void* otab, co
                         cudaGetLastError()));
 }
 
+// Node pass over the element-major scratch [ne][ncomp][n^3].
 template <typename T>
-cudaError_t launch_gather(const Grid& g, int k, int ncomp, int mask, const T* Ye, const Epi<T>& e, cudaStream_t st) {
+cudaError_t launch_gather_elem(const Grid& g, int k, int ncomp, int mask, const T* Ye, const Epi<T>& e,
+                               cudaStream_t st) {
+  const bool flat = g.NY > 65535 || g.NZ > 65535;
+  const int bs = flat || g.NX >= 128 ? 128 : (g.NX + 31) / 32 * 32;
+  const dim3 grid = flat ? dim3(nb(g.nn, bs)) : dim3(nb(g.NX, bs), (unsigned)g.NY, (unsigned)g.NZ);
   if (ncomp == 3) {
-    WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_gather<T, N, 3><<<nb(g.nn, 128), 128, 0, st>>>(g, mask, Ye, e)),
+    WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_gather<T, N, 3><<<grid, bs, 0, st>>>(g, mask, Ye, e)),
                           cudaGetLastError()));
   }
   if (ncomp == 1) {
-    WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_gather<T, N, 1><<<nb(g.nn, 128), 128, 0, st>>>(g, mask, Ye, e)),
+    WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_gather<T, N, 1><<<grid, bs, 0, st>>>(g, mask, Ye, e)),
                           cudaGetLastError()));
   }
   return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_gather(const Grid& g, int k, int ncomp, int mask, const T* Ye, const Epi<T>& e, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (row_path<T>(g, k)) return launch_q2_gather(g, ncomp, mask, Ye, e, st);
+  }
+  return launch_gather_elem<T>(g, k, ncomp, mask, Ye, e, st);
 }
 
 template <typename T>
@@ -596,6 +626,7 @@ void build_optab_host(const RefTables& t, const Grid& g, int k, void* out) {
   template cudaError_t launch_disc_to_cont_fused<T>(const Grid&, int, const void*, const T*, T*, T*, cudaStream_t);   \
   template cudaError_t launch_cont_to_disc_fused<T>(const Grid&, int, const void*, const T*, T*, int, cudaStream_t);  \
   template size_t optab_bytes<T>(int);                                                                                \
+  template size_t elem_scratch_size<T>(const Grid&, int);                                                                                \
   template void build_optab_host<T>(const RefTables&, const Grid&, int, void*);
 WB_FUSED_INST(double)
 WB_FUSED_INST(float)

@@ -1,0 +1,386 @@
+// Q2 (k = 2) single-precision operator kernels: one thread per element, warps along element rows.
+//
+// Element pass: a warp owns a row segment of up to 32 consecutive elements along x (fixed ey,
+// ez), one thread per element.  The thread loads its element's 27 nodal values per component
+// into registers, forms the gradient at each of the 27 GLL points by 1-D derivative sums along
+// the three axes (sum factorisation with the 3 x 3 derivative matrix), the quadrature-weighted
+// stress, and accumulates the transposed derivative sums into 27 register outputs per component
+// (Sec. 1.2: a(u,v) = int 2 mu eps(u):eps(v), b(v,q) = -int q div v; the scalar Poisson operator
+// of the two-space pressure cycle, Sec. 6, is int c grad u . grad v).  The operator tables
+// (derivatives scaled by 2/h, weights times |J|, pressure basis) are a kernel parameter, so every
+// table entry is a constant-bank operand of the FMAs that use it.
+// Row assembly: neighbouring threads share an x-face; each thread passes its right face to the
+// next lane (one warp shuffle per value) and adds it to its own left face, so the lane holding
+// element ex owns the x-nodes 2 ex and 2 ex + 1 of the segment (the last lane also 2 ex + 2).
+// The segment's partial node values are stored per x-line [seg][ez][ey][l][j][c][X] with
+// coalesced two-float stores.
+// Node pass: each mesh node adds the partials of the (up to 2 x 2 x 2) segment lines through it
+// in the fixed order z, y, x ascending and hands the sum to the fused epilogue.  No atomics: the
+// result is bitwise reproducible.
+#include "elem_common.cuh"
+#include "epi.cuh"
+#include "fused.h"
+#include "kernels.h"
+
+namespace {
+
+using namespace wb;
+
+using Tab2 = OpTab<float, 3>;
+constexpr int WARPS = 4;   // row segments per block
+
+__host__ __device__ constexpr int q3(int i, int j, int l) { return i + 3 * (j + 3 * l); }
+
+// Row segments along x, and the layout of the row scratch.
+struct Rows {
+  int nseg;             // segments along x
+  int nrows;            // nseg * ny * nz
+  FastDiv fseg, fny;    // warp index -> (segment, ey, ez)
+};
+
+Rows make_rows(const Grid& g) {
+  Rows r;
+  r.nseg = (g.nx + Q2_SEG - 1) / Q2_SEG;
+  r.nrows = r.nseg * g.ny * g.nz;
+  r.fseg = make_fastdiv(r.nseg);
+  r.fny = make_fastdiv(g.ny);
+  return r;
+}
+
+// Position of this thread: segment, element row and element.
+struct RowPos {
+  int seg, ey, ez, lane, ex, e;
+  bool act, warp_live;
+};
+
+__device__ inline RowPos row_pos(const Grid& g, const Rows& rw) {
+  RowPos r;
+  const unsigned w = blockIdx.x * WARPS + (threadIdx.x >> 5);
+  r.lane = threadIdx.x & 31;
+  r.warp_live = w < (unsigned)rw.nrows;
+  const unsigned rest = fdiv(w, rw.fseg);
+  r.seg = (int)(w - rest * rw.nseg);
+  r.ez = (int)fdiv(rest, rw.fny);
+  r.ey = (int)rest - r.ez * g.ny;
+  r.ex = r.seg * Q2_SEG + r.lane;
+  r.act = r.warp_live && r.ex < g.nx;
+  r.e = r.ex + g.nx * (r.ey + g.ny * r.ez);
+  return r;
+}
+
+// x-assembly of NC x 27 register outputs and the store of the segment's x-line partials.
+template <int NC>
+__device__ inline void row_store(const Grid& g, const RowPos& rp, float (*out)[27], float* __restrict__ R) {
+  const int last = min(Q2_SEG - 1, g.nx - 1 - rp.seg * Q2_SEG);   // lane of the segment's last element
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int jl = 0; jl < 9; ++jl) {
+      const float left = __shfl_up_sync(0xffffffffu, out[c][3 * jl + 2], 1);
+      if (rp.lane > 0) out[c][3 * jl] += left;
+    }
+  if (!rp.act) return;
+  const size_t line0 = (((size_t)rp.seg * g.nz + rp.ez) * g.ny + rp.ey) * 9;
+#pragma unroll
+  for (int jl = 0; jl < 9; ++jl)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float* row = R + ((line0 + jl) * NC + c) * Q2_ROW_LD;
+      *reinterpret_cast<float2*>(row + 2 * rp.lane) = make_float2(out[c][3 * jl], out[c][3 * jl + 1]);
+      if (rp.lane == last) row[2 * rp.lane + 2] = out[c][3 * jl + 2];
+    }
+}
+
+// Stokes-family element pass (ops: OP_A | OP_BT | OP_B).  Velocity contributions go to the row
+// scratch R; the B output (per element and pressure mode) takes the epilogue pe.
+template <int OPS>
+__global__ void __launch_bounds__(32 * WARPS)
+k_q2_elem(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restrict__ u,
+          const float* __restrict__ p, const float* __restrict__ coef, int coef_nodal, float* __restrict__ R,
+          Epi<float> pe) {
+  constexpr bool DA = OPS & OP_A, DBT = OPS & OP_BT, DB = OPS & OP_B;
+  constexpr bool GRAD = DA || DB, SCAT = DA || DBT;
+  const RowPos rp = row_pos(g, rw);
+  if (!rp.warp_live) return;   // whole warp: no shuffle partner is left behind
+  const size_t nn = (size_t)g.nn;
+  const int n0 = 2 * rp.ex + g.NX * (2 * rp.ey + g.NY * 2 * rp.ez);
+  // Dirichlet nodes read as zero: end planes of the element that lie on the domain boundary
+  const bool lo_x = rp.ex == 0, hi_x = rp.ex == g.nx - 1;
+  const bool lo_y = rp.ey == 0, hi_y = rp.ey == g.ny - 1;
+  const bool lo_z = rp.ez == 0, hi_z = rp.ez == g.nz - 1;
+
+  float ur[GRAD ? 3 : 1][27];
+  if (GRAD) {
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int roff = n0 + g.NX * (j + g.NY * l);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const bool bnd = (i == 0 && lo_x) || (i == 2 && hi_x) || (j == 0 && lo_y) || (j == 2 && hi_y) ||
+                           (l == 0 && lo_z) || (l == 2 && hi_z);
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            ur[c][q3(i, j, l)] = (rp.act && !bnd) ? __ldg(u + c * nn + roff + i) : 0.f;
+        }
+      }
+  }
+  float pm[4] = {0.f, 0.f, 0.f, 0.f};
+  if (DBT && rp.act) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) pm[m] = __ldg(p + (size_t)rp.e * 4 + m);
+  }
+  const float* mu_base = coef_nodal ? coef + n0 : coef + (size_t)rp.e * 27;
+
+  float out[SCAT ? 3 : 1][27];
+  if (SCAT) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int q = 0; q < 27; ++q) out[c][q] = 0.f;
+  }
+  float bacc[4] = {0.f, 0.f, 0.f, 0.f};
+
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int q = q3(i, j, l);
+        const float W = tb.W3[q];
+        float G[3][3];
+        if (GRAD) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              a0 += tb.Ds[0][i][a] * ur[c][q3(a, j, l)];
+              a1 += tb.Ds[1][j][a] * ur[c][q3(i, a, l)];
+              a2 += tb.Ds[2][l][a] * ur[c][q3(i, j, a)];
+            }
+            G[c][0] = a0;
+            G[c][1] = a1;
+            G[c][2] = a2;
+          }
+        }
+        if (DB) {
+          const float dv = W * (G[0][0] + G[1][1] + G[2][2]);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) bacc[m] -= tb.Psi[q][m] * dv;
+        }
+        if (SCAT) {
+          float sd[3] = {0.f, 0.f, 0.f};   // diagonal stress entries
+          float sxy = 0.f, sxz = 0.f, syz = 0.f;
+          if (DA) {
+            const int mo = coef_nodal ? i + g.NX * (j + g.NY * l) : q;
+            const float mu = rp.act ? __ldg(mu_base + mo) : 0.f;
+            const float f = 2.f * W * mu, hf = W * mu;
+            sd[0] = f * G[0][0];
+            sd[1] = f * G[1][1];
+            sd[2] = f * G[2][2];
+            sxy = hf * (G[0][1] + G[1][0]);
+            sxz = hf * (G[0][2] + G[2][0]);
+            syz = hf * (G[1][2] + G[2][1]);
+          }
+          if (DBT) {
+            float pq = 0.f;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) pq += tb.Psi[q][m] * pm[m];
+            const float tq = W * pq;
+            sd[0] -= tq;
+            sd[1] -= tq;
+            sd[2] -= tq;
+          }
+          // output component c, derivative direction d: out_c(node on the d-line) += Ds[d] S_cd
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            out[0][q3(a, j, l)] += tb.Ds[0][i][a] * sd[0];
+            out[1][q3(i, a, l)] += tb.Ds[1][j][a] * sd[1];
+            out[2][q3(i, j, a)] += tb.Ds[2][l][a] * sd[2];
+            if (DA) {
+              out[0][q3(i, a, l)] += tb.Ds[1][j][a] * sxy;
+              out[0][q3(i, j, a)] += tb.Ds[2][l][a] * sxz;
+              out[1][q3(a, j, l)] += tb.Ds[0][i][a] * sxy;
+              out[1][q3(i, j, a)] += tb.Ds[2][l][a] * syz;
+              out[2][q3(a, j, l)] += tb.Ds[0][i][a] * sxz;
+              out[2][q3(i, a, l)] += tb.Ds[1][j][a] * syz;
+            }
+          }
+        }
+      }
+
+  if (DB && rp.act) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) epi_apply(pe, (size_t)rp.e * 4 + m, 0, bacc[m]);
+  }
+  if (SCAT) row_store<3>(g, rp, out, R);
+}
+
+// Scalar Q2 Poisson element pass, c per element point (no Dirichlet rows: Neumann operator).
+__global__ void __launch_bounds__(32 * WARPS)
+k_q2_poisson(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restrict__ u,
+             const float* __restrict__ coef, float* __restrict__ R) {
+  const RowPos rp = row_pos(g, rw);
+  if (!rp.warp_live) return;
+  const int n0 = 2 * rp.ex + g.NX * (2 * rp.ey + g.NY * 2 * rp.ez);
+  float ur[27], out[1][27];
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int roff = n0 + g.NX * (j + g.NY * l);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        ur[q3(i, j, l)] = rp.act ? __ldg(u + roff + i) : 0.f;
+        out[0][q3(i, j, l)] = 0.f;
+      }
+    }
+  const float* cf = coef + (size_t)rp.e * 27;
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int q = q3(i, j, l);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          a0 += tb.Ds[0][i][a] * ur[q3(a, j, l)];
+          a1 += tb.Ds[1][j][a] * ur[q3(i, a, l)];
+          a2 += tb.Ds[2][l][a] * ur[q3(i, j, a)];
+        }
+        const float f = rp.act ? tb.W3[q] * __ldg(cf + q) : 0.f;
+        a0 *= f;
+        a1 *= f;
+        a2 *= f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          out[0][q3(a, j, l)] += tb.Ds[0][i][a] * a0;
+          out[0][q3(i, a, l)] += tb.Ds[1][j][a] * a1;
+          out[0][q3(i, j, a)] += tb.Ds[2][l][a] * a2;
+        }
+      }
+  row_store<1>(g, rp, out, R);
+}
+
+// Node pass: grid (x blocks, NY, NZ).  Lines through node (ix, iy, iz): along z the element rows
+// ez = iz / 2 (l = 1) for odd iz, else (iz / 2 - 1, l = 2) and (iz / 2, l = 0) where they exist;
+// the same along y; along x the segment s = ix / 64 at X = ix - 64 s, and also s - 1 at X = 64
+// when ix is a segment's first node.
+template <int NC>
+__global__ void k_q2_gather(Grid g, int nseg, int mask_boundary, const float* __restrict__ R, Epi<float> E) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iy = blockIdx.y, iz = blockIdx.z;
+  if (ix >= g.NX) return;
+  const int n = ix + g.NX * (iy + g.NY * iz);
+  float v[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) v[c] = 0.f;
+  if (!(mask_boundary && on_boundary(g, ix, iy, iz))) {
+    int zr[2] = {0, 0}, zl[2] = {0, 0}, nzr = 0, yr[2] = {0, 0}, yl[2] = {0, 0}, nyr = 0;
+    if (iz & 1) {
+      zr[0] = iz >> 1; zl[0] = 1; nzr = 1;
+    } else {
+      if (iz > 0) { zr[0] = (iz >> 1) - 1; zl[0] = 2; nzr = 1; }
+      if ((iz >> 1) < g.nz) { zr[nzr] = iz >> 1; zl[nzr] = 0; ++nzr; }
+    }
+    if (iy & 1) {
+      yr[0] = iy >> 1; yl[0] = 1; nyr = 1;
+    } else {
+      if (iy > 0) { yr[0] = (iy >> 1) - 1; yl[0] = 2; nyr = 1; }
+      if ((iy >> 1) < g.ny) { yr[nyr] = iy >> 1; yl[nyr] = 0; ++nyr; }
+    }
+    const int s = ix >> 6, X = ix & 63;
+    const bool prev = X == 0 && s > 0, cur = s < nseg;
+    const size_t per_seg = (size_t)g.nz * g.ny * 9;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      if (a < nzr) {
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          if (b < nyr) {
+            const size_t rowl = ((size_t)zr[a] * g.ny + yr[b]) * 9 + 3 * zl[a] + yl[b];   // within a segment
+            if (prev) {
+              const float* src = R + ((s - 1) * per_seg + rowl) * NC * Q2_ROW_LD + 2 * Q2_SEG;
+#pragma unroll
+              for (int c = 0; c < NC; ++c) v[c] += __ldg(src + c * Q2_ROW_LD);
+            }
+            if (cur) {
+              const float* src = R + ((size_t)s * per_seg + rowl) * NC * Q2_ROW_LD + X;
+#pragma unroll
+              for (int c = 0; c < NC; ++c) v[c] += __ldg(src + c * Q2_ROW_LD);
+            }
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) epi_apply(E, (size_t)c * g.nn + n, n, v[c]);
+}
+
+const RefTables& ref_tables_q2() {
+  static const RefTables t = [] {
+    RefTables r;
+    build_ref_tables(2, &r);
+    return r;
+  }();
+  return t;
+}
+
+Tab2 q2_tab(const Grid& g) {
+  Tab2 t;
+  make_optab<float, 3>(ref_tables_q2(), g, &t);
+  return t;
+}
+
+unsigned elem_grid(const Rows& rw) { return (unsigned)((rw.nrows + WARPS - 1) / WARPS); }
+
+}  // namespace
+
+size_t q2_row_scratch(const Grid& g, int ncomp) {
+  const Rows rw = make_rows(g);
+  return (size_t)rw.nrows * 9 * ncomp * Q2_ROW_LD;
+}
+
+cudaError_t launch_q2_elem(const Grid& g, int ops, const float* u, const float* p, const float* coef, int coef_nodal,
+                           float* R, const Epi<float>& pe, cudaStream_t st) {
+  const Rows rw = make_rows(g);
+  const Tab2 tb = q2_tab(g);
+  const unsigned nbk = elem_grid(rw), nt = 32 * WARPS;
+  switch (ops) {
+    case OP_A: wb_count_launch(), k_q2_elem<OP_A><<<nbk, nt, 0, st>>>(g, rw, tb, u, p, coef, coef_nodal, R, pe); break;
+    case OP_BT: wb_count_launch(), k_q2_elem<OP_BT><<<nbk, nt, 0, st>>>(g, rw, tb, u, p, coef, coef_nodal, R, pe); break;
+    case OP_B: wb_count_launch(), k_q2_elem<OP_B><<<nbk, nt, 0, st>>>(g, rw, tb, u, p, coef, coef_nodal, R, pe); break;
+    case OP_A | OP_BT | OP_B:
+      wb_count_launch(), k_q2_elem<OP_A | OP_BT | OP_B><<<nbk, nt, 0, st>>>(g, rw, tb, u, p, coef, coef_nodal, R, pe);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q2_poisson(const Grid& g, const float* u, const float* coef, float* R, cudaStream_t st) {
+  const Rows rw = make_rows(g);
+  wb_count_launch(), k_q2_poisson<<<elem_grid(rw), 32 * WARPS, 0, st>>>(g, rw, q2_tab(g), u, coef, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q2_gather(const Grid& g, int ncomp, int mask_boundary, const float* R, const Epi<float>& e,
+                             cudaStream_t st) {
+  const Rows rw = make_rows(g);
+  const int bs = g.NX >= 128 ? 128 : (g.NX + 31) / 32 * 32;
+  if (g.NY > 65535 || g.NZ > 65535) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((g.NX + bs - 1) / bs), (unsigned)g.NY, (unsigned)g.NZ);
+  if (ncomp == 3)
+    wb_count_launch(), k_q2_gather<3><<<grid, bs, 0, st>>>(g, rw.nseg, mask_boundary, R, e);
+  else if (ncomp == 1)
+    wb_count_launch(), k_q2_gather<1><<<grid, bs, 0, st>>>(g, rw.nseg, mask_boundary, R, e);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}

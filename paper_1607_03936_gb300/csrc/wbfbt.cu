@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <algorithm>
 #include <vector>
 
 #include "fused.h"
@@ -481,6 +482,15 @@ double power_lambda(wbfbt_ctx* c, Op M, long long n, const T* dinv, T* v, T* w, 
   return lam;
 }
 
+// Element-kernel family of a grid (the row kernels need enough elements to fill the GPU: one
+// thread per element gives a 16^3 level only 4096 threads).
+constexpr int ROW_MIN_ELEMS = 20000;
+Grid with_kernels(const wbfbt_ctx* c, Grid g) {
+  const int mode = c->opt.elem_kernels;
+  g.rowk = mode == WBFBT_ELEM_ROW || (mode == WBFBT_ELEM_AUTO && g.ne >= ROW_MIN_ELEMS);
+  return g;
+}
+
 Grid coarser(const Grid& g, int k) {
   return make_grid(g.nx / 2, g.ny / 2, g.nz / 2, k, g.h[0] * g.nx, g.h[1] * g.ny, g.h[2] * g.nz);
 }
@@ -538,7 +548,7 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
       else
         CK(launch_dinv_L<double>(g, c->k, c->dtab, L.coef64, L.d64, c->st));
       CK((launch_cast<double, T>((long long)nv, L.d64, L.dinv, c->st)));
-      Grid gc = coarser(g, c->k);
+      Grid gc = with_kernels(c, coarser(g, c->k));
       size_t ws = transfer_work_size(gc, c->k);
       c->pool.ensure(L.w1, ws * H.ncomp);   // restriction passes run all components at once
       c->pool.ensure(L.w2, ws * H.ncomp);
@@ -621,7 +631,16 @@ void build_precond(wbfbt_ctx* c) {
   for (T** q : {&P.vtmp, &P.sv1, &P.sv2, &P.urhs, &P.utmp}) c->pool.ensure(*q, nu);
   c->pool.ensure(P.vin, c->ntot);
   c->pool.ensure(P.vout, c->ntot);
-  c->pool.ensure(P.Ye, (size_t)3 * g.ne * c->N3);
+  {
+    // element-pass scratch: the largest any level's element pass writes
+    size_t ye = 0;
+    Grid gl = g;
+    for (int l = 0; l < c->nlev; ++l) {
+      ye = std::max(ye, elem_scratch_size<T>(gl, c->k));
+      if (l + 1 < c->nlev) gl = with_kernels(c, coarser(gl, c->k));
+    }
+    c->pool.ensure(P.Ye, ye);
+  }
   // A hierarchy: viscosity per node on the fine level
   build_hier<T>(c, P.HA, true, c->mu64, 1);
   // Poisson hierarchies: c = 1 / (a(e) sqrt(mu)) per point
@@ -902,6 +921,7 @@ void wbfbt_default_opts(wbfbt_opts* o) {
   o->precision = WBFBT_F64;
   o->schur_sign = -1;
   o->use_graphs = 1;
+  o->elem_kernels = WBFBT_ELEM_AUTO;
 }
 
 const char* wbfbt_status_string(int s) {
@@ -941,7 +961,8 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
   if (opts) c->opt = *opts;
   if (c->opt.restart < 1 || c->opt.restart > 1000 || c->opt.cheb_degree < 1 || c->opt.cheb_degree > 16 ||
       c->opt.a_l < 1.0 || (c->opt.a_r > 0 && c->opt.a_r < 1.0) ||
-      (c->opt.precision != WBFBT_F64 && c->opt.precision != WBFBT_MIXED) || c->opt.mg_min_n < 1)
+      (c->opt.precision != WBFBT_F64 && c->opt.precision != WBFBT_MIXED) || c->opt.mg_min_n < 1 ||
+      c->opt.elem_kernels < WBFBT_ELEM_AUTO || c->opt.elem_kernels > WBFBT_ELEM_ROW)
     return WBFBT_ERR_INVALID;
   if (c->opt.schur_sign >= 0) c->opt.schur_sign = 1; else c->opt.schur_sign = -1;
   c->ust = (cudaStream_t)stream;
@@ -953,7 +974,7 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
   c->N = k + 1;
   c->N3 = c->N * c->N * c->N;
   c->NP = k * (k + 1) * (k + 2) / 6;
-  c->g = make_grid(mesh->nx, mesh->ny, mesh->nz, k, mesh->lx, mesh->ly, mesh->lz);
+  c->g = with_kernels(c.get(), make_grid(mesh->nx, mesh->ny, mesh->nz, k, mesh->lx, mesh->ly, mesh->lz));
   if (c->opt.a_r <= 0) {
     const int N = std::max(mesh->nx, std::max(mesh->ny, mesh->nz));
     c->opt.a_r = std::max(1.0, (N / 16.0) * std::pow(2.0, k - 2));
@@ -980,7 +1001,7 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
     cp->dinv64 = cp->pool.get<double>(nn);
     cp->ntot = 3LL * nn + (long long)g.ne * cp->NP;
     cp->Ye64 = cp->pool.get<double>((size_t)3 * g.ne * cp->N3);
-    cp->Ye32 = cp->pool.get<float>((size_t)3 * g.ne * cp->N3);
+    cp->Ye32 = cp->pool.get<float>(elem_scratch_size<float>(g, k));
     cp->ot64 = make_device_optab<double>(cp, g);
     cp->ot32 = make_device_optab<float>(cp, g);
     cp->lx = cp->pool.get<float>((size_t)g.ne * (cp->NP + 1));

@@ -33,8 +33,8 @@ def test_status_strings_and_defaults_without_gpu():
     assert lib.wbfbt_status_string(0) == b"ok"
     assert b"iteration" in lib.wbfbt_status_string(-5)
     o = wbfbt.default_opts()
-    assert (o.a_l, o.a_r, o.restart, o.cheb_degree, o.mg_min_n, o.precision, o.schur_sign, o.use_graphs) == \
-        (1.0, 0.0, 50, 3, 4, 0, -1, 1)
+    assert (o.a_l, o.a_r, o.restart, o.cheb_degree, o.mg_min_n, o.precision, o.schur_sign, o.use_graphs,
+            o.elem_kernels) == (1.0, 0.0, 50, 3, 4, 0, -1, 1, 0)
     # argument validation happens before any device call
     m = wbfbt.Mesh(2, 2, 2, 1.0, 1.0, 1.0)
     h = ctypes.c_void_p()

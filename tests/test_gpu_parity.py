@@ -81,11 +81,18 @@ def test_fine_operators_fp64(wb, shape):
     assert rel(N(s.apply_K(T(x))), K) < 1e-12
 
 
-@pytest.mark.parametrize("shape", SHAPES[:2])
-def test_fine_operators_fp32(wb, shape):
+# FP32 shapes: single row segments, nx > 32 (two segments along x, the second one short) and
+# nx = 64 + 3, so segment seams and ragged segments are covered by the row kernels.
+SHAPES_F32 = SHAPES[:2] + [(33, 3, 2, 2, (1.0, 1.0, 1.0)), (6, 5, 4, 2, (1.0, 0.8, 1.2)), (67, 2, 1, 2, (1.0, 1.0, 1.0)),
+                          (4, 3, 5, 3, (1.0, 1.0, 1.0))]
+
+
+@pytest.mark.parametrize("kern", [1, 2])
+@pytest.mark.parametrize("shape", SHAPES_F32)
+def test_fine_operators_fp32(wb, shape, kern):
     nx, ny, nz, k, L = shape
     m, mu, _, _ = problem(nx, ny, nz, k, lengths=L)
-    s = gpu_solver(wb, m, mu)
+    s = gpu_solver(wb, m, mu, elem_kernels=kern)
     rng = np.random.default_rng(2)
     u, p = rng.standard_normal(m.n_u), rng.standard_normal(m.n_p)
     A = op.assemble_A(m, op.point_values(m, mu))
@@ -94,6 +101,49 @@ def test_fine_operators_fp32(wb, shape):
     assert rel(N(s.apply_A(T(u, f32))), A @ u) < 2e-5
     assert rel(N(s.apply_B(T(u, f32))), B @ u) < 2e-5
     assert rel(N(s.apply_BT(T(p, f32))), B.T @ p) < 2e-5
+
+
+@pytest.mark.parametrize("kern", [1, 2])
+@pytest.mark.parametrize("which", [0, 1])
+def test_Kw_fp32(wb, which, kern):
+    m, mu, _, _ = problem(6, 5, 4, 2, dr=1e6)
+    s = gpu_solver(wb, m, mu, a_r=3.0, precision=wb.MIXED, elem_kernels=kern)
+    prob = W.StokesProblem(m, mu, a_l=1.0, a_r=3.0)
+    K = op.assemble_Kw(prob.B, prob.Cdiag if which == 0 else prob.Ddiag, m)
+    p = np.random.default_rng(4).standard_normal(m.n_p)
+    assert rel(N(s.apply_Kw(which, T(p, torch.float32))), K @ p) < 5e-5
+
+
+@pytest.mark.parametrize("kern", [1, 2])
+def test_vcycle_A_fp32(wb, kern):
+    """FP32 V-cycle (FP64 coarsest solve) against the FP64 oracle V-cycle: 8^3 -> 4^3."""
+    m, mu, _, _ = problem(8, 8, 8, 2, dr=1e4)
+    s = gpu_solver(wb, m, mu, precision=wb.MIXED, elem_kernels=kern)
+    levels = mg.build_hierarchy(m, op.point_values(m, mu), vector=True)
+    b = np.random.default_rng(5).standard_normal(m.n_u) * m.interior_dof_mask()
+    assert rel(N(s.apply_Ainv(T(b, torch.float32))), mg.vcycle(levels, b)) < 1e-4
+
+
+@pytest.mark.parametrize("kern", [1, 2])
+@pytest.mark.parametrize("which", [0, 1])
+def test_pressure_poisson_vcycle_fp32(wb, which, kern):
+    m, mu, _, _ = problem(8, 8, 8, 2, dr=1e6, ns=8)
+    s = gpu_solver(wb, m, mu, a_r=2.0, precision=wb.MIXED, elem_kernels=kern)
+    prob = W.StokesProblem(m, mu, a_l=1.0, a_r=2.0)
+    pp = mg.PressurePoissonMG(m, prob.B, prob.Cdiag if which == 0 else prob.Ddiag, mu,
+                              1.0 if which == 0 else 2.0)
+    b = op.project_pressure(m, np.random.default_rng(6).standard_normal(m.n_p))
+    assert rel(N(s.apply_Kinv(which, T(b, torch.float32))), pp.apply(b)) < 1e-4
+
+
+@pytest.mark.parametrize("kern", [1, 2])
+def test_fp32_applies_are_deterministic(wb, kern):
+    m, mu, _, _ = problem(12, 10, 8, 2)
+    s = gpu_solver(wb, m, mu, precision=wb.MIXED, elem_kernels=kern)
+    rng = np.random.default_rng(11)
+    u, p = T(rng.standard_normal(m.n_u), torch.float32), T(rng.standard_normal(m.n_p), torch.float32)
+    assert torch.equal(s.apply_A(u), s.apply_A(u))
+    assert torch.equal(s.apply_Kinv(1, p), s.apply_Kinv(1, p))
 
 
 def test_apply_is_deterministic(wb):
@@ -221,6 +271,33 @@ def test_full_size_sampled_A_apply(wb):
     ref = op.sampled_apply_A(m, mu, u, nodes)
     err = np.abs(y[:, nodes].T - ref).max() / np.abs(ref).max()
     assert err < 1e-12
+
+
+def test_full_size_sampled_A_apply_fp32(wb):
+    """32^3 Q2 in FP32 with the default kernel choice (row segments on this level): sampled nodes."""
+    cfg = inputs.WORKLOADS["32^3-Q2-S24-DR1e6"]
+    n, k = cfg["n"], cfg["k"]
+    c = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
+    mu_g, _ = wb.sinker_setup(n, k, c, cfg["omega"], cfg["delta"], cfg["dr"])
+    s = wb.Solver(n, k, mu_g, precision=wb.MIXED)
+    m = M.Mesh(n, n, n, k)
+    mu = N(mu_g)
+    u = np.random.default_rng(8).standard_normal(m.n_u)
+    y = N(s.apply_A(T(u, torch.float32))).reshape(3, -1)
+    nodes = np.random.default_rng(9).choice(m.n_nodes, 200, replace=False)
+    ref = op.sampled_apply_A(m, mu, u.astype(np.float32).astype(np.float64), nodes)
+    err = np.abs(y[:, nodes].T - ref).max() / np.abs(ref).max()
+    assert err < 2e-5
+
+
+def test_mixed_solve_point_and_row_kernels_agree(wb):
+    """The two single-precision kernel families (per point, per element) agree up to FP32 rounding."""
+    m, mu, f, _ = problem(8, 8, 8, 2, dr=1e6, ns=8)
+    fg = T(f.T.ravel())
+    u1, p1, r1 = gpu_solver(wb, m, mu, precision=wb.MIXED, elem_kernels=1).solve(fg, rtol=1e-8)
+    u2, p2, r2 = gpu_solver(wb, m, mu, precision=wb.MIXED, elem_kernels=2).solve(fg, rtol=1e-8)
+    assert abs(r1.iters - r2.iters) <= 2
+    assert rel(N(u1), N(u2)) < 1e-6
 
 
 def test_graph_replay_matches_direct_launches(wb):
