@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <atomic>
 #include <cstdint>
+#include <utility>
 
 #include "tables.h"
 
@@ -62,6 +63,36 @@ inline std::atomic<long long>& wb_launch_counter() {
   return n;
 }
 inline void wb_count_launch() { wb_launch_counter().fetch_add(1, std::memory_order_relaxed); }
+
+// Programmatic dependent launch.  Every kernel of this library is launched by wb_launch with
+// programmatic stream serialisation, so the next kernel of a stream is set up while the current
+// one drains (its blocks are released as the current kernel's blocks exit), and pdl_entry() is
+// the first statement of every kernel: it waits until the previous grid has completed with its
+// memory visible.  Ordering is therefore exactly that of plain stream launches; only launch
+// latency overlaps.  (Releasing the next grid at kernel entry instead measured slower: its
+// waiting blocks hold registers and shared memory during long kernels.)
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+#endif
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t wb_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             Args&&... args) {
+  wb_count_launch();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 #define WB_CUDA_TRY(expr)                                  \
   do {                                                     \

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_stokes(Grid g, const RefTables* __restrict__ tab, int colour, int count, const T* __restrict__ u,
          const T* __restrict__ us, const T* __restrict__ p, const T* __restrict__ coef, int coef_nodal,
          T* __restrict__ yu, T* __restrict__ yp) {
+  pdl_entry();
   constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, EPB = Cfg<N>::EPB, K = N - 1;
   constexpr bool DA = OPS & OP_A, DBT = OPS & OP_BT, DB = OPS & OP_B;
   constexpr bool SCAT = DA || DBT, GRAD = DA || DB;
@@ -169,10 +170,10 @@ cudaError_t run_stokes(const Grid& g, const RefTables* tab, const T* u, const T*
     for (int c = 0; c < 8; ++c) {
       int cnt = colour_count(g, c);
       if (cnt == 0) continue;
-      wb_count_launch(), k_stokes<T, N, OPS><<<(cnt + EPB - 1) / EPB, TH, 0, st>>>(g, tab, c, cnt, u, us, p, coef, coef_nodal, yu, yp);
+      wb_launch(k_stokes<T, N, OPS>, (cnt + EPB - 1) / EPB, TH, 0, st, g, tab, c, cnt, u, us, p, coef, coef_nodal, yu, yp);
     }
   } else {
-    wb_count_launch(), k_stokes<T, N, OPS><<<(g.ne + EPB - 1) / EPB, TH, 0, st>>>(g, tab, -1, g.ne, u, us, p, coef, coef_nodal, yu, yp);
+    wb_launch(k_stokes<T, N, OPS>, (g.ne + EPB - 1) / EPB, TH, 0, st, g, tab, -1, g.ne, u, us, p, coef, coef_nodal, yu, yp);
   }
   return cudaGetLastError();
 }
@@ -195,6 +196,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_poisson(Grid g, const RefTables* __restrict__ tab, int colour, int count, const T* __restrict__ u,
           const T* __restrict__ coef, T* __restrict__ y) {
+  pdl_entry();
   constexpr int N3 = Cfg<N>::N3, EPB = Cfg<N>::EPB, K = N - 1;
   __shared__ OpTab<T, N> st;
   __shared__ T su[EPB][N3];
@@ -247,7 +249,7 @@ cudaError_t run_poisson(const Grid& g, const RefTables* tab, const T* u, const T
   for (int c = 0; c < 8; ++c) {
     int cnt = colour_count(g, c);
     if (cnt == 0) continue;
-    wb_count_launch(), k_poisson<T, N><<<(cnt + EPB - 1) / EPB, TH, 0, st>>>(g, tab, c, cnt, u, coef, y);
+    wb_launch(k_poisson<T, N>, (cnt + EPB - 1) / EPB, TH, 0, st, g, tab, c, cnt, u, coef, y);
   }
   return cudaGetLastError();
 }
@@ -260,6 +262,7 @@ template <int N, bool VEC>
 __global__ void __launch_bounds__(Cfg<N>::N3)
 k_dense_assemble(Grid g, const RefTables* __restrict__ tab, int colour, const double* __restrict__ coef,
                  int coef_nodal, const int* __restrict__ map, int nfree, double* __restrict__ M, int ld) {
+  pdl_entry();
   constexpr int N3 = Cfg<N>::N3, K = N - 1, NC = VEC ? 3 : 1, NS = VEC ? 6 : 3;
   __shared__ SmTab<double, N> st;
   __shared__ double su[NC][N3];
@@ -327,6 +330,7 @@ k_dense_assemble(Grid g, const RefTables* __restrict__ tab, int colour, const do
 template <typename T, int N, bool VEC>
 __global__ void k_dinv_stiff(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ coef, int coef_nodal,
                              T* __restrict__ dinv) {
+  pdl_entry();
   constexpr int N3 = Cfg<N>::N3, K = N - 1;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nn) return;
@@ -366,6 +370,7 @@ __global__ void k_dinv_stiff(Grid g, const RefTables* __restrict__ tab, const T*
 // diag(B C^-1 B^T) per (element, mode): sum over element velocity DOFs of B_e[m][(c,a)]^2 cinv(a).
 template <typename T, int N>
 __global__ void k_dinv_Kw(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ cinv, T* __restrict__ dinv) {
+  pdl_entry();
   constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, K = N - 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.ne * NP) return;
@@ -396,6 +401,7 @@ __global__ void k_dinv_Kw(Grid g, const RefTables* __restrict__ tab, const T* __
 // C(n) = sum_{e containing n} a(e) W_q |J| sqrt(mu(n))  (mu == nullptr: the plain lumped mass)
 __global__ void k_lumped(Grid g, int K, const RefTables* __restrict__ tab, const double* __restrict__ mu, double amp,
                          double* __restrict__ out) {
+  pdl_entry();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nn) return;
   const int ix = n % g.NX, iy = (n / g.NX) % g.NY, iz = n / (g.NX * g.NY);
@@ -410,6 +416,7 @@ __global__ void k_lumped(Grid g, int K, const RefTables* __restrict__ tab, const
 // r_c(n) = sum_{e containing n} W_q sum_m psi_m(q) sum_m' minv[m][m'] r_d[e][m']   (|J| cancels)
 template <typename T, int N>
 __global__ void k_disc_to_cont(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ rd, T* __restrict__ rc) {
+  pdl_entry();
   constexpr int NP = Cfg<N>::NP, K = N - 1;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nn) return;
@@ -433,6 +440,7 @@ __global__ void k_disc_to_cont(Grid g, const RefTables* __restrict__ tab, const 
 template <typename T, int N>
 __global__ void k_cont_to_disc(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ ec, T* __restrict__ ed,
                                int add) {
+  pdl_entry();
   constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, K = N - 1;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.ne) return;
@@ -456,6 +464,7 @@ __global__ void k_cont_to_disc(Grid g, const RefTables* __restrict__ tab, const 
 template <typename T, int N>
 __global__ void k_poisson_coef0(Grid g, const double* __restrict__ mu, double amp, int pointwise_mu_only,
                                 T* __restrict__ c) {
+  pdl_entry();
   constexpr int N3 = Cfg<N>::N3, K = N - 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.ne * N3) return;
@@ -473,6 +482,7 @@ __global__ void k_poisson_coef0(Grid g, const double* __restrict__ mu, double am
 // c_E(q) = sum_{children s} sum_{q'} Tc[sz][l][l'] Tc[sy][j][j'] Tc[sx][i][i'] c_e(q')
 template <typename T, int N>
 __global__ void k_coarsen_coef(Grid gf, const RefTables* __restrict__ tab, const T* __restrict__ cf, T* __restrict__ cc) {
+  pdl_entry();
   constexpr int N3 = Cfg<N>::N3;
   const int ncx = gf.nx / 2, ncy = gf.ny / 2, ncz = gf.nz / 2;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -505,6 +515,7 @@ __global__ void k_coarsen_coef(Grid gf, const RefTables* __restrict__ tab, const
 template <typename T>
 __global__ void k_pass(const RefTables* __restrict__ tab, int K, int axis, int d0, int d1, int d2, int nc_el, int prolong,
                        const T* __restrict__ in, T* __restrict__ out, int add) {
+  pdl_entry();
   // output extents: the axis extent becomes the fine (prolong) or coarse (restrict) count
   const int nfine = 2 * K * nc_el + 1, ncoarse = K * nc_el + 1;
   int od[3] = {d0, d1, d2};
@@ -549,6 +560,7 @@ __global__ void k_pass(const RefTables* __restrict__ tab, int K, int axis, int d
 
 template <typename T>
 __global__ void k_mask_boundary(Grid g, int ncomp, T* __restrict__ v) {
+  pdl_entry();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nn) return;
   const int ix = n % g.NX, iy = (n / g.NX) % g.NY, iz = n / (g.NX * g.NY);
@@ -565,6 +577,7 @@ struct Centres {
 
 __global__ void k_sinker(Grid g, int K, Centres cs, int ns, double omega,
                          double delta, double dr, double beta, double* __restrict__ mu, double* __restrict__ f) {
+  pdl_entry();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nn) return;
   const int idx[3] = {n % g.NX, (n / g.NX) % g.NY, n / (g.NX * g.NY)};
@@ -627,7 +640,7 @@ cudaError_t run_dense(const Grid& g, const RefTables* tab, const double* coef, i
     int cnt = colour_count(g, c);
     if (cnt == 0) continue;
     dim3 grid(cnt, (VEC ? 3 : 1) * N3);
-    wb_count_launch(), k_dense_assemble<N, VEC><<<grid, N3, 0, st>>>(g, tab, c, coef, cn, map, nfree, M, ld);
+    wb_launch(k_dense_assemble<N, VEC>, grid, N3, 0, st, g, tab, c, coef, cn, map, nfree, M, ld);
   }
   return cudaGetLastError();
 }
@@ -640,6 +653,7 @@ cudaError_t launch_assemble_dense_A(const Grid& g, int k, const RefTables* dtab,
 
 namespace {
 __global__ void k_iota(int n, int* m) {
+  pdl_entry();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) m[t] = t;
 }
@@ -651,67 +665,67 @@ cudaError_t launch_assemble_dense_L_mapped(const Grid& g, int k, const RefTables
 }
 
 cudaError_t launch_identity_map(int n, int* m, cudaStream_t st) {
-  wb_count_launch(), k_iota<<<blocks_for(n, 256), 256, 0, st>>>(n, m);
+  wb_launch(k_iota, blocks_for(n, 256), 256, 0, st, n, m);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_dinv_A(const Grid& g, int k, const RefTables* dtab, const T* coef, int cn, T* dinv,
                           cudaStream_t st) {
-  WB_DISPATCH_N(k, ((wb_count_launch(), k_dinv_stiff<T, N, true><<<blocks_for(g.nn, 128), 128, 0, st>>>(g, dtab, coef, cn, dinv)),
+  WB_DISPATCH_N(k, ((wb_launch(k_dinv_stiff<T, N, true>, blocks_for(g.nn, 128), 128, 0, st, g, dtab, coef, cn, dinv)),
                     cudaGetLastError()));
 }
 
 template <typename T>
 cudaError_t launch_dinv_L(const Grid& g, int k, const RefTables* dtab, const T* coef, T* dinv, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((wb_count_launch(), k_dinv_stiff<T, N, false><<<blocks_for(g.nn, 128), 128, 0, st>>>(g, dtab, coef, 0, dinv)),
+  WB_DISPATCH_N(k, ((wb_launch(k_dinv_stiff<T, N, false>, blocks_for(g.nn, 128), 128, 0, st, g, dtab, coef, 0, dinv)),
                     cudaGetLastError()));
 }
 
 template <typename T>
 cudaError_t launch_dinv_Kw(const Grid& g, int k, const RefTables* dtab, const T* cinv, T* dinv, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((wb_count_launch(), k_dinv_Kw<T, N><<<blocks_for((long long)g.ne * Cfg<N>::NP, 128), 128, 0, st>>>(g, dtab, cinv, dinv)),
+  WB_DISPATCH_N(k, ((wb_launch(k_dinv_Kw<T, N>, blocks_for((long long)g.ne * Cfg<N>::NP, 128), 128, 0, st, g, dtab, cinv, dinv)),
                     cudaGetLastError()));
 }
 
 cudaError_t launch_lumped_weight(const Grid& g, int k, const RefTables* dtab, const double* mu, double a, double* out,
                                  cudaStream_t st) {
-  wb_count_launch(), k_lumped<<<blocks_for(g.nn, 128), 128, 0, st>>>(g, k, dtab, mu, a, out);
+  wb_launch(k_lumped, blocks_for(g.nn, 128), 128, 0, st, g, k, dtab, mu, a, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lumped_mass(const Grid& g, int k, const RefTables* dtab, double* out, cudaStream_t st) {
-  wb_count_launch(), k_lumped<<<blocks_for(g.nn, 128), 128, 0, st>>>(g, k, dtab, nullptr, 1.0, out);
+  wb_launch(k_lumped, blocks_for(g.nn, 128), 128, 0, st, g, k, dtab, nullptr, 1.0, out);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_poisson_coef0(const Grid& g, int k, const double* mu, double a, T* c, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((wb_count_launch(), k_poisson_coef0<T, N><<<blocks_for((long long)g.ne * Cfg<N>::N3, 128), 128, 0, st>>>(g, mu, a, 0, c)),
+  WB_DISPATCH_N(k, ((wb_launch(k_poisson_coef0<T, N>, blocks_for((long long)g.ne * Cfg<N>::N3, 128), 128, 0, st, g, mu, a, 0, c)),
                     cudaGetLastError()));
 }
 
 template <typename T>
 cudaError_t launch_nodal_to_points(const Grid& g, int k, const double* mu, T* c, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((wb_count_launch(), k_poisson_coef0<T, N><<<blocks_for((long long)g.ne * Cfg<N>::N3, 128), 128, 0, st>>>(g, mu, 1.0, 1, c)),
+  WB_DISPATCH_N(k, ((wb_launch(k_poisson_coef0<T, N>, blocks_for((long long)g.ne * Cfg<N>::N3, 128), 128, 0, st, g, mu, 1.0, 1, c)),
                     cudaGetLastError()));
 }
 
 template <typename T>
 cudaError_t launch_coarsen_coef(const Grid& gf, int k, const RefTables* dtab, const T* cf, T* cc, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((wb_count_launch(), k_coarsen_coef<T, N><<<blocks_for((long long)(gf.ne / 8) * Cfg<N>::N3, 128), 128, 0, st>>>(gf, dtab, cf, cc)),
+  WB_DISPATCH_N(k, ((wb_launch(k_coarsen_coef<T, N>, blocks_for((long long)(gf.ne / 8) * Cfg<N>::N3, 128), 128, 0, st, gf, dtab, cf, cc)),
                     cudaGetLastError()));
 }
 
 template <typename T>
 cudaError_t launch_disc_to_cont(const Grid& g, int k, const RefTables* dtab, const T* rd, T* rc, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((wb_count_launch(), k_disc_to_cont<T, N><<<blocks_for(g.nn, 128), 128, 0, st>>>(g, dtab, rd, rc)), cudaGetLastError()));
+  WB_DISPATCH_N(k, ((wb_launch(k_disc_to_cont<T, N>, blocks_for(g.nn, 128), 128, 0, st, g, dtab, rd, rc)), cudaGetLastError()));
 }
 
 template <typename T>
 cudaError_t launch_cont_to_disc(const Grid& g, int k, const RefTables* dtab, const T* ec, T* ed, int add,
                                 cudaStream_t st) {
-  WB_DISPATCH_N(k, ((wb_count_launch(), k_cont_to_disc<T, N><<<blocks_for(g.ne, 128), 128, 0, st>>>(g, dtab, ec, ed, add)), cudaGetLastError()));
+  WB_DISPATCH_N(k, ((wb_launch(k_cont_to_disc<T, N>, blocks_for(g.ne, 128), 128, 0, st, g, dtab, ec, ed, add)), cudaGetLastError()));
 }
 
 size_t transfer_work_size(const Grid& gc, int k) {
@@ -733,9 +747,9 @@ cudaError_t launch_prolong(const Grid& gc, int k, const RefTables* dtab, int nco
   for (int c = 0; c < ncomp; ++c) {
     const T* in = in_c + c * nc;
     T* out = out_f + c * nf;
-    wb_count_launch(), k_pass<T><<<blocks_for((long long)nfx * ncy * ncz, bs), bs, 0, st>>>(dtab, k, 0, ncx, ncy, ncz, gc.nx, 1, in, w1, 0);
-    wb_count_launch(), k_pass<T><<<blocks_for((long long)nfx * nfy * ncz, bs), bs, 0, st>>>(dtab, k, 1, nfx, ncy, ncz, gc.ny, 1, w1, w2, 0);
-    wb_count_launch(), k_pass<T><<<blocks_for((long long)nfx * nfy * nfz, bs), bs, 0, st>>>(dtab, k, 2, nfx, nfy, ncz, gc.nz, 1, w2, out, add);
+    wb_launch(k_pass<T>, blocks_for((long long)nfx * ncy * ncz, bs), bs, 0, st, dtab, k, 0, ncx, ncy, ncz, gc.nx, 1, in, w1, 0);
+    wb_launch(k_pass<T>, blocks_for((long long)nfx * nfy * ncz, bs), bs, 0, st, dtab, k, 1, nfx, ncy, ncz, gc.ny, 1, w1, w2, 0);
+    wb_launch(k_pass<T>, blocks_for((long long)nfx * nfy * nfz, bs), bs, 0, st, dtab, k, 2, nfx, nfy, ncz, gc.nz, 1, w2, out, add);
   }
   return cudaGetLastError();
 }
@@ -750,11 +764,11 @@ cudaError_t launch_restrict(const Grid& gc, int k, const RefTables* dtab, int nc
   for (int c = 0; c < ncomp; ++c) {
     const T* in = in_f + c * nf;
     T* out = out_c + c * nc;
-    wb_count_launch(), k_pass<T><<<blocks_for((long long)ncx * nfy * nfz, bs), bs, 0, st>>>(dtab, k, 0, nfx, nfy, nfz, gc.nx, 0, in, w1, 0);
-    wb_count_launch(), k_pass<T><<<blocks_for((long long)ncx * ncy * nfz, bs), bs, 0, st>>>(dtab, k, 1, ncx, nfy, nfz, gc.ny, 0, w1, w2, 0);
-    wb_count_launch(), k_pass<T><<<blocks_for((long long)ncx * ncy * ncz, bs), bs, 0, st>>>(dtab, k, 2, ncx, ncy, nfz, gc.nz, 0, w2, out, 0);
+    wb_launch(k_pass<T>, blocks_for((long long)ncx * nfy * nfz, bs), bs, 0, st, dtab, k, 0, nfx, nfy, nfz, gc.nx, 0, in, w1, 0);
+    wb_launch(k_pass<T>, blocks_for((long long)ncx * ncy * nfz, bs), bs, 0, st, dtab, k, 1, ncx, nfy, nfz, gc.ny, 0, w1, w2, 0);
+    wb_launch(k_pass<T>, blocks_for((long long)ncx * ncy * ncz, bs), bs, 0, st, dtab, k, 2, ncx, ncy, nfz, gc.nz, 0, w2, out, 0);
   }
-  if (mask) wb_count_launch(), k_mask_boundary<T><<<blocks_for(gc.nn, 256), 256, 0, st>>>(gc, ncomp, out_c);
+  if (mask) wb_launch(k_mask_boundary<T>, blocks_for(gc.nn, 256), 256, 0, st, gc, ncomp, out_c);
   return cudaGetLastError();
 }
 
@@ -765,13 +779,13 @@ cudaError_t launch_sinker(const Grid& g, int k, const RefTables& htab, const dou
   for (int s = 0; s < ns; ++s)
     for (int d = 0; d < 3; ++d) cs.c[s][d] = centres[3 * s + d];
   for (int a = 0; a < WB_MAXN; ++a) cs.x[a] = htab.x[a];
-  wb_count_launch(), k_sinker<<<blocks_for(g.nn, 128), 128, 0, st>>>(g, k, cs, ns, omega, delta, dr, beta, mu, f);
+  wb_launch(k_sinker, blocks_for(g.nn, 128), 128, 0, st, g, k, cs, ns, omega, delta, dr, beta, mu, f);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_mask_boundary(const Grid& g, int ncomp, T* v, cudaStream_t st) {
-  wb_count_launch(), k_mask_boundary<T><<<blocks_for(g.nn, 256), 256, 0, st>>>(g, ncomp, v);
+  wb_launch(k_mask_boundary<T>, blocks_for(g.nn, 256), 256, 0, st, g, ncomp, v);
   return cudaGetLastError();
 }
 
@@ -780,6 +794,7 @@ namespace {
 // (SplitMix64: Steele, Lea & Flood, OOPSLA 2014).
 template <typename T>
 __global__ void k_splitmix_start(long long n, unsigned long long seed, T* __restrict__ v) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
@@ -791,6 +806,7 @@ __global__ void k_splitmix_start(long long n, unsigned long long seed, T* __rest
 
 // F_c(n) = lm(n) f_c(n) on interior nodes, 0 on the boundary
 __global__ void k_load_vector(Grid g, const double* __restrict__ lm, const double* __restrict__ f, double* __restrict__ F) {
+  pdl_entry();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nn) return;
   const int ix = n % g.NX, iy = (n / g.NX) % g.NY, iz = n / (g.NX * g.NY);
@@ -801,12 +817,12 @@ __global__ void k_load_vector(Grid g, const double* __restrict__ lm, const doubl
 
 template <typename T>
 cudaError_t launch_splitmix_start(long long n, unsigned long long seed, T* v, cudaStream_t st) {
-  wb_count_launch(), k_splitmix_start<T><<<blocks_for(n, 256), 256, 0, st>>>(n, seed, v);
+  wb_launch(k_splitmix_start<T>, blocks_for(n, 256), 256, 0, st, n, seed, v);
   return cudaGetLastError();
 }
 
 cudaError_t launch_load_vector(const Grid& g, const double* lm, const double* f, double* F, cudaStream_t st) {
-  wb_count_launch(), k_load_vector<<<blocks_for(g.nn, 256), 256, 0, st>>>(g, lm, f, F);
+  wb_launch(k_load_vector, blocks_for(g.nn, 256), 256, 0, st, g, lm, f, F);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 enum : int {
@@ -104,6 +106,22 @@ inline FastDiv make_fastdiv(unsigned d) {
 __device__ inline unsigned fdiv(unsigned n, const FastDiv& f) { return f.d == 1 ? n : __umulhi(n, f.m) >> f.s; }
 #endif
 
+// Node-pass launch shape: x blocks of bs threads (a multiple of 32, at most 256), y rows and z
+// planes; z planes (and y rows beyond 65535) are strided only when the grid would exceed about
+// four waves of resident blocks (152 SMs, 64 warps and 32 blocks each).
+inline void node_pass_geometry(const Grid& g, dim3& grid, int& bs) {
+  bs = ((g.NX + 31) / 32) * 32;
+  if (bs > 256) bs = 256;
+  const long long nxb = (g.NX + bs - 1) / bs;
+  const long long gy = g.NY < 65535 ? g.NY : 65535;
+  const long long per_sm = std::min(32, 64 / (bs / 32));
+  const long long cap = 4 * 152 * per_sm;
+  long long gz = g.NZ;
+  if (nxb * gy * gz > cap) gz = std::max(1LL, cap / (nxb * gy));
+  if (gz > 65535) gz = 65535;
+  grid = dim3((unsigned)nxb, (unsigned)gy, (unsigned)gz);
+}
+
 constexpr int Q2_SEG = 32;      // elements per row segment (one warp)
 constexpr int Q2_ROW_LD = 66;   // stored nodes per x-line of a segment (65, padded to even)
 // Scratch entries the row-segment element pass writes for ncomp components.
@@ -117,3 +135,5 @@ cudaError_t launch_q2_elem(const Grid& g, int ops, const float* u, const float* 
 cudaError_t launch_q2_poisson(const Grid& g, const float* u, const float* coef, float* R, cudaStream_t st);
 cudaError_t launch_q2_gather(const Grid& g, int ncomp, int mask_boundary, const float* R, const Epi<float>& e,
                              cudaStream_t st);
+cudaError_t launch_q2_d2c(const Grid& g, const float* rd, float* rc, float* R, cudaStream_t st);
+cudaError_t launch_q2_c2d(const Grid& g, const float* ec, float* ed, int add, cudaStream_t st);

@@ -174,6 +174,7 @@ template <typename T, int N, int OPS>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, const T* __restrict__ us,
        const T* __restrict__ p, const T* __restrict__ coef, int coef_nodal, T* __restrict__ Ye, Epi<T> pe) {
+  pdl_entry();
   __shared__ OpTab<T, N> st;
   copy_tab(st, otab);
   const int nbatch = (g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB;
@@ -232,6 +233,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_elem_poisson(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ u, const T* __restrict__ coef,
                T* __restrict__ Ye) {
+  pdl_entry();
   __shared__ OpTab<T, N> st;
   copy_tab(st, otab);
   const int nbatch = (g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB;
@@ -241,43 +243,40 @@ k_elem_poisson(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict
   }
 }
 
-// Node pass: thread per node, sum over the elements containing it in (ez, ey, ex) order.
-// Grid (x blocks, NY, NZ), or a flat grid when NY or NZ exceed the grid-dimension limit.
-template <typename T, int N, int NC>
+// Node pass: thread per node, sum over the elements containing it in (ez, ey, ex) order; launch
+// shape of node_pass_geometry, epilogue operands loaded before the contributions.
+template <typename T, int N, int NC, int MODE>
 __global__ void k_gather(Grid g, int mask_boundary, const T* __restrict__ Ye, Epi<T> E) {
+  pdl_entry();
   constexpr int N3 = Cfg<N>::N3, K = N - 1;
-  int ix, iy, iz, n;
-  if (gridDim.y > 1) {   // 3-D grid (NY >= 3 always)
-    ix = blockIdx.x * blockDim.x + threadIdx.x;
-    iy = blockIdx.y;
-    iz = blockIdx.z;
-    if (ix >= g.NX) return;
-    n = ix + g.NX * (iy + g.NY * iz);
-  } else {
-    n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= g.nn) return;
-    ix = n % g.NX;
-    iy = (n / g.NX) % g.NY;
-    iz = n / (g.NX * g.NY);
-  }
-  T v[NC];
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= g.NX) return;
+  for (int iz = blockIdx.z; iz < g.NZ; iz += gridDim.z)
+    for (int iy = blockIdx.y; iy < g.NY; iy += gridDim.y) {
+      const int n = ix + g.NX * (iy + g.NY * iz);
+      EpiOps<T> eo[NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) v[c] = T(0);
-  if (!(mask_boundary && on_boundary(g, ix, iy, iz))) {
-    for_elements_of_node(g, K, ix, iy, iz, [&](int e, int, int, int, int a0, int a1, int a2) {
-      const T* src = Ye + (size_t)e * NC * N3 + (a0 + N * (a1 + N * a2));
+      for (int c = 0; c < NC; ++c) eo[c] = epi_pre<MODE>(E, (size_t)c * g.nn + n, n);
+      T v[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) v[c] += src[c * N3];
-    });
-  }
+      for (int c = 0; c < NC; ++c) v[c] = T(0);
+      if (!(mask_boundary && on_boundary(g, ix, iy, iz))) {
+        for_elements_of_node(g, K, ix, iy, iz, [&](int e, int, int, int, int a0, int a1, int a2) {
+          const T* src = Ye + (size_t)e * NC * N3 + (a0 + N * (a1 + N * a2));
 #pragma unroll
-  for (int c = 0; c < NC; ++c) epi_apply(E, (size_t)c * g.nn + n, n, v[c]);
+          for (int c = 0; c < NC; ++c) v[c] += src[c * N3];
+        });
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) epi_post<MODE>(E, (size_t)c * g.nn + n, eo[c], v[c]);
+    }
 }
 
 // Fine node value = sum over the N^3 coarse nodes of its coarse element of the tensor weights.
 template <typename T, int N>
 __global__ void k_prolong3d(Grid gc, const OpTab<T, N>* __restrict__ otab, int ncomp, const T* __restrict__ in_c,
                             T* __restrict__ out_f, int add) {
+  pdl_entry();
   constexpr int K = N - 1;
   __shared__ T P1[2][N][N];
   for (int t = threadIdx.x; t < 2 * N * N; t += blockDim.x) (&P1[0][0][0])[t] = (&otab->P1[0][0][0])[t];
@@ -324,6 +323,7 @@ template <typename T, int N>
 __global__ void k_rpass(const OpTab<T, N>* __restrict__ otab, int axis, int d0, int d1, int d2, int nc_el,
                         long long in_stride, long long out_stride, const T* __restrict__ in, T* __restrict__ out,
                         int mask_last) {
+  pdl_entry();
   constexpr int K = N - 1;
   __shared__ T P1[2][N][N];
   for (int t = threadIdx.x; t < 2 * N * N; t += blockDim.x) (&P1[0][0][0])[t] = (&otab->P1[0][0][0])[t];
@@ -367,11 +367,87 @@ __global__ void k_rpass(const OpTab<T, N>* __restrict__ otab, int axis, int d0, 
   dst[t] = acc;
 }
 
+// Q2 restriction out_c = P^T in_f in one pass.  Along each axis coarse node i contributes the
+// fine nodes of the coarse elements that contain it with the interpolation weights P1[s][a][b]
+// (child s, fine local node a, coarse local node b): an odd i (b = 1) takes fine nodes 2i - 1,
+// 2i, 2i + 1; an even i (b = 0 of its right element, b = 2 of its left one) takes 2i - 3,
+// 2i - 1 (left element), 2i, 2i + 1, 2i + 3 (right element), where they exist; the other fine
+// nodes of those elements have zero weight.  The x sum runs innermost.
+// Taps of coarse node i along one axis in five fixed slots (ascending fine index; ok = used).
+template <typename T>
+struct Q2Taps {
+  int off[5];
+  T w[5];
+  bool ok[5];
+};
+
+template <typename T>
+__device__ inline Q2Taps<T> q2_taps(int i, int nf, const T (*P1)[3][3]) {
+  Q2Taps<T> t;
+  const bool odd = i & 1;
+  t.off[0] = odd ? 2 * i - 1 : 2 * i - 3;
+  t.w[0] = odd ? P1[0][1][1] : P1[0][1][2];
+  t.ok[0] = odd || i > 0;
+  t.off[1] = odd ? 2 * i : 2 * i - 1;
+  t.w[1] = odd ? P1[1][0][1] : P1[1][1][2];
+  t.ok[1] = odd || i > 0;
+  t.off[2] = odd ? 2 * i + 1 : 2 * i;
+  t.w[2] = odd ? P1[1][1][1] : P1[0][0][0];
+  t.ok[2] = true;
+  t.off[3] = 2 * i + 1;
+  t.w[3] = P1[0][1][0];
+  t.ok[3] = !odd && 2 * i + 1 < nf;
+  t.off[4] = 2 * i + 3;
+  t.w[4] = P1[1][1][0];
+  t.ok[4] = !odd && 2 * i + 1 < nf;
+  return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_restrict_q2(Grid gc, const OpTab<T, 3>* __restrict__ otab, int ncomp, const T* __restrict__ in,
+                              T* __restrict__ out, int mask) {
+  pdl_entry();
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= gc.NX) return;
+  const int NXf = 2 * gc.NX - 1, NYf = 2 * gc.NY - 1, NZf = 2 * gc.NZ - 1;
+  const size_t nf = (size_t)NXf * NYf * NZf;
+  const T(*P1)[3][3] = otab->P1;
+  const Q2Taps<T> tx = q2_taps<T>(ix, NXf, P1);
+  for (int iz = blockIdx.z; iz < gc.NZ; iz += gridDim.z)
+    for (int iy = blockIdx.y; iy < gc.NY; iy += gridDim.y) {
+      const size_t n = (size_t)ix + (size_t)gc.NX * (iy + (size_t)gc.NY * iz);
+      const bool zero = mask && on_boundary(gc, ix, iy, iz);
+      const Q2Taps<T> ty = q2_taps<T>(iy, NYf, P1), tz = q2_taps<T>(iz, NZf, P1);
+      for (int c = 0; c < ncomp; ++c) {
+        T acc = T(0);
+        if (!zero) {
+          const T* src = in + (size_t)c * nf;
+#pragma unroll
+          for (int a = 0; a < 5; ++a) {
+            if (!tz.ok[a]) continue;
+#pragma unroll
+            for (int b = 0; b < 5; ++b) {
+              if (!ty.ok[b]) continue;
+              const T* row = src + (size_t)NXf * (ty.off[b] + (size_t)NYf * tz.off[a]);
+              T r = T(0);
+#pragma unroll
+              for (int t = 0; t < 5; ++t)
+                if (tx.ok[t]) r += tx.w[t] * row[tx.off[t]];
+              acc += tz.w[a] * ty.w[b] * r;
+            }
+          }
+        }
+        out[(size_t)c * gc.nn + n] = acc;
+      }
+    }
+}
+
 // Pressure transfers of the two-space Poisson cycle (|J| cancels between M_d^-1 and the masses):
 //   element pass of r_c = M_cd M_d^-1 r_d: Ye[e][q] = W_q sum_m psi_m(q) (Minv r_e)_m
 template <typename T, int N>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_d2c_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ rd, T* __restrict__ Ye) {
+  pdl_entry();
   constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, EPB = Cfg<N>::EPB;
   __shared__ OpTab<T, N> st;
   __shared__ T sv[EPB][NP];
@@ -398,6 +474,7 @@ k_d2c_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ r
 template <typename T, int N>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_c2d_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ ec, T* __restrict__ ed, int add) {
+  pdl_entry();
   constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, EPB = Cfg<N>::EPB, K = N - 1;
   __shared__ OpTab<T, N> st;
   __shared__ T sw[EPB][N3];
@@ -445,11 +522,11 @@ cudaError_t run_elem(const Grid& g, const void* otab_v, int ops, const T* u, con
   const OpTab<T, N>* tab = static_cast<const OpTab<T, N>*>(otab_v);
   const unsigned blocks = elem_blocks(g.ne, EPB);
   switch (ops) {
-    case OP_A: wb_count_launch(), k_elem<T, N, OP_A><<<blocks, TH, 0, st>>>(g, tab, u, us, p, coef, cn, Ye, pe); break;
-    case OP_BT: wb_count_launch(), k_elem<T, N, OP_BT><<<blocks, TH, 0, st>>>(g, tab, u, us, p, coef, cn, Ye, pe); break;
-    case OP_B: wb_count_launch(), k_elem<T, N, OP_B><<<blocks, TH, 0, st>>>(g, tab, u, us, p, coef, cn, Ye, pe); break;
+    case OP_A: wb_launch(k_elem<T, N, OP_A>, blocks, TH, 0, st, g, tab, u, us, p, coef, cn, Ye, pe); break;
+    case OP_BT: wb_launch(k_elem<T, N, OP_BT>, blocks, TH, 0, st, g, tab, u, us, p, coef, cn, Ye, pe); break;
+    case OP_B: wb_launch(k_elem<T, N, OP_B>, blocks, TH, 0, st, g, tab, u, us, p, coef, cn, Ye, pe); break;
     case OP_A | OP_BT | OP_B:
-      wb_count_launch(), k_elem<T, N, OP_A | OP_BT | OP_B><<<blocks, TH, 0, st>>>(g, tab, u, us, p, coef, cn, Ye, pe);
+      wb_launch(k_elem<T, N, OP_A | OP_BT | OP_B>, blocks, TH, 0, st, g, tab, u, us, p, coef, cn, Ye, pe);
       break;
     default: return cudaErrorInvalidValue;
   }
@@ -500,8 +577,7 @@ cudaError_t launch_elem_poisson(const Grid& g, int k, const void* otab, const T*
   if constexpr (std::is_same<T, float>::value) {
     if (row_path<T>(g, k)) return launch_q2_poisson(g, u, coef, Ye, st);
   }
-  WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_elem_poisson<T, N><<<elem_blocks(g.ne, Cfg<N>::EPB), Cfg<N>::THREADS, 0,
-                                                                st>>>(g, WB_TAB(T), u, coef, Ye)),
+  WB_FUSED_DISPATCH(k, ((wb_launch(k_elem_poisson<T, N>, elem_blocks(g.ne, Cfg<N>::EPB), Cfg<N>::THREADS, 0, st, g, WB_TAB(T), u, coef, Ye)),
                         cudaGetLastError()));
 }
 
@@ -512,11 +588,14 @@ cudaError_t launch_gather_elem(const Grid& g, int k, int ncomp, int mask, const 
 template <typename T>
 cudaError_t launch_disc_to_cont_fused(const Grid& g, int k, const void* otab, const T* rd, T* rc, T* Ye,
                                       cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (row_path<T>(g, k)) return launch_q2_d2c(g, rd, rc, Ye, st);
+  }
   cudaError_t e = cudaSuccess;
   switch (k) {
-    case 2: { constexpr int N = 3; wb_count_launch(), k_d2c_elem<T, N><<<(unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB), Cfg<N>::THREADS, 0, st>>>(g, WB_TAB(T), rd, Ye); break; }
-    case 3: { constexpr int N = 4; wb_count_launch(), k_d2c_elem<T, N><<<(unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB), Cfg<N>::THREADS, 0, st>>>(g, WB_TAB(T), rd, Ye); break; }
-    case 4: { constexpr int N = 5; wb_count_launch(), k_d2c_elem<T, N><<<(unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB), Cfg<N>::THREADS, 0, st>>>(g, WB_TAB(T), rd, Ye); break; }
+    case 2: { constexpr int N = 3; wb_launch(k_d2c_elem<T, N>, (unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB), Cfg<N>::THREADS, 0, st, g, WB_TAB(T), rd, Ye); break; }
+    case 3: { constexpr int N = 4; wb_launch(k_d2c_elem<T, N>, (unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB), Cfg<N>::THREADS, 0, st, g, WB_TAB(T), rd, Ye); break; }
+    case 4: { constexpr int N = 5; wb_launch(k_d2c_elem<T, N>, (unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB), Cfg<N>::THREADS, 0, st, g, WB_TAB(T), rd, Ye); break; }
     default: return cudaErrorInvalidValue;
   }
   e = cudaGetLastError();
@@ -530,8 +609,10 @@ cudaError_t launch_disc_to_cont_fused(const Grid& g, int k, const void* otab, co
 template <typename T>
 cudaError_t launch_cont_to_disc_fused(const Grid& g, int k, const void* otab, const T* ec, T* ed, int add,
                                       cudaStream_t st) {
-  WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_c2d_elem<T, N><<<(unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB),
-                                                            Cfg<N>::THREADS, 0, st>>>(g, WB_TAB(T), ec, ed, add)),
+  if constexpr (std::is_same<T, float>::value) {
+    if (row_path<T>(g, k)) return launch_q2_c2d(g, ec, ed, add, st);
+  }
+  WB_FUSED_DISPATCH(k, ((wb_launch(k_c2d_elem<T, N>, (unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB), Cfg<N>::THREADS, 0, st, g, WB_TAB(T), ec, ed, add)),
                         cudaGetLastError()));
 }
 
@@ -539,18 +620,21 @@ cudaError_t launch_cont_to_disc_fused(const Grid& g, int k, const void* otab, co
 template <typename T>
 cudaError_t launch_gather_elem(const Grid& g, int k, int ncomp, int mask, const T* Ye, const Epi<T>& e,
                                cudaStream_t st) {
-  const bool flat = g.NY > 65535 || g.NZ > 65535;
-  const int bs = flat || g.NX >= 128 ? 128 : (g.NX + 31) / 32 * 32;
-  const dim3 grid = flat ? dim3(nb(g.nn, bs)) : dim3(nb(g.NX, bs), (unsigned)g.NY, (unsigned)g.NZ);
-  if (ncomp == 3) {
-    WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_gather<T, N, 3><<<grid, bs, 0, st>>>(g, mask, Ye, e)),
-                          cudaGetLastError()));
-  }
-  if (ncomp == 1) {
-    WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_gather<T, N, 1><<<grid, bs, 0, st>>>(g, mask, Ye, e)),
-                          cudaGetLastError()));
-  }
-  return cudaErrorInvalidValue;
+  dim3 grid;
+  int bs;
+  node_pass_geometry(g, grid, bs);
+  return epi_dispatch(e.mode, [&](auto m) -> cudaError_t {
+    constexpr int MODE = decltype(m)::value;
+    if (ncomp == 3) {
+      WB_FUSED_DISPATCH(k, ((wb_launch(k_gather<T, N, 3, MODE>, grid, bs, 0, st, g, mask, Ye, e)),
+                            cudaGetLastError()));
+    }
+    if (ncomp == 1) {
+      WB_FUSED_DISPATCH(k, ((wb_launch(k_gather<T, N, 1, MODE>, grid, bs, 0, st, g, mask, Ye, e)),
+                            cudaGetLastError()));
+    }
+    return cudaErrorInvalidValue;
+  });
 }
 
 template <typename T>
@@ -565,7 +649,7 @@ template <typename T>
 cudaError_t launch_prolong_fused(const Grid& gc, int k, const void* otab, int ncomp, const T* in_c, T* out_f, int add,
                                  cudaStream_t st) {
   const long long nf = (long long)(2 * k * gc.nx + 1) * (2 * k * gc.ny + 1) * (2 * k * gc.nz + 1);
-  WB_FUSED_DISPATCH(k, ((wb_count_launch(), k_prolong3d<T, N><<<nb(nf, 128), 128, 0, st>>>(gc, WB_TAB(T), ncomp, in_c,
+  WB_FUSED_DISPATCH(k, ((wb_launch(k_prolong3d<T, N>, nb(nf, 128), 128, 0, st, gc, WB_TAB(T), ncomp, in_c,
                                                                                             out_f, add)),
                         cudaGetLastError()));
 }
@@ -581,9 +665,9 @@ cudaError_t run_restrict(const Grid& gc, const void* otab, int ncomp, const T* i
   const long long nf = (long long)nfx * nfy * nfz, n1 = (long long)ncx * nfy * nfz, n2 = (long long)ncx * ncy * nfz;
   const long long nc = (long long)ncx * ncy * ncz;
   const int bs = 256;
-  wb_count_launch(), k_rpass<T, N><<<dim3(nb(n1, bs), ncomp), bs, 0, st>>>(tab, 0, nfx, nfy, nfz, gc.nx, nf, n1, in_f, w1, 0);
-  wb_count_launch(), k_rpass<T, N><<<dim3(nb(n2, bs), ncomp), bs, 0, st>>>(tab, 1, ncx, nfy, nfz, gc.ny, n1, n2, w1, w2, 0);
-  wb_count_launch(), k_rpass<T, N><<<dim3(nb(nc, bs), ncomp), bs, 0, st>>>(tab, 2, ncx, ncy, nfz, gc.nz, n2, nc, w2, out_c,
+  wb_launch(k_rpass<T, N>, dim3(nb(n1, bs), ncomp), bs, 0, st, tab, 0, nfx, nfy, nfz, gc.nx, nf, n1, in_f, w1, 0);
+  wb_launch(k_rpass<T, N>, dim3(nb(n2, bs), ncomp), bs, 0, st, tab, 1, ncx, nfy, nfz, gc.ny, n1, n2, w1, w2, 0);
+  wb_launch(k_rpass<T, N>, dim3(nb(nc, bs), ncomp), bs, 0, st, tab, 2, ncx, ncy, nfz, gc.nz, n2, nc, w2, out_c,
                                                                            mask);
   return cudaGetLastError();
 }
@@ -592,6 +676,16 @@ cudaError_t run_restrict(const Grid& gc, const void* otab, int ncomp, const T* i
 template <typename T>
 cudaError_t launch_restrict_batched(const Grid& gc, int k, const void* otab, int ncomp, const T* in_f, T* out_c,
                                     int mask, T* w1, T* w2, cudaStream_t st) {
+  // One pass (one thread per coarse node) pays off on large coarse grids; small ones keep three
+  // short separable passes, which have more threads per node.
+  if (k == 2 && gc.nn >= 100000) {
+    dim3 grid;
+    int bs;
+    node_pass_geometry(gc, grid, bs);
+    wb_launch(k_restrict_q2<T>, grid, bs, 0, st, gc, static_cast<const OpTab<T, 3>*>(otab), ncomp, in_f,
+                                                              out_c, mask);
+    return cudaGetLastError();
+  }
   WB_FUSED_DISPATCH(k, (run_restrict<T, N>(gc, otab, ncomp, in_f, out_c, mask, w1, w2, st)));
 }
 

@@ -52,6 +52,7 @@ int ensure_slot(DeviceSlot** out) {
 }
 
 __global__ void k_invert_interior(Grid g, double* __restrict__ c) {
+  pdl_entry();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nn) return;
   const int ix = n % g.NX, iy = (n / g.NX) % g.NY, iz = n / (g.NX * g.NY);
@@ -77,7 +78,7 @@ extern "C" int wbfbt_apply_Kw_noalloc(const wbfbt_mesh* mesh, int k, const doubl
   double* bt = slot->scratch + nn;
   // C = M~_u(a sqrt(mu)) per node, then its inverse with zeros on the Dirichlet nodes
   if (launch_lumped_weight(g, k, tab, mu_nodes, a, cinv, s) != cudaSuccess) return WBFBT_ERR_CUDA;
-  wb_count_launch(), k_invert_interior<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(g, cinv);
+  wb_launch(k_invert_interior, (unsigned)((nn + 255) / 256), 256, 0, s, g, cinv);
   // B^T p into the scratch velocity (the launcher zeroes it first), then B (C^-1 .)
   if (launch_stokes<double>(g, k, tab, OP_BT, nullptr, nullptr, p, nullptr, 0, bt, nullptr, s) != cudaSuccess)
     return WBFBT_ERR_CUDA;

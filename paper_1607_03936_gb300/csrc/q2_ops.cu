@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(32 * WARPS)
 k_q2_elem(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restrict__ u,
           const float* __restrict__ p, const float* __restrict__ coef, int coef_nodal, float* __restrict__ R,
           Epi<float> pe) {
+  pdl_entry();
   constexpr bool DA = OPS & OP_A, DBT = OPS & OP_BT, DB = OPS & OP_B;
   constexpr bool GRAD = DA || DB, SCAT = DA || DBT;
   const RowPos rp = row_pos(g, rw);
@@ -223,6 +224,7 @@ k_q2_elem(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restr
 __global__ void __launch_bounds__(32 * WARPS)
 k_q2_poisson(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restrict__ u,
              const float* __restrict__ coef, float* __restrict__ R) {
+  pdl_entry();
   const RowPos rp = row_pos(g, rw);
   if (!rp.warp_live) return;
   const int n0 = 2 * rp.ex + g.NX * (2 * rp.ey + g.NY * 2 * rp.ez);
@@ -267,60 +269,129 @@ k_q2_poisson(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __re
   row_store<1>(g, rp, out, R);
 }
 
-// Node pass: grid (x blocks, NY, NZ).  Lines through node (ix, iy, iz): along z the element rows
-// ez = iz / 2 (l = 1) for odd iz, else (iz / 2 - 1, l = 2) and (iz / 2, l = 0) where they exist;
-// the same along y; along x the segment s = ix / 64 at X = ix - 64 s, and also s - 1 at X = 64
-// when ix is a segment's first node.
-template <int NC>
+// Pressure transfers of the two-space Poisson cycle (Sec. 6), one thread per element (|J|
+// cancels between M_d^-1 and the masses):
+//   r_c = M_cd M_d^-1 r_d: element part out[q] = W_q sum_m psi_m(q) (Minv r_e)_m, assembled
+//   along rows like the operators (the node pass then stores the sums);
+__global__ void __launch_bounds__(32 * WARPS)
+k_q2_d2c(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restrict__ rd, float* __restrict__ R) {
+  pdl_entry();
+  const RowPos rp = row_pos(g, rw);
+  if (!rp.warp_live) return;
+  float rv[4], v[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) rv[m] = rp.act ? __ldg(rd + (size_t)rp.e * 4 + m) : 0.f;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float a = 0.f;
+#pragma unroll
+    for (int mp = 0; mp < 4; ++mp) a += tb.Minv[m][mp] * rv[mp];
+    v[m] = a;
+  }
+  float out[1][27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    float a = 0.f;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) a += tb.Psi[q][m] * v[m];
+    out[0][q] = tb.Wref[q] * a;
+  }
+  row_store<1>(g, rp, out, R);
+}
+
+//   e_d (+)= M_d^-1 M_dc e_c: e_d[e][m] = sum_m' Minv[m][m'] sum_q W_q psi_m'(q) e_c(node(e, q)).
+__global__ void __launch_bounds__(32 * WARPS)
+k_q2_c2d(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restrict__ ec, float* __restrict__ ed,
+         int add) {
+  pdl_entry();
+  const RowPos rp = row_pos(g, rw);
+  if (!rp.act) return;
+  const int n0 = 2 * rp.ex + g.NX * (2 * rp.ey + g.NY * 2 * rp.ez);
+  float mom[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int roff = n0 + g.NX * (j + g.NY * l);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int q = q3(i, j, l);
+        const float w = tb.Wref[q] * __ldg(ec + roff + i);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) mom[m] += tb.Psi[q][m] * w;
+      }
+    }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float a = 0.f;
+#pragma unroll
+    for (int mp = 0; mp < 4; ++mp) a += tb.Minv[m][mp] * mom[mp];
+    float* dst = ed + (size_t)rp.e * 4 + m;
+    *dst = add ? *dst + a : a;
+  }
+}
+
+// Node pass: grid (x blocks, y rows, z planes), z (and y) strided so the launch is about one
+// wave.  Lines through node (ix, iy, iz): along z the element rows ez = iz / 2 (l = 1) for odd
+// iz, else (iz / 2 - 1, l = 2) and (iz / 2, l = 0) where they exist; the same along y; along x
+// the segment s = ix / 64 at X = ix - 64 s, and also s - 1 at X = 64 when ix is a segment's
+// first node.  The epilogue operands are loaded before the partials.
+template <int NC, int MODE>
 __global__ void k_q2_gather(Grid g, int nseg, int mask_boundary, const float* __restrict__ R, Epi<float> E) {
+  pdl_entry();
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-  const int iy = blockIdx.y, iz = blockIdx.z;
   if (ix >= g.NX) return;
-  const int n = ix + g.NX * (iy + g.NY * iz);
-  float v[NC];
+  const int s = ix >> 6, X = ix & 63;
+  const bool prev = X == 0 && s > 0, cur = s < nseg;
+  const size_t per_seg = (size_t)g.nz * g.ny * 9;
+  for (int iz = blockIdx.z; iz < g.NZ; iz += gridDim.z)
+    for (int iy = blockIdx.y; iy < g.NY; iy += gridDim.y) {
+      const int n = ix + g.NX * (iy + g.NY * iz);
+      EpiOps<float> eo[NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) v[c] = 0.f;
-  if (!(mask_boundary && on_boundary(g, ix, iy, iz))) {
-    int zr[2] = {0, 0}, zl[2] = {0, 0}, nzr = 0, yr[2] = {0, 0}, yl[2] = {0, 0}, nyr = 0;
-    if (iz & 1) {
-      zr[0] = iz >> 1; zl[0] = 1; nzr = 1;
-    } else {
-      if (iz > 0) { zr[0] = (iz >> 1) - 1; zl[0] = 2; nzr = 1; }
-      if ((iz >> 1) < g.nz) { zr[nzr] = iz >> 1; zl[nzr] = 0; ++nzr; }
-    }
-    if (iy & 1) {
-      yr[0] = iy >> 1; yl[0] = 1; nyr = 1;
-    } else {
-      if (iy > 0) { yr[0] = (iy >> 1) - 1; yl[0] = 2; nyr = 1; }
-      if ((iy >> 1) < g.ny) { yr[nyr] = iy >> 1; yl[nyr] = 0; ++nyr; }
-    }
-    const int s = ix >> 6, X = ix & 63;
-    const bool prev = X == 0 && s > 0, cur = s < nseg;
-    const size_t per_seg = (size_t)g.nz * g.ny * 9;
+      for (int c = 0; c < NC; ++c) eo[c] = epi_pre<MODE>(E, (size_t)c * g.nn + n, n);
+      float v[NC];
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      if (a < nzr) {
+      for (int c = 0; c < NC; ++c) v[c] = 0.f;
+      if (!(mask_boundary && on_boundary(g, ix, iy, iz))) {
+        int zr[2] = {0, 0}, zl[2] = {0, 0}, nzr = 0, yr[2] = {0, 0}, yl[2] = {0, 0}, nyr = 0;
+        if (iz & 1) {
+          zr[0] = iz >> 1; zl[0] = 1; nzr = 1;
+        } else {
+          if (iz > 0) { zr[0] = (iz >> 1) - 1; zl[0] = 2; nzr = 1; }
+          if ((iz >> 1) < g.nz) { zr[nzr] = iz >> 1; zl[nzr] = 0; ++nzr; }
+        }
+        if (iy & 1) {
+          yr[0] = iy >> 1; yl[0] = 1; nyr = 1;
+        } else {
+          if (iy > 0) { yr[0] = (iy >> 1) - 1; yl[0] = 2; nyr = 1; }
+          if ((iy >> 1) < g.ny) { yr[nyr] = iy >> 1; yl[nyr] = 0; ++nyr; }
+        }
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          if (b < nyr) {
-            const size_t rowl = ((size_t)zr[a] * g.ny + yr[b]) * 9 + 3 * zl[a] + yl[b];   // within a segment
-            if (prev) {
-              const float* src = R + ((s - 1) * per_seg + rowl) * NC * Q2_ROW_LD + 2 * Q2_SEG;
+        for (int a = 0; a < 2; ++a) {
+          if (a < nzr) {
 #pragma unroll
-              for (int c = 0; c < NC; ++c) v[c] += __ldg(src + c * Q2_ROW_LD);
-            }
-            if (cur) {
-              const float* src = R + ((size_t)s * per_seg + rowl) * NC * Q2_ROW_LD + X;
+            for (int b = 0; b < 2; ++b) {
+              if (b < nyr) {
+                const size_t rowl = ((size_t)zr[a] * g.ny + yr[b]) * 9 + 3 * zl[a] + yl[b];   // within a segment
+                if (prev) {
+                  const float* src = R + ((s - 1) * per_seg + rowl) * NC * Q2_ROW_LD + 2 * Q2_SEG;
 #pragma unroll
-              for (int c = 0; c < NC; ++c) v[c] += __ldg(src + c * Q2_ROW_LD);
+                  for (int c = 0; c < NC; ++c) v[c] += __ldg(src + c * Q2_ROW_LD);
+                }
+                if (cur) {
+                  const float* src = R + ((size_t)s * per_seg + rowl) * NC * Q2_ROW_LD + X;
+#pragma unroll
+                  for (int c = 0; c < NC; ++c) v[c] += __ldg(src + c * Q2_ROW_LD);
+                }
+              }
             }
           }
         }
       }
-    }
-  }
 #pragma unroll
-  for (int c = 0; c < NC; ++c) epi_apply(E, (size_t)c * g.nn + n, n, v[c]);
+      for (int c = 0; c < NC; ++c) epi_post<MODE>(E, (size_t)c * g.nn + n, eo[c], v[c]);
+    }
 }
 
 const RefTables& ref_tables_q2() {
@@ -353,11 +424,11 @@ cudaError_t launch_q2_elem(const Grid& g, int ops, const float* u, const float* 
   const Tab2 tb = q2_tab(g);
   const unsigned nbk = elem_grid(rw), nt = 32 * WARPS;
   switch (ops) {
-    case OP_A: wb_count_launch(), k_q2_elem<OP_A><<<nbk, nt, 0, st>>>(g, rw, tb, u, p, coef, coef_nodal, R, pe); break;
-    case OP_BT: wb_count_launch(), k_q2_elem<OP_BT><<<nbk, nt, 0, st>>>(g, rw, tb, u, p, coef, coef_nodal, R, pe); break;
-    case OP_B: wb_count_launch(), k_q2_elem<OP_B><<<nbk, nt, 0, st>>>(g, rw, tb, u, p, coef, coef_nodal, R, pe); break;
+    case OP_A: wb_launch(k_q2_elem<OP_A>, nbk, nt, 0, st, g, rw, tb, u, p, coef, coef_nodal, R, pe); break;
+    case OP_BT: wb_launch(k_q2_elem<OP_BT>, nbk, nt, 0, st, g, rw, tb, u, p, coef, coef_nodal, R, pe); break;
+    case OP_B: wb_launch(k_q2_elem<OP_B>, nbk, nt, 0, st, g, rw, tb, u, p, coef, coef_nodal, R, pe); break;
     case OP_A | OP_BT | OP_B:
-      wb_count_launch(), k_q2_elem<OP_A | OP_BT | OP_B><<<nbk, nt, 0, st>>>(g, rw, tb, u, p, coef, coef_nodal, R, pe);
+      wb_launch(k_q2_elem<OP_A | OP_BT | OP_B>, nbk, nt, 0, st, g, rw, tb, u, p, coef, coef_nodal, R, pe);
       break;
     default: return cudaErrorInvalidValue;
   }
@@ -366,21 +437,41 @@ cudaError_t launch_q2_elem(const Grid& g, int ops, const float* u, const float* 
 
 cudaError_t launch_q2_poisson(const Grid& g, const float* u, const float* coef, float* R, cudaStream_t st) {
   const Rows rw = make_rows(g);
-  wb_count_launch(), k_q2_poisson<<<elem_grid(rw), 32 * WARPS, 0, st>>>(g, rw, q2_tab(g), u, coef, R);
+  wb_launch(k_q2_poisson, elem_grid(rw), 32 * WARPS, 0, st, g, rw, q2_tab(g), u, coef, R);
   return cudaGetLastError();
 }
 
 cudaError_t launch_q2_gather(const Grid& g, int ncomp, int mask_boundary, const float* R, const Epi<float>& e,
                              cudaStream_t st) {
   const Rows rw = make_rows(g);
-  const int bs = g.NX >= 128 ? 128 : (g.NX + 31) / 32 * 32;
-  if (g.NY > 65535 || g.NZ > 65535) return cudaErrorInvalidValue;
-  const dim3 grid((unsigned)((g.NX + bs - 1) / bs), (unsigned)g.NY, (unsigned)g.NZ);
-  if (ncomp == 3)
-    wb_count_launch(), k_q2_gather<3><<<grid, bs, 0, st>>>(g, rw.nseg, mask_boundary, R, e);
-  else if (ncomp == 1)
-    wb_count_launch(), k_q2_gather<1><<<grid, bs, 0, st>>>(g, rw.nseg, mask_boundary, R, e);
-  else
-    return cudaErrorInvalidValue;
+  dim3 grid;
+  int bs;
+  node_pass_geometry(g, grid, bs);
+  return epi_dispatch(e.mode, [&](auto m) {
+    constexpr int MODE = decltype(m)::value;
+    if (ncomp == 3)
+      wb_launch(k_q2_gather<3, MODE>, grid, bs, 0, st, g, rw.nseg, mask_boundary, R, e);
+    else if (ncomp == 1)
+      wb_launch(k_q2_gather<1, MODE>, grid, bs, 0, st, g, rw.nseg, mask_boundary, R, e);
+    else
+      return cudaErrorInvalidValue;
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_q2_d2c(const Grid& g, const float* rd, float* rc, float* R, cudaStream_t st) {
+  const Rows rw = make_rows(g);
+  wb_launch(k_q2_d2c, elem_grid(rw), 32 * WARPS, 0, st, g, rw, q2_tab(g), rd, R);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  Epi<float> ep;
+  ep.mode = EPI_STORE;
+  ep.y = rc;
+  return launch_q2_gather(g, 1, 0, R, ep, st);
+}
+
+cudaError_t launch_q2_c2d(const Grid& g, const float* ec, float* ed, int add, cudaStream_t st) {
+  const Rows rw = make_rows(g);
+  wb_launch(k_q2_c2d, elem_grid(rw), 32 * WARPS, 0, st, g, rw, q2_tab(g), ec, ed, add);
   return cudaGetLastError();
 }

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(128) k_conv(int n, int batch, const bf16* __re
                                               const bf16* __restrict__ W, const float* __restrict__ bias, int relu,
                                               const bf16* __restrict__ mask, int ldm, int cvalid,
                                               bf16* __restrict__ y, int ldy, float* __restrict__ yf, int ldyf) {
+  pdl_entry();
   const int V = n * n * n;
   const int tiles = (V + 15) / 16;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -116,6 +117,7 @@ template <int NT>
 __global__ void __launch_bounds__(256) k_wgrad(int n, int batch, const bf16* __restrict__ x, int ldx, int cin,
                                                const bf16* __restrict__ g, int ldg, int cout,
                                                float* __restrict__ dW) {
+  pdl_entry();
   const int V = n * n * n, tot = V * batch;
   const int tap = blockIdx.x, ci0 = blockIdx.y * 16;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
@@ -184,6 +186,7 @@ __global__ void __launch_bounds__(256) k_wgrad(int n, int batch, const bf16* __r
 
 // db[co] = sum over rows of g[row][co] (one block per channel, fixed tree)
 __global__ void k_colsum(const bf16* __restrict__ g, int ldg, long long rows, float* __restrict__ db) {
+  pdl_entry();
   const int co = blockIdx.x;
   float s = 0.f;
   for (long long r = threadIdx.x; r < rows; r += blockDim.x) s += __bfloat162float(g[r * ldg + co]);
@@ -200,6 +203,7 @@ __global__ void k_colsum(const bf16* __restrict__ g, int ldg, long long rows, fl
 // 2x2x2 average pooling: out [b][n/2 grid][c] from in [b][n grid][c]
 __global__ void k_pool(int n, int batch, int c, const bf16* __restrict__ in, int ldi, bf16* __restrict__ out,
                        int ldo) {
+  pdl_entry();
   const int m = n / 2, Vo = m * m * m;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)Vo * batch * c) return;
@@ -220,6 +224,7 @@ __global__ void k_pool(int n, int batch, int c, const bf16* __restrict__ in, int
 // nearest upsampling: out [b][2m grid][c] (channel slice) from in [b][m grid][c]
 __global__ void k_upsample(int m, int batch, int c, const bf16* __restrict__ in, int ldi, bf16* __restrict__ out,
                            int ldo) {
+  pdl_entry();
   const int n = 2 * m, V = n * n * n;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)V * batch * c) return;
@@ -234,6 +239,7 @@ __global__ void k_upsample(int m, int batch, int c, const bf16* __restrict__ in,
 // g_out[b][vp][c] = sum over the 8 children of g_in (backward of nearest upsampling)
 __global__ void k_upsample_bwd(int m, int batch, int c, const bf16* __restrict__ gin, int ldi, bf16* __restrict__ gout,
                                int ldo) {
+  pdl_entry();
   const int n = 2 * m, Vp = m * m * m;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)Vp * batch * c) return;
@@ -256,6 +262,7 @@ __global__ void k_upsample_bwd(int m, int batch, int c, const bf16* __restrict__
 __global__ void k_skip_pool_bwd(int n, int batch, int c, const bf16* __restrict__ skip, int lds,
                                 const bf16* __restrict__ act, int lda, const bf16* __restrict__ gp, int ldp,
                                 bf16* __restrict__ g, int ldg) {
+  pdl_entry();
   const int V = n * n * n, m = n / 2;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)V * batch * c) return;
@@ -272,6 +279,7 @@ __global__ void k_skip_pool_bwd(int n, int batch, int c, const bf16* __restrict_
 
 // input FP32 [rows][cin] -> BF16 [rows][ld] (padding zero)
 __global__ void k_pack_input(long long rows, int cin, int ld, const float* __restrict__ x, bf16* __restrict__ out) {
+  pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows * ld) return;
   const long long r = t / ld;
@@ -282,6 +290,7 @@ __global__ void k_pack_input(long long rows, int cin, int ld, const float* __res
 // MSE: diff = y - target; per-block partial sums of squares; gradient 2 diff / count in BF16 [rows][ld]
 __global__ void k_mse(long long rows, int cout, const float* __restrict__ y, const float* __restrict__ tgt, int ld,
                       double inv_count, bf16* __restrict__ g, double* __restrict__ part) {
+  pdl_entry();
   double s = 0.0;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < rows * ld;
        t += (long long)gridDim.x * blockDim.x) {
@@ -306,6 +315,7 @@ __global__ void k_mse(long long rows, int cout, const float* __restrict__ y, con
 }
 
 __global__ void k_sum_parts(int np, const double* __restrict__ part, double scale, double* __restrict__ out) {
+  pdl_entry();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double s = 0.0;
     for (int i = 0; i < np; ++i) s += part[i];
@@ -315,6 +325,7 @@ __global__ void k_sum_parts(int np, const double* __restrict__ part, double scal
 
 __global__ void k_adam(long long n, float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ g, float lr, float b1, float b2, float eps, float c1, float c2) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float gi = g[i];
@@ -329,6 +340,7 @@ __global__ void k_adam(long long n, float* __restrict__ w, float* __restrict__ m
 //   Wt[t][co][ci]  (np8 x kp16, forward)     Wf[t][ci][co] = W[26 - t][ci][co] (npb8 x kpb16, backward data)
 __global__ void k_refresh_weights(int cin, int cout, const float* __restrict__ W, int kp, int npf, bf16* __restrict__ Wt,
                                   int kpb, int npb, bf16* __restrict__ Wf) {
+  pdl_entry();
   const int tap = blockIdx.x;
   for (int idx = threadIdx.x; idx < npf * kp; idx += blockDim.x) {
     const int co = idx / kp, ci = idx % kp;
@@ -352,7 +364,7 @@ template <int NT>
 void conv_launch(int n, int batch, const bf16* x, int ldx, int kp, const bf16* W, const float* bias, int relu,
                  const bf16* mask, int ldm, int cvalid, bf16* y, int ldy, float* yf, int ldyf, cudaStream_t st) {
   const long long warps = (long long)((n * n * n + 15) / 16) * batch;
-  wb_count_launch(), k_conv<NT><<<nb(warps * 32, 128), 128, 0, st>>>(n, batch, x, ldx, kp, W, bias, relu, mask, ldm, cvalid,
+  wb_launch(k_conv<NT>, nb(warps * 32, 128), 128, 0, st, n, batch, x, ldx, kp, W, bias, relu, mask, ldm, cvalid,
                                                                       y, ldy, yf, ldyf);
 }
 
@@ -373,10 +385,10 @@ void wgrad(int n, int batch, const bf16* x, int ldx, int cin, const bf16* g, int
            cudaStream_t st) {
   dim3 grid(27, (cin + 15) / 16);
   switch (r8(cout) / 8) {
-    case 1: wb_count_launch(), k_wgrad<1><<<grid, 256, 0, st>>>(n, batch, x, ldx, cin, g, ldg, cout, dW); break;
-    case 2: wb_count_launch(), k_wgrad<2><<<grid, 256, 0, st>>>(n, batch, x, ldx, cin, g, ldg, cout, dW); break;
-    case 4: wb_count_launch(), k_wgrad<4><<<grid, 256, 0, st>>>(n, batch, x, ldx, cin, g, ldg, cout, dW); break;
-    case 8: wb_count_launch(), k_wgrad<8><<<grid, 256, 0, st>>>(n, batch, x, ldx, cin, g, ldg, cout, dW); break;
+    case 1: wb_launch(k_wgrad<1>, grid, 256, 0, st, n, batch, x, ldx, cin, g, ldg, cout, dW); break;
+    case 2: wb_launch(k_wgrad<2>, grid, 256, 0, st, n, batch, x, ldx, cin, g, ldg, cout, dW); break;
+    case 4: wb_launch(k_wgrad<4>, grid, 256, 0, st, n, batch, x, ldx, cin, g, ldg, cout, dW); break;
+    case 8: wb_launch(k_wgrad<8>, grid, 256, 0, st, n, batch, x, ldx, cin, g, ldg, cout, dW); break;
     default: break;
   }
 }
@@ -417,7 +429,7 @@ const int kLayerCout[11] = {16, 16, 32, 32, 64, 64, 32, 32, 16, 16, -1};
 
 void refresh_all(wbfbt_net* net) {
   for (auto& l : net->L)
-    wb_count_launch(), k_refresh_weights<<<27, 256, 0, net->st>>>(l.cin, l.cout, net->theta + l.woff, l.kp, l.npf, l.Wt,
+    wb_launch(k_refresh_weights, 27, 256, 0, net->st, l.cin, l.cout, net->theta + l.woff, l.kp, l.npf, l.Wt,
                                                                    l.kpb, l.npb, l.Wf);
 }
 
@@ -427,19 +439,19 @@ void forward(wbfbt_net* N, const float* x, int B) {
   const long long V0 = (long long)n0 * n0 * n0;
   auto& L = N->L;
   auto bias = [&](int i) { return N->theta + L[i].boff; };
-  wb_count_launch(), k_pack_input<<<nb(V0 * B * 16, 256), 256, 0, st>>>(V0 * B, N->cin, 16, x, N->x0);
+  wb_launch(k_pack_input, nb(V0 * B * 16, 256), 256, 0, st, V0 * B, N->cin, 16, x, N->x0);
   conv(L[0].npf, n0, B, N->x0, 16, L[0].kp, L[0].Wt, bias(0), 1, nullptr, 0, 16, N->a1, 16, nullptr, 0, st);
   conv(L[1].npf, n0, B, N->a1, 16, L[1].kp, L[1].Wt, bias(1), 1, nullptr, 0, 16, N->cat2 + 32, 48, nullptr, 0, st);
-  wb_count_launch(), k_pool<<<nb((long long)n1 * n1 * n1 * B * 16, 256), 256, 0, st>>>(n0, B, 16, N->cat2 + 32, 48, N->p2, 16);
+  wb_launch(k_pool, nb((long long)n1 * n1 * n1 * B * 16, 256), 256, 0, st, n0, B, 16, N->cat2 + 32, 48, N->p2, 16);
   conv(L[2].npf, n1, B, N->p2, 16, L[2].kp, L[2].Wt, bias(2), 1, nullptr, 0, 32, N->a3, 32, nullptr, 0, st);
   conv(L[3].npf, n1, B, N->a3, 32, L[3].kp, L[3].Wt, bias(3), 1, nullptr, 0, 32, N->cat1 + 64, 96, nullptr, 0, st);
-  wb_count_launch(), k_pool<<<nb((long long)n2 * n2 * n2 * B * 32, 256), 256, 0, st>>>(n1, B, 32, N->cat1 + 64, 96, N->p4, 32);
+  wb_launch(k_pool, nb((long long)n2 * n2 * n2 * B * 32, 256), 256, 0, st, n1, B, 32, N->cat1 + 64, 96, N->p4, 32);
   conv(L[4].npf, n2, B, N->p4, 32, L[4].kp, L[4].Wt, bias(4), 1, nullptr, 0, 64, N->a5, 64, nullptr, 0, st);
   conv(L[5].npf, n2, B, N->a5, 64, L[5].kp, L[5].Wt, bias(5), 1, nullptr, 0, 64, N->a6, 64, nullptr, 0, st);
-  wb_count_launch(), k_upsample<<<nb((long long)n1 * n1 * n1 * B * 64, 256), 256, 0, st>>>(n2, B, 64, N->a6, 64, N->cat1, 96);
+  wb_launch(k_upsample, nb((long long)n1 * n1 * n1 * B * 64, 256), 256, 0, st, n2, B, 64, N->a6, 64, N->cat1, 96);
   conv(L[6].npf, n1, B, N->cat1, 96, L[6].kp, L[6].Wt, bias(6), 1, nullptr, 0, 32, N->a7, 32, nullptr, 0, st);
   conv(L[7].npf, n1, B, N->a7, 32, L[7].kp, L[7].Wt, bias(7), 1, nullptr, 0, 32, N->a8, 32, nullptr, 0, st);
-  wb_count_launch(), k_upsample<<<nb(V0 * B * 32, 256), 256, 0, st>>>(n1, B, 32, N->a8, 32, N->cat2, 48);
+  wb_launch(k_upsample, nb(V0 * B * 32, 256), 256, 0, st, n1, B, 32, N->a8, 32, N->cat2, 48);
   conv(L[8].npf, n0, B, N->cat2, 48, L[8].kp, L[8].Wt, bias(8), 1, nullptr, 0, 16, N->a9, 16, nullptr, 0, st);
   conv(L[9].npf, n0, B, N->a9, 16, L[9].kp, L[9].Wt, bias(9), 1, nullptr, 0, 16, N->a10, 16, nullptr, 0, st);
   conv(L[10].npf, n0, B, N->a10, 16, L[10].kp, L[10].Wt, bias(10), 0, nullptr, 0, N->cout, nullptr, 0, N->yout,
@@ -454,7 +466,7 @@ void backward(wbfbt_net* N, int B) {
   float* G = N->grad;
   auto layer_grads = [&](int i, int n, const bf16* xin, int ldx, const bf16* g, int ldg, long long rows) {
     wgrad(n, B, xin, ldx, L[i].cin, g, ldg, L[i].cout, G + L[i].woff, st);
-    wb_count_launch(), k_colsum<<<L[i].cout, 256, 0, st>>>(g, ldg, rows, G + L[i].boff);
+    wb_launch(k_colsum, L[i].cout, 256, 0, st, g, ldg, rows, G + L[i].boff);
   };
   // bwd data: input g (ld kpb), output (ld of the layer input), ReLU mask of the layer input
   auto bwd = [&](int i, int n, const bf16* g, const bf16* mask, int ldm, bf16* out, int ldo) {
@@ -466,23 +478,23 @@ void backward(wbfbt_net* N, int B) {
   bwd(9, n0, N->g10, N->a9, 16, N->g9, 16);
   layer_grads(8, n0, N->cat2, 48, N->g9, 16, V0 * B);
   bwd(8, n0, N->g9, N->cat2, 48, N->gcat2, 48);
-  wb_count_launch(), k_upsample_bwd<<<nb(V1 * B * 32, 256), 256, 0, st>>>(n1, B, 32, N->gcat2, 48, N->g8, 32);
+  wb_launch(k_upsample_bwd, nb(V1 * B * 32, 256), 256, 0, st, n1, B, 32, N->gcat2, 48, N->g8, 32);
   layer_grads(7, n1, N->a7, 32, N->g8, 32, V1 * B);
   bwd(7, n1, N->g8, N->a7, 32, N->g7, 32);
   layer_grads(6, n1, N->cat1, 96, N->g7, 32, V1 * B);
   bwd(6, n1, N->g7, N->cat1, 96, N->gcat1, 96);
-  wb_count_launch(), k_upsample_bwd<<<nb(V2 * B * 64, 256), 256, 0, st>>>(n2, B, 64, N->gcat1, 96, N->g6, 64);
+  wb_launch(k_upsample_bwd, nb(V2 * B * 64, 256), 256, 0, st, n2, B, 64, N->gcat1, 96, N->g6, 64);
   layer_grads(5, n2, N->a5, 64, N->g6, 64, V2 * B);
   bwd(5, n2, N->g6, N->a5, 64, N->g5, 64);
   layer_grads(4, n2, N->p4, 32, N->g5, 64, V2 * B);
   bwd(4, n2, N->g5, nullptr, 0, N->gp4, 32);
-  wb_count_launch(), k_skip_pool_bwd<<<nb(V1 * B * 32, 256), 256, 0, st>>>(n1, B, 32, N->gcat1 + 64, 96, N->cat1 + 64, 96,
+  wb_launch(k_skip_pool_bwd, nb(V1 * B * 32, 256), 256, 0, st, n1, B, 32, N->gcat1 + 64, 96, N->cat1 + 64, 96,
                                                                            N->gp4, 32, N->g4, 32);
   layer_grads(3, n1, N->a3, 32, N->g4, 32, V1 * B);
   bwd(3, n1, N->g4, N->a3, 32, N->g3, 32);
   layer_grads(2, n1, N->p2, 16, N->g3, 32, V1 * B);
   bwd(2, n1, N->g3, nullptr, 0, N->gp2, 16);
-  wb_count_launch(), k_skip_pool_bwd<<<nb(V0 * B * 16, 256), 256, 0, st>>>(n0, B, 16, N->gcat2 + 32, 48, N->cat2 + 32, 48,
+  wb_launch(k_skip_pool_bwd, nb(V0 * B * 16, 256), 256, 0, st, n0, B, 16, N->gcat2 + 32, 48, N->cat2 + 32, 48,
                                                                            N->gp2, 16, N->g2, 16);
   layer_grads(1, n0, N->a1, 16, N->g2, 16, V0 * B);
   bwd(1, n0, N->g2, N->a1, 16, N->g1, 16);
@@ -626,8 +638,8 @@ int wbfbt_net_loss_grad(wbfbt_net* N, const float* x, const float* target, int b
     const long long rows = (long long)batch * N->n * N->n * N->n;
     const double inv = 1.0 / (double)(rows * N->cout);
     const int blocks = 512;
-    wb_count_launch(), k_mse<<<blocks, 256, 0, N->st>>>(rows, N->cout, N->yout, target, 16, inv, N->g11, N->part);
-    wb_count_launch(), k_sum_parts<<<1, 32, 0, N->st>>>(blocks, N->part, inv, N->dloss);
+    wb_launch(k_mse, blocks, 256, 0, N->st, rows, N->cout, N->yout, target, 16, inv, N->g11, N->part);
+    wb_launch(k_sum_parts, 1, 32, 0, N->st, blocks, N->part, inv, N->dloss);
     backward(N, batch);
     if (grad && cudaMemcpyAsync(grad, N->grad, sizeof(float) * N->nparam, cudaMemcpyDefault, N->st) != cudaSuccess)
       throw 1;
@@ -644,7 +656,7 @@ int wbfbt_net_adam_step(wbfbt_net* N, float lr) {
     N->adam_t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)N->adam_t), c2 = 1.f - powf(b2, (float)N->adam_t);
-    wb_count_launch(), k_adam<<<nb(N->nparam, 256), 256, 0, N->st>>>(N->nparam, N->theta, N->m1, N->m2, N->grad, lr, b1, b2,
+    wb_launch(k_adam, nb(N->nparam, 256), 256, 0, N->st, N->nparam, N->theta, N->m1, N->m2, N->grad, lr, b1, b2,
                                                                       1e-8f, c1, c2);
     refresh_all(N);
   });

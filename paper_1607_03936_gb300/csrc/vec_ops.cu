@@ -33,6 +33,7 @@ __device__ inline double block_sum(double v) {
 template <typename A, typename B>
 __global__ void k_dot_partial(const A* __restrict__ x, const B* __restrict__ y, long long n, long long stride,
                               double* __restrict__ part) {
+  pdl_entry();
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double a = (double)x[i * stride];
@@ -43,6 +44,7 @@ __global__ void k_dot_partial(const A* __restrict__ x, const B* __restrict__ y, 
 }
 
 __global__ void k_final(const double* __restrict__ part, int np, int ncols, double* __restrict__ out, int sqrt_out) {
+  pdl_entry();
   // one block per column; partials of column c at part[c * np + b]
   double acc = 0.0;
   for (int b = threadIdx.x; b < np; b += blockDim.x) acc += part[(size_t)blockIdx.x * np + b];
@@ -58,6 +60,7 @@ int partial_blocks(long long n) {
 template <typename T>
 __global__ void k_cheb_init0(long long n, const T* __restrict__ b, const T* __restrict__ dinv, T inv_theta,
                              T* __restrict__ r, T* __restrict__ d, T* __restrict__ x) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const T rv = b[i];
@@ -70,6 +73,7 @@ __global__ void k_cheb_init0(long long n, const T* __restrict__ b, const T* __re
 template <typename T>
 __global__ void k_cheb_init1(long long n, const T* __restrict__ b, const T* __restrict__ mx, const T* __restrict__ dinv,
                              T inv_theta, T* __restrict__ r, T* __restrict__ d, T* __restrict__ x) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const T rv = b[i] - mx[i];
@@ -82,6 +86,7 @@ __global__ void k_cheb_init1(long long n, const T* __restrict__ b, const T* __re
 template <typename T>
 __global__ void k_cheb_step(long long n, const T* __restrict__ md, const T* __restrict__ dinv, T a, T bc,
                             T* __restrict__ r, T* __restrict__ d, T* __restrict__ x) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const T rv = r[i] - md[i];
@@ -93,36 +98,42 @@ __global__ void k_cheb_step(long long n, const T* __restrict__ md, const T* __re
 
 template <typename T>
 __global__ void k_sub(long long n, const T* __restrict__ a, T* __restrict__ r) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) r[i] -= a[i];
 }
 
 template <typename T>
 __global__ void k_axpby(long long n, T a, const T* __restrict__ x, T b, const T* __restrict__ y, T* __restrict__ z) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) z[i] = a * x[i] + b * y[i];
 }
 
 template <typename T>
 __global__ void k_mul(long long n, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ z) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) z[i] = a[i] * b[i];
 }
 
 template <typename T>
 __global__ void k_scale(long long n, T s, const T* __restrict__ x, T* __restrict__ z) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) z[i] = x[i] * s;
 }
 
 template <typename T>
 __global__ void k_scale_by_inv(long long n, const double* __restrict__ s, const T* __restrict__ x, T* __restrict__ z) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) z[i] = T((double)x[i] / s[0]);
 }
 
 template <typename A, typename B>
 __global__ void k_cast(long long n, const A* __restrict__ x, B* __restrict__ y) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = (B)x[i];
 }
@@ -130,6 +141,7 @@ __global__ void k_cast(long long n, const A* __restrict__ x, B* __restrict__ y) 
 // p[e * np] -= sum / count, sum from device memory (the constant-mode total)
 template <typename T>
 __global__ void k_sub_const_mode(long long count, int np, const double* __restrict__ sum, T* __restrict__ p) {
+  pdl_entry();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < count) p[e * np] = T((double)p[e * np] - sum[0] / (double)count);
 }
@@ -137,6 +149,7 @@ __global__ void k_sub_const_mode(long long count, int np, const double* __restri
 template <typename T>
 __global__ void k_copy_proj(long long count, int np, const double* __restrict__ sum, const T* __restrict__ src,
                             T* __restrict__ dst) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count * np) return;
   T v = src[i];
@@ -149,6 +162,7 @@ __global__ void k_copy_proj(long long count, int np, const double* __restrict__ 
 template <typename T>
 __global__ void k_coarse_gather(int nn, int ncomp, const int* __restrict__ map, int nfree, const T* __restrict__ b,
                                 double* __restrict__ bf, int pin0) {
+  pdl_entry();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
   const int m = map[n];
@@ -162,6 +176,7 @@ __global__ void k_coarse_gather(int nn, int ncomp, const int* __restrict__ map, 
 // xf = Ainv bf, one warp per row
 __global__ void k_gemv_rows(const double* __restrict__ Ainv, int n, const double* __restrict__ bf,
                             double* __restrict__ xf) {
+  pdl_entry();
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -175,6 +190,7 @@ __global__ void k_gemv_rows(const double* __restrict__ Ainv, int n, const double
 
 // single block: xf -= mean(xf)
 __global__ void k_sub_mean_small(int n, double* __restrict__ xf) {
+  pdl_entry();
   double acc = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) acc += xf[i];
   acc = block_sum(acc);
@@ -187,6 +203,7 @@ __global__ void k_sub_mean_small(int n, double* __restrict__ xf) {
 template <typename T>
 __global__ void k_coarse_scatter(int nn, int ncomp, const int* __restrict__ map, int nfree, const double* __restrict__ xf,
                                  T* __restrict__ x) {
+  pdl_entry();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
   const int m = map[n];
@@ -194,6 +211,7 @@ __global__ void k_coarse_scatter(int nn, int ncomp, const int* __restrict__ map,
 }
 
 __global__ void k_pin_first(double* M, int n) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   M[t] = t == 0 ? 1.0 : 0.0;            // row 0
@@ -216,6 +234,7 @@ struct GjJobs {
 };
 
 __global__ void k_bgj_pivot(GjJobs jobs, int J0, int* __restrict__ flag) {
+  pdl_entry();
   const int z = blockIdx.x;
   const int n = jobs.n[z];
   if (J0 >= n) return;
@@ -246,6 +265,7 @@ __global__ void k_bgj_pivot(GjJobs jobs, int J0, int* __restrict__ flag) {
 
 // A[J][k] <- P A[J][k] for k not in J: one thread per column k, in place (only it touches column k of rows J)
 __global__ void k_bgj_rows(GjJobs jobs, int J0) {
+  pdl_entry();
   const int z = blockIdx.y;
   const int n = jobs.n[z];
   if (J0 >= n) return;
@@ -269,6 +289,7 @@ __global__ void k_bgj_rows(GjJobs jobs, int J0) {
 
 // A[i][k] -= sum_s A[i][J0+s] A[J0+s][k] for i, k not in J (32 x 8 threads, 32 x 32 tile)
 __global__ void k_bgj_update(GjJobs jobs, int J0) {
+  pdl_entry();
   const int z = blockIdx.z;
   const int n = jobs.n[z];
   if (J0 >= n) return;
@@ -299,6 +320,7 @@ __global__ void k_bgj_update(GjJobs jobs, int J0) {
 
 // A[i][J] <- -A[i][J] P for i not in J (thread per row); A[J][J] <- P
 __global__ void k_bgj_cols(GjJobs jobs, int J0) {
+  pdl_entry();
   const int z = blockIdx.y;
   const int n = jobs.n[z];
   if (J0 >= n) return;
@@ -329,6 +351,7 @@ __global__ void k_bgj_cols(GjJobs jobs, int J0) {
 
 __global__ void k_mdot_partial(const double* __restrict__ V, long long ld, const double* __restrict__ w, long long n,
                                int np, double* __restrict__ part) {
+  pdl_entry();
   const double* v = V + (size_t)blockIdx.y * ld;
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)np * blockDim.x)
@@ -339,6 +362,7 @@ __global__ void k_mdot_partial(const double* __restrict__ V, long long ld, const
 
 __global__ void k_gemv_sub(const double* __restrict__ V, long long ld, int ncols, const double* __restrict__ h,
                            double* __restrict__ w, long long n) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double acc = w[i];
@@ -348,6 +372,7 @@ __global__ void k_gemv_sub(const double* __restrict__ V, long long ld, int ncols
 
 __global__ void k_gemv_add(const double* __restrict__ Z, long long ld, int ncols, const double* __restrict__ y,
                            double* __restrict__ x, long long n) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double acc = x[i];
@@ -356,6 +381,7 @@ __global__ void k_gemv_add(const double* __restrict__ Z, long long ld, int ncols
 }
 
 __global__ void k_add2(long long n, const double* __restrict__ a, double* __restrict__ h) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) h[i] += a[i];
 }
@@ -368,56 +394,56 @@ template <typename A, typename B>
 cudaError_t launch_dot(const A* x, const B* y, long long n, long long stride, double* part, double* out, int sqrt_out,
                        cudaStream_t st) {
   const int np = partial_blocks(n);
-  wb_count_launch(), k_dot_partial<A, B><<<np, RB, 0, st>>>(x, y, n, stride, part);
-  wb_count_launch(), k_final<<<1, RB, 0, st>>>(part, np, 1, out, sqrt_out);
+  wb_launch(k_dot_partial<A, B>, np, RB, 0, st, x, y, n, stride, part);
+  wb_launch(k_final, 1, RB, 0, st, part, np, 1, out, sqrt_out);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_cheb_init0(long long n, const T* b, const T* dinv, T inv_theta, T* r, T* d, T* x, cudaStream_t st) {
-  wb_count_launch(), k_cheb_init0<T><<<nblk(n, 256), 256, 0, st>>>(n, b, dinv, inv_theta, r, d, x);
+  wb_launch(k_cheb_init0<T>, nblk(n, 256), 256, 0, st, n, b, dinv, inv_theta, r, d, x);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_cheb_init1(long long n, const T* b, const T* mx, const T* dinv, T inv_theta, T* r, T* d, T* x,
                               cudaStream_t st) {
-  wb_count_launch(), k_cheb_init1<T><<<nblk(n, 256), 256, 0, st>>>(n, b, mx, dinv, inv_theta, r, d, x);
+  wb_launch(k_cheb_init1<T>, nblk(n, 256), 256, 0, st, n, b, mx, dinv, inv_theta, r, d, x);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_cheb_step(long long n, const T* md, const T* dinv, T a, T bc, T* r, T* d, T* x, cudaStream_t st) {
-  wb_count_launch(), k_cheb_step<T><<<nblk(n, 256), 256, 0, st>>>(n, md, dinv, a, bc, r, d, x);
+  wb_launch(k_cheb_step<T>, nblk(n, 256), 256, 0, st, n, md, dinv, a, bc, r, d, x);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_sub(long long n, const T* a, T* r, cudaStream_t st) {
-  wb_count_launch(), k_sub<T><<<nblk(n, 256), 256, 0, st>>>(n, a, r);
+  wb_launch(k_sub<T>, nblk(n, 256), 256, 0, st, n, a, r);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_axpby(long long n, T a, const T* x, T b, const T* y, T* z, cudaStream_t st) {
-  wb_count_launch(), k_axpby<T><<<nblk(n, 256), 256, 0, st>>>(n, a, x, b, y, z);
+  wb_launch(k_axpby<T>, nblk(n, 256), 256, 0, st, n, a, x, b, y, z);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_mul(long long n, const T* a, const T* b, T* z, cudaStream_t st) {
-  wb_count_launch(), k_mul<T><<<nblk(n, 256), 256, 0, st>>>(n, a, b, z);
+  wb_launch(k_mul<T>, nblk(n, 256), 256, 0, st, n, a, b, z);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_scale(long long n, T s, const T* x, T* z, cudaStream_t st) {
-  wb_count_launch(), k_scale<T><<<nblk(n, 256), 256, 0, st>>>(n, s, x, z);
+  wb_launch(k_scale<T>, nblk(n, 256), 256, 0, st, n, s, x, z);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_scale_by_inv(long long n, const double* s, const T* x, T* z, cudaStream_t st) {
-  wb_count_launch(), k_scale_by_inv<T><<<nblk(n, 256), 256, 0, st>>>(n, s, x, z);
+  wb_launch(k_scale_by_inv<T>, nblk(n, 256), 256, 0, st, n, s, x, z);
   return cudaGetLastError();
 }
 
 template <typename A, typename B>
 cudaError_t launch_cast(long long n, const A* x, B* y, cudaStream_t st) {
-  wb_count_launch(), k_cast<A, B><<<nblk(n, 256), 256, 0, st>>>(n, x, y);
+  wb_launch(k_cast<A, B>, nblk(n, 256), 256, 0, st, n, x, y);
   return cudaGetLastError();
 }
 
@@ -426,17 +452,17 @@ cudaError_t launch_project_pressure(long long ne, int np, const T* src, T* dst, 
                                     cudaStream_t st) {
   cudaError_t e = launch_dot<T, T>(src, (const T*)nullptr, ne, np, part, sum, 0, st);
   if (e != cudaSuccess) return e;
-  wb_count_launch(), k_copy_proj<T><<<nblk(ne * np, 256), 256, 0, st>>>(ne, np, sum, src, dst);
+  wb_launch(k_copy_proj<T>, nblk(ne * np, 256), 256, 0, st, ne, np, sum, src, dst);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_coarse_solve(int nn, int ncomp, const int* map, int nfree_nodes, int ndense, const double* Ainv,
                                 int neumann, const T* b, T* x, double* bf, double* xf, cudaStream_t st) {
-  wb_count_launch(), k_coarse_gather<T><<<nblk(nn, 256), 256, 0, st>>>(nn, ncomp, map, nfree_nodes, b, bf, neumann);
-  wb_count_launch(), k_gemv_rows<<<nblk((long long)ndense * 32, 256), 256, 0, st>>>(Ainv, ndense, bf, xf);
-  if (neumann) wb_count_launch(), k_sub_mean_small<<<1, 1024, 0, st>>>(ndense, xf);
-  wb_count_launch(), k_coarse_scatter<T><<<nblk(nn, 256), 256, 0, st>>>(nn, ncomp, map, nfree_nodes, xf, x);
+  wb_launch(k_coarse_gather<T>, nblk(nn, 256), 256, 0, st, nn, ncomp, map, nfree_nodes, b, bf, neumann);
+  wb_launch(k_gemv_rows, nblk((long long)ndense * 32, 256), 256, 0, st, Ainv, ndense, bf, xf);
+  if (neumann) wb_launch(k_sub_mean_small, 1, 1024, 0, st, ndense, xf);
+  wb_launch(k_coarse_scatter<T>, nblk(nn, 256), 256, 0, st, nn, ncomp, map, nfree_nodes, xf, x);
   return cudaGetLastError();
 }
 
@@ -450,13 +476,13 @@ cudaError_t launch_dense_inverse_batch(int count, double* const* M, const int* n
     jobs.n[z] = n[z];
     jobs.P[z] = pwork + (size_t)z * GJB * GJB;
     if (n[z] > nmax) nmax = n[z];
-    if (pin_first[z]) wb_count_launch(), k_pin_first<<<nblk(n[z], 256), 256, 0, st>>>(M[z], n[z]);
+    if (pin_first[z]) wb_launch(k_pin_first, nblk(n[z], 256), 256, 0, st, M[z], n[z]);
   }
   for (int J0 = 0; J0 < nmax; J0 += GJB) {
-    wb_count_launch(), k_bgj_pivot<<<count, dim3(32, 32), 0, st>>>(jobs, J0, flag);
-    wb_count_launch(), k_bgj_rows<<<dim3(nblk(nmax, 128), count), 128, 0, st>>>(jobs, J0);
-    wb_count_launch(), k_bgj_update<<<dim3((nmax + 31) / 32, (nmax + 31) / 32, count), dim3(32, 8), 0, st>>>(jobs, J0);
-    wb_count_launch(), k_bgj_cols<<<dim3(nblk(nmax, 128), count), 128, 0, st>>>(jobs, J0);
+    wb_launch(k_bgj_pivot, count, dim3(32, 32), 0, st, jobs, J0, flag);
+    wb_launch(k_bgj_rows, dim3(nblk(nmax, 128), count), 128, 0, st, jobs, J0);
+    wb_launch(k_bgj_update, dim3((nmax + 31) / 32, (nmax + 31) / 32, count), dim3(32, 8), 0, st, jobs, J0);
+    wb_launch(k_bgj_cols, dim3(nblk(nmax, 128), count), 128, 0, st, jobs, J0);
   }
   return cudaGetLastError();
 }
@@ -464,25 +490,25 @@ cudaError_t launch_dense_inverse_batch(int count, double* const* M, const int* n
 cudaError_t launch_mdot(const double* V, long long ld, int ncols, const double* w, long long n, double* part,
                         double* out, cudaStream_t st) {
   const int np = partial_blocks(n);
-  wb_count_launch(), k_mdot_partial<<<dim3(np, ncols), RB, 0, st>>>(V, ld, w, n, np, part);
-  wb_count_launch(), k_final<<<ncols, RB, 0, st>>>(part, np, ncols, out, 0);
+  wb_launch(k_mdot_partial, dim3(np, ncols), RB, 0, st, V, ld, w, n, np, part);
+  wb_launch(k_final, ncols, RB, 0, st, part, np, ncols, out, 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemv_sub(const double* V, long long ld, int ncols, const double* h, double* w, long long n,
                             cudaStream_t st) {
-  wb_count_launch(), k_gemv_sub<<<nblk(n, 256), 256, 0, st>>>(V, ld, ncols, h, w, n);
+  wb_launch(k_gemv_sub, nblk(n, 256), 256, 0, st, V, ld, ncols, h, w, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemv_add(const double* Z, long long ld, int ncols, const double* y, double* x, long long n,
                             cudaStream_t st) {
-  wb_count_launch(), k_gemv_add<<<nblk(n, 256), 256, 0, st>>>(Z, ld, ncols, y, x, n);
+  wb_launch(k_gemv_add, nblk(n, 256), 256, 0, st, Z, ld, ncols, y, x, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_add_vec(long long n, const double* a, double* h, cudaStream_t st) {
-  wb_count_launch(), k_add2<<<nblk(n, 256), 256, 0, st>>>(n, a, h);
+  wb_launch(k_add2, nblk(n, 256), 256, 0, st, n, a, h);
   return cudaGetLastError();
 }
 

@@ -316,6 +316,7 @@ void kinv(wbfbt_ctx* c, int which, const T* bd, T* xd) {
 // ------------------------------------------------------------------ learned correction
 
 __global__ void k_elem_logmu(Grid g, int K, const double* __restrict__ mu, float* __restrict__ out) {
+  pdl_entry();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.ne) return;
   const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
@@ -330,6 +331,7 @@ __global__ void k_elem_logmu(Grid g, int K, const double* __restrict__ mu, float
 // q = diag(K_w)^-1/2 r   (dK holds diag(K_w)^-1)
 template <typename T>
 __global__ void k_learn_q(long long n, const T* __restrict__ dK, const T* __restrict__ r, float* __restrict__ q) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) q[i] = (float)(sqrt((double)dK[i]) * (double)r[i]);
 }
@@ -337,6 +339,7 @@ __global__ void k_learn_q(long long n, const T* __restrict__ dK, const T* __rest
 // x[e] = (logmu[e], q[e][0..np) / s),  s = ||q|| / sqrt(count)
 __global__ void k_learn_pack(int ne, int np, const float* __restrict__ logmu, const float* __restrict__ q,
                              const double* __restrict__ qnorm, long long count, float* __restrict__ x) {
+  pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)ne * (np + 1)) return;
   const int e = (int)(t / (np + 1)), c = (int)(t % (np + 1));
@@ -348,6 +351,7 @@ __global__ void k_learn_pack(int ne, int np, const float* __restrict__ logmu, co
 template <typename T>
 __global__ void k_learn_unpack(long long n, const T* __restrict__ dK, const float* __restrict__ y,
                                const double* __restrict__ qnorm, long long count, T* __restrict__ z) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double s = qnorm[0] / sqrt((double)count);
@@ -358,6 +362,7 @@ __global__ void k_learn_unpack(long long n, const T* __restrict__ dK, const floa
 template <typename T>
 __global__ void k_learn_target(long long n, const T* __restrict__ dK, const T* __restrict__ z,
                                const double* __restrict__ qnorm, long long count, float* __restrict__ y) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double s = qnorm[0] / sqrt((double)count);
@@ -372,9 +377,9 @@ template <typename T>
 void learned_features(wbfbt_ctx* c, int which, const T* r, float* x) {
   Precond<T>& P = prec<T>(c);
   const long long n = (long long)c->g.ne * c->NP;
-  wb_count_launch(), k_learn_q<T><<<nb256(n), 256, 0, c->st>>>(n, P.dKw[which], r, c->lq);
+  wb_launch(k_learn_q<T>, nb256(n), 256, 0, c->st, n, P.dKw[which], r, c->lq);
   CK(launch_dot<float, float>(c->lq, c->lq, n, 1, c->part, c->dsc + 16, 1, c->st));
-  wb_count_launch(), k_learn_pack<<<nb256((long long)c->g.ne * (c->NP + 1)), 256, 0, c->st>>>(
+  wb_launch(k_learn_pack, nb256((long long)c->g.ne * (c->NP + 1)), 256, 0, c->st,
       c->g.ne, c->NP, c->llogmu, c->lq, c->dsc + 16, n, x);
   CK(cudaGetLastError());
 }
@@ -386,7 +391,7 @@ void kinv_learned(wbfbt_ctx* c, int which, const T* bd, T* xd) {
   const long long n = (long long)c->g.ne * c->NP;
   learned_features<T>(c, which, bd, c->lx);
   if (unet_forward_into(c->net, c->lx, c->ly, c->st) != WBFBT_OK) throw WbErr{WBFBT_ERR_CUDA};
-  wb_count_launch(), k_learn_unpack<T><<<nb256(n), 256, 0, c->st>>>(n, P.dKw[which], c->ly, c->dsc + 16, n, xd);
+  wb_launch(k_learn_unpack<T>, nb256(n), 256, 0, c->st, n, P.dKw[which], c->ly, c->dsc + 16, n, xd);
   CK(cudaGetLastError());
   Epi<T> e;
   e.mode = EPI_BMINUS;
@@ -661,6 +666,7 @@ void build_precond(wbfbt_ctx* c) {
 }
 
 __global__ void k_inv_masked(Grid g, const double* __restrict__ w, double* __restrict__ inv) {
+  pdl_entry();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nn) return;
   const int ix = n % g.NX, iy = (n / g.NX) % g.NY, iz = n / (g.NX * g.NY);
@@ -862,6 +868,7 @@ int fgmres(wbfbt_ctx* c, double rtol, int maxit, int* iters, double* relres) {
 namespace {
 
 __global__ void k_check_positive(long long n, const double* __restrict__ v, int* __restrict__ flag) {
+  pdl_entry();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n && (!(v[i] > 0.0) || !isfinite(v[i]))) atomicExch(flag, 1);
 }
@@ -873,7 +880,7 @@ void run_setup(wbfbt_ctx* cp, const double* mu_nodes) {
   const size_t nn = g.nn;
   CK(cudaMemcpyAsync(cp->mu64, mu_nodes, sizeof(double) * nn, cudaMemcpyDefault, cp->st));
   CK(cudaMemsetAsync(cp->dflag, 0, sizeof(int), cp->st));
-  wb_count_launch(), k_check_positive<<<(unsigned)((nn + 255) / 256), 256, 0, cp->st>>>((long long)nn, cp->mu64, cp->dflag);
+  wb_launch(k_check_positive, (unsigned)((nn + 255) / 256), 256, 0, cp->st, (long long)nn, cp->mu64, cp->dflag);
   CK(cudaGetLastError());
   int bad = 0;
   CK(cudaMemcpyAsync(&bad, cp->dflag, sizeof(int), cudaMemcpyDeviceToHost, cp->st));
@@ -882,15 +889,15 @@ void run_setup(wbfbt_ctx* cp, const double* mu_nodes) {
   CK((launch_cast<double, float>((long long)nn, cp->mu64, cp->mu32, cp->st)));
   CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_l, cp->C, cp->st));
   CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_r, cp->D, cp->st));
-  wb_count_launch(), k_inv_masked<<<(unsigned)((nn + 255) / 256), 256, 0, cp->st>>>(g, cp->C, cp->cinv64);
-  wb_count_launch(), k_inv_masked<<<(unsigned)((nn + 255) / 256), 256, 0, cp->st>>>(g, cp->D, cp->dinv64);
+  wb_launch(k_inv_masked, (unsigned)((nn + 255) / 256), 256, 0, cp->st, g, cp->C, cp->cinv64);
+  wb_launch(k_inv_masked, (unsigned)((nn + 255) / 256), 256, 0, cp->st, g, cp->D, cp->dinv64);
   CK(cudaGetLastError());
   if (cp->mixed)
     build_precond<float>(cp);
   else
     build_precond<double>(cp);
   cp->graph_dirty = true;   // Chebyshev coefficients are baked into the captured launches
-  wb_count_launch(), k_elem_logmu<<<(unsigned)((g.ne + 127) / 128), 128, 0, cp->st>>>(g, cp->k, cp->mu64, cp->llogmu);
+  wb_launch(k_elem_logmu, (unsigned)((g.ne + 127) / 128), 128, 0, cp->st, g, cp->k, cp->mu64, cp->llogmu);
   CK(cudaGetLastError());
 }
 
@@ -1051,7 +1058,7 @@ int wbfbt_learned_sample(wbfbt_ctx* c, int which, const double* r, float* x_out,
       CK((launch_cast<double, T>(n, r, P.pb, c->st)));
       kinv<T>(c, which, P.pb, P.px);
       learned_features<T>(c, which, P.pb, x_out);
-      wb_count_launch(), k_learn_target<T><<<nb256(n), 256, 0, c->st>>>(n, P.dKw[which], P.px, c->dsc + 16, n, y_out);
+      wb_launch(k_learn_target<T>, nb256(n), 256, 0, c->st, n, P.dKw[which], P.px, c->dsc + 16, n, y_out);
       CK(cudaGetLastError());
     };
     if (c->mixed)
