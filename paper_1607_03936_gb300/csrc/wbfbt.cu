@@ -403,7 +403,8 @@ void kinv_learned(wbfbt_ctx* c, int which, const T* bd, T* xd) {
   double nr[2];
   CK(cudaMemcpyAsync(nr, c->dsc + 17, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  if (std::isfinite(nr[0]) && nr[0] < c->net_accept * nr[1]) {
+  // nr holds squared norms: keep z if ||r - K_w z|| < accept ||r||
+  if (std::isfinite(nr[0]) && nr[0] < c->net_accept * c->net_accept * nr[1]) {
     ++c->learned_acc;
   } else {
     ++c->learned_rej;
