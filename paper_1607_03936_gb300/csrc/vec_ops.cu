@@ -52,9 +52,22 @@ __global__ void k_final(const double* __restrict__ part, int np, int ncols, doub
   if (threadIdx.x == 0) out[blockIdx.x] = sqrt_out ? sqrt(acc) : acc;
 }
 
-int partial_blocks(long long n) {
-  long long b = (n + RB - 1) / RB;
+// Partial blocks of a single dot product: about 3300 entries per block (measured best on GB300
+// between 0.96M and 7.5M entries), at most RMAX.
+int dot_blocks(long long n) {
+  long long b = (n + 3299) / 3300;
+  const long long cap = (n + RB - 1) / RB;
+  if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : (b > RMAX ? RMAX : b));
+}
+
+// Blocks per column of the multi-column dot V^T w: about 4864 blocks in total (measured best for
+// 25 columns of 0.96M and 7.5M entries), at most RMAX and at most one per 256 entries.
+int mdot_blocks(long long n, int ncols) {
+  long long b = 4864 / (ncols > 0 ? ncols : 1);
+  const long long cap = (n + RB - 1) / RB;
+  if (b > cap) b = cap;
+  return (int)(b < 16 ? (cap < 16 ? cap : 16) : (b > RMAX ? RMAX : b));
 }
 
 template <typename T>
@@ -393,7 +406,7 @@ __global__ void k_add2(long long n, const double* __restrict__ a, double* __rest
 template <typename A, typename B>
 cudaError_t launch_dot(const A* x, const B* y, long long n, long long stride, double* part, double* out, int sqrt_out,
                        cudaStream_t st) {
-  const int np = partial_blocks(n);
+  const int np = dot_blocks(n);
   wb_launch(k_dot_partial<A, B>, np, RB, 0, st, x, y, n, stride, part);
   wb_launch(k_final, 1, RB, 0, st, part, np, 1, out, sqrt_out);
   return cudaGetLastError();
@@ -489,7 +502,7 @@ cudaError_t launch_dense_inverse_batch(int count, double* const* M, const int* n
 
 cudaError_t launch_mdot(const double* V, long long ld, int ncols, const double* w, long long n, double* part,
                         double* out, cudaStream_t st) {
-  const int np = partial_blocks(n);
+  const int np = mdot_blocks(n, ncols);
   wb_launch(k_mdot_partial, dim3(np, ncols), RB, 0, st, V, ld, w, n, np, part);
   wb_launch(k_final, ncols, RB, 0, st, part, np, ncols, out, 0);
   return cudaGetLastError();
