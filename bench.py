@@ -299,7 +299,7 @@ def run_ours(args, cfg, rank, world):
                 "peak_note": "FP64 ALU peak derived from 152 SMs x 2 DFMA/clk x 2.07 GHz"}
     roofline_fp32 = {"bound": "hbm", "achieved": bytes32 / t_a32 / 1e9, "peak": hbm_peak, "unit": "GB/s",
                      "frac": bytes32 / t_a32 / 1e9 / hbm_peak, "traffic": traffic_for("apply_A_f32"),
-                     "kernel": "k_elem<float,3,OP_A> + k_gather<float,3,3> (one A apply)", "peak_note": hbm_note}
+                     "kernel": "k_q2_elem<OP_A> + k_q2_gather<3,STORE> (one A apply)", "peak_note": hbm_note}
 
     # end-to-end through the C ABI with host buffers (copies inside the timed region)
     mu_h = torch.empty(solver.n_nodes, dtype=torch.float64).pin_memory()
@@ -320,6 +320,40 @@ def run_ours(args, cfg, rank, world):
     h2d = 8 * solver.n_nodes + 8 * solver.n_u
     d2h = 8 * solver.n_u + 8 * solver.n_p
 
+    # the metric's other side: the mixed-precision solve of the same problem, timed the same way
+    # (outside the FP64 timed region), and its distance from the FP64 solution
+    mixed = None
+    if precision == wb.F64:
+        u64, p64 = u.clone(), p.clone()
+        sm = wb.Solver(n, k, mu, precision=wb.MIXED)
+        um = torch.empty_like(u)
+        pm = torch.empty_like(p)
+
+        def step_mixed():
+            m2, f2 = wb.sinker_setup(n, k, centres, cfg["omega"], cfg["delta"], cfg["dr"])
+            sm.setup(m2)
+            return sm.solve(f2, rtol=RTOL, u=um, p=pm)[2]
+
+        for _ in range(args.warmup):
+            step_mixed()
+        tm = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            rm = step_mixed()
+            e1.record(st)
+            torch.cuda.synchronize()
+            tm.append(e0.elapsed_time(e1) / 1e3)
+        t_mixed = max_over_ranks(statistics.mean(tm), world, dev)
+        mixed = {"s_per_step": t_mixed, "speedup_vs_fp64": t_step / t_mixed, "iters": rm.iters,
+                 "final_rel_res": rm.rel_res,
+                 "rel_err_u_vs_fp64": float(torch.linalg.norm(um - u64) / torch.linalg.norm(u64)),
+                 "rel_err_p_vs_fp64": float(torch.linalg.norm(pm - p64) / torch.linalg.norm(p64)),
+                 "learned": "not attached (no measured gain; every learned step was rejected on held-out problems)"}
+        sm.close()
+
     if rank != 0:
         return
     cpu = None
@@ -339,7 +373,7 @@ def run_ours(args, cfg, rank, world):
         "a_apply_dof_per_s": {"fp64": solver.n_u / t_a64, "fp32": solver.n_u / t_a32},
         "roofline": roofline, "roofline_fp32": roofline_fp32, "cpu_baseline": cpu,
         "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches, "clocks": clk,
+        "gpu_launches": launches, "clocks": clk, "mixed": mixed,
     }
     print(json.dumps(line), flush=True)
     solver.close()
@@ -365,6 +399,37 @@ def run_profile(args, cfg):
     solver.close()
 
 
+def run_profile_apply(args, cfg):
+    """One fine-level A apply in FP64 and one in FP32 inside an NVTX range "prof" (after three
+    warm-up applies each), for ncu --nvtx --nvtx-include prof/ captures of the operator kernels."""
+    import torch
+
+    from paper_1607_03936_gb300 import build
+    build.build()
+    from paper_1607_03936_gb300 import inputs
+    from paper_1607_03936_gb300 import wbfbt as wb
+
+    n, k = cfg["n"], cfg["k"]
+    centres = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
+    mu, _ = wb.sinker_setup(n, k, centres, cfg["omega"], cfg["delta"], cfg["dr"])
+    s64 = wb.Solver(n, k, mu, precision=wb.F64, restart=5)
+    s32 = wb.Solver(n, k, mu, precision=wb.MIXED, restart=5)
+    u64 = torch.randn(s64.n_u, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    u32 = u64.float()
+    for _ in range(3):
+        s64.apply_A(u64)
+        s32.apply_A(u32)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("prof")
+    s64.apply_A(u64)
+    s32.apply_A(u32)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_apply": WORKLOAD, "n_u": s64.n_u}), flush=True)
+    s64.close()
+    s32.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -375,6 +440,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="one setup + solve of the workload and nothing else (for an ncu launch list)")
+    ap.add_argument("--profile-apply", action="store_true",
+                    help="one FP64 and one FP32 A apply in an NVTX range 'prof' (for ncu --set full)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -384,6 +451,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, cfg, rank, world)
+        return
+    if args.profile_apply:
+        run_profile_apply(args, cfg)
         return
     if args.profile:
         run_profile(args, cfg)
