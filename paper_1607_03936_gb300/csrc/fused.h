@@ -137,3 +137,16 @@ cudaError_t launch_q2_gather(const Grid& g, int ncomp, int mask_boundary, const 
                              cudaStream_t st);
 cudaError_t launch_q2_d2c(const Grid& g, const float* rd, float* rc, float* R, cudaStream_t st);
 cudaError_t launch_q2_c2d(const Grid& g, const float* ec, float* ed, int add, cudaStream_t st);
+
+// ---- Assembled K_w = B C_w^-1 B^T (kw_ops.cu), k = 2 and 3: a 27-neighbour block stencil of
+// Np x Np blocks per element, stored [o][m][m'][e] in the preconditioner precision.
+size_t kw_stencil_entries(const Grid& g, int k);
+size_t kw_bref_entries(int k);
+// bref: the reference divergence matrix B_e[m][(a, c)] scaled to grid g (FP64, kw_bref_entries).
+cudaError_t launch_kw_bref(const Grid& g, int k, const RefTables* dtab, double* bref, cudaStream_t st);
+// Kst from bref and the nodal inverse weight cinv (C^-1 or D^-1, zero on Dirichlet nodes).
+template <typename T>
+cudaError_t launch_kw_assemble(const Grid& g, int k, const double* bref, const double* cinv, T* Kst, cudaStream_t st);
+// epilogue(K_w p) on every pressure entry.
+template <typename T>
+cudaError_t launch_kw_apply(const Grid& g, int k, const T* Kst, const T* p, const Epi<T>& e, cudaStream_t st);

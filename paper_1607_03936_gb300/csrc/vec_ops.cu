@@ -543,3 +543,4 @@ WB_VINST(float)
 template cudaError_t launch_cast<double, float>(long long, const double*, float*, cudaStream_t);
 template cudaError_t launch_cast<float, double>(long long, const float*, double*, cudaStream_t);
 template cudaError_t launch_cast<double, double>(long long, const double*, double*, cudaStream_t);
+template cudaError_t launch_cast<float, float>(long long, const float*, float*, cudaStream_t);

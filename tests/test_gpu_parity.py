@@ -165,9 +165,11 @@ def test_sinker_setup_matches_oracle(wb):
     assert rel(N(f_g), f_o.T.ravel()) < 1e-14
 
 
+@pytest.mark.parametrize("shape", [(4, 3, 5, 2), (3, 2, 4, 3)])
 @pytest.mark.parametrize("which", [0, 1])
-def test_Kw_fp64(wb, which):
-    m, mu, _, _ = problem(4, 3, 5, 2, dr=1e6)
+def test_Kw_fp64(wb, which, shape):
+    """FP64 contexts apply K_w as an assembled 27-neighbour block stencil (k = 2, 3)."""
+    m, mu, _, _ = problem(*shape, dr=1e6)
     s = gpu_solver(wb, m, mu, a_r=3.0)
     prob = W.StokesProblem(m, mu, a_l=1.0, a_r=3.0)
     K = op.assemble_Kw(prob.B, prob.Cdiag if which == 0 else prob.Ddiag, m)

@@ -145,3 +145,28 @@ def test_solver_with_attached_net_falls_back_and_converges(wb):
     assert acc + rej >= r1.iters          # one learned attempt per K_r application
     if acc == 0:                           # all rejected: exactly the plain method
         assert r1.iters == r0.iters
+
+
+def test_trained_net_gain_is_measured(wb):
+    """Train on solver-generated pairs (8^3 Q2) and measure FGMRES with and without the net.
+
+    The test pins what the method guarantees -- training lowers the loss, the gated learned step
+    keeps convergence, and a fully rejected net reproduces the plain method exactly -- and
+    reports the measured gain (iterations and time with the net minus without).  The gate keeps a
+    learned step only if it cuts the K_w residual to 0.3 of its size (a V-cycle's contraction):
+    with the bare criterion ||r - K_w z|| < ||r||, steps that barely reduce the residual were
+    accepted and FGMRES stagnated (relative residual 1.7e-2 after 1000 iterations)."""
+    from paper_1607_03936_gb300 import learned
+    net, info = learned.train(n=8, n_fields=8, per_field=8, epochs=12, batch=4, lr=2e-3, seed=1000,
+                              log=lambda s: None)
+    hist = info["loss_hist"]
+    assert hist[-1] < 0.8 * hist[0]
+    rows = learned.evaluate(net, n=8, seeds=range(5000, 5004), accept_ratio=0.3, log=lambda s: None)
+    gains = []
+    for r in rows:
+        assert r["vcycle"]["rel_res"] <= 1e-6 and r["learned"]["rel_res"] <= 1e-6
+        if r["learned"]["accepted"] == 0:
+            assert r["learned"]["iters"] == r["vcycle"]["iters"] and r["u_diff"] == 0.0
+        gains.append((r["vcycle"]["iters"] - r["learned"]["iters"],
+                      r["vcycle"]["solve_s"] - r["learned"]["solve_s"], r["learned"]["accepted"]))
+    print("learned gain per held-out problem (iterations saved, seconds saved, accepted steps):", gains)
