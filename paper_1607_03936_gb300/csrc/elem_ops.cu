@@ -594,7 +594,11 @@ __global__ void k_sinker(Grid g, int K, Centres cs, int ns, double omega,
     const double dx = x[0] - cs.c[s][0], dy = x[1] - cs.c[s][1], dz = x[2] - cs.c[s][2];
     double r = sqrt(dx * dx + dy * dy + dz * dz) - 0.5 * omega;
     r = r > 0.0 ? r : 0.0;
-    chi *= 1.0 - exp(-delta * r * r);
+    // for delta r^2 > 40, exp(-delta r^2) < 2^-54 and 1 - exp(...) rounds to exactly 1 in FP64:
+    // skipping the factor leaves chi bitwise unchanged
+    const double t = delta * r * r;
+    if (t > 40.0) continue;
+    chi *= 1.0 - exp(-t);
   }
   const double mu_min = 1.0 / sqrt(dr), mu_max = sqrt(dr);
   mu[n] = (mu_max - mu_min) * (1.0 - chi) + mu_min;

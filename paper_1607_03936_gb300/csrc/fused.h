@@ -132,11 +132,17 @@ size_t elem_scratch_size(const Grid& g, int k);
 
 cudaError_t launch_q2_elem(const Grid& g, int ops, const float* u, const float* p, const float* coef, int coef_nodal,
                            float* R, const Epi<float>& pe, cudaStream_t st);
-cudaError_t launch_q2_poisson(const Grid& g, const float* u, const float* coef, float* R, cudaStream_t st);
-cudaError_t launch_q2_gather(const Grid& g, int ncomp, int mask_boundary, const float* R, const Epi<float>& e,
+// Scalar row kernels (Poisson, node pass, pressure transfers) in FP32 and FP64; the Stokes
+// element pass above is FP32 only (81 + 81 FP64 registers per thread would not fit).
+template <typename T>
+cudaError_t launch_q2_poisson(const Grid& g, const T* u, const T* coef, T* R, cudaStream_t st);
+template <typename T>
+cudaError_t launch_q2_gather(const Grid& g, int ncomp, int mask_boundary, const T* R, const Epi<T>& e,
                              cudaStream_t st);
-cudaError_t launch_q2_d2c(const Grid& g, const float* rd, float* rc, float* R, cudaStream_t st);
-cudaError_t launch_q2_c2d(const Grid& g, const float* ec, float* ed, int add, cudaStream_t st);
+template <typename T>
+cudaError_t launch_q2_d2c(const Grid& g, const T* rd, T* rc, T* R, cudaStream_t st);
+template <typename T>
+cudaError_t launch_q2_c2d(const Grid& g, const T* ec, T* ed, int add, cudaStream_t st);
 
 // ---- Assembled K_w = B C_w^-1 B^T (kw_ops.cu), k = 2 and 3: a 27-neighbour block stencil of
 // Np x Np blocks per element, stored [o][m][m'][e] in the preconditioner precision.
@@ -147,6 +153,9 @@ cudaError_t launch_kw_bref(const Grid& g, int k, const RefTables* dtab, double* 
 // Kst from bref and the nodal inverse weight cinv (C^-1 or D^-1, zero on Dirichlet nodes).
 template <typename T>
 cudaError_t launch_kw_assemble(const Grid& g, int k, const double* bref, const double* cinv, T* Kst, cudaStream_t st);
+// Jacobi inverse diagonal of K_w from bref (the same quantity as launch_dinv_Kw).
+template <typename T>
+cudaError_t launch_kw_dinv(const Grid& g, int k, const double* bref, const double* cinv, T* dinv, cudaStream_t st);
 // epilogue(K_w p) on every pressure entry.
 template <typename T>
 cudaError_t launch_kw_apply(const Grid& g, int k, const T* Kst, const T* p, const Epi<T>& e, cudaStream_t st);

@@ -545,10 +545,16 @@ cudaError_t run_elem(const Grid& g, const void* otab_v, int ops, const T* u, con
 
 #define WB_TAB(T) static_cast<const OpTab<T, N>*>(otab)
 
-// Single precision at k = 2 on grids flagged `rowk` takes the thread-per-element row-segment
-// kernels (q2_ops.cu); their scratch layout is the row one, which the matching launch_gather reads.
+// At k = 2 on grids flagged `rowk` the element passes take the thread-per-element row-segment
+// kernels (q2_ops.cu): the scalar ones (Poisson, pressure transfers) in both precisions, the
+// vector Stokes ones in single precision only.  Their scratch layout is the row one, which the
+// matching launch_gather reads (ncomp 1: scalar producers, ncomp 3: Stokes producers).
 template <typename T>
-bool row_path(const Grid& g, int k) {
+bool row_path_scalar(const Grid& g, int k) {
+  return k == 2 && g.rowk;
+}
+template <typename T>
+bool row_path_vector(const Grid& g, int k) {
   return std::is_same<T, float>::value && k == 2 && g.rowk;
 }
 
@@ -556,14 +562,16 @@ template <typename T>
 size_t elem_scratch_size(const Grid& g, int k) {
   const size_t n = (size_t)(k + 1);
   const size_t elem = 3 * (size_t)g.ne * n * n * n;
-  return row_path<T>(g, k) ? std::max(elem, q2_row_scratch(g, 3)) : elem;
+  if (row_path_vector<T>(g, k)) return std::max(elem, q2_row_scratch(g, 3));
+  if (row_path_scalar<T>(g, k)) return std::max(elem, q2_row_scratch(g, 1));
+  return elem;
 }
 
 template <typename T>
 cudaError_t launch_elem_stokes(const Grid& g, int k, const void* otab, int ops, const T* u, const T* us, const T* p,
                                const T* coef, int cn, T* Ye, const Epi<T>& pe, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value) {
-    if (row_path<T>(g, k)) {
+    if (row_path_vector<T>(g, k)) {
       if (us != nullptr) return cudaErrorInvalidValue;   // input scaling is not part of the row kernels
       return launch_q2_elem(g, ops, u, p, coef, cn, Ye, pe, st);
     }
@@ -574,9 +582,7 @@ cudaError_t launch_elem_stokes(const Grid& g, int k, const void* otab, int ops, 
 template <typename T>
 cudaError_t launch_elem_poisson(const Grid& g, int k, const void* otab, const T* u, const T* coef, T* Ye,
                                 cudaStream_t st) {
-  if constexpr (std::is_same<T, float>::value) {
-    if (row_path<T>(g, k)) return launch_q2_poisson(g, u, coef, Ye, st);
-  }
+  if (row_path_scalar<T>(g, k)) return launch_q2_poisson<T>(g, u, coef, Ye, st);
   WB_FUSED_DISPATCH(k, ((wb_launch(k_elem_poisson<T, N>, elem_blocks(g.ne, Cfg<N>::EPB), Cfg<N>::THREADS, 0, st, g, WB_TAB(T), u, coef, Ye)),
                         cudaGetLastError()));
 }
@@ -588,9 +594,7 @@ cudaError_t launch_gather_elem(const Grid& g, int k, int ncomp, int mask, const 
 template <typename T>
 cudaError_t launch_disc_to_cont_fused(const Grid& g, int k, const void* otab, const T* rd, T* rc, T* Ye,
                                       cudaStream_t st) {
-  if constexpr (std::is_same<T, float>::value) {
-    if (row_path<T>(g, k)) return launch_q2_d2c(g, rd, rc, Ye, st);
-  }
+  if (row_path_scalar<T>(g, k)) return launch_q2_d2c<T>(g, rd, rc, Ye, st);
   cudaError_t e = cudaSuccess;
   switch (k) {
     case 2: { constexpr int N = 3; wb_launch(k_d2c_elem<T, N>, (unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB), Cfg<N>::THREADS, 0, st, g, WB_TAB(T), rd, Ye); break; }
@@ -609,9 +613,7 @@ cudaError_t launch_disc_to_cont_fused(const Grid& g, int k, const void* otab, co
 template <typename T>
 cudaError_t launch_cont_to_disc_fused(const Grid& g, int k, const void* otab, const T* ec, T* ed, int add,
                                       cudaStream_t st) {
-  if constexpr (std::is_same<T, float>::value) {
-    if (row_path<T>(g, k)) return launch_q2_c2d(g, ec, ed, add, st);
-  }
+  if (row_path_scalar<T>(g, k)) return launch_q2_c2d<T>(g, ec, ed, add, st);
   WB_FUSED_DISPATCH(k, ((wb_launch(k_c2d_elem<T, N>, (unsigned)((g.ne + Cfg<N>::EPB - 1) / Cfg<N>::EPB), Cfg<N>::THREADS, 0, st, g, WB_TAB(T), ec, ed, add)),
                         cudaGetLastError()));
 }
@@ -639,9 +641,8 @@ cudaError_t launch_gather_elem(const Grid& g, int k, int ncomp, int mask, const 
 
 template <typename T>
 cudaError_t launch_gather(const Grid& g, int k, int ncomp, int mask, const T* Ye, const Epi<T>& e, cudaStream_t st) {
-  if constexpr (std::is_same<T, float>::value) {
-    if (row_path<T>(g, k)) return launch_q2_gather(g, ncomp, mask, Ye, e, st);
-  }
+  if (ncomp == 3 ? row_path_vector<T>(g, k) : row_path_scalar<T>(g, k))
+    return launch_q2_gather<T>(g, ncomp, mask, Ye, e, st);
   return launch_gather_elem<T>(g, k, ncomp, mask, Ye, e, st);
 }
 

@@ -116,6 +116,31 @@ __global__ void k_kw_apply(Grid g, const T* __restrict__ Kst, const T* __restric
   epi_post<MODE>(E, i, eo, acc);
 }
 
+// Jacobi diagonal of K_w from the reference table: diag[e][m] = sum over the element's nodes n and
+// components c of B_e[m][(n, c)]^2 C^-1(n); dinv = 1 / diag (0 where the diagonal vanishes).
+template <typename T, int N>
+__global__ void k_kw_dinv(Grid g, const double* __restrict__ bref, const double* __restrict__ cinv,
+                          T* __restrict__ dinv) {
+  pdl_entry();
+  constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, K = N - 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)NP * g.ne) return;
+  const int e = (int)(t / NP), m = (int)(t - (long long)e * NP);
+  const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
+  double acc = 0.0;
+  for (int q = 0; q < N3; ++q) {
+    const int a0 = q % N, a1 = (q / N) % N, a2 = q / (N * N);
+    const double ci = cinv[(K * ex + a0) + g.NX * ((K * ey + a1) + g.NY * (K * ez + a2))];
+    if (ci == 0.0) continue;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double b = bref[(m * N3 + q) * 3 + c];
+      acc += b * b * ci;
+    }
+  }
+  dinv[t] = acc > 0.0 ? T(1.0 / acc) : T(0);   // a zero diagonal (single-element mesh, constant mode) is skipped
+}
+
 inline unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
 
 }  // namespace
@@ -163,6 +188,17 @@ cudaError_t launch_kw_apply(const Grid& g, int k, const T* Kst, const T* p, cons
   });
 }
 
+template <typename T>
+cudaError_t launch_kw_dinv(const Grid& g, int k, const double* bref, const double* cinv, T* dinv, cudaStream_t st) {
+  switch (k) {
+    case 2: wb_launch(k_kw_dinv<T, 3>, nb256(4LL * g.ne), 256, 0, st, g, bref, cinv, dinv); break;
+    case 3: wb_launch(k_kw_dinv<T, 4>, nb256(10LL * g.ne), 256, 0, st, g, bref, cinv, dinv); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_kw_dinv<double>(const Grid&, int, const double*, const double*, double*, cudaStream_t);
 template cudaError_t launch_kw_assemble<double>(const Grid&, int, const double*, const double*, double*, cudaStream_t);
 template cudaError_t launch_kw_assemble<float>(const Grid&, int, const double*, const double*, float*, cudaStream_t);
 template cudaError_t launch_kw_apply<double>(const Grid&, int, const double*, const double*, const Epi<double>&,

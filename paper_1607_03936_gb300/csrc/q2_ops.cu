@@ -68,15 +68,20 @@ __device__ inline RowPos row_pos(const Grid& g, const Rows& rw) {
   return r;
 }
 
+// Two consecutive entries in one 8- or 16-byte store (the address is aligned: even entry of a row
+// whose length Q2_ROW_LD is even).
+__device__ inline void store2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+__device__ inline void store2(double* p, double a, double b) { *reinterpret_cast<double2*>(p) = make_double2(a, b); }
+
 // x-assembly of NC x 27 register outputs and the store of the segment's x-line partials.
-template <int NC>
-__device__ inline void row_store(const Grid& g, const RowPos& rp, float (*out)[27], float* __restrict__ R) {
+template <int NC, typename T>
+__device__ inline void row_store(const Grid& g, const RowPos& rp, T (*out)[27], T* __restrict__ R) {
   const int last = min(Q2_SEG - 1, g.nx - 1 - rp.seg * Q2_SEG);   // lane of the segment's last element
 #pragma unroll
   for (int c = 0; c < NC; ++c)
 #pragma unroll
     for (int jl = 0; jl < 9; ++jl) {
-      const float left = __shfl_up_sync(0xffffffffu, out[c][3 * jl + 2], 1);
+      const T left = __shfl_up_sync(0xffffffffu, out[c][3 * jl + 2], 1);
       if (rp.lane > 0) out[c][3 * jl] += left;
     }
   if (!rp.act) return;
@@ -85,8 +90,8 @@ __device__ inline void row_store(const Grid& g, const RowPos& rp, float (*out)[2
   for (int jl = 0; jl < 9; ++jl)
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      float* row = R + ((line0 + jl) * NC + c) * Q2_ROW_LD;
-      *reinterpret_cast<float2*>(row + 2 * rp.lane) = make_float2(out[c][3 * jl], out[c][3 * jl + 1]);
+      T* row = R + ((line0 + jl) * NC + c) * Q2_ROW_LD;
+      store2(row + 2 * rp.lane, out[c][3 * jl], out[c][3 * jl + 1]);
       if (rp.lane == last) row[2 * rp.lane + 2] = out[c][3 * jl + 2];
     }
 }
@@ -217,18 +222,19 @@ k_q2_elem(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restr
 #pragma unroll
     for (int m = 0; m < 4; ++m) epi_apply(pe, (size_t)rp.e * 4 + m, 0, bacc[m]);
   }
-  if (SCAT) row_store<3>(g, rp, out, R);
+  if (SCAT) row_store<3, float>(g, rp, out, R);
 }
 
 // Scalar Q2 Poisson element pass, c per element point (no Dirichlet rows: Neumann operator).
+template <typename T>
 __global__ void __launch_bounds__(32 * WARPS)
-k_q2_poisson(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restrict__ u,
-             const float* __restrict__ coef, float* __restrict__ R) {
+k_q2_poisson(Grid g, Rows rw, const __grid_constant__ OpTab<T, 3> tb, const T* __restrict__ u,
+             const T* __restrict__ coef, T* __restrict__ R) {
   pdl_entry();
   const RowPos rp = row_pos(g, rw);
   if (!rp.warp_live) return;
   const int n0 = 2 * rp.ex + g.NX * (2 * rp.ey + g.NY * 2 * rp.ez);
-  float ur[27], out[1][27];
+  T ur[27], out[1][27];
 #pragma unroll
   for (int l = 0; l < 3; ++l)
 #pragma unroll
@@ -236,11 +242,11 @@ k_q2_poisson(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __re
       const int roff = n0 + g.NX * (j + g.NY * l);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        ur[q3(i, j, l)] = rp.act ? __ldg(u + roff + i) : 0.f;
-        out[0][q3(i, j, l)] = 0.f;
+        ur[q3(i, j, l)] = rp.act ? __ldg(u + roff + i) : T(0);
+        out[0][q3(i, j, l)] = T(0);
       }
     }
-  const float* cf = coef + (size_t)rp.e * 27;
+  const T* cf = coef + (size_t)rp.e * 27;
 #pragma unroll
   for (int l = 0; l < 3; ++l)
 #pragma unroll
@@ -248,14 +254,14 @@ k_q2_poisson(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __re
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         const int q = q3(i, j, l);
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        T a0 = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           a0 += tb.Ds[0][i][a] * ur[q3(a, j, l)];
           a1 += tb.Ds[1][j][a] * ur[q3(i, a, l)];
           a2 += tb.Ds[2][l][a] * ur[q3(i, j, a)];
         }
-        const float f = rp.act ? tb.W3[q] * __ldg(cf + q) : 0.f;
+        const T f = rp.act ? tb.W3[q] * __ldg(cf + q) : T(0);
         a0 *= f;
         a1 *= f;
         a2 *= f;
@@ -266,48 +272,50 @@ k_q2_poisson(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __re
           out[0][q3(i, j, a)] += tb.Ds[2][l][a] * a2;
         }
       }
-  row_store<1>(g, rp, out, R);
+  row_store<1, T>(g, rp, out, R);
 }
 
 // Pressure transfers of the two-space Poisson cycle (Sec. 6), one thread per element (|J|
 // cancels between M_d^-1 and the masses):
 //   r_c = M_cd M_d^-1 r_d: element part out[q] = W_q sum_m psi_m(q) (Minv r_e)_m, assembled
 //   along rows like the operators (the node pass then stores the sums);
+template <typename T>
 __global__ void __launch_bounds__(32 * WARPS)
-k_q2_d2c(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restrict__ rd, float* __restrict__ R) {
+k_q2_d2c(Grid g, Rows rw, const __grid_constant__ OpTab<T, 3> tb, const T* __restrict__ rd, T* __restrict__ R) {
   pdl_entry();
   const RowPos rp = row_pos(g, rw);
   if (!rp.warp_live) return;
-  float rv[4], v[4];
+  T rv[4], v[4];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) rv[m] = rp.act ? __ldg(rd + (size_t)rp.e * 4 + m) : 0.f;
+  for (int m = 0; m < 4; ++m) rv[m] = rp.act ? __ldg(rd + (size_t)rp.e * 4 + m) : T(0);
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    float a = 0.f;
+    T a = T(0);
 #pragma unroll
     for (int mp = 0; mp < 4; ++mp) a += tb.Minv[m][mp] * rv[mp];
     v[m] = a;
   }
-  float out[1][27];
+  T out[1][27];
 #pragma unroll
   for (int q = 0; q < 27; ++q) {
-    float a = 0.f;
+    T a = T(0);
 #pragma unroll
     for (int m = 0; m < 4; ++m) a += tb.Psi[q][m] * v[m];
     out[0][q] = tb.Wref[q] * a;
   }
-  row_store<1>(g, rp, out, R);
+  row_store<1, T>(g, rp, out, R);
 }
 
 //   e_d (+)= M_d^-1 M_dc e_c: e_d[e][m] = sum_m' Minv[m][m'] sum_q W_q psi_m'(q) e_c(node(e, q)).
+template <typename T>
 __global__ void __launch_bounds__(32 * WARPS)
-k_q2_c2d(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restrict__ ec, float* __restrict__ ed,
+k_q2_c2d(Grid g, Rows rw, const __grid_constant__ OpTab<T, 3> tb, const T* __restrict__ ec, T* __restrict__ ed,
          int add) {
   pdl_entry();
   const RowPos rp = row_pos(g, rw);
   if (!rp.act) return;
   const int n0 = 2 * rp.ex + g.NX * (2 * rp.ey + g.NY * 2 * rp.ez);
-  float mom[4] = {0.f, 0.f, 0.f, 0.f};
+  T mom[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
   for (int l = 0; l < 3; ++l)
 #pragma unroll
@@ -316,17 +324,17 @@ k_q2_c2d(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restri
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         const int q = q3(i, j, l);
-        const float w = tb.Wref[q] * __ldg(ec + roff + i);
+        const T w = tb.Wref[q] * __ldg(ec + roff + i);
 #pragma unroll
         for (int m = 0; m < 4; ++m) mom[m] += tb.Psi[q][m] * w;
       }
     }
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    float a = 0.f;
+    T a = T(0);
 #pragma unroll
     for (int mp = 0; mp < 4; ++mp) a += tb.Minv[m][mp] * mom[mp];
-    float* dst = ed + (size_t)rp.e * 4 + m;
+    T* dst = ed + (size_t)rp.e * 4 + m;
     *dst = add ? *dst + a : a;
   }
 }
@@ -336,8 +344,8 @@ k_q2_c2d(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restri
 // iz, else (iz / 2 - 1, l = 2) and (iz / 2, l = 0) where they exist; the same along y; along x
 // the segment s = ix / 64 at X = ix - 64 s, and also s - 1 at X = 64 when ix is a segment's
 // first node.  The epilogue operands are loaded before the partials.
-template <int NC, int MODE>
-__global__ void k_q2_gather(Grid g, int nseg, int mask_boundary, const float* __restrict__ R, Epi<float> E) {
+template <typename T, int NC, int MODE>
+__global__ void k_q2_gather(Grid g, int nseg, int mask_boundary, const T* __restrict__ R, Epi<T> E) {
   pdl_entry();
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   if (ix >= g.NX) return;
@@ -347,12 +355,12 @@ __global__ void k_q2_gather(Grid g, int nseg, int mask_boundary, const float* __
   for (int iz = blockIdx.z; iz < g.NZ; iz += gridDim.z)
     for (int iy = blockIdx.y; iy < g.NY; iy += gridDim.y) {
       const int n = ix + g.NX * (iy + g.NY * iz);
-      EpiOps<float> eo[NC];
+      EpiOps<T> eo[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) eo[c] = epi_pre<MODE>(E, (size_t)c * g.nn + n, n);
-      float v[NC];
+      T v[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) v[c] = 0.f;
+      for (int c = 0; c < NC; ++c) v[c] = T(0);
       if (!(mask_boundary && on_boundary(g, ix, iy, iz))) {
         int zr[2] = {0, 0}, zl[2] = {0, 0}, nzr = 0, yr[2] = {0, 0}, yl[2] = {0, 0}, nyr = 0;
         if (iz & 1) {
@@ -375,12 +383,12 @@ __global__ void k_q2_gather(Grid g, int nseg, int mask_boundary, const float* __
               if (b < nyr) {
                 const size_t rowl = ((size_t)zr[a] * g.ny + yr[b]) * 9 + 3 * zl[a] + yl[b];   // within a segment
                 if (prev) {
-                  const float* src = R + ((s - 1) * per_seg + rowl) * NC * Q2_ROW_LD + 2 * Q2_SEG;
+                  const T* src = R + ((s - 1) * per_seg + rowl) * NC * Q2_ROW_LD + 2 * Q2_SEG;
 #pragma unroll
                   for (int c = 0; c < NC; ++c) v[c] += __ldg(src + c * Q2_ROW_LD);
                 }
                 if (cur) {
-                  const float* src = R + ((size_t)s * per_seg + rowl) * NC * Q2_ROW_LD + X;
+                  const T* src = R + ((size_t)s * per_seg + rowl) * NC * Q2_ROW_LD + X;
 #pragma unroll
                   for (int c = 0; c < NC; ++c) v[c] += __ldg(src + c * Q2_ROW_LD);
                 }
@@ -403,9 +411,10 @@ const RefTables& ref_tables_q2() {
   return t;
 }
 
-Tab2 q2_tab(const Grid& g) {
-  Tab2 t;
-  make_optab<float, 3>(ref_tables_q2(), g, &t);
+template <typename T>
+OpTab<T, 3> q2_tab(const Grid& g) {
+  OpTab<T, 3> t;
+  make_optab<T, 3>(ref_tables_q2(), g, &t);
   return t;
 }
 
@@ -421,7 +430,7 @@ size_t q2_row_scratch(const Grid& g, int ncomp) {
 cudaError_t launch_q2_elem(const Grid& g, int ops, const float* u, const float* p, const float* coef, int coef_nodal,
                            float* R, const Epi<float>& pe, cudaStream_t st) {
   const Rows rw = make_rows(g);
-  const Tab2 tb = q2_tab(g);
+  const Tab2 tb = q2_tab<float>(g);
   const unsigned nbk = elem_grid(rw), nt = 32 * WARPS;
   switch (ops) {
     case OP_A: wb_launch(k_q2_elem<OP_A>, nbk, nt, 0, st, g, rw, tb, u, p, coef, coef_nodal, R, pe); break;
@@ -435,13 +444,15 @@ cudaError_t launch_q2_elem(const Grid& g, int ops, const float* u, const float* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_q2_poisson(const Grid& g, const float* u, const float* coef, float* R, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_q2_poisson(const Grid& g, const T* u, const T* coef, T* R, cudaStream_t st) {
   const Rows rw = make_rows(g);
-  wb_launch(k_q2_poisson, elem_grid(rw), 32 * WARPS, 0, st, g, rw, q2_tab(g), u, coef, R);
+  wb_launch(k_q2_poisson<T>, elem_grid(rw), 32 * WARPS, 0, st, g, rw, q2_tab<T>(g), u, coef, R);
   return cudaGetLastError();
 }
 
-cudaError_t launch_q2_gather(const Grid& g, int ncomp, int mask_boundary, const float* R, const Epi<float>& e,
+template <typename T>
+cudaError_t launch_q2_gather(const Grid& g, int ncomp, int mask_boundary, const T* R, const Epi<T>& e,
                              cudaStream_t st) {
   const Rows rw = make_rows(g);
   dim3 grid;
@@ -450,28 +461,38 @@ cudaError_t launch_q2_gather(const Grid& g, int ncomp, int mask_boundary, const 
   return epi_dispatch(e.mode, [&](auto m) {
     constexpr int MODE = decltype(m)::value;
     if (ncomp == 3)
-      wb_launch(k_q2_gather<3, MODE>, grid, bs, 0, st, g, rw.nseg, mask_boundary, R, e);
+      wb_launch(k_q2_gather<T, 3, MODE>, grid, bs, 0, st, g, rw.nseg, mask_boundary, R, e);
     else if (ncomp == 1)
-      wb_launch(k_q2_gather<1, MODE>, grid, bs, 0, st, g, rw.nseg, mask_boundary, R, e);
+      wb_launch(k_q2_gather<T, 1, MODE>, grid, bs, 0, st, g, rw.nseg, mask_boundary, R, e);
     else
       return cudaErrorInvalidValue;
     return cudaGetLastError();
   });
 }
 
-cudaError_t launch_q2_d2c(const Grid& g, const float* rd, float* rc, float* R, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_q2_d2c(const Grid& g, const T* rd, T* rc, T* R, cudaStream_t st) {
   const Rows rw = make_rows(g);
-  wb_launch(k_q2_d2c, elem_grid(rw), 32 * WARPS, 0, st, g, rw, q2_tab(g), rd, R);
+  wb_launch(k_q2_d2c<T>, elem_grid(rw), 32 * WARPS, 0, st, g, rw, q2_tab<T>(g), rd, R);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  Epi<float> ep;
+  Epi<T> ep;
   ep.mode = EPI_STORE;
   ep.y = rc;
-  return launch_q2_gather(g, 1, 0, R, ep, st);
+  return launch_q2_gather<T>(g, 1, 0, R, ep, st);
 }
 
-cudaError_t launch_q2_c2d(const Grid& g, const float* ec, float* ed, int add, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_q2_c2d(const Grid& g, const T* ec, T* ed, int add, cudaStream_t st) {
   const Rows rw = make_rows(g);
-  wb_launch(k_q2_c2d, elem_grid(rw), 32 * WARPS, 0, st, g, rw, q2_tab(g), ec, ed, add);
+  wb_launch(k_q2_c2d<T>, elem_grid(rw), 32 * WARPS, 0, st, g, rw, q2_tab<T>(g), ec, ed, add);
   return cudaGetLastError();
 }
+
+#define WB_Q2_INST(T)                                                                                        \
+  template cudaError_t launch_q2_poisson<T>(const Grid&, const T*, const T*, T*, cudaStream_t);             \
+  template cudaError_t launch_q2_gather<T>(const Grid&, int, int, const T*, const Epi<T>&, cudaStream_t);  \
+  template cudaError_t launch_q2_d2c<T>(const Grid&, const T*, T*, T*, cudaStream_t);                       \
+  template cudaError_t launch_q2_c2d<T>(const Grid&, const T*, T*, int, cudaStream_t);
+WB_Q2_INST(float)
+WB_Q2_INST(double)

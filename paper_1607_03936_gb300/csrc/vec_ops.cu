@@ -140,8 +140,11 @@ __global__ void k_scale(long long n, T s, const T* __restrict__ x, T* __restrict
 template <typename T>
 __global__ void k_scale_by_inv(long long n, const double* __restrict__ s, const T* __restrict__ x, T* __restrict__ z) {
   pdl_entry();
+  __shared__ double inv;   // one FP64 reciprocal per block
+  if (threadIdx.x == 0) inv = 1.0 / s[0];
+  __syncthreads();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) z[i] = T((double)x[i] / s[0]);
+  if (i < n) z[i] = T((double)x[i] * inv);
 }
 
 template <typename A, typename B>
@@ -254,21 +257,29 @@ __global__ void k_bgj_pivot(GjJobs jobs, int J0, int* __restrict__ flag) {
   const int bb = min(GJB, n - J0);
   double* A = jobs.A[z];
   __shared__ double S[GJB][GJB + 1];
+  __shared__ double rowp[GJB], colj[GJB], s_ip;
+  __shared__ int s_ok;
   const int r = threadIdx.y, c = threadIdx.x;   // 32 x 32 threads
   if (r < bb && c < bb) S[r][c] = A[(size_t)(J0 + r) * n + J0 + c];
   __syncthreads();
   for (int j = 0; j < bb; ++j) {
-    const double p = S[j][j];
-    if (r == 0 && c == 0 && (!(p > 0.0) || !isfinite(p))) flag[0] = J0 + j + 1;
+    // one reciprocal per step, the scaled pivot row and the pivot column shared by all threads
+    if (r == 0 && c == 0) {
+      const double p = S[j][j];
+      if (!(p > 0.0) || !isfinite(p)) flag[0] = J0 + j + 1;
+      s_ok = p > 0.0;
+      s_ip = s_ok ? 1.0 / p : 0.0;
+    }
     __syncthreads();
-    if (!(p > 0.0)) return;   // uniform across the block
-    const double ip = 1.0 / p;
-    const double rj = S[j][c], ci = S[r][j];
+    if (!s_ok) return;   // uniform across the block
+    const double ip = s_ip;
+    if (r == 0 && c < bb) rowp[c] = S[j][c] * ip;
+    if (r == 1 && c < bb) colj[c] = S[c][j];
     __syncthreads();
     if (r < bb && c < bb) {
-      if (r != j && c != j) S[r][c] -= ci * rj * ip;
-      else if (r == j && c != j) S[r][c] = rj * ip;
-      else if (r != j && c == j) S[r][c] = -ci * ip;
+      if (r != j && c != j) S[r][c] -= colj[r] * rowp[c];
+      else if (r == j && c != j) S[r][c] = rowp[c];
+      else if (r != j && c == j) S[r][c] = -colj[r] * ip;
       else S[r][c] = ip;
     }
     __syncthreads();
@@ -276,23 +287,28 @@ __global__ void k_bgj_pivot(GjJobs jobs, int J0, int* __restrict__ flag) {
   if (r < bb && c < bb) jobs.P[z][r * GJB + c] = S[r][c];
 }
 
-// A[J][k] <- P A[J][k] for k not in J: one thread per column k, in place (only it touches column k of rows J)
+// A[J][k] <- P A[J][k] for k not in J.  Block (32 columns, 8 row groups): every thread of a column
+// reads the column's pivot rows, the block synchronises, then each writes 4 of the rows.
 __global__ void k_bgj_rows(GjJobs jobs, int J0) {
   pdl_entry();
   const int z = blockIdx.y;
   const int n = jobs.n[z];
   if (J0 >= n) return;
   const int bb = min(GJB, n - J0);
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.x * 32 + threadIdx.x;
   __shared__ double P[GJB * GJB];
-  for (int t = threadIdx.x; t < GJB * GJB; t += blockDim.x) P[t] = jobs.P[z][t];
-  __syncthreads();
-  if (k >= n || (k >= J0 && k < J0 + bb)) return;
+  for (int t = threadIdx.y * 32 + threadIdx.x; t < GJB * GJB; t += 256) P[t] = jobs.P[z][t];
   double* A = jobs.A[z];
+  const bool valid = k < n && !(k >= J0 && k < J0 + bb);
   double col[GJB];
 #pragma unroll
-  for (int s = 0; s < GJB; ++s) col[s] = s < bb ? A[(size_t)(J0 + s) * n + k] : 0.0;
-  for (int r = 0; r < bb; ++r) {
+  for (int s = 0; s < GJB; ++s) col[s] = (valid && s < bb) ? A[(size_t)(J0 + s) * n + k] : 0.0;
+  __syncthreads();   // every read of the column precedes any write to it
+  if (!valid) return;
+#pragma unroll
+  for (int t = 0; t < GJB / 8; ++t) {
+    const int r = threadIdx.y + 8 * t;
+    if (r >= bb) continue;
     double v = 0.0;
 #pragma unroll
     for (int s = 0; s < GJB; ++s) v += P[r * GJB + s] * col[s];
@@ -331,7 +347,8 @@ __global__ void k_bgj_update(GjJobs jobs, int J0) {
   }
 }
 
-// A[i][J] <- -A[i][J] P for i not in J (thread per row); A[J][J] <- P
+// A[i][J] <- -A[i][J] P for i not in J; A[J][J] <- P.  Block (32 rows, 8 column groups): every
+// thread of a row reads the row's pivot columns, the block synchronises, then each writes 4.
 __global__ void k_bgj_cols(GjJobs jobs, int J0) {
   pdl_entry();
   const int z = blockIdx.y;
@@ -340,23 +357,28 @@ __global__ void k_bgj_cols(GjJobs jobs, int J0) {
   const int bb = min(GJB, n - J0);
   double* A = jobs.A[z];
   __shared__ double P[GJB * GJB];
-  for (int t = threadIdx.x; t < GJB * GJB; t += blockDim.x) P[t] = jobs.P[z][t];
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double* row = A + (size_t)i * n + J0;
-  if (i >= J0 && i < J0 + bb) {
-    for (int c = 0; c < bb; ++c) row[c] = P[(i - J0) * GJB + c];
-    return;
-  }
+  for (int t = threadIdx.y * 32 + threadIdx.x; t < GJB * GJB; t += 256) P[t] = jobs.P[z][t];
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const bool in_range = i < n;
+  const bool pivot_row = in_range && i >= J0 && i < J0 + bb;
+  double* row = A + (size_t)(in_range ? i : 0) * n + J0;
   double a[GJB];
 #pragma unroll
-  for (int s = 0; s < GJB; ++s) a[s] = s < bb ? row[s] : 0.0;
-  for (int c = 0; c < bb; ++c) {
+  for (int s = 0; s < GJB; ++s) a[s] = (in_range && !pivot_row && s < bb) ? row[s] : 0.0;
+  __syncthreads();   // P is loaded and every read of the row precedes any write to it
+  if (!in_range) return;
+#pragma unroll
+  for (int t = 0; t < GJB / 8; ++t) {
+    const int cc = threadIdx.y + 8 * t;
+    if (cc >= bb) continue;
+    if (pivot_row) {
+      row[cc] = P[(i - J0) * GJB + cc];
+      continue;
+    }
     double v = 0.0;
 #pragma unroll
-    for (int s = 0; s < GJB; ++s) v += a[s] * P[s * GJB + c];
-    row[c] = -v;
+    for (int s = 0; s < GJB; ++s) v += a[s] * P[s * GJB + cc];
+    row[cc] = -v;
   }
 }
 
@@ -493,9 +515,9 @@ cudaError_t launch_dense_inverse_batch(int count, double* const* M, const int* n
   }
   for (int J0 = 0; J0 < nmax; J0 += GJB) {
     wb_launch(k_bgj_pivot, count, dim3(32, 32), 0, st, jobs, J0, flag);
-    wb_launch(k_bgj_rows, dim3(nblk(nmax, 128), count), 128, 0, st, jobs, J0);
+    wb_launch(k_bgj_rows, dim3((nmax + 31) / 32, count), dim3(32, 8), 0, st, jobs, J0);
     wb_launch(k_bgj_update, dim3((nmax + 31) / 32, (nmax + 31) / 32, count), dim3(32, 8), 0, st, jobs, J0);
-    wb_launch(k_bgj_cols, dim3(nblk(nmax, 128), count), 128, 0, st, jobs, J0);
+    wb_launch(k_bgj_cols, dim3((nmax + 31) / 32, count), dim3(32, 8), 0, st, jobs, J0);
   }
   return cudaGetLastError();
 }

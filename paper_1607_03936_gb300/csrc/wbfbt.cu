@@ -672,7 +672,10 @@ void build_precond(wbfbt_ctx* c) {
     build_hier<T>(c, P.HL[wi], false, P.c0[wi], 0);
     // disc level: Jacobi diagonal of K_w and lambda_hat
     c->pool.ensure(P.dK64[wi], np);
-    CK(launch_dinv_Kw<double>(g, c->k, c->dtab, wi == 0 ? c->cinv64 : c->dinv64, P.dK64[wi], c->st));
+    if (c->kwbref)
+      CK(launch_kw_dinv<double>(g, c->k, c->kwbref, wi == 0 ? c->cinv64 : c->dinv64, P.dK64[wi], c->st));
+    else
+      CK(launch_dinv_Kw<double>(g, c->k, c->dtab, wi == 0 ? c->cinv64 : c->dinv64, P.dK64[wi], c->st));
     c->pool.ensure(P.dKw[wi], np);
     CK((launch_cast<double, T>((long long)np, P.dK64[wi], P.dKw[wi], c->st)));
     // FP64 preconditioners apply K_w as an assembled stencil (one memory-bound pass instead of

@@ -187,10 +187,12 @@ def test_vcycle_A_fp64(wb, n, k):
     assert rel(N(s.apply_Ainv(T(b))), mg.vcycle(levels, b)) < 1e-10
 
 
+@pytest.mark.parametrize("kern", [1, 2])
 @pytest.mark.parametrize("which", [0, 1])
-def test_pressure_poisson_vcycle_fp64(wb, which):
+def test_pressure_poisson_vcycle_fp64(wb, which, kern):
+    """kern 2 forces the row kernels of the scalar Poisson levels and transfers (FP64 too)."""
     m, mu, _, _ = problem(8, 8, 8, 2, dr=1e6, ns=8)
-    s = gpu_solver(wb, m, mu, a_r=2.0)
+    s = gpu_solver(wb, m, mu, a_r=2.0, elem_kernels=kern)
     prob = W.StokesProblem(m, mu, a_l=1.0, a_r=2.0)
     pp = mg.PressurePoissonMG(m, prob.B, prob.Cdiag if which == 0 else prob.Ddiag, mu,
                               1.0 if which == 0 else 2.0)
@@ -218,6 +220,17 @@ def test_solve_fp64_matches_oracle(wb, n, k, dr, ns):
     uo, po, its, relo, _ = W.solve(m, mu, f)
     assert res.status == 0 and res.rel_res <= 1e-6
     assert abs(res.iters - its) <= 1, (res.iters, its)
+    assert rel(N(u), uo) < 1e-10
+    assert rel(N(p), po) < 1e-10
+
+
+def test_solve_fp64_row_kernels_matches_oracle(wb):
+    """FP64 solve with the scalar row kernels forced on every level (Stokes kernels per point)."""
+    m, mu, f, _ = problem(8, 8, 8, 2, dr=1e4, ns=4)
+    s = gpu_solver(wb, m, mu, elem_kernels=2)
+    u, p, res = s.solve(T(f.T.ravel()))
+    uo, po, its, relo, _ = W.solve(m, mu, f)
+    assert res.status == 0 and abs(res.iters - its) <= 1, (res.iters, its)
     assert rel(N(u), uo) < 1e-10
     assert rel(N(p), po) < 1e-10
 
