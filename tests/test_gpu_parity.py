@@ -305,6 +305,40 @@ def test_full_size_sampled_A_apply_fp32(wb):
     assert err < 2e-5
 
 
+def test_full_size_64cubed_sampled_A_apply_fp32(wb):
+    """64^3 Q2 (the largest configuration; two row segments along x) in FP32: sampled nodes."""
+    cfg = inputs.WORKLOADS["64^3-Q2-S64-DR1e10"]
+    n, k = cfg["n"], cfg["k"]
+    c = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
+    mu_g, _ = wb.sinker_setup(n, k, c, cfg["omega"], cfg["delta"], cfg["dr"])
+    s = wb.Solver(n, k, mu_g, precision=wb.MIXED, restart=5)
+    m = M.Mesh(n, n, n, k)
+    mu = N(mu_g)
+    u = np.random.default_rng(10).standard_normal(m.n_u)
+    y = N(s.apply_A(T(u, torch.float32))).reshape(3, -1)
+    rng = np.random.default_rng(11)
+    nodes = np.concatenate([rng.choice(m.n_nodes, 150, replace=False),
+                            # nodes on the seam between the two x-segments (x index 64)
+                            64 + m.NX * rng.integers(1, m.NY - 1, 50) + m.NX * m.NY * rng.integers(1, m.NZ - 1, 50)])
+    ref = op.sampled_apply_A(m, mu, u.astype(np.float32).astype(np.float64), nodes)
+    err = np.abs(y[:, nodes].T - ref).max() / np.abs(ref).max()
+    assert err < 2e-5
+
+
+def test_q3_dr1e8_mixed_solve_matches_fp64(wb):
+    """24^3 Q3, 32 sinkers, DR 1e8 (the mixed-precision configuration): mixed vs FP64 GPU solve."""
+    cfg = inputs.WORKLOADS["24^3-Q3-S32-DR1e8"]
+    n, k = cfg["n"], cfg["k"]
+    c = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
+    mu_g, f_g = wb.sinker_setup(n, k, c, cfg["omega"], cfg["delta"], cfg["dr"])
+    u64, p64, r64 = wb.Solver(n, k, mu_g).solve(f_g)
+    u32, p32, r32 = wb.Solver(n, k, mu_g, precision=wb.MIXED).solve(f_g)
+    assert r64.status == 0 and r32.status == 0
+    assert abs(r32.iters - r64.iters) <= 3, (r32.iters, r64.iters)
+    assert rel(N(u32), N(u64)) < 1e-6
+    assert rel(N(p32), N(p64)) < 1e-6
+
+
 def test_mixed_solve_point_and_row_kernels_agree(wb):
     """The two single-precision kernel families (per point, per element) agree up to FP32 rounding."""
     m, mu, f, _ = problem(8, 8, 8, 2, dr=1e6, ns=8)
