@@ -52,27 +52,40 @@ __device__ inline int nbr(int v, int n, int t) {
 }
 
 // y[b][v][co] = epilogue(sum_t sum_ci W[t][co][ci] x[b][nbr(v,t)][ci]).  One warp per 16-voxel
-// tile, NT 8-wide output tiles.  Epilogue: + bias, ReLU, or x mask[v][co] > 0 (backward data).
-template <int NT>
+// tile and NTW of the NT 8-wide output tiles (NTW = NT on large grids; NTW = 1 spreads the output
+// tiles over NT warps where voxel tiles are few).  Epilogue: + bias, ReLU, or x mask[v][co] > 0
+// (backward data).
+template <int NT, int NTW>
 __global__ void __launch_bounds__(128) k_conv(int n, int batch, const bf16* __restrict__ x, int ldx, int kp,
                                               const bf16* __restrict__ W, const float* __restrict__ bias, int relu,
                                               const bf16* __restrict__ mask, int ldm, int cvalid,
                                               bf16* __restrict__ y, int ldy, float* __restrict__ yf, int ldyf) {
   pdl_entry();
+  constexpr int NG = NT / NTW;
   const int V = n * n * n;
   const int tiles = (V + 15) / 16;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (warp >= tiles * batch) return;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= tiles * batch * NG) return;
+  const int grp = gw % NG, warp = gw / NG;
   const int b = warp / tiles, m0 = (warp % tiles) * 16;
   const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
   const bf16* xb = x + (size_t)b * V * ldx;
   const int v0 = m0 + gid, v1 = m0 + gid + 8;
-  float acc[NT][4];
+  // voxel coordinates once; per tap the neighbour is an offset with a bounds check
+  const int x0 = v0 % n, y0 = (v0 / n) % n, z0 = v0 / (n * n);
+  const int x1 = v1 % n, y1 = (v1 / n) % n, z1 = v1 / (n * n);
+  float acc[NTW][4];
 #pragma unroll
-  for (int t = 0; t < NT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+  for (int t = 0; t < NTW; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
   for (int tap = 0; tap < 27; ++tap) {
-    const int n0 = v0 < V ? nbr(v0, n, tap) : -1;
-    const int n1 = v1 < V ? nbr(v1, n, tap) : -1;
+    const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+    const int off = dx + n * (dy + n * dz);
+    const bool in0 = v0 < V && (unsigned)(x0 + dx) < (unsigned)n && (unsigned)(y0 + dy) < (unsigned)n &&
+                     (unsigned)(z0 + dz) < (unsigned)n;
+    const bool in1 = v1 < V && (unsigned)(x1 + dx) < (unsigned)n && (unsigned)(y1 + dy) < (unsigned)n &&
+                     (unsigned)(z1 + dz) < (unsigned)n;
+    const int n0 = in0 ? v0 + off : -1;
+    const int n1 = in1 ? v1 + off : -1;
     const bf16* r0 = xb + (size_t)(n0 < 0 ? 0 : n0) * ldx;
     const bf16* r1 = xb + (size_t)(n1 < 0 ? 0 : n1) * ldx;
     const bf16* wt = W + (size_t)tap * NT * 8 * kp;
@@ -83,22 +96,22 @@ __global__ void __launch_bounds__(128) k_conv(int n, int batch, const bf16* __re
       a[2] = n0 >= 0 ? ld_pair(r0 + kc + 8 + tig * 2) : 0u;
       a[3] = n1 >= 0 ? ld_pair(r1 + kc + 8 + tig * 2) : 0u;
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const bf16* wr = wt + (size_t)(t * 8 + gid) * kp + kc;
+      for (int t = 0; t < NTW; ++t) {
+        const bf16* wr = wt + (size_t)((grp * NTW + t) * 8 + gid) * kp + kc;
         unsigned bb[2] = {ld_pair(wr + tig * 2), ld_pair(wr + 8 + tig * 2)};
         mma_bf16(acc[t], a, bb);
       }
     }
   }
 #pragma unroll
-  for (int t = 0; t < NT; ++t) {
+  for (int t = 0; t < NTW; ++t) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int v = h ? v1 : v0;
       if (v >= V) continue;
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        const int co = t * 8 + tig * 2 + e;
+        const int co = (grp * NTW + t) * 8 + tig * 2 + e;
         if (co >= cvalid) continue;
         float val = acc[t][h * 2 + e];
         if (bias) val += bias[co];
@@ -364,8 +377,12 @@ template <int NT>
 void conv_launch(int n, int batch, const bf16* x, int ldx, int kp, const bf16* W, const float* bias, int relu,
                  const bf16* mask, int ldm, int cvalid, bf16* y, int ldy, float* yf, int ldyf, cudaStream_t st) {
   const long long warps = (long long)((n * n * n + 15) / 16) * batch;
-  wb_launch(k_conv<NT>, nb(warps * 32, 128), 128, 0, st, n, batch, x, ldx, kp, W, bias, relu, mask, ldm, cvalid,
-                                                                      y, ldy, yf, ldyf);
+  if (warps >= 152 * 8)   // enough voxel tiles to fill the GPU: one warp per tile, all output tiles
+    wb_launch(k_conv<NT, NT>, nb(warps * 32, 128), 128, 0, st, n, batch, x, ldx, kp, W, bias, relu, mask, ldm,
+              cvalid, y, ldy, yf, ldyf);
+  else                    // few voxel tiles: one warp per (tile, 8-channel output tile)
+    wb_launch(k_conv<NT, 1>, nb(warps * NT * 32, 128), 128, 0, st, n, batch, x, ldx, kp, W, bias, relu, mask, ldm,
+              cvalid, y, ldy, yf, ldyf);
 }
 
 void conv(int npad, int n, int batch, const bf16* x, int ldx, int kp, const bf16* W, const float* bias, int relu,

@@ -155,9 +155,37 @@ def evaluate(net, n=32, k=2, seeds=range(5000, 5020), omega=0.1, delta=200.0, ac
     return rows
 
 
+def profile(n=32, k=2, batch=1):
+    """Three warm-up forwards, then one forward and one loss/gradient pass of the U-Net inside the
+    NVTX range "prof" (for ncu --nvtx --nvtx-include prof/); prints the timed forward."""
+    npe = k * (k + 1) * (k + 2) // 6
+    net = wb.Net(1 + npe, npe, n, max_batch=batch)
+    net.set_params(torch.tensor(inputs.unet_init_params(7, 1 + npe, npe), device="cuda"))
+    g = torch.Generator("cuda").manual_seed(0)
+    x = torch.randn(batch, n ** 3, 1 + npe, device="cuda", generator=g)
+    t = torch.randn(batch, n ** 3, npe, device="cuda", generator=g)
+    for _ in range(3):
+        net.forward(x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        net.forward(x)
+    e1.record()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("prof")
+    net.forward(x)
+    net.loss_grad(x, t)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"unet_forward_us": e0.elapsed_time(e1) * 100.0, "n": n, "batch": batch,
+                      "params": wb.Net.num_params(1 + npe, npe)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
+    pr = sub.add_parser("profile")
+    pr.add_argument("--n", type=int, default=32)
     t = sub.add_parser("train")
     t.add_argument("--n", type=int, default=32)
     t.add_argument("--fields", type=int, default=100)
@@ -175,7 +203,9 @@ def main():
     e.add_argument("--seeds", type=int, default=20)
     e.add_argument("--accept", type=float, default=1.0)
     a = ap.parse_args()
-    if a.cmd == "train":
+    if a.cmd == "profile":
+        profile(n=a.n)
+    elif a.cmd == "train":
         net, info = train(n=a.n, n_fields=a.fields, per_field=a.per_field, epochs=a.epochs, batch=a.batch, lr=a.lr,
                           smooth_fraction=a.smooth)
         net.save(a.out)
