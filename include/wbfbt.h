@@ -68,7 +68,8 @@ typedef struct {
                                       the paper; the results agree to FP32 rounding):
                                       WBFBT_ELEM_AUTO (default) one thread per element for
                                       levels of >= 20000 elements, else one thread per point;
-                                      WBFBT_ELEM_POINT / WBFBT_ELEM_ROW force either         */
+                                      WBFBT_ELEM_POINT / WBFBT_ELEM_ROW force either (and
+                                      the three- or one-pass k = 2 restriction)             */
 } wbfbt_opts;
 
 #define WBFBT_ELEM_AUTO 0

@@ -17,7 +17,8 @@ struct Grid {
   double h[3];          // element sizes
   double s[3];          // 2 / h: reference-to-physical derivative scale per axis
   double detJ;          // hx hy hz / 8
-  int rowk;             // 1: single-precision k = 2 element passes use the row-segment kernels
+  int rowk;             // 1: k = 2 element passes use the row-segment kernels
+  int kern;             // the element-kernel option (0 automatic, 1 per point, 2 per element)
 };
 
 inline Grid make_grid(int nx, int ny, int nz, int k, double lx, double ly, double lz) {
@@ -30,6 +31,7 @@ inline Grid make_grid(int nx, int ny, int nz, int k, double lx, double ly, doubl
   g.s[0] = 2.0 / g.h[0]; g.s[1] = 2.0 / g.h[1]; g.s[2] = 2.0 / g.h[2];
   g.detJ = g.h[0] * g.h[1] * g.h[2] / 8.0;
   g.rowk = 0;
+  g.kern = 0;
   return g;
 }
 

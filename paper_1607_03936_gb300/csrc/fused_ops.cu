@@ -678,8 +678,10 @@ template <typename T>
 cudaError_t launch_restrict_batched(const Grid& gc, int k, const void* otab, int ncomp, const T* in_f, T* out_c,
                                     int mask, T* w1, T* w2, cudaStream_t st) {
   // One pass (one thread per coarse node) pays off on large coarse grids; small ones keep three
-  // short separable passes, which have more threads per node.
-  if (k == 2 && gc.nn >= 100000) {
+  // short separable passes, which have more threads per node (the element-kernel option forces
+  // either: per element -> one pass, per point -> three passes).
+  const bool one_pass = gc.kern == 2 || (gc.kern == 0 && gc.nn >= 100000);
+  if (k == 2 && one_pass) {
     dim3 grid;
     int bs;
     node_pass_geometry(gc, grid, bs);

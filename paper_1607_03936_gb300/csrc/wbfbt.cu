@@ -515,6 +515,7 @@ constexpr int ROW_MIN_ELEMS = 20000;
 Grid with_kernels(const wbfbt_ctx* c, Grid g) {
   const int mode = c->opt.elem_kernels;
   g.rowk = mode == WBFBT_ELEM_ROW || (mode == WBFBT_ELEM_AUTO && g.ne >= ROW_MIN_ELEMS);
+  g.kern = mode;
   return g;
 }
 
