@@ -177,7 +177,7 @@ int wbfbt_apply_Kw_noalloc(const wbfbt_mesh* mesh, int k, const double* mu_nodes
                            const double* p, double* y, void* stream);
 
 /* ---------------------------------------------------------------- learned correction
- * (not in the paper: the task's learned part).  A 3-level 3-D convolutional U-Net on the
+ * (not in the paper: a learned pressure-Poisson correction).  A 3-level 3-D convolutional U-Net on the
  * element grid (channels 16/32/64, 3x3x3 kernels, 2x2x2 average pooling, nearest upsampling,
  * skip concatenation [up, skip], ReLU after every convolution but the last, zero padding).
  * Tensors are voxel-major [batch][n^3][channels], voxel ex + n (ey + n ez).  Parameters are

@@ -1,7 +1,7 @@
 """CPU oracle of the learned pressure-Poisson correction: a 3-level 3-D convolutional U-Net.
 
 TEST INFRASTRUCTURE: plain FP64 NumPy, forward and backward written out from the definitions.
-The paper has no learned component; the architecture is the one the task fixes (3 levels,
+The paper has no learned component; the architecture is fixed as follows (3 levels,
 16/32/64 channels, 3x3x3 kernels, per-element inputs and outputs):
 
   c1 (Cin -> 16), c2 (16 -> 16)                         level 0, n^3 voxels   -> skip a2

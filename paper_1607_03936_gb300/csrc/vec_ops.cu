@@ -1,6 +1,6 @@
 // Vector kernels of the solver: deterministic reductions, Chebyshev-Jacobi updates,
 // projections, casts, FGMRES Gram-Schmidt kernels, and the FP64 dense coarsest
-// solve (right-looking Cholesky, explicit inverse, GEMV).
+// solve (blocked Gauss-Jordan explicit inverse at setup, GEMV per V-cycle).
 //
 // Reductions are two-stage with a grid that depends only on the vector length and
 // a fixed tree inside each block, so repeated runs give bitwise-identical sums.

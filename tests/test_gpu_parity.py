@@ -3,7 +3,7 @@
 Tolerances: FP64 kernels 1e-12 relative (sum-factorised vs assembled CSR, so
 only summation order differs); FP32 kernels 2e-5 relative; composite FP64
 preconditioner pieces 1e-10; FP64 solves: iterations within +-1 and solution
-relative L2 difference <= 1e-10 (spec bar).
+relative L2 difference <= 1e-10.
 """
 import numpy as np
 import pytest
