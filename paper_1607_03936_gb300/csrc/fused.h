@@ -83,8 +83,9 @@ template <typename T>
 cudaError_t launch_restrict_batched(const Grid& gc, int k, const void* optab, int ncomp, const T* in_f, T* out_c,
                                     int mask_dirichlet, T* w1, T* w2, cudaStream_t st);
 
-// ---- Q2 single-precision path (q2_ops.cu): one thread per element, warps along element rows.
-// A warp owns a row segment of up to 32 consecutive elements along x (fixed ey, ez); its
+// ---- Q2 row-segment path (q2_ops.cu, q2_fp64.cu): element rows split into segments of 32.
+// A row segment is up to 32 consecutive elements along x (fixed ey, ez), owned by one warp (a
+// lane per element) or, in the FP64 Stokes pass, by one block of 27 such warps; its
 // partial node values, summed along x within the segment, are stored per x-line of nodes as
 // [segment][ez][ey][l][j][component][X], X = 0 .. 64 padded to Q2_ROW_LD entries.
 // n / d for 0 <= n < 2^31 as a multiply-high and a shift (Granlund & Montgomery, "Division by
@@ -124,6 +125,22 @@ inline void node_pass_geometry(const Grid& g, dim3& grid, int& bs) {
 
 constexpr int Q2_SEG = 32;      // elements per row segment (one warp)
 constexpr int Q2_ROW_LD = 66;   // stored nodes per x-line of a segment (65, padded to even)
+
+// Row segments along x: segment index w = seg + nseg (ey + ny ez).
+struct Rows {
+  int nseg;             // segments along x
+  int nrows;            // nseg * ny * nz
+  FastDiv fseg, fny;    // segment index -> (seg, ey, ez)
+};
+
+inline Rows make_rows(const Grid& g) {
+  Rows r;
+  r.nseg = (g.nx + Q2_SEG - 1) / Q2_SEG;
+  r.nrows = r.nseg * g.ny * g.nz;
+  r.fseg = make_fastdiv(r.nseg);
+  r.fny = make_fastdiv(g.ny);
+  return r;
+}
 // Scratch entries the row-segment element pass writes for ncomp components.
 size_t q2_row_scratch(const Grid& g, int ncomp);
 // Scratch entries (precision T, order k) an element pass on grid g may write for 3 components.
@@ -132,8 +149,13 @@ size_t elem_scratch_size(const Grid& g, int k);
 
 cudaError_t launch_q2_elem(const Grid& g, int ops, const float* u, const float* p, const float* coef, int coef_nodal,
                            float* R, const Epi<float>& pe, cudaStream_t st);
-// Scalar row kernels (Poisson, node pass, pressure transfers) in FP32 and FP64; the Stokes
-// element pass above is FP32 only (81 + 81 FP64 registers per thread would not fit).
+// The FP64 Stokes element pass on the same segments and scratch layout (q2_fp64.cu): one warp
+// per element point and one lane per element (81 + 81 FP64 registers per thread would not fit).
+cudaError_t launch_q2_elem64(const Grid& g, int ops, const double* u, const double* p, const double* coef,
+                             int coef_nodal, double* R, const Epi<double>& pe, cudaStream_t st);
+// One-time launch set-up of that pass (shared-memory opt-in, occupancy); call outside any capture.
+cudaError_t q2_elem64_prepare();
+// Scalar row kernels (Poisson, node pass, pressure transfers) in FP32 and FP64.
 template <typename T>
 cudaError_t launch_q2_poisson(const Grid& g, const T* u, const T* coef, T* R, cudaStream_t st);
 template <typename T>

@@ -545,17 +545,18 @@ cudaError_t run_elem(const Grid& g, const void* otab_v, int ops, const T* u, con
 
 #define WB_TAB(T) static_cast<const OpTab<T, N>*>(otab)
 
-// At k = 2 on grids flagged `rowk` the element passes take the thread-per-element row-segment
-// kernels (q2_ops.cu): the scalar ones (Poisson, pressure transfers) in both precisions, the
-// vector Stokes ones in single precision only.  Their scratch layout is the row one, which the
-// matching launch_gather reads (ncomp 1: scalar producers, ncomp 3: Stokes producers).
+// At k = 2 on grids flagged `rowk` the element passes take the row-segment kernels: the scalar
+// ones (Poisson, pressure transfers; q2_ops.cu) in both precisions, the vector Stokes ones with
+// a thread per element in single precision (q2_ops.cu) and a warp per element point in double
+// precision (q2_fp64.cu).  Their scratch layout is the row one, which the matching launch_gather
+// reads (ncomp 1: scalar producers, ncomp 3: Stokes producers).
 template <typename T>
 bool row_path_scalar(const Grid& g, int k) {
   return k == 2 && g.rowk;
 }
 template <typename T>
 bool row_path_vector(const Grid& g, int k) {
-  return std::is_same<T, float>::value && k == 2 && g.rowk;
+  return k == 2 && g.rowk;
 }
 
 template <typename T>
@@ -570,11 +571,10 @@ size_t elem_scratch_size(const Grid& g, int k) {
 template <typename T>
 cudaError_t launch_elem_stokes(const Grid& g, int k, const void* otab, int ops, const T* u, const T* us, const T* p,
                                const T* coef, int cn, T* Ye, const Epi<T>& pe, cudaStream_t st) {
-  if constexpr (std::is_same<T, float>::value) {
-    if (row_path_vector<T>(g, k)) {
-      if (us != nullptr) return cudaErrorInvalidValue;   // input scaling is not part of the row kernels
-      return launch_q2_elem(g, ops, u, p, coef, cn, Ye, pe, st);
-    }
+  if (row_path_vector<T>(g, k)) {
+    if (us != nullptr) return cudaErrorInvalidValue;   // input scaling is not part of the row kernels
+    if constexpr (std::is_same<T, float>::value) return launch_q2_elem(g, ops, u, p, coef, cn, Ye, pe, st);
+    else return launch_q2_elem64(g, ops, u, p, coef, cn, Ye, pe, st);
   }
   WB_FUSED_DISPATCH(k, (run_elem<T, N>(g, otab, ops, u, us, p, coef, cn, Ye, pe, st)));
 }

@@ -1,0 +1,405 @@
+// Q2 (k = 2) double-precision Stokes-family element pass: one warp per element point, one lane
+// per element.
+//
+// A block owns a row segment of up to 32 consecutive elements along x (fixed ey, ez) -- the
+// segments and row-scratch layout of the single-precision row kernels, so the node pass
+// (launch_q2_gather) is shared -- and has 27 warps, one per GLL point of the element: lane e of
+// warp q works on point q of element e of the segment.  The operators are those of Sec. 1.2:
+// a(u, v) = int 2 mu eps(u) : eps(v), b(v, q) = -int q div v, by GLL quadrature at the nodes.
+//
+// Why this shape.  The FP64 pipe of GB300 retires 2 operations per clock and SM, so the FP64
+// pass is bound by its operation count and by how full its warps are.  Every warp here is full
+// (27 x 32 threads per segment), and because a warp's point is fixed, each 1-D derivative sum is
+// a constant expression: on the Q2 GLL nodes (-1, 0, 1) the derivative matrix is D = Dt / 2 with
+//   Dt = [[-3, 4, -1], [-1, 0, 1], [1, -4, 3]]   (row: point, column: basis function),
+// so a derivative at a line position costs 2, 1 or 2 operations instead of 3 FMAs, and a
+// transposed sum 2 or 3.  On an isotropic mesh (h equal on all axes) the scale kappa = 1/h (the
+// physical derivative is kappa Dt) folds into the point weights; otherwise the transposed sums are
+// scaled per axis.
+//
+// Phases per segment, with a barrier after each:
+//   load      nodal velocity (Dirichlet nodes as zero) from registers into shared [c][q][lane],
+//             then the next segment's inputs are requested into registers (software prefetch);
+//   forward   the reference derivatives at the warp's point, the weighted stress into shared
+//             [slot][q][lane] and, for B, the weighted divergence;
+//   backward  y_c at the warp's point, sum over axes d of the transposed derivative sums of the
+//             stress S_cd, into shared [c][q][lane]; for B, the divergence summed along x-lines;
+//   store     one warp per node x-line (l, j, c) of the segment writes its 65 partial node values
+//             (node 2m: point 0 of element m plus point 2 of element m - 1; node 2m + 1: point 1
+//             of element m), coalesced; for B four warps finish B u per pressure mode.
+#include "elem_common.cuh"
+#include "epi.cuh"
+#include "fused.h"
+#include "kernels.h"
+
+namespace {
+
+using namespace wb;
+
+constexpr int NW = 27;        // warps per block: one per element point
+constexpr int NT = 32 * NW;
+constexpr int PL = NW * 32;   // doubles per shared plane [q][lane]
+
+struct Coef64 {
+  double H[27];    // isotropic: W_q |J| kappa^2; otherwise W_q |J|
+  double T[27];    // isotropic: W_q |J| kappa;   otherwise W_q |J|
+  double kap[3];   // kappa_d = 1 / h_d
+};
+
+__host__ __device__ constexpr int pt(int i, int j, int l) { return i + 3 * (j + 3 * l); }
+
+// Stress slot of (c, d): the diagonal in 0..2, then xy, xz, yz.
+__host__ __device__ constexpr int slot(int c, int d) {
+  return c == d ? c : (c + d == 1 ? 3 : (c + d == 2 ? 4 : 5));
+}
+
+// Dt[P][.] . (v0, v1, v2): reference derivative at line position P.
+template <int P>
+__device__ __forceinline__ double dfw(double v0, double v1, double v2) {
+  if constexpr (P == 0) return fma(4.0, v1, fma(-3.0, v0, -v2));
+  else if constexpr (P == 1) return v2 - v0;
+  else return fma(3.0, v2, fma(-4.0, v1, v0));
+}
+// Dt[.][P] . (s0, s1, s2): transposed sum; column P of Dt is (-3, -1, 1), (4, 0, -4), (-1, 1, 3).
+template <int P>
+__device__ __forceinline__ double dbw(double s0, double s1, double s2) {
+  if constexpr (P == 0) return fma(-3.0, s0, s2 - s1);
+  else if constexpr (P == 1) return 4.0 * (s0 - s2);
+  else return fma(3.0, s2, s1 - s0);
+}
+// acc + Dt[.][P] . (s0, s1, s2)
+template <int P>
+__device__ __forceinline__ double dbw_acc(double s0, double s1, double s2, double acc) {
+  if constexpr (P == 0) return fma(-3.0, s0, (acc + s2) - s1);
+  else if constexpr (P == 1) return fma(4.0, s0 - s2, acc);
+  else return fma(3.0, s2, (acc + s1) - s0);
+}
+
+// Shared layout (doubles): velocity / output [3][q][lane], stress [NS][q][lane], weighted
+// divergence [q][lane], divergence x-line sums [2][9][lane], pressure modes [4][lane].
+template <int OPS>
+struct Lay {
+  static constexpr bool DA = OPS & OP_A, DBT = OPS & OP_BT, DB = OPS & OP_B;
+  static constexpr int NS = DA ? 6 : (DBT ? 1 : 0);
+  static constexpr int U = 0;
+  static constexpr int S = U + 3 * PL;
+  static constexpr int DIV = S + NS * PL;
+  static constexpr int RED = DIV + (DB ? PL : 0);
+  static constexpr int P = RED + (DB ? 2 * 9 * 32 : 0);
+  static constexpr int TOTAL = P + (DBT ? 4 * 32 : 0);
+};
+
+template <int OPS, bool ISO, int Q>
+__device__ __forceinline__ void forward(const Coef64& cf, double* __restrict__ sh, int lane, double mu) {
+  using LY = Lay<OPS>;
+  constexpr int I = Q % 3, J = (Q / 3) % 3, L = Q / 9;
+  constexpr bool DA = LY::DA, DBT = LY::DBT, DB = LY::DB;
+  const double* su = sh + LY::U + lane;
+  double* sS = sh + LY::S + Q * 32 + lane;   // this point's entry of stress plane `slot`: sS[slot * PL]
+  auto U = [&](int c, int qq) { return su[(c * NW + qq) * 32]; };
+  // reference derivatives g[c][d] = Dt-sum of component c along axis d (only the diagonal for B)
+  double g[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (!(DA || DB)) break;
+    if (DA || c == 0) g[c][0] = dfw<I>(U(c, pt(0, J, L)), U(c, pt(1, J, L)), U(c, pt(2, J, L)));
+    if (DA || c == 1) g[c][1] = dfw<J>(U(c, pt(I, 0, L)), U(c, pt(I, 1, L)), U(c, pt(I, 2, L)));
+    if (DA || c == 2) g[c][2] = dfw<L>(U(c, pt(I, J, 0)), U(c, pt(I, J, 1)), U(c, pt(I, J, 2)));
+  }
+  if constexpr (DB) {
+    // W_q |J| div u = T_q (kappa-weighted trace of g)
+    const double tr = ISO ? (g[0][0] + g[1][1]) + g[2][2]
+                          : fma(cf.kap[2], g[2][2], fma(cf.kap[1], g[1][1], cf.kap[0] * g[0][0]));
+    sh[LY::DIV + Q * 32 + lane] = cf.T[Q] * tr;
+  }
+  double t = 0.0;
+  if constexpr (DBT) {
+    // p at the point: psi = (1, xi, eta, zeta) on the nodes -1, 0, 1
+    const double* sp = sh + LY::P + lane;
+    double pq = sp[0];
+    if constexpr (I == 0) pq -= sp[32];
+    if constexpr (I == 2) pq += sp[32];
+    if constexpr (J == 0) pq -= sp[64];
+    if constexpr (J == 2) pq += sp[64];
+    if constexpr (L == 0) pq -= sp[96];
+    if constexpr (L == 2) pq += sp[96];
+    t = cf.T[Q] * pq;
+  }
+  if constexpr (DA) {
+    const double h = cf.H[Q] * mu;
+    if constexpr (ISO) {
+      // kappa S: diagonal 2 h g_cc - t, off-diagonal h (g_cd + g_dc)
+      const double f = h + h;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sS[slot(c, c) * PL] = DBT ? fma(f, g[c][c], -t) : f * g[c][c];
+      sS[3 * PL] = h * (g[0][1] + g[1][0]);
+      sS[4 * PL] = h * (g[0][2] + g[2][0]);
+      sS[5 * PL] = h * (g[1][2] + g[2][1]);
+    } else {
+      // S: diagonal 2 h kappa_c g_cc - t, off-diagonal h (kappa_d g_cd + kappa_c g_dc)
+      const double hk[3] = {h * cf.kap[0], h * cf.kap[1], h * cf.kap[2]};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sS[slot(c, c) * PL] = fma(hk[c], g[c][c], fma(hk[c], g[c][c], -t));
+      sS[3 * PL] = fma(hk[1], g[0][1], hk[0] * g[1][0]);
+      sS[4 * PL] = fma(hk[2], g[0][2], hk[0] * g[2][0]);
+      sS[5 * PL] = fma(hk[2], g[1][2], hk[1] * g[2][1]);
+    }
+  } else if constexpr (DBT) {
+    sS[0] = -t;
+  }
+}
+
+template <int OPS, bool ISO, int Q>
+__device__ __forceinline__ void backward(const Coef64& cf, double* __restrict__ sh, int lane) {
+  using LY = Lay<OPS>;
+  constexpr int I = Q % 3, J = (Q / 3) % 3, L = Q / 9;
+  constexpr bool DA = LY::DA;
+  const double* sS = sh + LY::S + lane;
+  double* sy = sh + LY::U + lane;
+  auto S = [&](int s, int qq) { return sS[(s * NW + qq) * 32]; };
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double y;
+    if constexpr (DA) {
+      const int s0 = slot(c, 0), s1 = slot(c, 1), s2 = slot(c, 2);
+      if constexpr (ISO) {
+        y = dbw<I>(S(s0, pt(0, J, L)), S(s0, pt(1, J, L)), S(s0, pt(2, J, L)));
+        y = dbw_acc<J>(S(s1, pt(I, 0, L)), S(s1, pt(I, 1, L)), S(s1, pt(I, 2, L)), y);
+        y = dbw_acc<L>(S(s2, pt(I, J, 0)), S(s2, pt(I, J, 1)), S(s2, pt(I, J, 2)), y);
+      } else {
+        y = cf.kap[0] * dbw<I>(S(s0, pt(0, J, L)), S(s0, pt(1, J, L)), S(s0, pt(2, J, L)));
+        y = fma(cf.kap[1], dbw<J>(S(s1, pt(I, 0, L)), S(s1, pt(I, 1, L)), S(s1, pt(I, 2, L))), y);
+        y = fma(cf.kap[2], dbw<L>(S(s2, pt(I, J, 0)), S(s2, pt(I, J, 1)), S(s2, pt(I, J, 2))), y);
+      }
+    } else {
+      // B^T alone: the stress is -t on the diagonal, so only axis c contributes to y_c
+      if (c == 0) y = dbw<I>(S(0, pt(0, J, L)), S(0, pt(1, J, L)), S(0, pt(2, J, L)));
+      else if (c == 1) y = dbw<J>(S(0, pt(I, 0, L)), S(0, pt(I, 1, L)), S(0, pt(I, 2, L)));
+      else y = dbw<L>(S(0, pt(I, J, 0)), S(0, pt(I, J, 1)), S(0, pt(I, J, 2)));
+      if constexpr (!ISO) y *= cf.kap[c];
+    }
+    sy[(c * NW + Q) * 32] = y;
+  }
+}
+
+#define WB_Q27(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) \
+  X(14) X(15) X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26)
+
+// Segment index -> first element row and element coordinates.
+struct Seg {
+  int seg, ey, ez, last;   // last: lane of the segment's last element
+};
+
+__device__ __forceinline__ Seg seg_of(const Grid& g, const Rows& rw, int w) {
+  Seg s;
+  const unsigned rest = fdiv((unsigned)w, rw.fseg);
+  s.seg = w - (int)rest * rw.nseg;
+  s.ez = (int)fdiv(rest, rw.fny);
+  s.ey = (int)rest - s.ez * g.ny;
+  s.last = min(Q2_SEG - 1, g.nx - 1 - s.seg * Q2_SEG);
+  return s;
+}
+
+template <int OPS, bool ISO>
+__global__ void __launch_bounds__(NT, 1)
+k_q2_elem64(Grid g, Rows rw, const __grid_constant__ Coef64 cf, const double* __restrict__ u,
+            const double* __restrict__ p, const double* __restrict__ coef, int coef_nodal, double* __restrict__ R,
+            Epi<double> pe) {
+  pdl_entry();
+  using LY = Lay<OPS>;
+  constexpr bool DA = LY::DA, DBT = LY::DBT, DB = LY::DB, GRAD = DA || DB, SCAT = DA || DBT;
+  extern __shared__ double sh[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int I = warp % 3, J = (warp / 3) % 3, L = warp / 9;
+  const size_t nn = (size_t)g.nn;
+
+  // inputs of one segment for this thread (point `warp` of element `lane`)
+  double un[3] = {0.0, 0.0, 0.0}, mun = 0.0, pn = 0.0;
+  auto fetch = [&](int w) {
+    const Seg s = seg_of(g, rw, w);
+    const int ex = s.seg * Q2_SEG + lane;
+    const bool act = lane <= s.last;
+    const int ix = 2 * ex + I, iy = 2 * s.ey + J, iz = 2 * s.ez + L;
+    const int n = ix + g.NX * (iy + g.NY * iz);
+    const int e = ex + g.nx * (s.ey + g.ny * s.ez);
+    if (GRAD) {
+      const bool live = act && !on_boundary(g, ix, iy, iz);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) un[c] = live ? __ldg(u + c * nn + n) : 0.0;
+    }
+    if (DA) mun = act ? __ldg(coef_nodal ? coef + n : coef + (size_t)e * 27 + warp) : 0.0;
+    if (DBT && warp < 4) pn = act ? __ldg(p + (size_t)e * 4 + warp) : 0.0;
+  };
+
+  int w = blockIdx.x;
+  if (w >= rw.nrows) return;   // whole block
+  fetch(w);
+  for (; w < rw.nrows; w += gridDim.x) {
+    const Seg s = seg_of(g, rw, w);
+    // load
+    if (GRAD) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sh[LY::U + (c * NW + warp) * 32 + lane] = un[c];
+    }
+    if (DBT && warp < 4) sh[LY::P + warp * 32 + lane] = pn;
+    const double mu = mun;
+    __syncthreads();
+    if (w + (int)gridDim.x < rw.nrows) fetch(w + gridDim.x);
+    // forward
+    switch (warp) {
+#define WB_F(Q) \
+  case Q: forward<OPS, ISO, Q>(cf, sh, lane, mu); break;
+      WB_Q27(WB_F)
+#undef WB_F
+    }
+    __syncthreads();
+    // backward (and, for B, x-line sums of the weighted divergence: T = d0 + d1 + d2, X = d2 - d0)
+    if (SCAT) {
+      switch (warp) {
+#define WB_B(Q) \
+  case Q: backward<OPS, ISO, Q>(cf, sh, lane); break;
+        WB_Q27(WB_B)
+#undef WB_B
+      }
+    }
+    if (DB && warp < 9) {
+      const double* dv = sh + LY::DIV + lane;
+      const double d0 = dv[(3 * warp) * 32], d1 = dv[(3 * warp + 1) * 32], d2 = dv[(3 * warp + 2) * 32];
+      sh[LY::RED + warp * 32 + lane] = (d0 + d1) + d2;
+      sh[LY::RED + (9 + warp) * 32 + lane] = d2 - d0;
+    }
+    __syncthreads();
+    // store: warp = (jl, c) owns the node x-line (j, l) of component c
+    if (SCAT) {
+      const int jl = warp / 3, c = warp - 3 * jl;
+      const double* y0 = sh + LY::U + (c * NW + 3 * jl) * 32;   // points 0, 1, 2 of the line
+      double* row = R + ((((size_t)s.seg * g.nz + s.ez) * g.ny + s.ey) * 9 + jl) * 3 * Q2_ROW_LD +
+                    (size_t)c * Q2_ROW_LD;
+      const int xmax = 2 * s.last + 2;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int X = lane + 32 * k;
+        if (X <= xmax) {
+          const int m = X >> 1;
+          double v;
+          if (X & 1) {
+            v = y0[32 + m];
+          } else {
+            v = m <= s.last ? y0[m] : 0.0;
+            if (m >= 1) v += y0[64 + m - 1];
+          }
+          row[X] = v;
+        }
+      }
+    }
+    if (DB && warp < 4 && lane <= s.last) {
+      // B u = -sum_q psi_m(q) W_q |J| div u(q); psi = (1, xi, eta, zeta), x-line jl = j + 3 l
+      const double* T = sh + LY::RED + lane;
+      const double* X = T + 9 * 32;
+      double v;
+      if (warp == 0) {
+        v = T[0];
+#pragma unroll
+        for (int jl = 1; jl < 9; ++jl) v += T[jl * 32];
+      } else if (warp == 1) {
+        v = X[0];
+#pragma unroll
+        for (int jl = 1; jl < 9; ++jl) v += X[jl * 32];
+      } else if (warp == 2) {
+        v = T[2 * 32] - T[0];
+#pragma unroll
+        for (int l = 1; l < 3; ++l) v += T[(2 + 3 * l) * 32] - T[(3 * l) * 32];
+      } else {
+        v = T[6 * 32] - T[0];
+#pragma unroll
+        for (int j = 1; j < 3; ++j) v += T[(j + 6) * 32] - T[j * 32];
+      }
+      const int e = s.seg * Q2_SEG + lane + g.nx * (s.ey + g.ny * s.ez);
+      epi_apply(pe, (size_t)e * 4 + warp, 0, -v);
+    }
+    __syncthreads();
+  }
+}
+
+int g_nsm = 0;
+
+// Per instantiation: the dynamic shared-memory opt-in and the resident blocks per SM, set once
+// (q2_elem64_prepare, called at context creation, before any stream capture).
+template <int OPS, bool ISO>
+int& blocks_per_sm() {
+  static int b = -1;
+  return b;
+}
+
+template <int OPS, bool ISO>
+cudaError_t prepare_one() {
+  constexpr size_t smem = sizeof(double) * Lay<OPS>::TOTAL;
+  if (blocks_per_sm<OPS, ISO>() > 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_q2_elem64<OPS, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_q2_elem64<OPS, ISO>, NT, smem)) != cudaSuccess)
+    return e;
+  blocks_per_sm<OPS, ISO>() = occ > 0 ? occ : 1;
+  return cudaSuccess;
+}
+
+template <int OPS, bool ISO>
+cudaError_t launch_one(const Grid& g, const Rows& rw, const Coef64& cf, const double* u, const double* p,
+                       const double* coef, int coef_nodal, double* R, const Epi<double>& pe, cudaStream_t st) {
+  if (blocks_per_sm<OPS, ISO>() < 0) {
+    const cudaError_t e = q2_elem64_prepare();
+    if (e != cudaSuccess) return e;
+  }
+  const long long cap = (long long)g_nsm * blocks_per_sm<OPS, ISO>();
+  const unsigned grid = (unsigned)(rw.nrows < cap ? rw.nrows : cap);
+  wb_launch(k_q2_elem64<OPS, ISO>, grid, NT, sizeof(double) * Lay<OPS>::TOTAL, st, g, rw, cf, u, p, coef, coef_nodal,
+            R, pe);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t q2_elem64_prepare() {
+  if (g_nsm == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e;
+  if ((e = prepare_one<OP_A, true>()) != cudaSuccess) return e;
+  if ((e = prepare_one<OP_A, false>()) != cudaSuccess) return e;
+  if ((e = prepare_one<OP_A | OP_BT | OP_B, true>()) != cudaSuccess) return e;
+  if ((e = prepare_one<OP_A | OP_BT | OP_B, false>()) != cudaSuccess) return e;
+  if ((e = prepare_one<OP_BT, false>()) != cudaSuccess) return e;
+  return prepare_one<OP_B, false>();
+}
+
+cudaError_t launch_q2_elem64(const Grid& g, int ops, const double* u, const double* p, const double* coef,
+                             int coef_nodal, double* R, const Epi<double>& pe, cudaStream_t st) {
+  const Rows rw = make_rows(g);
+  if (rw.nrows == 0) return cudaSuccess;
+  // the isotropic form is taken by the passes with A (B^T or B alone have little FP64 work)
+  const bool iso = (ops & OP_A) && g.h[0] == g.h[1] && g.h[1] == g.h[2];
+  // GLL weights of the Q2 nodes (-1, 0, 1): 1/3, 4/3, 1/3
+  const double w1[3] = {1.0 / 3.0, 4.0 / 3.0, 1.0 / 3.0};
+  Coef64 cf;
+  for (int d = 0; d < 3; ++d) cf.kap[d] = 0.5 * g.s[d];
+  for (int q = 0; q < 27; ++q) {
+    const double W = w1[q % 3] * w1[(q / 3) % 3] * w1[q / 9] * g.detJ;
+    cf.H[q] = iso ? W * cf.kap[0] * cf.kap[0] : W;
+    cf.T[q] = iso ? W * cf.kap[0] : W;
+  }
+  switch (ops) {
+    case OP_A:
+      return iso ? launch_one<OP_A, true>(g, rw, cf, u, p, coef, coef_nodal, R, pe, st)
+                 : launch_one<OP_A, false>(g, rw, cf, u, p, coef, coef_nodal, R, pe, st);
+    case OP_A | OP_BT | OP_B:
+      return iso ? launch_one<OP_A | OP_BT | OP_B, true>(g, rw, cf, u, p, coef, coef_nodal, R, pe, st)
+                 : launch_one<OP_A | OP_BT | OP_B, false>(g, rw, cf, u, p, coef, coef_nodal, R, pe, st);
+    case OP_BT: return launch_one<OP_BT, false>(g, rw, cf, u, p, coef, coef_nodal, R, pe, st);
+    case OP_B: return launch_one<OP_B, false>(g, rw, cf, u, p, coef, coef_nodal, R, pe, st);
+    default: return cudaErrorInvalidValue;
+  }
+}

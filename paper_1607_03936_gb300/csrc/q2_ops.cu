@@ -31,22 +31,6 @@ constexpr int WARPS = 4;   // row segments per block
 
 __host__ __device__ constexpr int q3(int i, int j, int l) { return i + 3 * (j + 3 * l); }
 
-// Row segments along x, and the layout of the row scratch.
-struct Rows {
-  int nseg;             // segments along x
-  int nrows;            // nseg * ny * nz
-  FastDiv fseg, fny;    // warp index -> (segment, ey, ez)
-};
-
-Rows make_rows(const Grid& g) {
-  Rows r;
-  r.nseg = (g.nx + Q2_SEG - 1) / Q2_SEG;
-  r.nrows = r.nseg * g.ny * g.nz;
-  r.fseg = make_fastdiv(r.nseg);
-  r.fny = make_fastdiv(g.ny);
-  return r;
-}
-
 // Position of this thread: segment, element row and element.
 struct RowPos {
   int seg, ey, ez, lane, ex, e;

@@ -1030,6 +1030,7 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
     const size_t nn = g.nn;
     cp->dtab = cp->pool.get<RefTables>(1);
     CK(cudaMemcpyAsync(cp->dtab, &cp->htab, sizeof(RefTables), cudaMemcpyHostToDevice, cp->st));
+    if (k == 2) CK(q2_elem64_prepare());
     if (k <= 3) {
       cp->kwbref = cp->pool.get<double>(kw_bref_entries(k));
       CK(launch_kw_bref(g, k, cp->dtab, cp->kwbref, cp->st));
@@ -1045,7 +1046,7 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
     cp->cinv64 = cp->pool.get<double>(nn);
     cp->dinv64 = cp->pool.get<double>(nn);
     cp->ntot = 3LL * nn + (long long)g.ne * cp->NP;
-    cp->Ye64 = cp->pool.get<double>((size_t)3 * g.ne * cp->N3);
+    cp->Ye64 = cp->pool.get<double>(elem_scratch_size<double>(g, k));
     cp->Ye32 = cp->pool.get<float>(elem_scratch_size<float>(g, k));
     cp->ot64 = make_device_optab<double>(cp, g);
     cp->ot32 = make_device_optab<float>(cp, g);

@@ -64,11 +64,18 @@ SHAPES = [(5, 4, 3, 2, (1.0, 0.7, 1.3)), (3, 2, 2, 3, (1.0, 1.0, 1.0)), (1, 1, 1
           (2, 3, 1, 4, (0.5, 1.0, 2.0))]
 
 
-@pytest.mark.parametrize("shape", SHAPES)
-def test_fine_operators_fp64(wb, shape):
+# Isotropic meshes (equal h, exact in binary) with one or several row segments along x, the last
+# one short: the FP64 row kernel takes its isotropic form there, the general one on SHAPES.
+SHAPES_ISO = [(33, 3, 2, 2, (8.25, 0.75, 0.5)), (6, 5, 4, 2, (1.5, 1.25, 1.0)), (67, 2, 1, 2, (33.5, 1.0, 0.5))]
+
+
+@pytest.mark.parametrize("kern", [1, 2])
+@pytest.mark.parametrize("shape", SHAPES + SHAPES_ISO)
+def test_fine_operators_fp64(wb, shape, kern):
+    """kern 1: per-point element passes; kern 2: at k = 2 the row-segment passes (warp per point)."""
     nx, ny, nz, k, L = shape
     m, mu, _, _ = problem(nx, ny, nz, k, lengths=L)
-    s = gpu_solver(wb, m, mu)
+    s = gpu_solver(wb, m, mu, elem_kernels=kern)
     rng = np.random.default_rng(1)
     u, p = rng.standard_normal(m.n_u), rng.standard_normal(m.n_p)
     A = op.assemble_A(m, op.point_values(m, mu))
@@ -177,10 +184,12 @@ def test_Kw_fp64(wb, which, shape):
     assert rel(N(s.apply_Kw(which, T(p))), K @ p) < 1e-12
 
 
+@pytest.mark.parametrize("kern", [1, 2])
 @pytest.mark.parametrize("n,k", [(8, 2), (6, 3), (3, 2)])
-def test_vcycle_A_fp64(wb, n, k):
+def test_vcycle_A_fp64(wb, n, k, kern):
+    """kern 2 forces the row-segment Stokes passes on every level (nodal and per-point viscosity)."""
     m, mu, _, _ = problem(n, n, n, k, dr=1e4)
-    s = gpu_solver(wb, m, mu)
+    s = gpu_solver(wb, m, mu, elem_kernels=kern)
     levels = mg.build_hierarchy(m, op.point_values(m, mu), vector=True)
     assert len(levels) == s.n_levels
     b = np.random.default_rng(5).standard_normal(m.n_u) * m.interior_dof_mask()
@@ -225,7 +234,7 @@ def test_solve_fp64_matches_oracle(wb, n, k, dr, ns):
 
 
 def test_solve_fp64_row_kernels_matches_oracle(wb):
-    """FP64 solve with the scalar row kernels forced on every level (Stokes kernels per point)."""
+    """FP64 solve with the row-segment kernels (scalar and Stokes) forced on every level."""
     m, mu, f, _ = problem(8, 8, 8, 2, dr=1e4, ns=4)
     s = gpu_solver(wb, m, mu, elem_kernels=2)
     u, p, res = s.solve(T(f.T.ravel()))
