@@ -153,7 +153,10 @@ cudaError_t launch_q2_elem(const Grid& g, int ops, const float* u, const float* 
 // per element point and one lane per element (81 + 81 FP64 registers per thread would not fit).
 cudaError_t launch_q2_elem64(const Grid& g, int ops, const double* u, const double* p, const double* coef,
                              int coef_nodal, double* R, const Epi<double>& pe, cudaStream_t st);
-// One-time launch set-up of that pass (shared-memory opt-in, occupancy); call outside any capture.
+// The FP64 scalar Poisson pass in the same layout (q2_fp64.cu, warp per element point).
+cudaError_t launch_q2_poisson64(const Grid& g, const double* u, const double* coef, double* R, cudaStream_t st);
+// One-time launch set-up of the q2_fp64.cu passes (shared-memory opt-in, occupancy); call it
+// outside any stream capture.
 cudaError_t q2_elem64_prepare();
 // Scalar row kernels (Poisson, node pass, pressure transfers) in FP32 and FP64.
 template <typename T>

@@ -582,7 +582,10 @@ cudaError_t launch_elem_stokes(const Grid& g, int k, const void* otab, int ops, 
 template <typename T>
 cudaError_t launch_elem_poisson(const Grid& g, int k, const void* otab, const T* u, const T* coef, T* Ye,
                                 cudaStream_t st) {
-  if (row_path_scalar<T>(g, k)) return launch_q2_poisson<T>(g, u, coef, Ye, st);
+  if (row_path_scalar<T>(g, k)) {
+    if constexpr (std::is_same<T, double>::value) return launch_q2_poisson64(g, u, coef, Ye, st);
+    else return launch_q2_poisson<T>(g, u, coef, Ye, st);
+  }
   WB_FUSED_DISPATCH(k, ((wb_launch(k_elem_poisson<T, N>, elem_blocks(g.ne, Cfg<N>::EPB), Cfg<N>::THREADS, 0, st, g, WB_TAB(T), u, coef, Ye)),
                         cudaGetLastError()));
 }

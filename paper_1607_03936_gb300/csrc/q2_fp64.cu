@@ -321,6 +321,115 @@ k_q2_elem64(Grid g, Rows rw, const __grid_constant__ Coef64 cf, const double* __
   }
 }
 
+// Scalar Q2 Poisson element pass (the continuous Q2 level of the two-space pressure cycle, Sec.
+// 6: int c grad u . grad v, c per element point, no Dirichlet rows), same segment and warp
+// layout: y = sum_d Dt^T (W_q |J| kappa_d^2 c g_d), g_d the reference derivative along axis d.
+// Shared: u / output [q][lane], fluxes [3][q][lane].
+struct PoisCoef64 {
+  double Wk[3][27];   // W_q |J| kappa_d^2
+};
+
+template <bool ISO, int Q>
+__device__ __forceinline__ void pois_forward(const PoisCoef64& cf, double* __restrict__ sh, int lane, double c) {
+  constexpr int I = Q % 3, J = (Q / 3) % 3, L = Q / 9;
+  const double* su = sh + lane;
+  double* sF = sh + PL + Q * 32 + lane;
+  const double g0 = dfw<I>(su[pt(0, J, L) * 32], su[pt(1, J, L) * 32], su[pt(2, J, L) * 32]);
+  const double g1 = dfw<J>(su[pt(I, 0, L) * 32], su[pt(I, 1, L) * 32], su[pt(I, 2, L) * 32]);
+  const double g2 = dfw<L>(su[pt(I, J, 0) * 32], su[pt(I, J, 1) * 32], su[pt(I, J, 2) * 32]);
+  if constexpr (ISO) {
+    const double f = cf.Wk[0][Q] * c;
+    sF[0] = f * g0;
+    sF[PL] = f * g1;
+    sF[2 * PL] = f * g2;
+  } else {
+    sF[0] = cf.Wk[0][Q] * c * g0;
+    sF[PL] = cf.Wk[1][Q] * c * g1;
+    sF[2 * PL] = cf.Wk[2][Q] * c * g2;
+  }
+}
+
+template <int Q>
+__device__ __forceinline__ void pois_backward(double* __restrict__ sh, int lane) {
+  constexpr int I = Q % 3, J = (Q / 3) % 3, L = Q / 9;
+  const double* sF = sh + PL + lane;
+  double y = dbw<I>(sF[pt(0, J, L) * 32], sF[pt(1, J, L) * 32], sF[pt(2, J, L) * 32]);
+  y = dbw_acc<J>(sF[PL + pt(I, 0, L) * 32], sF[PL + pt(I, 1, L) * 32], sF[PL + pt(I, 2, L) * 32], y);
+  y = dbw_acc<L>(sF[2 * PL + pt(I, J, 0) * 32], sF[2 * PL + pt(I, J, 1) * 32], sF[2 * PL + pt(I, J, 2) * 32], y);
+  sh[Q * 32 + lane] = y;
+}
+
+constexpr int POIS_SMEM = 4 * PL;   // doubles
+
+template <bool ISO>
+__global__ void __launch_bounds__(NT, 2)
+k_q2_poisson64(Grid g, Rows rw, const __grid_constant__ PoisCoef64 cf, const double* __restrict__ u,
+               const double* __restrict__ coef, double* __restrict__ R) {
+  pdl_entry();
+  extern __shared__ double sh[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int I = warp % 3, J = (warp / 3) % 3, L = warp / 9;
+  double un = 0.0, cn = 0.0;
+  auto fetch = [&](int w) {
+    const Seg s = seg_of(g, rw, w);
+    const int ex = s.seg * Q2_SEG + lane;
+    if (lane <= s.last) {
+      const int n = (2 * ex + I) + g.NX * ((2 * s.ey + J) + g.NY * (2 * s.ez + L));
+      un = __ldg(u + n);
+      cn = __ldg(coef + (size_t)(ex + g.nx * (s.ey + g.ny * s.ez)) * 27 + warp);
+    } else {
+      un = 0.0;
+      cn = 0.0;
+    }
+  };
+  int w = blockIdx.x;
+  if (w >= rw.nrows) return;
+  fetch(w);
+  for (; w < rw.nrows; w += gridDim.x) {
+    const Seg s = seg_of(g, rw, w);
+    sh[warp * 32 + lane] = un;
+    const double c = cn;
+    __syncthreads();
+    if (w + (int)gridDim.x < rw.nrows) fetch(w + gridDim.x);
+    switch (warp) {
+#define WB_F(Q) \
+  case Q: pois_forward<ISO, Q>(cf, sh, lane, c); break;
+      WB_Q27(WB_F)
+#undef WB_F
+    }
+    __syncthreads();
+    switch (warp) {
+#define WB_B(Q) \
+  case Q: pois_backward<Q>(sh, lane); break;
+      WB_Q27(WB_B)
+#undef WB_B
+    }
+    __syncthreads();
+    if (warp < 9) {
+      // node x-line jl = warp of the segment: node 2m = point 0 of element m + point 2 of m - 1
+      const double* y0 = sh + 3 * warp * 32;
+      double* row = R + (((size_t)s.seg * g.nz + s.ez) * g.ny + s.ey) * 9 * Q2_ROW_LD + (size_t)warp * Q2_ROW_LD;
+      const int xmax = 2 * s.last + 2;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int X = lane + 32 * k;
+        if (X <= xmax) {
+          const int m = X >> 1;
+          double v;
+          if (X & 1) {
+            v = y0[32 + m];
+          } else {
+            v = m <= s.last ? y0[m] : 0.0;
+            if (m >= 1) v += y0[64 + m - 1];
+          }
+          row[X] = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 int g_nsm = 0;
 
 // Per instantiation: the dynamic shared-memory opt-in and the resident blocks per SM, set once
@@ -358,6 +467,37 @@ cudaError_t launch_one(const Grid& g, const Rows& rw, const Coef64& cf, const do
   return cudaGetLastError();
 }
 
+template <bool ISO>
+int& pois_blocks_per_sm() {
+  static int b = -1;
+  return b;
+}
+
+template <bool ISO>
+cudaError_t prepare_pois() {
+  constexpr size_t smem = sizeof(double) * POIS_SMEM;
+  if (pois_blocks_per_sm<ISO>() > 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_q2_poisson64<ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_q2_poisson64<ISO>, NT, smem)) != cudaSuccess) return e;
+  pois_blocks_per_sm<ISO>() = occ > 0 ? occ : 1;
+  return cudaSuccess;
+}
+
+template <bool ISO>
+cudaError_t launch_pois(const Grid& g, const Rows& rw, const PoisCoef64& cf, const double* u, const double* coef,
+                        double* R, cudaStream_t st) {
+  if (pois_blocks_per_sm<ISO>() < 0) {
+    const cudaError_t e = q2_elem64_prepare();
+    if (e != cudaSuccess) return e;
+  }
+  const long long cap = (long long)g_nsm * pois_blocks_per_sm<ISO>();
+  const unsigned grid = (unsigned)(rw.nrows < cap ? rw.nrows : cap);
+  wb_launch(k_q2_poisson64<ISO>, grid, NT, sizeof(double) * POIS_SMEM, st, g, rw, cf, u, coef, R);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t q2_elem64_prepare() {
@@ -373,7 +513,22 @@ cudaError_t q2_elem64_prepare() {
   if ((e = prepare_one<OP_A | OP_BT | OP_B, true>()) != cudaSuccess) return e;
   if ((e = prepare_one<OP_A | OP_BT | OP_B, false>()) != cudaSuccess) return e;
   if ((e = prepare_one<OP_BT, false>()) != cudaSuccess) return e;
-  return prepare_one<OP_B, false>();
+  if ((e = prepare_one<OP_B, false>()) != cudaSuccess) return e;
+  if ((e = prepare_pois<true>()) != cudaSuccess) return e;
+  return prepare_pois<false>();
+}
+
+cudaError_t launch_q2_poisson64(const Grid& g, const double* u, const double* coef, double* R, cudaStream_t st) {
+  const Rows rw = make_rows(g);
+  if (rw.nrows == 0) return cudaSuccess;
+  const bool iso = g.h[0] == g.h[1] && g.h[1] == g.h[2];
+  const double w1[3] = {1.0 / 3.0, 4.0 / 3.0, 1.0 / 3.0};
+  PoisCoef64 cf;
+  for (int q = 0; q < 27; ++q) {
+    const double W = w1[q % 3] * w1[(q / 3) % 3] * w1[q / 9] * g.detJ;
+    for (int d = 0; d < 3; ++d) cf.Wk[d][q] = W * (0.25 * g.s[d] * g.s[d]);
+  }
+  return iso ? launch_pois<true>(g, rw, cf, u, coef, R, st) : launch_pois<false>(g, rw, cf, u, coef, R, st);
 }
 
 cudaError_t launch_q2_elem64(const Grid& g, int ops, const double* u, const double* p, const double* coef,
