@@ -36,9 +36,23 @@ namespace {
 
 using namespace wb;
 
-constexpr int NW = 27;        // warps per block: one per element point
-constexpr int NT = 32 * NW;
-constexpr int PL = NW * 32;   // doubles per shared plane [q][lane]
+constexpr int NPT = 27;        // element points
+constexpr int NWB = 28;        // warps per block: one per element point and one spare (see kPermA)
+constexpr int NT = 32 * NWB;
+constexpr int PL = NPT * 32;   // doubles per shared plane [q][lane]
+
+// Point of each warp (27: none).  Warp w runs on SMSP w mod 4; the FP64 operations of a point
+// depend on its line positions (2, 1, 2 for a derivative, 2, 2, 2 / 3, 2, 3 for a transposed
+// sum), so the points are spread such that the four SMSPs get equal shares in the forward and
+// backward phases (found by a local search over the per-point operation counts).
+constexpr int kPermA[NWB] = {15, 20, 3, 25, 10, 6, 7, 1, 19, 18, 16, 11, 13, 27,
+                             4, 5, 8, 2, 17, 22, 21, 24, 12, 9, 23, 0, 26, 14};
+constexpr int kPermP[NWB] = {11, 21, 6, 1, 3, 22, 27, 12, 24, 23, 8, 15, 9, 17,
+                             0, 14, 13, 5, 20, 25, 16, 4, 26, 10, 19, 7, 18, 2};
+__constant__ int c_permA[NWB] = {15, 20, 3, 25, 10, 6, 7, 1, 19, 18, 16, 11, 13, 27,
+                                 4, 5, 8, 2, 17, 22, 21, 24, 12, 9, 23, 0, 26, 14};
+__constant__ int c_permP[NWB] = {11, 21, 6, 1, 3, 22, 27, 12, 24, 23, 8, 15, 9, 17,
+                                 0, 14, 13, 5, 20, 25, 16, 4, 26, 10, 19, 7, 18, 2};
 
 struct Coef64 {
   double H[27];    // isotropic: W_q |J| kappa^2; otherwise W_q |J|
@@ -75,14 +89,15 @@ __device__ __forceinline__ double dbw_acc(double s0, double s1, double s2, doubl
   else return fma(3.0, s2, (acc + s1) - s0);
 }
 
-// Shared layout (doubles): velocity / output [3][q][lane], stress [NS][q][lane], weighted
-// divergence [q][lane], divergence x-line sums [2][9][lane], pressure modes [4][lane].
+// Shared layout (doubles): velocity [3][q][lane], output [3][q][lane], stress [NS][q][lane],
+// weighted divergence [q][lane], divergence x-line sums [2][9][lane], pressure modes [4][lane].
 template <int OPS>
 struct Lay {
   static constexpr bool DA = OPS & OP_A, DBT = OPS & OP_BT, DB = OPS & OP_B;
   static constexpr int NS = DA ? 6 : (DBT ? 1 : 0);
   static constexpr int U = 0;
-  static constexpr int S = U + 3 * PL;
+  static constexpr int Y = U + 3 * PL;
+  static constexpr int S = Y + 3 * PL;
   static constexpr int DIV = S + NS * PL;
   static constexpr int RED = DIV + (DB ? PL : 0);
   static constexpr int P = RED + (DB ? 2 * 9 * 32 : 0);
@@ -96,7 +111,7 @@ __device__ __forceinline__ void forward(const Coef64& cf, double* __restrict__ s
   constexpr bool DA = LY::DA, DBT = LY::DBT, DB = LY::DB;
   const double* su = sh + LY::U + lane;
   double* sS = sh + LY::S + Q * 32 + lane;   // this point's entry of stress plane `slot`: sS[slot * PL]
-  auto U = [&](int c, int qq) { return su[(c * NW + qq) * 32]; };
+  auto U = [&](int c, int qq) { return su[(c * NPT + qq) * 32]; };
   // reference derivatives g[c][d] = Dt-sum of component c along axis d (only the diagonal for B)
   double g[3][3];
 #pragma unroll
@@ -155,8 +170,8 @@ __device__ __forceinline__ void backward(const Coef64& cf, double* __restrict__ 
   constexpr int I = Q % 3, J = (Q / 3) % 3, L = Q / 9;
   constexpr bool DA = LY::DA;
   const double* sS = sh + LY::S + lane;
-  double* sy = sh + LY::U + lane;
-  auto S = [&](int s, int qq) { return sS[(s * NW + qq) * 32]; };
+  double* sy = sh + LY::Y + lane;
+  auto S = [&](int s, int qq) { return sS[(s * NPT + qq) * 32]; };
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     double y;
@@ -178,12 +193,12 @@ __device__ __forceinline__ void backward(const Coef64& cf, double* __restrict__ 
       else y = dbw<L>(S(0, pt(I, J, 0)), S(0, pt(I, J, 1)), S(0, pt(I, J, 2)));
       if constexpr (!ISO) y *= cf.kap[c];
     }
-    sy[(c * NW + Q) * 32] = y;
+    sy[(c * NPT + Q) * 32] = y;
   }
 }
 
-#define WB_Q27(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) \
-  X(14) X(15) X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26)
+#define WB_W28(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) \
+  X(14) X(15) X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27)
 
 // Segment index -> first element row and element coordinates.
 struct Seg {
@@ -200,6 +215,66 @@ __device__ __forceinline__ Seg seg_of(const Grid& g, const Rows& rw, int w) {
   return s;
 }
 
+// Node x-lines of a finished segment from the output tile, and B u for its elements.
+template <int OPS>
+__device__ __forceinline__ void finish_seg(const Grid& g, const Seg& s, const double* __restrict__ sh, int warp,
+                                           int lane, double* __restrict__ R, const Epi<double>& pe) {
+  using LY = Lay<OPS>;
+  if ((LY::DA || LY::DBT) && warp < 27) {
+    // warp = (jl, c) owns the node x-line (j, l) of component c
+    const int jl = warp / 3, c = warp - 3 * jl;
+    const double* y0 = sh + LY::Y + (c * NPT + 3 * jl) * 32;   // points 0, 1, 2 of the line
+    double* row = R + ((((size_t)s.seg * g.nz + s.ez) * g.ny + s.ey) * 9 + jl) * 3 * Q2_ROW_LD +
+                  (size_t)c * Q2_ROW_LD;
+    const int xmax = 2 * s.last + 2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int X = lane + 32 * k;
+      if (X <= xmax) {
+        const int m = X >> 1;
+        double v;
+        if (X & 1) {
+          v = y0[32 + m];
+        } else {
+          v = m <= s.last ? y0[m] : 0.0;
+          if (m >= 1) v += y0[64 + m - 1];
+        }
+        row[X] = v;
+      }
+    }
+  }
+  if (LY::DB && warp < 4 && lane <= s.last) {
+    // B u = -sum_q psi_m(q) W_q |J| div u(q); psi = (1, xi, eta, zeta), x-line jl = j + 3 l
+    const double* T = sh + LY::RED + lane;
+    const double* X = T + 9 * 32;
+    double v;
+    if (warp == 0) {
+      v = T[0];
+#pragma unroll
+      for (int jl = 1; jl < 9; ++jl) v += T[jl * 32];
+    } else if (warp == 1) {
+      v = X[0];
+#pragma unroll
+      for (int jl = 1; jl < 9; ++jl) v += X[jl * 32];
+    } else if (warp == 2) {
+      v = T[2 * 32] - T[0];
+#pragma unroll
+      for (int l = 1; l < 3; ++l) v += T[(2 + 3 * l) * 32] - T[(3 * l) * 32];
+    } else {
+      v = T[6 * 32] - T[0];
+#pragma unroll
+      for (int j = 1; j < 3; ++j) v += T[(j + 6) * 32] - T[j * 32];
+    }
+    const int e = s.seg * Q2_SEG + lane + g.nx * (s.ey + g.ny * s.ez);
+    epi_apply(pe, (size_t)e * 4 + warp, 0, -v);
+  }
+}
+
+// Two barriers per segment: [load k | A | forward k, finish k-1 | B | backward k].  Hazards:
+// the velocity tile is written (load k+1) after barrier B of k, when forward k has read it; the
+// stress and divergence are written (forward k+1) after barrier A of k+1, when backward k has read
+// them; the output tile and line sums are written (backward k+1) after barrier B of k+1, when
+// finish k (in the forward phase of k+1) has read them.
 template <int OPS, bool ISO>
 __global__ void __launch_bounds__(NT, 1)
 k_q2_elem64(Grid g, Rows rw, const __grid_constant__ Coef64 cf, const double* __restrict__ u,
@@ -210,15 +285,16 @@ k_q2_elem64(Grid g, Rows rw, const __grid_constant__ Coef64 cf, const double* __
   constexpr bool DA = LY::DA, DBT = LY::DBT, DB = LY::DB, GRAD = DA || DB, SCAT = DA || DBT;
   extern __shared__ double sh[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int I = warp % 3, J = (warp / 3) % 3, L = warp / 9;
+  const int q = c_permA[warp];   // this warp's element point (27: none)
+  const int I = q % 3, J = (q / 3) % 3, L = q / 9;
   const size_t nn = (size_t)g.nn;
 
-  // inputs of one segment for this thread (point `warp` of element `lane`)
+  // inputs of one segment for this thread (point q of element `lane`)
   double un[3] = {0.0, 0.0, 0.0}, mun = 0.0, pn = 0.0;
   auto fetch = [&](int w) {
     const Seg s = seg_of(g, rw, w);
     const int ex = s.seg * Q2_SEG + lane;
-    const bool act = lane <= s.last;
+    const bool act = lane <= s.last && q < NPT;
     const int ix = 2 * ex + I, iy = 2 * s.ey + J, iz = 2 * s.ez + L;
     const int n = ix + g.NX * (iy + g.NY * iz);
     const int e = ex + g.nx * (s.ey + g.ny * s.ez);
@@ -227,38 +303,40 @@ k_q2_elem64(Grid g, Rows rw, const __grid_constant__ Coef64 cf, const double* __
 #pragma unroll
       for (int c = 0; c < 3; ++c) un[c] = live ? __ldg(u + c * nn + n) : 0.0;
     }
-    if (DA) mun = act ? __ldg(coef_nodal ? coef + n : coef + (size_t)e * 27 + warp) : 0.0;
-    if (DBT && warp < 4) pn = act ? __ldg(p + (size_t)e * 4 + warp) : 0.0;
+    if (DA) mun = act ? __ldg(coef_nodal ? coef + n : coef + (size_t)e * 27 + q) : 0.0;
+    if (DBT && warp < 4) pn = lane <= s.last ? __ldg(p + (size_t)e * 4 + warp) : 0.0;
   };
 
   int w = blockIdx.x;
   if (w >= rw.nrows) return;   // whole block
   fetch(w);
+  Seg prev{0, 0, 0, -1};
   for (; w < rw.nrows; w += gridDim.x) {
     const Seg s = seg_of(g, rw, w);
     // load
-    if (GRAD) {
+    if (GRAD && q < NPT) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) sh[LY::U + (c * NW + warp) * 32 + lane] = un[c];
+      for (int c = 0; c < 3; ++c) sh[LY::U + (c * NPT + q) * 32 + lane] = un[c];
     }
     if (DBT && warp < 4) sh[LY::P + warp * 32 + lane] = pn;
     const double mu = mun;
     __syncthreads();
     if (w + (int)gridDim.x < rw.nrows) fetch(w + gridDim.x);
-    // forward
+    // forward k; the previous segment's output goes out meanwhile
     switch (warp) {
-#define WB_F(Q) \
-  case Q: forward<OPS, ISO, Q>(cf, sh, lane, mu); break;
-      WB_Q27(WB_F)
+#define WB_F(W) \
+  case W: if constexpr (kPermA[W] < NPT) forward<OPS, ISO, kPermA[W]>(cf, sh, lane, mu); break;
+      WB_W28(WB_F)
 #undef WB_F
     }
+    if (prev.last >= 0) finish_seg<OPS>(g, prev, sh, warp, lane, R, pe);
     __syncthreads();
     // backward (and, for B, x-line sums of the weighted divergence: T = d0 + d1 + d2, X = d2 - d0)
     if (SCAT) {
       switch (warp) {
-#define WB_B(Q) \
-  case Q: backward<OPS, ISO, Q>(cf, sh, lane); break;
-        WB_Q27(WB_B)
+#define WB_B(W) \
+  case W: if constexpr (kPermA[W] < NPT) backward<OPS, ISO, kPermA[W]>(cf, sh, lane); break;
+        WB_W28(WB_B)
 #undef WB_B
       }
     }
@@ -268,63 +346,16 @@ k_q2_elem64(Grid g, Rows rw, const __grid_constant__ Coef64 cf, const double* __
       sh[LY::RED + warp * 32 + lane] = (d0 + d1) + d2;
       sh[LY::RED + (9 + warp) * 32 + lane] = d2 - d0;
     }
-    __syncthreads();
-    // store: warp = (jl, c) owns the node x-line (j, l) of component c
-    if (SCAT) {
-      const int jl = warp / 3, c = warp - 3 * jl;
-      const double* y0 = sh + LY::U + (c * NW + 3 * jl) * 32;   // points 0, 1, 2 of the line
-      double* row = R + ((((size_t)s.seg * g.nz + s.ez) * g.ny + s.ey) * 9 + jl) * 3 * Q2_ROW_LD +
-                    (size_t)c * Q2_ROW_LD;
-      const int xmax = 2 * s.last + 2;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int X = lane + 32 * k;
-        if (X <= xmax) {
-          const int m = X >> 1;
-          double v;
-          if (X & 1) {
-            v = y0[32 + m];
-          } else {
-            v = m <= s.last ? y0[m] : 0.0;
-            if (m >= 1) v += y0[64 + m - 1];
-          }
-          row[X] = v;
-        }
-      }
-    }
-    if (DB && warp < 4 && lane <= s.last) {
-      // B u = -sum_q psi_m(q) W_q |J| div u(q); psi = (1, xi, eta, zeta), x-line jl = j + 3 l
-      const double* T = sh + LY::RED + lane;
-      const double* X = T + 9 * 32;
-      double v;
-      if (warp == 0) {
-        v = T[0];
-#pragma unroll
-        for (int jl = 1; jl < 9; ++jl) v += T[jl * 32];
-      } else if (warp == 1) {
-        v = X[0];
-#pragma unroll
-        for (int jl = 1; jl < 9; ++jl) v += X[jl * 32];
-      } else if (warp == 2) {
-        v = T[2 * 32] - T[0];
-#pragma unroll
-        for (int l = 1; l < 3; ++l) v += T[(2 + 3 * l) * 32] - T[(3 * l) * 32];
-      } else {
-        v = T[6 * 32] - T[0];
-#pragma unroll
-        for (int j = 1; j < 3; ++j) v += T[(j + 6) * 32] - T[j * 32];
-      }
-      const int e = s.seg * Q2_SEG + lane + g.nx * (s.ey + g.ny * s.ez);
-      epi_apply(pe, (size_t)e * 4 + warp, 0, -v);
-    }
-    __syncthreads();
+    prev = s;
   }
+  __syncthreads();
+  finish_seg<OPS>(g, prev, sh, warp, lane, R, pe);
 }
 
 // Scalar Q2 Poisson element pass (the continuous Q2 level of the two-space pressure cycle, Sec.
 // 6: int c grad u . grad v, c per element point, no Dirichlet rows), same segment and warp
-// layout: y = sum_d Dt^T (W_q |J| kappa_d^2 c g_d), g_d the reference derivative along axis d.
-// Shared: u / output [q][lane], fluxes [3][q][lane].
+// layout and the same two-barrier pipeline: y = sum_d Dt^T (W_q |J| kappa_d^2 c g_d), g_d the
+// reference derivative along axis d.  Shared: u [q][lane], output [q][lane], fluxes [3][q][lane].
 struct PoisCoef64 {
   double Wk[3][27];   // W_q |J| kappa_d^2
 };
@@ -333,7 +364,7 @@ template <bool ISO, int Q>
 __device__ __forceinline__ void pois_forward(const PoisCoef64& cf, double* __restrict__ sh, int lane, double c) {
   constexpr int I = Q % 3, J = (Q / 3) % 3, L = Q / 9;
   const double* su = sh + lane;
-  double* sF = sh + PL + Q * 32 + lane;
+  double* sF = sh + 2 * PL + Q * 32 + lane;
   const double g0 = dfw<I>(su[pt(0, J, L) * 32], su[pt(1, J, L) * 32], su[pt(2, J, L) * 32]);
   const double g1 = dfw<J>(su[pt(I, 0, L) * 32], su[pt(I, 1, L) * 32], su[pt(I, 2, L) * 32]);
   const double g2 = dfw<L>(su[pt(I, J, 0) * 32], su[pt(I, J, 1) * 32], su[pt(I, J, 2) * 32]);
@@ -352,14 +383,38 @@ __device__ __forceinline__ void pois_forward(const PoisCoef64& cf, double* __res
 template <int Q>
 __device__ __forceinline__ void pois_backward(double* __restrict__ sh, int lane) {
   constexpr int I = Q % 3, J = (Q / 3) % 3, L = Q / 9;
-  const double* sF = sh + PL + lane;
+  const double* sF = sh + 2 * PL + lane;
   double y = dbw<I>(sF[pt(0, J, L) * 32], sF[pt(1, J, L) * 32], sF[pt(2, J, L) * 32]);
   y = dbw_acc<J>(sF[PL + pt(I, 0, L) * 32], sF[PL + pt(I, 1, L) * 32], sF[PL + pt(I, 2, L) * 32], y);
   y = dbw_acc<L>(sF[2 * PL + pt(I, J, 0) * 32], sF[2 * PL + pt(I, J, 1) * 32], sF[2 * PL + pt(I, J, 2) * 32], y);
-  sh[Q * 32 + lane] = y;
+  sh[PL + Q * 32 + lane] = y;
 }
 
-constexpr int POIS_SMEM = 4 * PL;   // doubles
+constexpr int POIS_SMEM = 5 * PL;   // doubles
+
+__device__ __forceinline__ void pois_finish(const Grid& g, const Seg& s, const double* __restrict__ sh, int warp,
+                                            int lane, double* __restrict__ R) {
+  if (warp >= 9) return;
+  // node x-line jl = warp of the segment: node 2m = point 0 of element m + point 2 of m - 1
+  const double* y0 = sh + PL + 3 * warp * 32;
+  double* row = R + (((size_t)s.seg * g.nz + s.ez) * g.ny + s.ey) * 9 * Q2_ROW_LD + (size_t)warp * Q2_ROW_LD;
+  const int xmax = 2 * s.last + 2;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int X = lane + 32 * k;
+    if (X <= xmax) {
+      const int m = X >> 1;
+      double v;
+      if (X & 1) {
+        v = y0[32 + m];
+      } else {
+        v = m <= s.last ? y0[m] : 0.0;
+        if (m >= 1) v += y0[64 + m - 1];
+      }
+      row[X] = v;
+    }
+  }
+}
 
 template <bool ISO>
 __global__ void __launch_bounds__(NT, 2)
@@ -368,15 +423,16 @@ k_q2_poisson64(Grid g, Rows rw, const __grid_constant__ PoisCoef64 cf, const dou
   pdl_entry();
   extern __shared__ double sh[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int I = warp % 3, J = (warp / 3) % 3, L = warp / 9;
+  const int q = c_permP[warp];   // this warp's element point (27: none)
+  const int I = q % 3, J = (q / 3) % 3, L = q / 9;
   double un = 0.0, cn = 0.0;
   auto fetch = [&](int w) {
     const Seg s = seg_of(g, rw, w);
     const int ex = s.seg * Q2_SEG + lane;
-    if (lane <= s.last) {
+    if (lane <= s.last && q < NPT) {
       const int n = (2 * ex + I) + g.NX * ((2 * s.ey + J) + g.NY * (2 * s.ez + L));
       un = __ldg(u + n);
-      cn = __ldg(coef + (size_t)(ex + g.nx * (s.ey + g.ny * s.ez)) * 27 + warp);
+      cn = __ldg(coef + (size_t)(ex + g.nx * (s.ey + g.ny * s.ez)) * 27 + q);
     } else {
       un = 0.0;
       cn = 0.0;
@@ -385,49 +441,31 @@ k_q2_poisson64(Grid g, Rows rw, const __grid_constant__ PoisCoef64 cf, const dou
   int w = blockIdx.x;
   if (w >= rw.nrows) return;
   fetch(w);
+  Seg prev{0, 0, 0, -1};
   for (; w < rw.nrows; w += gridDim.x) {
     const Seg s = seg_of(g, rw, w);
-    sh[warp * 32 + lane] = un;
+    if (q < NPT) sh[q * 32 + lane] = un;
     const double c = cn;
     __syncthreads();
     if (w + (int)gridDim.x < rw.nrows) fetch(w + gridDim.x);
     switch (warp) {
-#define WB_F(Q) \
-  case Q: pois_forward<ISO, Q>(cf, sh, lane, c); break;
-      WB_Q27(WB_F)
+#define WB_F(W) \
+  case W: if constexpr (kPermP[W] < NPT) pois_forward<ISO, kPermP[W]>(cf, sh, lane, c); break;
+      WB_W28(WB_F)
 #undef WB_F
     }
+    if (prev.last >= 0) pois_finish(g, prev, sh, warp, lane, R);
     __syncthreads();
     switch (warp) {
-#define WB_B(Q) \
-  case Q: pois_backward<Q>(sh, lane); break;
-      WB_Q27(WB_B)
+#define WB_B(W) \
+  case W: if constexpr (kPermP[W] < NPT) pois_backward<kPermP[W]>(sh, lane); break;
+      WB_W28(WB_B)
 #undef WB_B
     }
-    __syncthreads();
-    if (warp < 9) {
-      // node x-line jl = warp of the segment: node 2m = point 0 of element m + point 2 of m - 1
-      const double* y0 = sh + 3 * warp * 32;
-      double* row = R + (((size_t)s.seg * g.nz + s.ez) * g.ny + s.ey) * 9 * Q2_ROW_LD + (size_t)warp * Q2_ROW_LD;
-      const int xmax = 2 * s.last + 2;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int X = lane + 32 * k;
-        if (X <= xmax) {
-          const int m = X >> 1;
-          double v;
-          if (X & 1) {
-            v = y0[32 + m];
-          } else {
-            v = m <= s.last ? y0[m] : 0.0;
-            if (m >= 1) v += y0[64 + m - 1];
-          }
-          row[X] = v;
-        }
-      }
-    }
-    __syncthreads();
+    prev = s;
   }
+  __syncthreads();
+  pois_finish(g, prev, sh, warp, lane, R);
 }
 
 int g_nsm = 0;
