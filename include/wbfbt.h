@@ -64,12 +64,14 @@ typedef struct {
     int precision;                 /* WBFBT_F64 or WBFBT_MIXED                              */
     int schur_sign;                /* -1 (default): [A B^T; 0 -S~]; +1: printed block      */
     int use_graphs;                /* 1 (default): replay the preconditioner as a CUDA graph */
-    int elem_kernels;              /* single-precision k = 2 element kernels (no counterpart in
-                                      the paper; the results agree to FP32 rounding):
-                                      WBFBT_ELEM_AUTO (default) one thread per element for
-                                      levels of >= 20000 elements, else one thread per point;
-                                      WBFBT_ELEM_POINT / WBFBT_ELEM_ROW force either (and
-                                      the three- or one-pass k = 2 restriction)             */
+    int elem_kernels;              /* k = 2 element kernels (no counterpart in the paper;
+                                      the results agree to rounding):
+                                      WBFBT_ELEM_AUTO (default) row-segment kernels (FP32:
+                                      a thread per element, FP64: a warp per element
+                                      point) on levels of >= 20000 elements, else one
+                                      thread per point; WBFBT_ELEM_POINT / WBFBT_ELEM_ROW
+                                      force either (and the three- or one-pass k = 2
+                                      restriction)                                          */
 } wbfbt_opts;
 
 #define WBFBT_ELEM_AUTO 0

@@ -17,7 +17,7 @@ from . import build as _build
 
 F64, F32 = 0, 1
 MIXED = 1
-ELEM_AUTO, ELEM_POINT, ELEM_ROW = 0, 1, 2   # single-precision k = 2 element kernels
+ELEM_AUTO, ELEM_POINT, ELEM_ROW = 0, 1, 2   # k = 2 element kernels: by level size, per point, row segments
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "non-finite value", -4: "Krylov breakdown",
           -5: "iteration limit reached", -6: "setup failed"}
 

@@ -334,6 +334,35 @@ def test_full_size_64cubed_sampled_A_apply_fp32(wb):
     assert err < 2e-5
 
 
+def test_full_size_64cubed_sampled_K_apply_fp64(wb):
+    """64^3 Q2 DR 1e10 in FP64 (the largest configuration, row-segment FP64 passes with two
+    segments along x): the fused K apply (A + B^T, B) at sampled nodes and elements."""
+    cfg = inputs.WORKLOADS["64^3-Q2-S64-DR1e10"]
+    n, k = cfg["n"], cfg["k"]
+    c = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
+    mu_g, _ = wb.sinker_setup(n, k, c, cfg["omega"], cfg["delta"], cfg["dr"])
+    s = wb.Solver(n, k, mu_g, restart=5)
+    m = M.Mesh(n, n, n, k)
+    mu = N(mu_g)
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal(m.n_u)
+    y = N(s.apply_A(T(u))).reshape(3, -1)
+    nodes = np.concatenate([rng.choice(m.n_nodes, 150, replace=False),
+                            64 + m.NX * rng.integers(1, m.NY - 1, 50) + m.NX * m.NY * rng.integers(1, m.NZ - 1, 50)])
+    ref = op.sampled_apply_A(m, mu, u, nodes)
+    err = np.abs(y[:, nodes].T - ref).max() / np.abs(ref).max()
+    assert err < 1e-12
+    # B on sampled elements: the element divergence matrix on the element's masked velocity
+    yp = N(s.apply_B(T(u))).reshape(m.n_elem, m.Np)
+    Be = op.element_B(m)
+    bmask = m.boundary_node_mask()
+    ids_all = m.point_to_node()
+    elems = rng.choice(m.n_elem, 100, replace=False)
+    refp = np.stack([Be @ np.concatenate([u[cc * m.n_nodes + ids_all[e]] * (~bmask[ids_all[e]]) for cc in range(3)])
+                     for e in elems])
+    assert np.abs(yp[elems] - refp).max() / np.abs(refp).max() < 1e-12
+
+
 def test_q3_dr1e8_mixed_solve_matches_fp64(wb):
     """24^3 Q3, 32 sinkers, DR 1e8 (the mixed-precision configuration): mixed vs FP64 GPU solve."""
     cfg = inputs.WORKLOADS["24^3-Q3-S32-DR1e8"]
