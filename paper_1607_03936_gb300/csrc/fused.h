@@ -155,6 +155,11 @@ cudaError_t launch_q2_elem64(const Grid& g, int ops, const double* u, const doub
                              int coef_nodal, double* R, const Epi<double>& pe, cudaStream_t st);
 // The FP64 scalar Poisson pass in the same layout (q2_fp64.cu, warp per element point).
 cudaError_t launch_q2_poisson64(const Grid& g, const double* u, const double* coef, double* R, cudaStream_t st);
+// Flat FP64 variants (q2_fp64.cu) for k = 2 levels below the row-segment size: 32 consecutive
+// elements per block in linear order, element-major scratch (A: [E][3][27], Poisson [E][27]).
+cudaError_t launch_q2_elem64_flat(const Grid& g, const double* u, const double* coef, int coef_nodal, double* Ye,
+                                  cudaStream_t st);
+cudaError_t launch_q2_poisson64_flat(const Grid& g, const double* u, const double* coef, double* Ye, cudaStream_t st);
 // One-time launch set-up of the q2_fp64.cu passes (shared-memory opt-in, occupancy); call it
 // outside any stream capture.
 cudaError_t q2_elem64_prepare();

@@ -559,6 +559,14 @@ bool row_path_vector(const Grid& g, int k) {
   return k == 2 && g.rowk;
 }
 
+// Below the row-segment size, FP64 k = 2 levels of at least 2048 elements take the flat
+// warp-per-point passes (q2_fp64.cu, element-major scratch) unless the option asks for the
+// per-point kernels; smaller levels keep the per-point kernels (more blocks than SMs).
+template <typename T>
+bool flat_path(const Grid& g, int k) {
+  return std::is_same<T, double>::value && k == 2 && !g.rowk && g.kern != 1 && g.ne >= 2048;
+}
+
 template <typename T>
 size_t elem_scratch_size(const Grid& g, int k) {
   const size_t n = (size_t)(k + 1);
@@ -576,6 +584,9 @@ cudaError_t launch_elem_stokes(const Grid& g, int k, const void* otab, int ops, 
     if constexpr (std::is_same<T, float>::value) return launch_q2_elem(g, ops, u, p, coef, cn, Ye, pe, st);
     else return launch_q2_elem64(g, ops, u, p, coef, cn, Ye, pe, st);
   }
+  if constexpr (std::is_same<T, double>::value) {
+    if (flat_path<T>(g, k) && ops == OP_A && us == nullptr) return launch_q2_elem64_flat(g, u, coef, cn, Ye, st);
+  }
   WB_FUSED_DISPATCH(k, (run_elem<T, N>(g, otab, ops, u, us, p, coef, cn, Ye, pe, st)));
 }
 
@@ -585,6 +596,9 @@ cudaError_t launch_elem_poisson(const Grid& g, int k, const void* otab, const T*
   if (row_path_scalar<T>(g, k)) {
     if constexpr (std::is_same<T, double>::value) return launch_q2_poisson64(g, u, coef, Ye, st);
     else return launch_q2_poisson<T>(g, u, coef, Ye, st);
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    if (flat_path<T>(g, k)) return launch_q2_poisson64_flat(g, u, coef, Ye, st);
   }
   WB_FUSED_DISPATCH(k, ((wb_launch(k_elem_poisson<T, N>, elem_blocks(g.ne, Cfg<N>::EPB), Cfg<N>::THREADS, 0, st, g, WB_TAB(T), u, coef, Ye)),
                         cudaGetLastError()));

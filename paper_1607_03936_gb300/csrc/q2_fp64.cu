@@ -91,22 +91,22 @@ __device__ __forceinline__ double dbw_acc(double s0, double s1, double s2, doubl
 
 // Shared layout (doubles): velocity [3][q][lane], output [3][q][lane], stress [NS][q][lane],
 // weighted divergence [q][lane], divergence x-line sums [2][9][lane], pressure modes [4][lane].
-template <int OPS>
+template <int OPS, int YLD = 32>
 struct Lay {
   static constexpr bool DA = OPS & OP_A, DBT = OPS & OP_BT, DB = OPS & OP_B;
   static constexpr int NS = DA ? 6 : (DBT ? 1 : 0);
   static constexpr int U = 0;
-  static constexpr int Y = U + 3 * PL;
-  static constexpr int S = Y + 3 * PL;
+  static constexpr int Y = U + 3 * PL;   // output [c][q][YLD] (YLD 33: padded for transposed reads)
+  static constexpr int S = Y + 3 * NPT * YLD;
   static constexpr int DIV = S + NS * PL;
   static constexpr int RED = DIV + (DB ? PL : 0);
   static constexpr int P = RED + (DB ? 2 * 9 * 32 : 0);
   static constexpr int TOTAL = P + (DBT ? 4 * 32 : 0);
 };
 
-template <int OPS, bool ISO, int Q>
+template <int OPS, bool ISO, int Q, int YLD = 32>
 __device__ __forceinline__ void forward(const Coef64& cf, double* __restrict__ sh, int lane, double mu) {
-  using LY = Lay<OPS>;
+  using LY = Lay<OPS, YLD>;
   constexpr int I = Q % 3, J = (Q / 3) % 3, L = Q / 9;
   constexpr bool DA = LY::DA, DBT = LY::DBT, DB = LY::DB;
   const double* su = sh + LY::U + lane;
@@ -164,9 +164,9 @@ __device__ __forceinline__ void forward(const Coef64& cf, double* __restrict__ s
   }
 }
 
-template <int OPS, bool ISO, int Q>
+template <int OPS, bool ISO, int Q, int YLD = 32>
 __device__ __forceinline__ void backward(const Coef64& cf, double* __restrict__ sh, int lane) {
-  using LY = Lay<OPS>;
+  using LY = Lay<OPS, YLD>;
   constexpr int I = Q % 3, J = (Q / 3) % 3, L = Q / 9;
   constexpr bool DA = LY::DA;
   const double* sS = sh + LY::S + lane;
@@ -193,7 +193,7 @@ __device__ __forceinline__ void backward(const Coef64& cf, double* __restrict__ 
       else y = dbw<L>(S(0, pt(I, J, 0)), S(0, pt(I, J, 1)), S(0, pt(I, J, 2)));
       if constexpr (!ISO) y *= cf.kap[c];
     }
-    sy[(c * NPT + Q) * 32] = y;
+    sy[(c * NPT + Q) * YLD] = y;
   }
 }
 
@@ -360,11 +360,15 @@ struct PoisCoef64 {
   double Wk[3][27];   // W_q |J| kappa_d^2
 };
 
-template <bool ISO, int Q>
+// Poisson shared layout (doubles): u [q][32], output [q][YLD], fluxes [3][q][32] from pois_F.
+template <int YLD>
+__host__ __device__ constexpr int pois_F() { return PL + NPT * YLD; }
+
+template <bool ISO, int Q, int YLD = 32>
 __device__ __forceinline__ void pois_forward(const PoisCoef64& cf, double* __restrict__ sh, int lane, double c) {
   constexpr int I = Q % 3, J = (Q / 3) % 3, L = Q / 9;
   const double* su = sh + lane;
-  double* sF = sh + 2 * PL + Q * 32 + lane;
+  double* sF = sh + pois_F<YLD>() + Q * 32 + lane;
   const double g0 = dfw<I>(su[pt(0, J, L) * 32], su[pt(1, J, L) * 32], su[pt(2, J, L) * 32]);
   const double g1 = dfw<J>(su[pt(I, 0, L) * 32], su[pt(I, 1, L) * 32], su[pt(I, 2, L) * 32]);
   const double g2 = dfw<L>(su[pt(I, J, 0) * 32], su[pt(I, J, 1) * 32], su[pt(I, J, 2) * 32]);
@@ -380,17 +384,18 @@ __device__ __forceinline__ void pois_forward(const PoisCoef64& cf, double* __res
   }
 }
 
-template <int Q>
+template <int Q, int YLD = 32>
 __device__ __forceinline__ void pois_backward(double* __restrict__ sh, int lane) {
   constexpr int I = Q % 3, J = (Q / 3) % 3, L = Q / 9;
-  const double* sF = sh + 2 * PL + lane;
+  const double* sF = sh + pois_F<YLD>() + lane;
   double y = dbw<I>(sF[pt(0, J, L) * 32], sF[pt(1, J, L) * 32], sF[pt(2, J, L) * 32]);
   y = dbw_acc<J>(sF[PL + pt(I, 0, L) * 32], sF[PL + pt(I, 1, L) * 32], sF[PL + pt(I, 2, L) * 32], y);
   y = dbw_acc<L>(sF[2 * PL + pt(I, J, 0) * 32], sF[2 * PL + pt(I, J, 1) * 32], sF[2 * PL + pt(I, J, 2) * 32], y);
-  sh[PL + Q * 32 + lane] = y;
+  sh[PL + Q * YLD + lane] = y;
 }
 
-constexpr int POIS_SMEM = 5 * PL;   // doubles
+constexpr int POIS_SMEM = 5 * PL;                       // doubles, row kernel
+constexpr int POIS_SMEM_FLAT = pois_F<33>() + 3 * PL;   // doubles, flat kernel
 
 __device__ __forceinline__ void pois_finish(const Grid& g, const Seg& s, const double* __restrict__ sh, int warp,
                                             int lane, double* __restrict__ R) {
@@ -468,6 +473,133 @@ k_q2_poisson64(Grid g, Rows rw, const __grid_constant__ PoisCoef64 cf, const dou
   pois_finish(g, prev, sh, warp, lane, R);
 }
 
+// ---- Flat variants for levels below the row-segment size (k = 2, FP64): block w owns the 32
+// consecutive elements 32 w .. 32 w + 31 in linear order (lane = element), so short rows still
+// fill the warps; the output goes to the element-major scratch [E][ncomp][27] of the per-point
+// kernels (read by their node pass), written through the padded tile [c][q][33] so that the
+// transposed reads are nearly free of bank conflicts.  A only (coarse levels apply nothing else).
+constexpr int FLAT_YLD = 33;
+
+template <bool ISO>
+__global__ void __launch_bounds__(NT, 1)
+k_q2_elem64_flat(Grid g, int nblk, const __grid_constant__ Coef64 cf, const double* __restrict__ u,
+                 const double* __restrict__ coef, int coef_nodal, double* __restrict__ Ye) {
+  pdl_entry();
+  using LY = Lay<OP_A, FLAT_YLD>;
+  extern __shared__ double sh[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = c_permA[warp];
+  const int I = q % 3, J = (q / 3) % 3, L = q / 9;
+  const size_t nn = (size_t)g.nn;
+  double un[3] = {0.0, 0.0, 0.0}, mun = 0.0;
+  auto fetch = [&](int w) {
+    const int e = w * 32 + lane;
+    const bool act = e < g.ne && q < NPT;
+    const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
+    const int ix = 2 * ex + I, iy = 2 * ey + J, iz = 2 * ez + L;
+    const int n = ix + g.NX * (iy + g.NY * iz);
+    const bool live = act && !on_boundary(g, ix, iy, iz);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) un[c] = live ? __ldg(u + c * nn + n) : 0.0;
+    mun = act ? __ldg(coef_nodal ? coef + n : coef + (size_t)e * 27 + q) : 0.0;
+  };
+  // element-major store of a finished block of elements from the output tile
+  auto finish = [&](int w) {
+    const int e0 = w * 32, cnt = min(32, g.ne - e0);
+    for (int t = threadIdx.x; t < cnt * 81; t += NT) {
+      const int el = t / 81, r = t - 81 * el, c = r / 27, qq = r - 27 * c;
+      Ye[(size_t)e0 * 81 + t] = sh[LY::Y + (c * NPT + qq) * FLAT_YLD + el];
+    }
+  };
+  int w = blockIdx.x;
+  if (w >= nblk) return;
+  fetch(w);
+  int prev = -1;
+  for (; w < nblk; w += gridDim.x) {
+    if (q < NPT) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sh[LY::U + (c * NPT + q) * 32 + lane] = un[c];
+    }
+    const double mu = mun;
+    __syncthreads();
+    if (w + (int)gridDim.x < nblk) fetch(w + gridDim.x);
+    switch (warp) {
+#define WB_F(W) \
+  case W: if constexpr (kPermA[W] < NPT) forward<OP_A, ISO, kPermA[W], FLAT_YLD>(cf, sh, lane, mu); break;
+      WB_W28(WB_F)
+#undef WB_F
+    }
+    if (prev >= 0) finish(prev);
+    __syncthreads();
+    switch (warp) {
+#define WB_B(W) \
+  case W: if constexpr (kPermA[W] < NPT) backward<OP_A, ISO, kPermA[W], FLAT_YLD>(cf, sh, lane); break;
+      WB_W28(WB_B)
+#undef WB_B
+    }
+    prev = w;
+  }
+  __syncthreads();
+  finish(prev);
+}
+
+template <bool ISO>
+__global__ void __launch_bounds__(NT, 2)
+k_q2_poisson64_flat(Grid g, int nblk, const __grid_constant__ PoisCoef64 cf, const double* __restrict__ u,
+                    const double* __restrict__ coef, double* __restrict__ Ye) {
+  pdl_entry();
+  extern __shared__ double sh[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = c_permP[warp];
+  const int I = q % 3, J = (q / 3) % 3, L = q / 9;
+  double un = 0.0, cn = 0.0;
+  auto fetch = [&](int w) {
+    const int e = w * 32 + lane;
+    if (e < g.ne && q < NPT) {
+      const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
+      un = __ldg(u + (2 * ex + I) + g.NX * ((2 * ey + J) + g.NY * (2 * ez + L)));
+      cn = __ldg(coef + (size_t)e * 27 + q);
+    } else {
+      un = 0.0;
+      cn = 0.0;
+    }
+  };
+  auto finish = [&](int w) {
+    const int e0 = w * 32, cnt = min(32, g.ne - e0);
+    for (int t = threadIdx.x; t < cnt * 27; t += NT) {
+      const int el = t / 27, qq = t - 27 * el;
+      Ye[(size_t)e0 * 27 + t] = sh[PL + qq * FLAT_YLD + el];
+    }
+  };
+  int w = blockIdx.x;
+  if (w >= nblk) return;
+  fetch(w);
+  int prev = -1;
+  for (; w < nblk; w += gridDim.x) {
+    if (q < NPT) sh[q * 32 + lane] = un;
+    const double c = cn;
+    __syncthreads();
+    if (w + (int)gridDim.x < nblk) fetch(w + gridDim.x);
+    switch (warp) {
+#define WB_F(W) \
+  case W: if constexpr (kPermP[W] < NPT) pois_forward<ISO, kPermP[W], FLAT_YLD>(cf, sh, lane, c); break;
+      WB_W28(WB_F)
+#undef WB_F
+    }
+    if (prev >= 0) finish(prev);
+    __syncthreads();
+    switch (warp) {
+#define WB_B(W) \
+  case W: if constexpr (kPermP[W] < NPT) pois_backward<kPermP[W], FLAT_YLD>(sh, lane); break;
+      WB_W28(WB_B)
+#undef WB_B
+    }
+    prev = w;
+  }
+  __syncthreads();
+  finish(prev);
+}
+
 int g_nsm = 0;
 
 // Per instantiation: the dynamic shared-memory opt-in and the resident blocks per SM, set once
@@ -536,7 +668,84 @@ cudaError_t launch_pois(const Grid& g, const Rows& rw, const PoisCoef64& cf, con
   return cudaGetLastError();
 }
 
+template <typename K>
+cudaError_t prepare_kernel(K kernel, size_t smem, int& bps) {
+  if (bps > 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, NT, smem)) != cudaSuccess) return e;
+  bps = occ > 0 ? occ : 1;
+  return cudaSuccess;
+}
+
+int g_flat_bps[2][2] = {{-1, -1}, {-1, -1}};   // [pass: 0 A, 1 Poisson][ISO]
+constexpr size_t FLAT_A_SMEM = sizeof(double) * Lay<OP_A, FLAT_YLD>::TOTAL;
+constexpr size_t FLAT_P_SMEM = sizeof(double) * POIS_SMEM_FLAT;
+
+cudaError_t prepare_flat() {
+  cudaError_t e;
+  if ((e = prepare_kernel(k_q2_elem64_flat<false>, FLAT_A_SMEM, g_flat_bps[0][0])) != cudaSuccess) return e;
+  if ((e = prepare_kernel(k_q2_elem64_flat<true>, FLAT_A_SMEM, g_flat_bps[0][1])) != cudaSuccess) return e;
+  if ((e = prepare_kernel(k_q2_poisson64_flat<false>, FLAT_P_SMEM, g_flat_bps[1][0])) != cudaSuccess) return e;
+  return prepare_kernel(k_q2_poisson64_flat<true>, FLAT_P_SMEM, g_flat_bps[1][1]);
+}
+
+unsigned flat_grid(int nblk, int bps) {
+  const long long cap = (long long)g_nsm * bps;
+  return (unsigned)(nblk < cap ? nblk : cap);
+}
+
 }  // namespace
+
+cudaError_t launch_q2_elem64_flat(const Grid& g, const double* u, const double* coef, int coef_nodal, double* Ye,
+                                  cudaStream_t st) {
+  const int nblk = (g.ne + 31) / 32;
+  if (nblk == 0) return cudaSuccess;
+  if (g_flat_bps[0][0] < 0) {
+    const cudaError_t e = q2_elem64_prepare();
+    if (e != cudaSuccess) return e;
+  }
+  const bool iso = g.h[0] == g.h[1] && g.h[1] == g.h[2];
+  const double w1[3] = {1.0 / 3.0, 4.0 / 3.0, 1.0 / 3.0};
+  Coef64 cf;
+  for (int d = 0; d < 3; ++d) cf.kap[d] = 0.5 * g.s[d];
+  for (int q = 0; q < 27; ++q) {
+    const double W = w1[q % 3] * w1[(q / 3) % 3] * w1[q / 9] * g.detJ;
+    cf.H[q] = iso ? W * cf.kap[0] * cf.kap[0] : W;
+    cf.T[q] = iso ? W * cf.kap[0] : W;
+  }
+  if (iso)
+    wb_launch(k_q2_elem64_flat<true>, flat_grid(nblk, g_flat_bps[0][1]), NT, FLAT_A_SMEM, st, g, nblk, cf, u, coef,
+              coef_nodal, Ye);
+  else
+    wb_launch(k_q2_elem64_flat<false>, flat_grid(nblk, g_flat_bps[0][0]), NT, FLAT_A_SMEM, st, g, nblk, cf, u, coef,
+              coef_nodal, Ye);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q2_poisson64_flat(const Grid& g, const double* u, const double* coef, double* Ye, cudaStream_t st) {
+  const int nblk = (g.ne + 31) / 32;
+  if (nblk == 0) return cudaSuccess;
+  if (g_flat_bps[1][0] < 0) {
+    const cudaError_t e = q2_elem64_prepare();
+    if (e != cudaSuccess) return e;
+  }
+  const bool iso = g.h[0] == g.h[1] && g.h[1] == g.h[2];
+  const double w1[3] = {1.0 / 3.0, 4.0 / 3.0, 1.0 / 3.0};
+  PoisCoef64 cf;
+  for (int q = 0; q < 27; ++q) {
+    const double W = w1[q % 3] * w1[(q / 3) % 3] * w1[q / 9] * g.detJ;
+    for (int d = 0; d < 3; ++d) cf.Wk[d][q] = W * (0.25 * g.s[d] * g.s[d]);
+  }
+  if (iso)
+    wb_launch(k_q2_poisson64_flat<true>, flat_grid(nblk, g_flat_bps[1][1]), NT, FLAT_P_SMEM, st, g, nblk, cf, u, coef,
+              Ye);
+  else
+    wb_launch(k_q2_poisson64_flat<false>, flat_grid(nblk, g_flat_bps[1][0]), NT, FLAT_P_SMEM, st, g, nblk, cf, u,
+              coef, Ye);
+  return cudaGetLastError();
+}
 
 cudaError_t q2_elem64_prepare() {
   if (g_nsm == 0) {
@@ -553,7 +762,8 @@ cudaError_t q2_elem64_prepare() {
   if ((e = prepare_one<OP_BT, false>()) != cudaSuccess) return e;
   if ((e = prepare_one<OP_B, false>()) != cudaSuccess) return e;
   if ((e = prepare_pois<true>()) != cudaSuccess) return e;
-  return prepare_pois<false>();
+  if ((e = prepare_pois<false>()) != cudaSuccess) return e;
+  return prepare_flat();
 }
 
 cudaError_t launch_q2_poisson64(const Grid& g, const double* u, const double* coef, double* R, cudaStream_t st) {

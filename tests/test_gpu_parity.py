@@ -209,6 +209,28 @@ def test_pressure_poisson_vcycle_fp64(wb, which, kern):
     assert rel(N(s.apply_Kinv(which, T(b))), pp.apply(b)) < 1e-10
 
 
+@pytest.mark.parametrize("lengths", [(1.0, 0.5, 1.0), (1.0, 1.0, 1.0)])
+def test_flat_fp64_passes(wb, lengths):
+    """A fine level of 2048 elements (16 x 8 x 16) takes the flat FP64 passes (32 consecutive
+    elements per block, element-major scratch) for A and the Q2 Poisson level; isotropic
+    (h = 1/16) and anisotropic meshes; A, the A V-cycle and both pressure-Poisson V-cycles."""
+    m, mu, _, _ = problem(16, 8, 16, 2, dr=1e4, lengths=lengths)
+    s = gpu_solver(wb, m, mu, a_r=2.0)
+    rng = np.random.default_rng(13)
+    u = rng.standard_normal(m.n_u)
+    A = op.assemble_A(m, op.point_values(m, mu))
+    assert rel(N(s.apply_A(T(u))), A @ u) < 1e-12
+    levels = mg.build_hierarchy(m, op.point_values(m, mu), vector=True)
+    b = u * m.interior_dof_mask()
+    assert rel(N(s.apply_Ainv(T(b))), mg.vcycle(levels, b)) < 1e-10
+    prob = W.StokesProblem(m, mu, a_l=1.0, a_r=2.0)
+    for which in (0, 1):
+        pp = mg.PressurePoissonMG(m, prob.B, prob.Cdiag if which == 0 else prob.Ddiag, mu,
+                                  1.0 if which == 0 else 2.0)
+        bp = op.project_pressure(m, rng.standard_normal(m.n_p))
+        assert rel(N(s.apply_Kinv(which, T(bp))), pp.apply(bp)) < 1e-10
+
+
 def test_schur_inverse_and_block_preconditioner_fp64(wb):
     m, mu, _, _ = problem(8, 8, 8, 2, dr=1e4)
     s = gpu_solver(wb, m, mu)
