@@ -1,32 +1,37 @@
-// Q2 (k = 2) double-precision Stokes-family element pass: one warp per element point, one lane
-// per element.
+// Q2 (k = 2) double-precision element passes: one warp per element point, one lane per element.
 //
 // A block owns a row segment of up to 32 consecutive elements along x (fixed ey, ez) -- the
 // segments and row-scratch layout of the single-precision row kernels, so the node pass
-// (launch_q2_gather) is shared -- and has 27 warps, one per GLL point of the element: lane e of
-// warp q works on point q of element e of the segment.  The operators are those of Sec. 1.2:
-// a(u, v) = int 2 mu eps(u) : eps(v), b(v, q) = -int q div v, by GLL quadrature at the nodes.
+// (launch_q2_gather) is shared -- and has 28 warps: one per GLL point of the element (lane e of
+// the warp of point q works on point q of element e of the segment) and one spare.  The
+// operators are those of Sec. 1.2, a(u, v) = int 2 mu eps(u) : eps(v) and b(v, q) = -int q div v,
+// and the scalar Poisson operator int c grad u . grad v of the two-space pressure cycle (Sec. 6),
+// all by GLL quadrature at the nodes.
 //
 // Why this shape.  The FP64 pipe of GB300 retires 2 operations per clock and SM, so the FP64
-// pass is bound by its operation count and by how full its warps are.  Every warp here is full
-// (27 x 32 threads per segment), and because a warp's point is fixed, each 1-D derivative sum is
-// a constant expression: on the Q2 GLL nodes (-1, 0, 1) the derivative matrix is D = Dt / 2 with
+// passes are bound by their operation count and by how full their warps are.  Every warp here is
+// full, and because a warp's point is fixed, each 1-D derivative sum is a constant expression: on
+// the Q2 GLL nodes (-1, 0, 1) the derivative matrix is D = Dt / 2 with
 //   Dt = [[-3, 4, -1], [-1, 0, 1], [1, -4, 3]]   (row: point, column: basis function),
 // so a derivative at a line position costs 2, 1 or 2 operations instead of 3 FMAs, and a
 // transposed sum 2 or 3.  On an isotropic mesh (h equal on all axes) the scale kappa = 1/h (the
 // physical derivative is kappa Dt) folds into the point weights; otherwise the transposed sums are
-// scaled per axis.
+// scaled per axis.  The points are spread over the warps so that the four SMSPs get equal FP64
+// work (kPermA, kPermP).
 //
-// Phases per segment, with a barrier after each:
+// Phases per segment k, two barriers each ([load k | A | forward k, finish k-1 | B | backward k]):
 //   load      nodal velocity (Dirichlet nodes as zero) from registers into shared [c][q][lane],
 //             then the next segment's inputs are requested into registers (software prefetch);
 //   forward   the reference derivatives at the warp's point, the weighted stress into shared
 //             [slot][q][lane] and, for B, the weighted divergence;
 //   backward  y_c at the warp's point, sum over axes d of the transposed derivative sums of the
-//             stress S_cd, into shared [c][q][lane]; for B, the divergence summed along x-lines;
-//   store     one warp per node x-line (l, j, c) of the segment writes its 65 partial node values
-//             (node 2m: point 0 of element m plus point 2 of element m - 1; node 2m + 1: point 1
-//             of element m), coalesced; for B four warps finish B u per pressure mode.
+//             stress S_cd, into the output tile [c][q][lane]; for B, the divergence summed along
+//             x-lines;
+//   finish    (during the next segment's forward phase) one warp per node x-line (l, j, c) of the
+//             segment writes its 65 partial node values (node 2m: point 0 of element m plus point
+//             2 of element m - 1; node 2m + 1: point 1 of element m), coalesced; for B four warps
+//             finish B u per pressure mode.
+// The flat variants at the end serve levels whose rows are too short for full warps.
 #include "elem_common.cuh"
 #include "epi.cuh"
 #include "fused.h"

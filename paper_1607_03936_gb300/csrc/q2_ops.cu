@@ -1,4 +1,6 @@
-// Q2 (k = 2) single-precision operator kernels: one thread per element, warps along element rows.
+// Q2 (k = 2) row-segment kernels with one thread per element (warps along element rows): the
+// single-precision operator passes, and in both precisions the pressure transfers of the
+// two-space cycle and the node pass that all row-segment producers share.
 //
 // Element pass: a warp owns a row segment of up to 32 consecutive elements along x (fixed ey,
 // ez), one thread per element.  The thread loads its element's 27 nodal values per component
@@ -473,8 +475,8 @@ cudaError_t launch_q2_c2d(const Grid& g, const T* ec, T* ed, int add, cudaStream
   return cudaGetLastError();
 }
 
+template cudaError_t launch_q2_poisson<float>(const Grid&, const float*, const float*, float*, cudaStream_t);
 #define WB_Q2_INST(T)                                                                                        \
-  template cudaError_t launch_q2_poisson<T>(const Grid&, const T*, const T*, T*, cudaStream_t);             \
   template cudaError_t launch_q2_gather<T>(const Grid&, int, int, const T*, const Epi<T>&, cudaStream_t);  \
   template cudaError_t launch_q2_d2c<T>(const Grid&, const T*, T*, T*, cudaStream_t);                       \
   template cudaError_t launch_q2_c2d<T>(const Grid&, const T*, T*, int, cudaStream_t);
