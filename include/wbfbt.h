@@ -223,6 +223,24 @@ int wbfbt_attach_net(wbfbt_ctx* ctx, wbfbt_net* net, int which_mask, double acce
 int wbfbt_learned_sample(wbfbt_ctx* ctx, int which, const double* r, float* x_out, float* y_out);
 /* Learned applications kept / replaced by the V-cycle since the context was created. */
 int wbfbt_learned_stats(const wbfbt_ctx* ctx, long long* accepted, long long* rejected);
+/* Load a checkpoint (wbfbt_net_save or wbfbt_train_learned) into a network owned by the context
+ * (released by wbfbt_destroy or by a later call) and attach it for K_r = B D^-1 B^T with
+ * accept_ratio 1, as wbfbt_attach_net does.  The element grid must be a cube whose edge count
+ * is a multiple of 4.  Errors: WBFBT_ERR_INVALID (arguments, grid, checkpoint format). */
+int wbfbt_load_learned(wbfbt_ctx* ctx, const char* path);
+/* Train the learned correction on pairs the solver generates and write the checkpoint to
+ * out_path.  cfg_json (may be NULL) is a flat JSON object with any of "fields" (viscosity
+ * fields, default 100), "per_field" (residuals per field, 20), "epochs" (20), "batch" (4),
+ * "lr" (1e-3, cosine decay), "seed" (1000), "init_seed" (7), "omega" (0.1), "delta" (200).
+ * Field f draws 8-48 sinkers and a dynamic ratio log-uniform in [1e4, 1e8] from seed + f
+ * (SplitMix64); its residuals are standard normal per coefficient with the constant mode
+ * removed; the targets are the context's K_r V-cycle corrections (wbfbt_learned_sample); the
+ * U-Net starts from He-normal weights and trains with Adam on shuffled mini-batches.  The call
+ * allocates its pair store (fields x per_field x E x (2 Np + 1) floats) and frees it, runs
+ * wbfbt_setup for every field and again with the context's own viscosity at the end, and
+ * returns when the checkpoint is written.  Errors: WBFBT_ERR_INVALID (arguments, grid,
+ * malformed or out-of-range configuration), WBFBT_ERR_CUDA, or the status of a failing step. */
+int wbfbt_train_learned(wbfbt_ctx* ctx, const char* cfg_json, const char* out_path);
 
 /* Number of CUDA kernels this library has launched in the process so far (all contexts). */
 long long wbfbt_launch_count(void);

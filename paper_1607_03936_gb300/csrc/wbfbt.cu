@@ -158,6 +158,7 @@ struct wbfbt_ctx {
   double* gj_work = nullptr;          // 4 x 32 x 32 pivot-block workspace
   // learned correction
   wbfbt_net* net = nullptr;
+  wbfbt_net* own_net = nullptr;   // created by wbfbt_load_learned, destroyed with the context
   int net_mask = 0;
   double net_accept = 1.0;
   float *lx = nullptr, *ly = nullptr, *lq = nullptr, *llogmu = nullptr;
@@ -1121,7 +1122,201 @@ int wbfbt_setup(wbfbt_ctx* c, const double* mu_nodes) {
 
 void wbfbt_destroy(wbfbt_ctx* c) {
   if (!c) return;
+  if (c->own_net) wbfbt_net_destroy(c->own_net);
   delete c;
+}
+
+// ---- learned correction: checkpoint loading and native training (the loop the Python driver
+// runs, over the same entry points)
+
+}  // extern "C"
+
+namespace {
+
+// SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014)
+struct SplitMix64 {
+  unsigned long long s;
+  unsigned long long next() {
+    unsigned long long z = (s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }   // [0, 1)
+  double normal() {   // Box-Muller
+    const double u1 = ((double)(next() >> 11) + 1.0) * (1.0 / 9007199254740992.0);   // (0, 1]
+    const double u2 = uniform();
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+  }
+};
+
+struct TrainCfg {
+  int fields = 100, per_field = 20, epochs = 20, batch = 4;
+  double lr = 1e-3, omega = 0.1, delta = 200.0;
+  long long seed = 1000, init_seed = 7;
+};
+
+// Flat JSON object of numbers; known keys are read, others ignored.  False on a malformed value.
+bool parse_train_cfg(const char* js, TrainCfg* c) {
+  auto num = [&](const char* key, double* out) -> bool {
+    char pat[64];
+    std::snprintf(pat, sizeof(pat), "\"%s\"", key);
+    const char* p = std::strstr(js, pat);
+    if (!p) return true;
+    p += std::strlen(pat);
+    while (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r') ++p;
+    if (*p != ':') return false;
+    ++p;
+    char* end = nullptr;
+    const double v = std::strtod(p, &end);
+    if (end == p || !std::isfinite(v)) return false;
+    *out = v;
+    return true;
+  };
+  double f = c->fields, pf = c->per_field, ep = c->epochs, b = c->batch, sd = (double)c->seed,
+         is = (double)c->init_seed;
+  if (!num("fields", &f) || !num("per_field", &pf) || !num("epochs", &ep) || !num("batch", &b) ||
+      !num("lr", &c->lr) || !num("omega", &c->omega) || !num("delta", &c->delta) || !num("seed", &sd) ||
+      !num("init_seed", &is))
+    return false;
+  c->fields = (int)f;
+  c->per_field = (int)pf;
+  c->epochs = (int)ep;
+  c->batch = (int)b;
+  c->seed = (long long)sd;
+  c->init_seed = (long long)is;
+  return c->fields >= 1 && c->per_field >= 1 && c->epochs >= 1 && c->batch >= 1 && c->lr > 0 && c->omega > 0 &&
+         c->delta > 0 && c->fields * (long long)c->per_field >= c->batch;
+}
+
+bool learned_grid_ok(const wbfbt_ctx* c) {
+  return c->g.nx == c->g.ny && c->g.nx == c->g.nz && c->g.nx % 4 == 0 && 1 + c->NP <= 16;
+}
+
+struct DevBufs {
+  std::vector<void*> p;
+  template <typename T>
+  T* get(size_t n) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, n * sizeof(T)) != cudaSuccess) return nullptr;
+    p.push_back(q);
+    return static_cast<T*>(q);
+  }
+  ~DevBufs() {
+    for (void* q : p) cudaFree(q);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int wbfbt_load_learned(wbfbt_ctx* c, const char* path) {
+  if (!c || !path || !learned_grid_ok(c)) return WBFBT_ERR_INVALID;
+  wbfbt_net* net = nullptr;
+  int st = wbfbt_net_create(1 + c->NP, c->NP, c->g.nx, 1, c->ust, &net);
+  if (st != WBFBT_OK) return st;
+  if ((st = wbfbt_net_load(net, path)) != WBFBT_OK || (st = wbfbt_attach_net(c, net, 2, 1.0)) != WBFBT_OK) {
+    wbfbt_net_destroy(net);
+    return st;
+  }
+  if (c->own_net) wbfbt_net_destroy(c->own_net);
+  c->own_net = net;
+  return WBFBT_OK;
+}
+
+int wbfbt_train_learned(wbfbt_ctx* c, const char* cfg_json, const char* out_path) {
+  if (!c || !out_path || !learned_grid_ok(c)) return WBFBT_ERR_INVALID;
+  TrainCfg cfg;
+  if (cfg_json && !parse_train_cfg(cfg_json, &cfg)) return WBFBT_ERR_INVALID;
+  const int n = c->g.nx, np = c->NP, cin = 1 + np;
+  const long long E = c->g.ne, nn = c->g.nn, P = (long long)cfg.fields * cfg.per_field;
+  const cudaStream_t us = c->ust;
+  DevBufs B;
+  float* X = B.get<float>((size_t)P * E * cin);
+  float* Y = B.get<float>((size_t)P * E * np);
+  float* xb = B.get<float>((size_t)cfg.batch * E * cin);
+  float* yb = B.get<float>((size_t)cfg.batch * E * np);
+  double* r = B.get<double>((size_t)E * np);
+  double* mu = B.get<double>((size_t)nn);
+  double* mu0 = B.get<double>((size_t)nn);
+  if (!X || !Y || !xb || !yb || !r || !mu || !mu0) return WBFBT_ERR_CUDA;
+  if (cudaMemcpyAsync(mu0, c->mu64, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess)
+    return WBFBT_ERR_CUDA;
+  const wbfbt_mesh mesh{c->g.nx, c->g.ny, c->g.nz, c->g.h[0] * c->g.nx, c->g.h[1] * c->g.ny, c->g.h[2] * c->g.nz};
+  // training pairs: multi-sinker fields with 8-48 sinkers and DR log-uniform in [1e4, 1e8] (the
+  // learned-correction workload), standard-normal mean-free residuals, the solver's own
+  // K_r V-cycle corrections as targets
+  std::vector<double> rh((size_t)E * np), ch(3 * 48);
+  int st = WBFBT_OK;
+  for (int f = 0; f < cfg.fields && st == WBFBT_OK; ++f) {
+    const long long seed = cfg.seed + f;
+    SplitMix64 pd{(unsigned long long)(seed * 7919 + 17)};
+    const int ns = 8 + (int)(pd.uniform() * 41);
+    const double dr = std::pow(10.0, 4.0 + 4.0 * pd.uniform());
+    SplitMix64 pc{(unsigned long long)seed};
+    for (int i = 0; i < 3 * ns; ++i) ch[i] = 0.1 + 0.8 * pc.uniform();   // host array, as the call takes it
+    if ((st = wbfbt_sinker_setup(&mesh, c->k, ch.data(), ns, cfg.omega, cfg.delta, dr, 10.0, mu, nullptr, us)) !=
+            WBFBT_OK ||
+        (st = wbfbt_setup(c, mu)) != WBFBT_OK)
+      break;
+    for (int j = 0; j < cfg.per_field; ++j) {
+      SplitMix64 pr{(unsigned long long)(1000003LL * seed + j)};
+      double mean = 0.0;
+      for (long long i = 0; i < E * np; ++i) rh[i] = pr.normal();
+      for (long long e = 0; e < E; ++e) mean += rh[e * np];
+      mean /= (double)E;
+      for (long long e = 0; e < E; ++e) rh[e * np] -= mean;   // constant mode removed
+      if (cudaMemcpyAsync(r, rh.data(), sizeof(double) * E * np, cudaMemcpyHostToDevice, us) != cudaSuccess)
+        return WBFBT_ERR_CUDA;
+      const long long pidx = (long long)f * cfg.per_field + j;
+      if ((st = wbfbt_learned_sample(c, 1, r, X + pidx * E * cin, Y + pidx * E * np)) != WBFBT_OK) break;
+    }
+  }
+  const int st_restore = wbfbt_setup(c, mu0);   // the context's own viscosity again
+  if (st != WBFBT_OK) return st;
+  if (st_restore != WBFBT_OK) return st_restore;
+  // the U-Net: He-normal initial weights (N(0, 2 / (27 cin)), zero biases), Adam with a cosine
+  // learning-rate decay, shuffled mini-batches
+  wbfbt_net* net = nullptr;
+  if ((st = wbfbt_net_create(cin, np, n, cfg.batch, us, &net)) != WBFBT_OK) return st;
+  std::unique_ptr<wbfbt_net, void (*)(wbfbt_net*)> hold(net, wbfbt_net_destroy);
+  {
+    const int chans[11][2] = {{cin, 16}, {16, 16}, {16, 32}, {32, 32}, {32, 64}, {64, 64},
+                              {96, 32},  {32, 32}, {48, 16}, {16, 16}, {16, np}};
+    std::vector<float> theta;
+    SplitMix64 pi{(unsigned long long)cfg.init_seed};
+    for (const auto& ch2 : chans) {
+      const double sd = std::sqrt(2.0 / (27.0 * ch2[0]));
+      for (long long i = 0; i < 27LL * ch2[0] * ch2[1]; ++i) theta.push_back((float)(pi.normal() * sd));
+      for (int i = 0; i < ch2[1]; ++i) theta.push_back(0.f);
+    }
+    if ((long long)theta.size() != wbfbt_net_param_count(net)) return WBFBT_ERR_INVALID;
+    if ((st = wbfbt_net_set_params(net, theta.data())) != WBFBT_OK) return st;
+  }
+  const long long nb = P / cfg.batch, steps = (long long)cfg.epochs * nb;
+  std::vector<long long> perm(P);
+  SplitMix64 po{(unsigned long long)(cfg.seed + 12345)};
+  long long step = 0;
+  for (int ep = 0; ep < cfg.epochs; ++ep) {
+    for (long long i = 0; i < P; ++i) perm[i] = i;
+    for (long long i = P - 1; i > 0; --i) std::swap(perm[i], perm[(long long)(po.uniform() * (i + 1))]);
+    for (long long b = 0; b < nb; ++b, ++step) {
+      for (int t = 0; t < cfg.batch; ++t) {
+        const long long q = perm[b * cfg.batch + t];
+        if (cudaMemcpyAsync(xb + (size_t)t * E * cin, X + (size_t)q * E * cin, sizeof(float) * E * cin,
+                            cudaMemcpyDeviceToDevice, us) != cudaSuccess ||
+            cudaMemcpyAsync(yb + (size_t)t * E * np, Y + (size_t)q * E * np, sizeof(float) * E * np,
+                            cudaMemcpyDeviceToDevice, us) != cudaSuccess)
+          return WBFBT_ERR_CUDA;
+      }
+      if ((st = wbfbt_net_loss_grad(net, xb, yb, cfg.batch, nullptr, nullptr)) != WBFBT_OK) return st;
+      const double lr_t = cfg.lr * 0.5 * (1.0 + std::cos(3.141592653589793 * (double)step / (double)steps));
+      if ((st = wbfbt_net_adam_step(net, (float)std::max(lr_t, 1e-5))) != WBFBT_OK) return st;
+    }
+  }
+  return wbfbt_net_save(net, out_path);
 }
 
 int wbfbt_sizes(const wbfbt_ctx* c, long long* nn, long long* ne, int* np, int* nl) {

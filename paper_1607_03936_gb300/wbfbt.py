@@ -8,6 +8,7 @@ fallback.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 from dataclasses import dataclass
 
@@ -28,7 +29,7 @@ SYMBOLS = ["wbfbt_default_opts", "wbfbt_sinker_setup", "wbfbt_create", "wbfbt_se
            "wbfbt_net_num_params", "wbfbt_net_create", "wbfbt_net_set_params", "wbfbt_net_get_params",
            "wbfbt_net_param_count", "wbfbt_net_forward", "wbfbt_net_loss_grad", "wbfbt_net_adam_step",
            "wbfbt_net_save", "wbfbt_net_load", "wbfbt_net_destroy", "wbfbt_attach_net", "wbfbt_learned_sample",
-           "wbfbt_learned_stats"]
+           "wbfbt_learned_stats", "wbfbt_load_learned", "wbfbt_train_learned"]
 NOALLOC_MAX_NODES = 1 << 19
 
 
@@ -97,6 +98,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.wbfbt_attach_net.argtypes = [vp, vp, i, d]
     lib.wbfbt_learned_sample.argtypes = [vp, i, vp, vp, vp]
     lib.wbfbt_learned_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.wbfbt_load_learned.argtypes = [vp, ctypes.c_char_p]
+    lib.wbfbt_train_learned.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p]
     lib.wbfbt_status_string.argtypes = [i]
     lib.wbfbt_status_string.restype = ctypes.c_char_p
     return lib   # every other entry point returns int, ctypes' default
@@ -228,6 +231,16 @@ class Solver:
         y = torch.empty((self.n_elem, self.np), dtype=torch.float32, device=r.device)
         _check(lib().wbfbt_learned_sample(self.h, which, _ptr(r), _ptr(x), _ptr(y)), "wbfbt_learned_sample")
         return x, y
+
+    def load_learned(self, path: str):
+        """Load a checkpoint into a network owned by the context and attach it for K_r."""
+        _check(lib().wbfbt_load_learned(self.h, str(path).encode()), "wbfbt_load_learned")
+
+    def train_learned(self, out_path: str, **cfg):
+        """Train the learned correction in the library (keys: fields, per_field, epochs, batch,
+        lr, seed, init_seed, omega, delta) and write the checkpoint to out_path."""
+        js = json.dumps(cfg).encode() if cfg else None
+        _check(lib().wbfbt_train_learned(self.h, js, str(out_path).encode()), "wbfbt_train_learned")
 
     def learned_stats(self):
         a, r = ctypes.c_longlong(), ctypes.c_longlong()

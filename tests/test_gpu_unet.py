@@ -147,6 +147,33 @@ def test_solver_with_attached_net_falls_back_and_converges(wb):
         assert r1.iters == r0.iters
 
 
+def test_native_training_and_checkpoint_loading(wb):
+    """wbfbt_train_learned trains in the library on solver-generated pairs, writes a checkpoint
+    and leaves the context's own problem in place; wbfbt_load_learned attaches it."""
+    n, k = 8, 2
+    m = M.Mesh(n, n, n, k)
+    c = inputs.sinker_centres(0, 4)
+    X = m.node_coords()
+    mu = sinker.viscosity(X, c, 0.1, 200.0, 1e4)
+    ft = torch.tensor(sinker.forcing(X, c, 0.1, 200.0).T.ravel(), device="cuda")
+    s = wb.Solver(n, k, torch.tensor(mu, device="cuda"), precision=wb.MIXED)
+    u0, p0, r0 = s.solve(ft)
+    with pytest.raises(wb.WbfbtError):
+        s.train_learned(os.path.join(tempfile.gettempdir(), "never.bin"), epochs=-1)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "net.bin")
+        s.train_learned(path, fields=2, per_field=2, epochs=1, batch=2, seed=1000)
+        assert os.path.getsize(path) > 4 * wb.Net.num_params(1 + s.np, s.np)
+        # the viscosity was restored: the same solve, bit for bit
+        u1, p1, r1 = s.solve(ft)
+        assert r1.iters == r0.iters and torch.equal(u1, u0) and torch.equal(p1, p0)
+        s.load_learned(path)
+        _, _, r2 = s.solve(ft)
+        acc, rej = s.learned_stats()
+        assert r2.status == 0 and r2.rel_res <= 1e-6
+        assert acc + rej >= r2.iters          # the loaded net was consulted for every K_r
+
+
 def test_trained_net_gain_is_measured(wb):
     """Train on solver-generated pairs (8^3 Q2) and measure FGMRES with and without the net.
 
