@@ -316,7 +316,12 @@ __global__ void k_bgj_rows(GjJobs jobs, int J0) {
   }
 }
 
-// A[i][k] -= sum_s A[i][J0+s] A[J0+s][k] for i, k not in J (32 x 8 threads, 32 x 32 tile)
+// A[i][k] -= sum_s A[i][J0+s] A[J0+s][k] for i, k not in J (32 x 8 threads, 32 x 32 tile), on
+// the tiles on or above the tile diagonal only.  Symmetry: at every stage of the sweep
+// A[k][i] = s(i) s(k) A[i][k] with s = -1 for indices already pivoted and +1 otherwise (the
+// pivoted part holds the inverse of its leading block, the cross blocks P A and -A P), and the
+// update keeps that relation; k_bgj_mirror restores the tiles below the diagonal from it, so
+// the FP64 work of the trailing update is halved.
 __global__ void k_bgj_update(GjJobs jobs, int J0) {
   pdl_entry();
   const int z = blockIdx.z;
@@ -325,7 +330,7 @@ __global__ void k_bgj_update(GjJobs jobs, int J0) {
   const int bb = min(GJB, n - J0);
   double* A = jobs.A[z];
   const int k0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
-  if (k0 >= n || i0 >= n) return;
+  if (k0 >= n || i0 >= n || i0 > k0) return;
   __shared__ double Rj[GJB][33];   // A[J0+s][k0+x]
   __shared__ double Ci[32][GJB + 1];   // A[i0+y][J0+s]
   for (int t = threadIdx.y * 32 + threadIdx.x; t < GJB * 32; t += 256) {
@@ -344,6 +349,33 @@ __global__ void k_bgj_update(GjJobs jobs, int J0) {
 #pragma unroll
     for (int s = 0; s < GJB; ++s) acc += Ci[yy][s] * Rj[s][threadIdx.x];
     A[(size_t)i * n + k] -= acc;
+  }
+}
+
+// Tiles below the diagonal (i0 > k0, neither in J) from their transposes after the update:
+// A[i][k] = s(i) s(k) A[k][i], s(x) = -1 for x < J0 (pivoted before this block), else +1.
+__global__ void k_bgj_mirror(GjJobs jobs, int J0) {
+  pdl_entry();
+  const int z = blockIdx.z;
+  const int n = jobs.n[z];
+  if (J0 >= n) return;
+  const int bb = min(GJB, n - J0);
+  double* A = jobs.A[z];
+  const int k0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+  if (k0 >= n || i0 >= n || i0 <= k0 || (i0 >= J0 && i0 < J0 + bb) || (k0 >= J0 && k0 < J0 + bb)) return;
+  __shared__ double T[32][33];
+  // T[x][y] = A[k0 + x][i0 + y] (coalesced reads along y)
+  for (int x = threadIdx.y; x < 32; x += 8) {
+    const int k = k0 + x, i = i0 + threadIdx.x;
+    T[x][threadIdx.x] = (k < n && i < n) ? A[(size_t)k * n + i] : 0.0;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int i = i0 + y, k = k0 + threadIdx.x;
+    if (i < n && k < n) {
+      const double sg = ((i < J0) != (k < J0)) ? -1.0 : 1.0;
+      A[(size_t)i * n + k] = sg * T[threadIdx.x][y];
+    }
   }
 }
 
@@ -517,6 +549,7 @@ cudaError_t launch_dense_inverse_batch(int count, double* const* M, const int* n
     wb_launch(k_bgj_pivot, count, dim3(32, 32), 0, st, jobs, J0, flag);
     wb_launch(k_bgj_rows, dim3((nmax + 31) / 32, count), dim3(32, 8), 0, st, jobs, J0);
     wb_launch(k_bgj_update, dim3((nmax + 31) / 32, (nmax + 31) / 32, count), dim3(32, 8), 0, st, jobs, J0);
+    wb_launch(k_bgj_mirror, dim3((nmax + 31) / 32, (nmax + 31) / 32, count), dim3(32, 8), 0, st, jobs, J0);
     wb_launch(k_bgj_cols, dim3((nmax + 31) / 32, count), dim3(32, 8), 0, st, jobs, J0);
   }
   return cudaGetLastError();
