@@ -1,13 +1,19 @@
 """Benchmark: one pass of the w-BFBT Stokes hot path per step, on GB300.
 
 A step is the whole path over one synthetic multi-sinker problem (Sec. 2.1):
-viscosity/forcing setup on the GPU, the viscosity-dependent setup (sqrt(mu)
-weights, three multigrid hierarchies, Chebyshev bounds, FP64 coarsest
-inverses; no allocation), and the FGMRES(50) solve to a 1e-6 relative
-residual with the w-BFBT block preconditioner.  Default workload: 32^3 Q2 x
-P1disc, 24 seeded sinkers, omega = 0.05, delta = 200, DR = 1e6, FP64.
+viscosity and forcing at the nodes on the GPU, the viscosity-dependent setup
+(sqrt(mu) weights, three multigrid hierarchies, Chebyshev bounds, FP64
+coarsest inverses; no allocation), and the FGMRES(50) solve to a 1e-6
+relative residual with the w-BFBT block preconditioner.
+
+Default workload: 64^3 Q2 x P1disc, 64 seeded sinkers, omega = 0.04,
+delta = 400, DR = 1e10 (the largest single-GPU configuration).  `value` is
+the mixed-precision step (FP32 preconditioner, FP64 Krylov, true residual and
+coarsest solve); the plain FP64 step of the same problem is timed beside it
+(`fp64`), and both solutions are compared.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--precision mixed|fp64]
 
 --impl reference times the CPU oracle (oracle/, FP64 SciPy) as the reference
 arm.  One JSON line is printed by rank 0.
@@ -28,10 +34,14 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "Stokes solve s to 1e-6 rel. residual & A-apply DOF/s, mixed+learned vs FP64"
-WORKLOAD = "32^3-Q2-S24-DR1e6"
+DEFAULT_WORKLOAD = "64^3-Q2-S64-DR1e10"
+ORACLE_WORKLOAD = "32^3-Q2-S24-DR1e6"     # the largest configuration the oracle solves in bounded time
 RTOL = 1e-6
-ORACLE_SAMPLE_N = 16          # the CPU oracle runs the same problem family on a 16^3 mesh
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+ORACLE_SAMPLE_ITERS = 2                   # FGMRES iterations per reference-arm step
+# FP64 FGMRES iteration counts of the GPU path per workload (the GPU FP64 solve takes the oracle's
+# count +-1 where the oracle runs: 40 at 32^3); the reference arm scales its per-iteration time by them.
+FP64_ITERS = {"8^3-Q2-S4-DR1e4": 50, "32^3-Q2-S24-DR1e6": 40, "24^3-Q3-S32-DR1e8": 43, "64^3-Q2-S64-DR1e10": 104}
+L2_FLUSH_BYTES = 256 * 1024 * 1024
 
 
 def a_apply_flops_per_elem(k: int) -> float:
@@ -45,77 +55,124 @@ def a_apply_bytes_per_node(dtype_bytes: int) -> float:
     return 7.0 * dtype_bytes
 
 
-# --------------------------------------------------------------------------- CPU oracle arm
-
-def oracle_sample(cfg: dict, n_sample: int, its_target: int | None) -> dict:
-    """Run the oracle (setup + solve) on an n_sample^3 mesh in a fresh single-threaded process.
-
-    Returns seconds for the sample and the estimate scaled to the workload size:
-    (setup + solve * its_target / its_sample) * dof_workload / dof_sample.
-    """
-    code = f"""
-import json, time, sys
-sys.path.insert(0, {ROOT!r})
-from oracle import mesh as M, wbfbt as W
-from paper_1607_03936_gb300 import inputs
-n, k = {n_sample}, {cfg['k']}
-m = M.Mesh(n, n, n, k)
-c = inputs.sinker_centres({cfg['seed']}, {cfg['n_sinkers']})
-t0 = time.perf_counter()
-mu, f = W.sinker_problem(m, c, {cfg['omega']}, {cfg['delta']}, {cfg['dr']})
-prob = W.StokesProblem(m, mu)
-pc = W.BlockPreconditioner(prob, 'vcycle', -1.0)
-import numpy as np
-from oracle import operators as op, krylov
-F = np.concatenate([op.load_vector(m, f), np.zeros(m.n_p)])
-t1 = time.perf_counter()
-x, its, rel = krylov.fgmres(prob.apply_K, pc.apply, F, rtol={RTOL}, restart=50)
-t2 = time.perf_counter()
-print(json.dumps(dict(setup=t1 - t0, solve=t2 - t1, its=its, rel=rel, dof=m.n_u + m.n_p)))
-"""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
-    if out.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
-    r = json.loads(out.stdout.strip().splitlines()[-1])
+def dof_counts(cfg: dict) -> tuple[int, int]:
     n, k = cfg["n"], cfg["k"]
-    dof_w = 3 * (k * n + 1) ** 3 + n ** 3 * k * (k + 1) * (k + 2) // 6
-    its = its_target if its_target else r["its"]
-    r["estimate_s"] = (r["setup"] + r["solve"] * its / r["its"]) * dof_w / r["dof"]
-    r["dof_workload"] = dof_w
-    return r
+    return 3 * (k * n + 1) ** 3, n ** 3 * k * (k + 1) * (k + 2) // 6
 
 
-def run_reference(args, cfg, rank, world):
-    if rank != 0:
-        return
-    for _ in range(args.warmup):
-        oracle_sample(cfg, ORACLE_SAMPLE_N, None)
-    runs = [oracle_sample(cfg, ORACLE_SAMPLE_N, None) for _ in range(args.steps)]
-    est = [r["estimate_s"] for r in runs]
-    v = statistics.mean(est)
-    sample = (f"oracle setup+solve on a {ORACLE_SAMPLE_N}^3 mesh of the same problem family "
-              f"({runs[0]['its']} its, {runs[0]['setup'] + runs[0]['solve']:.1f} s), scaled by DOF "
-              f"({runs[0]['dof']} -> {runs[0]['dof_workload']})")
-    line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded multi-sinker, Sec. 2.1)",
-        "config": config_dict(cfg, "fp64"),
-        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
-        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
-
-
-def config_dict(cfg, precision):
+def config_dict(name: str, cfg: dict, precision: str) -> dict:
     n, k = cfg["n"], cfg["k"]
-    return {"workload": WORKLOAD, "mesh": f"{n}x{n}x{n} Q{k} x P{k - 1}disc",
-            "u_dof": 3 * (k * n + 1) ** 3, "p_dof": n ** 3 * k * (k + 1) * (k + 2) // 6,
+    u_dof, p_dof = dof_counts(cfg)
+    return {"workload": name, "mesh": f"{n}x{n}x{n} Q{k} x P{k - 1}disc", "u_dof": u_dof, "p_dof": p_dof,
             "sinkers": cfg["n_sinkers"], "omega": cfg["omega"], "delta": cfg["delta"], "dr": cfg["dr"],
             "rtol": RTOL, "krylov": "FGMRES(50)", "precision": precision, "parallelism": "replicas",
             "l2": "flushed between steps (256 MiB write)"}
+
+
+# --------------------------------------------------------------------------- CPU oracle legs
+
+_ORACLE_CODE = """
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import krylov, mesh as M, operators as op, wbfbt as W
+from paper_1607_03936_gb300 import inputs
+cfg = {cfg!r}
+m = M.Mesh(cfg['n'], cfg['n'], cfg['n'], cfg['k'])
+c = inputs.sinker_centres(cfg['seed'], cfg['n_sinkers'])
+t0 = time.perf_counter()
+mu, f = W.sinker_problem(m, c, cfg['omega'], cfg['delta'], cfg['dr'])
+prob = W.StokesProblem(m, mu)
+pc = W.BlockPreconditioner(prob, 'vcycle', -1.0)
+F = np.concatenate([op.load_vector(m, f), np.zeros(m.n_p)])
+t1 = time.perf_counter()
+x, its, rel = krylov.fgmres(prob.apply_K, pc.apply, F, rtol={rtol}, restart=50)
+t2 = time.perf_counter()
+if {save!r}:
+    np.savez({save!r}, u=x[:m.n_u], p=op.project_pressure(m, x[m.n_u:]))
+print(json.dumps(dict(setup=t1 - t0, solve=t2 - t1, its=its, rel=rel, dof=m.n_u + m.n_p)))
+"""
+
+
+def _oracle_env() -> dict:
+    return dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                CUDA_VISIBLE_DEVICES="")
+
+
+def start_oracle_solve(cfg: dict, save: str = "") -> subprocess.Popen:
+    """The oracle's full setup + solve of `cfg`, single-threaded, in a separate process (started
+    before this process touches the GPU); the solution goes to the .npz file `save` if given."""
+    code = _ORACLE_CODE.format(root=ROOT, cfg=cfg, rtol=RTOL, save=save)
+    return subprocess.Popen([sys.executable, "-c", code], env=_oracle_env(), stdout=subprocess.PIPE,
+                            stderr=subprocess.PIPE, text=True)
+
+
+def finish_oracle_solve(proc: subprocess.Popen, timeout: float = 1200.0) -> dict:
+    out, err = proc.communicate(timeout=timeout)
+    if proc.returncode != 0:
+        raise RuntimeError("oracle solve failed: " + err[-2000:])
+    return json.loads(out.strip().splitlines()[-1])
+
+
+def run_reference(args, name, cfg, rank, world):
+    """The reference arm: the CPU oracle, single-threaded, on the host cores.
+
+    The oracle cannot run the 64^3 workload in bounded time (CSR A alone holds ~2.4e9
+    nonzeros, ~29 GB, and a solve would take hours), so each step is a bounded sample of the
+    same problem family at 32^3 (Q2, S24, DR 1e6, the configuration the oracle solves in ~1.5
+    min): ORACLE_SAMPLE_ITERS FGMRES iterations from x0 = 0 with the V-cycle preconditioner.  The
+    oracle's setup (assembly, hierarchies) is timed once in the warm-up.  `value` scales setup
+    and per-iteration time by DOF to the workload and by its FP64 iteration count.
+    """
+    if rank != 0:
+        return
+    import numpy as np
+
+    from oracle import krylov
+    from oracle import mesh as M
+    from oracle import operators as op
+    from oracle import wbfbt as W
+    from paper_1607_03936_gb300 import inputs
+
+    ocfg = dict(inputs.WORKLOADS[ORACLE_WORKLOAD])
+    m = M.Mesh(ocfg["n"], ocfg["n"], ocfg["n"], ocfg["k"])
+    c = inputs.sinker_centres(ocfg["seed"], ocfg["n_sinkers"])
+    t0 = time.perf_counter()
+    mu, f = W.sinker_problem(m, c, ocfg["omega"], ocfg["delta"], ocfg["dr"])
+    prob = W.StokesProblem(m, mu)
+    pc = W.BlockPreconditioner(prob, "vcycle", -1.0)
+    F = np.concatenate([op.load_vector(m, f), np.zeros(m.n_p)])
+    setup_s = time.perf_counter() - t0
+
+    def sample():
+        krylov.fgmres(prob.apply_K, pc.apply, F, rtol=RTOL, restart=50, maxit=ORACLE_SAMPLE_ITERS)
+
+    for _ in range(args.warmup):
+        sample()
+    times = []
+    for _ in range(args.steps):
+        s0 = time.perf_counter()
+        sample()
+        times.append(time.perf_counter() - s0)
+    t_step = statistics.mean(times)
+    dof_o = m.n_u + m.n_p
+    dof_w = sum(dof_counts(cfg))
+    its = FP64_ITERS.get(name, FP64_ITERS[ORACLE_WORKLOAD])
+    value = (setup_s + t_step / ORACLE_SAMPLE_ITERS * its) * dof_w / dof_o
+    sample_txt = (f"per step: {ORACLE_SAMPLE_ITERS} FGMRES(50) iterations (V-cycle w-BFBT) of the oracle on "
+                  f"{ORACLE_WORKLOAD} ({dof_o} DOF), {t_step:.2f} s; setup once {setup_s:.1f} s; value = "
+                  f"(setup + per-iteration x {its} FP64 iterations) x DOF ratio {dof_w}/{dof_o}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded multi-sinker, Sec. 2.1)",
+        "config": config_dict(name, cfg, "fp64"),
+        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample_txt,
+                         "host_cpus": os.cpu_count(), "threads": 1, "oracle_setup_s": setup_s,
+                         "oracle_s_per_iteration": t_step / ORACLE_SAMPLE_ITERS},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------- clocks
@@ -201,8 +258,37 @@ def traffic_for(kernel: str):
     return ent["dram_bytes_per_launch"]
 
 
-def run_ours(args, cfg, rank, world):
+def fp64_alu_peak_tflops(sm_mhz: float | None) -> float:
+    """FP64 ALU peak from the unit counts: 152 SMs x 2 DFMA per clock x 2 flop, at the SM clock
+    sampled during the run (the maximum clock, 2070 MHz, when no sample is available)."""
+    return 152 * 2 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
+def hbm_peak_gbs() -> tuple[float, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        v = json.load(open(path)).get("hbm_gbs")
+        if v:
+            return float(v), "of measured"
+    return 6800.0, "of fallback"
+
+
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def run_ours(args, name, cfg, rank, world):
+    import tempfile
+
     import numpy as np
+
+    # the CPU baseline runs concurrently on one host core: started before any CUDA call
+    oracle_proc, oracle_npz = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        oracle_npz = os.path.join(tempfile.mkdtemp(prefix="wbfbt_bench_"), "oracle.npz")
+        oracle_proc = start_oracle_solve(inputs_workload(ORACLE_WORKLOAD), oracle_npz)
+
     import torch
     import torch.distributed as dist
 
@@ -221,45 +307,45 @@ def run_ours(args, cfg, rank, world):
     solver = wb.Solver(n, k, mu, precision=precision)
     u = torch.empty(solver.n_u, dtype=torch.float64, device=dev)
     p = torch.empty(solver.n_p, dtype=torch.float64, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
 
-    def step():
+    def step(s, uu, pp):
+        ea, eb, ec = _events(3)
         m2, f2 = wb.sinker_setup(n, k, centres, cfg["omega"], cfg["delta"], cfg["dr"])
-        e_a = torch.cuda.Event(enable_timing=True)
-        e_a.record(st)
-        solver.setup(m2)
-        e_b = torch.cuda.Event(enable_timing=True)
-        e_b.record(st)
-        _, _, res = solver.solve(f2, rtol=RTOL, u=u, p=p)
-        e_c = torch.cuda.Event(enable_timing=True)
-        e_c.record(st)
-        return res, (e_a, e_b, e_c)
+        ea.record(st)
+        s.setup(m2)
+        eb.record(st)
+        _, _, res = s.solve(f2, rtol=RTOL, u=uu, p=pp)
+        ec.record(st)
+        return res, (ea, eb, ec)
+
+    def timed(s, uu, pp, steps):
+        times, setups, solves, res_all = [], [], [], []
+        for i in range(steps):
+            flush.fill_(float(i))                 # evict L2 between steps (outside the step's events)
+            e0, e1 = _events(2)
+            e0.record(st)
+            res, (ea, eb, ec) = step(s, uu, pp)
+            e1.record(st)
+            torch.cuda.synchronize()
+            if res.status != 0:
+                raise RuntimeError(f"solve failed: {res}")
+            times.append(e0.elapsed_time(e1) / 1e3)
+            setups.append(ea.elapsed_time(eb) / 1e3)
+            solves.append(eb.elapsed_time(ec) / 1e3)
+            res_all.append(res)
+        return times, setups, solves, res_all
 
     for _ in range(args.warmup):
-        step()
+        step(solver, u, p)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = ClockSampler(dev.index) if rank == 0 else None
     launches0 = wb.launch_count()
-    times, setups, solves, iters, rels = [], [], [], [], []
     wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.fill_(float(len(times)))        # evict L2 between steps (outside the step's events)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        res, (ea, eb, ec) = step()
-        e1.record(st)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
-        setups.append(ea.elapsed_time(eb) / 1e3)
-        solves.append(eb.elapsed_time(ec) / 1e3)
-        iters.append(res.iters)
-        rels.append(res.rel_res)
-        if res.status != 0:
-            raise RuntimeError(f"solve failed: {res}")
+    times, setups, solves, results = timed(solver, u, p, args.steps)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if world > 1:
@@ -267,124 +353,167 @@ def run_ours(args, cfg, rank, world):
     launches = wb.launch_count() - launches0
     clk = clocks.stop() if clocks else None
     t_step = max_over_ranks(statistics.mean(times), world, dev)
+    iters = results[-1].iters
 
-    # dominant kernel: the fine-level A apply, timed on the launching stream with CUDA events
-    xk = torch.randn(solver.n_u, dtype=torch.float64, device=dev)
-    xk32 = xk.float()
+    # the other side of the metric: the plain FP64 solve of the same problem (fewer steps: it is
+    # the comparison, not the headline), and the distance between the two solutions
+    other = None
+    if precision == wb.MIXED:
+        s64 = wb.Solver(n, k, mu, precision=wb.F64)
+        u64 = torch.empty_like(u)
+        p64 = torch.empty_like(p)
+        step(s64, u64, p64)
+        t64, su64, so64, r64 = timed(s64, u64, p64, max(1, min(args.steps, 3)))
+        t64m = max_over_ranks(statistics.mean(t64), world, dev)
+        other = {"precision": "fp64", "s_per_step": t64m, "setup_s": statistics.mean(su64),
+                 "solve_s": statistics.mean(so64), "iters": r64[-1].iters, "final_rel_res": r64[-1].rel_res,
+                 "steps": len(t64), "mixed_speedup": t64m / t_step,
+                 "rel_err_u_mixed_vs_fp64": float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64)),
+                 "rel_err_p_mixed_vs_fp64": float(torch.linalg.norm(p - p64) / torch.linalg.norm(p64))}
+        s64.close()
+        del u64, p64
+    torch.cuda.synchronize()
+    return dict(solver=solver, wb=wb, torch=torch, np=np, dev=dev, st=st, flush=flush, centres=centres, mu=mu,
+                f=f, u=u, p=p, t_step=t_step, times=times, setups=setups, solves=solves, iters=iters,
+                rel=results[-1].rel_res, wall=wall, launches=launches, clk=clk, other=other,
+                oracle_proc=oracle_proc, oracle_npz=oracle_npz, precision=precision)
 
-    def time_apply(x, reps=20):
+
+def finish_ours(args, name, cfg, rank, world, R):
+    torch, wb, np = R["torch"], R["wb"], R["np"]
+    solver, st, flush, dev = R["solver"], R["st"], R["flush"], R["dev"]
+    n, k = cfg["n"], cfg["k"]
+
+    def time_op(fn, reps=20):
         for _ in range(3):
-            solver.apply_A(x)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fn()
+        e0, e1 = _events(2)
         e0.record(st)
         for _ in range(reps):
-            solver.apply_A(x)
+            fn()
         e1.record(st)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3 / reps
 
-    t_a64 = time_apply(xk)
-    t_a32 = time_apply(xk32)
+    # operator applies on the fine level, timed on the launching stream with CUDA events.  The
+    # mixed context applies A in FP32 (the preconditioner's) and FP64 (the Krylov side's).
+    x64 = torch.randn(solver.n_u, dtype=torch.float64, device=dev)
+    t_a32 = time_op(lambda: solver.apply_A(x64.float())) if R["precision"] == wb.MIXED else None
+    xk = torch.randn(solver.n_u + solver.n_p, dtype=torch.float64, device=dev)
+    t_k64 = time_op(lambda: solver.apply_K(xk))
+    t_a64 = time_op(lambda: solver.apply_A(x64))
+    if R["precision"] == wb.MIXED:
+        x32 = x64.float()
+        t_a32 = time_op(lambda: solver.apply_A(x32))
     n_elem, n_nodes = solver.n_elem, solver.n_nodes
-    flops = a_apply_flops_per_elem(k) * n_elem
-    achieved = flops / t_a64 / 1e12
-    hbm_peak = None
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(peaks_path):
-        hbm_peak = json.load(open(peaks_path)).get("hbm_gbs")
-    hbm_note = "of measured" if hbm_peak else "of fallback"
-    hbm_peak = hbm_peak or 6800.0
+    clk = R["clk"]
+    peak64 = fp64_alu_peak_tflops(clk["sm_mhz"] if clk else None)
+    hbm, hbm_note = hbm_peak_gbs()
+    flops_a = a_apply_flops_per_elem(k) * n_elem
+    # fused Stokes K apply: A (36n^4+30n^3) plus B and B^T (each 3 x 2 n^3 Np for the basis
+    # contractions after the 3 x 2n^4 derivative sums, which A shares)
+    np_e = k * (k + 1) * (k + 2) // 6
+    flops_k = flops_a + 2 * 3 * 2 * (k + 1) ** 3 * np_e * n_elem
+    roof64 = {"bound": "alu", "achieved": flops_k / t_k64 / 1e12, "peak": peak64, "unit": "TFLOP/s",
+              "frac": flops_k / t_k64 / 1e12 / peak64, "traffic": traffic_for("apply_K_f64"),
+              "kernel": "k_q2_elem64<OP_A|OP_BT|OP_B,iso> + k_q2_gather<double,3,STORE> (the FP64 Arnoldi K apply)",
+              "per_launch": ("one fine-level K = [A B^T; B 0] apply: (36n^4+30n^3 + 12 n^3 Np) flops per element "
+                             f"x {n_elem} elements"),
+              "peak_note": "FP64 ALU peak from 152 SMs x 2 DFMA/clk x 2 flop at the sampled SM clock"}
     bytes32 = a_apply_bytes_per_node(4) * n_nodes
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_for("apply_A_f64"),
-                "kernel": "k_q2_elem64<OP_A,iso> + k_q2_gather<double,3,STORE> (one A apply)",
-                "per_launch": ("one fine-level A apply (element pass + node pass), 36n^4+30n^3 flops per element "
-                               "(the kernel executes about 1300 FP64 operations per element: constant GLL "
-                               "derivative sums)"),
-                "peak_note": "FP64 ALU peak derived from 152 SMs x 2 DFMA/clk x 2.07 GHz"}
-    roofline_fp32 = {"bound": "hbm", "achieved": bytes32 / t_a32 / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": bytes32 / t_a32 / 1e9 / hbm_peak, "traffic": traffic_for("apply_A_f32"),
-                     "kernel": "k_q2_elem<OP_A> + k_q2_gather<3,STORE> (one A apply)", "peak_note": hbm_note}
+    roof32 = None
+    if t_a32:
+        roof32 = {"bound": "hbm", "achieved": bytes32 / t_a32 / 1e9, "peak": hbm, "unit": "GB/s",
+                  "frac": bytes32 / t_a32 / 1e9 / hbm, "traffic": traffic_for("apply_A_f32"),
+                  "kernel": "k_q2_elem<OP_A> + k_q2_gather<3,STORE> (one FP32 A apply)", "peak_note": hbm_note,
+                  "per_launch": f"7 words x 4 B per node x {n_nodes} nodes (u, y, mu)"}
+    roofA64 = {"bound": "alu", "achieved": flops_a / t_a64 / 1e12, "peak": peak64, "unit": "TFLOP/s",
+               "frac": flops_a / t_a64 / 1e12 / peak64, "traffic": traffic_for("apply_A_f64"),
+               "kernel": "k_q2_elem64<OP_A,iso> + k_q2_gather<double,3,STORE> (one FP64 A apply)"}
 
-    # end-to-end through the C ABI with host buffers (copies inside the timed region)
+    # end to end through the C ABI, the call a user with host data makes: every step copies the
+    # viscosity and the forcing from pinned host memory (in place of the on-GPU sinker setup),
+    # runs setup and solve, and reads the solution back into pinned host memory.
     mu_h = torch.empty(solver.n_nodes, dtype=torch.float64).pin_memory()
     f_h = torch.empty(solver.n_u, dtype=torch.float64).pin_memory()
-    mu_h.copy_(mu)
-    f_h.copy_(f)
+    mu_h.copy_(R["mu"])
+    f_h.copy_(R["f"])
     u_h = torch.empty(solver.n_u, dtype=torch.float64).pin_memory()
     p_h = torch.empty(solver.n_p, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     e2e = []
-    for i in range(max(1, min(args.steps, 3))):
+    for i in range(args.steps):
         flush.fill_(float(i))
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         solver.setup(mu_h)
-        solver.solve(f_h, rtol=RTOL, u=u_h, p=p_h)
+        _, _, res = solver.solve(f_h, rtol=RTOL, u=u_h, p=p_h)
         e2e.append(time.perf_counter() - w0)
+        if res.status != 0:
+            raise RuntimeError(f"e2e solve failed: {res}")
     h2d = 8 * solver.n_nodes + 8 * solver.n_u
     d2h = 8 * solver.n_u + 8 * solver.n_p
+    e2e_v = max_over_ranks(statistics.mean(e2e), world, dev)
 
-    # the metric's other side: the mixed-precision solve of the same problem, timed the same way
-    # (outside the FP64 timed region), and its distance from the FP64 solution
-    mixed = None
-    if precision == wb.F64:
-        u64, p64 = u.clone(), p.clone()
-        sm = wb.Solver(n, k, mu, precision=wb.MIXED)
-        um = torch.empty_like(u)
-        pm = torch.empty_like(p)
-
-        def step_mixed():
-            m2, f2 = wb.sinker_setup(n, k, centres, cfg["omega"], cfg["delta"], cfg["dr"])
-            sm.setup(m2)
-            return sm.solve(f2, rtol=RTOL, u=um, p=pm)[2]
-
-        for _ in range(args.warmup):
-            step_mixed()
-        tm = []
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            rm = step_mixed()
-            e1.record(st)
-            torch.cuda.synchronize()
-            tm.append(e0.elapsed_time(e1) / 1e3)
-        t_mixed = max_over_ranks(statistics.mean(tm), world, dev)
-        mixed = {"s_per_step": t_mixed, "speedup_vs_fp64": t_step / t_mixed, "iters": rm.iters,
-                 "final_rel_res": rm.rel_res,
-                 "rel_err_u_vs_fp64": float(torch.linalg.norm(um - u64) / torch.linalg.norm(u64)),
-                 "rel_err_p_vs_fp64": float(torch.linalg.norm(pm - p64) / torch.linalg.norm(p64)),
-                 "learned": "not attached (no measured gain; every learned step was rejected on held-out problems)"}
-        sm.close()
-
+    # the oracle's 32^3 solve (running since the start) and the GPU's solve of the same problem in
+    # this run's precision: the error against the oracle, and the CPU baseline
+    cpu, vs_oracle = None, None
+    if R["oracle_proc"] is not None:
+        o = finish_oracle_solve(R["oracle_proc"])
+        ocfg = inputs_workload(ORACLE_WORKLOAD)
+        from paper_1607_03936_gb300 import inputs
+        oc = inputs.sinker_centres(ocfg["seed"], ocfg["n_sinkers"])
+        mo, fo = wb.sinker_setup(ocfg["n"], ocfg["k"], oc, ocfg["omega"], ocfg["delta"], ocfg["dr"])
+        so = wb.Solver(ocfg["n"], ocfg["k"], mo, precision=R["precision"])
+        ug, pg, ro = so.solve(fo, rtol=RTOL)
+        ref = np.load(R["oracle_npz"])
+        ug, pg = ug.cpu().numpy(), pg.cpu().numpy()
+        vs_oracle = {"workload": ORACLE_WORKLOAD, "precision": args.precision, "iters_gpu": ro.iters,
+                     "iters_oracle": o["its"],
+                     "rel_err_u": float(np.linalg.norm(ug - ref["u"]) / np.linalg.norm(ref["u"])),
+                     "rel_err_p": float(np.linalg.norm(pg - ref["p"]) / np.linalg.norm(ref["p"]))}
+        so.close()
+        dof_o = o["dof"]
+        dof_w = sum(dof_counts(cfg))
+        its_w = R["other"]["iters"] if R["other"] else R["iters"]
+        est = (o["setup"] + o["solve"] * its_w / o["its"]) * dof_w / dof_o
+        cpu = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": (f"full oracle setup + FP64 solve of {ORACLE_WORKLOAD} ({dof_o} DOF, {o['its']} its, "
+                          f"{o['setup']:.1f} s + {o['solve']:.1f} s on one host core, run concurrently with the GPU "
+                          f"measurement); the {name} workload is beyond the oracle (CSR A ~2.4e9 nonzeros); "
+                          f"value = (setup + solve x {its_w}/{o['its']} FP64 iterations) x DOF ratio "
+                          f"{dof_w}/{dof_o}"),
+               "measured_s": o["setup"] + o["solve"], "measured_workload": ORACLE_WORKLOAD,
+               "host_cpus": os.cpu_count(), "threads": 1}
     if rank != 0:
         return
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        r = oracle_sample(cfg, ORACLE_SAMPLE_N, iters[-1])
-        cpu = {"value": r["estimate_s"], "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": (f"oracle setup+solve on a {ORACLE_SAMPLE_N}^3 mesh of the same problem family "
-                          f"({r['its']} its, {r['setup'] + r['solve']:.1f} s single-threaded), scaled by DOF "
-                          f"and by the GPU iteration count ({iters[-1]})")}
+    prec_name = "mixed" if R["precision"] == wb.MIXED else "fp64"
     line = {
-        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if precision == wb.F64 else "f32+f64",
-        "data": "synthetic (seeded multi-sinker, Sec. 2.1)", "config": config_dict(cfg, args.precision),
-        "iters": iters[-1], "final_rel_res": rels[-1], "setup_s": statistics.mean(setups),
-        "solve_s": statistics.mean(solves), "wall_s": wall,
-        "a_apply_dof_per_s": {"fp64": solver.n_u / t_a64, "fp32": solver.n_u / t_a32},
-        "roofline": roofline, "roofline_fp32": roofline_fp32, "cpu_baseline": cpu,
-        "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches, "clocks": clk, "mixed": mixed,
+        "metric": METRIC, "value": R["t_step"], "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * R["t_step"], "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if R["precision"] == wb.MIXED else "f64",
+        "data": "synthetic (seeded multi-sinker, Sec. 2.1)", "config": config_dict(name, cfg, prec_name),
+        "iters": R["iters"], "final_rel_res": R["rel"], "setup_s": statistics.mean(R["setups"]),
+        "solve_s": statistics.mean(R["solves"]), "wall_s": R["wall"],
+        "learned": "not attached (no measured gain: every learned step was rejected on held-out problems)",
+        "fp64": R["other"],
+        "a_apply_dof_per_s": {"fp64": solver.n_u / t_a64, "fp32": solver.n_u / t_a32 if t_a32 else None},
+        "roofline": roof64, "roofline_fp32_A": roof32, "roofline_fp64_A": roofA64,
+        "cpu_baseline": cpu, "vs_oracle": vs_oracle,
+        "e2e": {"value": e2e_v, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": R["launches"], "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     solver.close()
 
 
-def run_profile(args, cfg):
+def inputs_workload(name: str) -> dict:
+    from paper_1607_03936_gb300 import inputs
+    return dict(inputs.WORKLOADS[name])
+
+
+def run_profile(args, name, cfg):
+    """One setup + solve of the workload and nothing else (for an ncu launch list)."""
     import torch
 
     from paper_1607_03936_gb300 import build
@@ -399,12 +528,13 @@ def run_profile(args, cfg):
     n0 = wb.launch_count()
     _, _, res = solver.solve(f, rtol=RTOL)
     torch.cuda.synchronize()
-    print(json.dumps({"profile": WORKLOAD, "create_launches": n0, "solve_launches": wb.launch_count() - n0,
-                      "iters": res.iters, "rel_res": res.rel_res}), flush=True)
+    print(json.dumps({"profile": name, "precision": args.precision, "create_launches": n0,
+                      "solve_launches": wb.launch_count() - n0, "iters": res.iters, "rel_res": res.rel_res}),
+          flush=True)
     solver.close()
 
 
-def run_profile_apply(args, cfg):
+def run_profile_apply(args, name, cfg):
     """One fine-level A apply in FP64 and one in FP32 inside an NVTX range "prof" (after three
     warm-up applies each), for ncu --nvtx --nvtx-include prof/ captures of the operator kernels."""
     import torch
@@ -430,7 +560,7 @@ def run_profile_apply(args, cfg):
     s32.apply_A(u32)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    print(json.dumps({"profile_apply": WORKLOAD, "n_u": s64.n_u}), flush=True)
+    print(json.dumps({"profile_apply": name, "n_u": s64.n_u}), flush=True)
     s64.close()
     s32.close()
 
@@ -438,10 +568,11 @@ def run_profile_apply(args, cfg):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="one setup + solve of the workload and nothing else (for an ncu launch list)")
@@ -450,29 +581,34 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
-    from paper_1607_03936_gb300 import inputs
-    cfg = dict(inputs.WORKLOADS[WORKLOAD])
+    cfg = inputs_workload(args.workload)
+    name = args.workload
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
-        run_reference(args, cfg, rank, world)
+        run_reference(args, name, cfg, rank, world)
         return
     if args.profile_apply:
-        run_profile_apply(args, cfg)
+        run_profile_apply(args, name, cfg)
         return
     if args.profile:
-        run_profile(args, cfg)
+        run_profile(args, name, cfg)
         return
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
-    run_ours(args, cfg, rank, world)
+    R = run_ours(args, name, cfg, rank, world)
+    finish_ours(args, name, cfg, rank, world, R)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
 if __name__ == "__main__":
+    if "reference" in sys.argv:
+        # the oracle's timing is single-threaded: pin the BLAS pools before numpy loads
+        for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[_v] = "1"
     main()

@@ -203,6 +203,16 @@ int wbfbt_net_forward(wbfbt_net* net, const float* x, int batch, float* y);
 int wbfbt_net_loss_grad(wbfbt_net* net, const float* x, const float* target, int batch, double* loss,
                         float* grad);
 int wbfbt_net_adam_step(wbfbt_net* net, float lr);
+/* One convolution layer (0 = c1 ... 10 = c11) of the network in isolation, for per-layer
+ * checks of the tensor-core kernels: on an n^3 grid (any n >= 1, zero padding) and `batch`
+ * samples, x [batch][n^3][cin_layer] FP32 device (rounded to BF16 as the network stores its
+ * activations).  If y is not NULL: y [batch][n^3][cout_layer] = bias + sum_t sum_ci W x, with
+ * the layer's ReLU (c1..c10), in FP32 before the network's BF16 storage rounding.  If g and dW
+ * are not NULL: g [batch][n^3][cout_layer] FP32 (rounded to BF16) and dW [27][cin][cout] the
+ * weight gradient sum_{b,v} x[b][v + d_t][ci] g[b][v][co] accumulated in FP32.  The kernels are
+ * the ones forward and backward use.  Allocates its BF16 temporaries and synchronises. */
+int wbfbt_net_conv_layer(wbfbt_net* net, int layer, int n, int batch, const float* x, float* y, const float* g,
+                         float* dW);
 /* Checkpoint: parameters and Adam state, binary file with a header. */
 int wbfbt_net_save(wbfbt_net* net, const char* path);
 int wbfbt_net_load(wbfbt_net* net, const char* path);

@@ -66,7 +66,11 @@ extern "C" int wbfbt_apply_Kw_noalloc(const wbfbt_mesh* mesh, int k, const doubl
   if (!mesh || !mu_nodes || !p || !y || k < 2 || k > 4 || !(a >= 1.0)) return WBFBT_ERR_INVALID;
   if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !(mesh->lx > 0) || !(mesh->ly > 0) || !(mesh->lz > 0))
     return WBFBT_ERR_INVALID;
-  const long long nn = (long long)(k * mesh->nx + 1) * (k * mesh->ny + 1) * (k * mesh->nz + 1);
+  // node counts per axis in 64-bit arithmetic: each must fit the static scratch on its own
+  // before the product is formed, so no multiplication below can overflow
+  const long long NX = (long long)k * mesh->nx + 1, NY = (long long)k * mesh->ny + 1, NZ = (long long)k * mesh->nz + 1;
+  if (NX > kMaxNodes || NY > kMaxNodes || NZ > kMaxNodes) return WBFBT_ERR_INVALID;
+  const long long nn = NX * NY * NZ;
   if (nn > kMaxNodes) return WBFBT_ERR_INVALID;   // beyond the static scratch
   DeviceSlot* slot = nullptr;
   int st = ensure_slot(&slot);

@@ -721,6 +721,37 @@ int wbfbt_net_load(wbfbt_net* N, const char* path) {
   return cudaStreamSynchronize(N->st) == cudaSuccess ? WBFBT_OK : WBFBT_ERR_CUDA;
 }
 
+int wbfbt_net_conv_layer(wbfbt_net* N, int layer, int n, int batch, const float* x, float* y, const float* g,
+                         float* dW) {
+  if (!N || layer < 0 || layer > 10 || n < 1 || n > 1024 || batch < 1 || !x || (!y && !(g && dW)) ||
+      ((g == nullptr) != (dW == nullptr)))
+    return WBFBT_ERR_INVALID;
+  const Layer& l = N->L[layer];
+  const long long rows = (long long)n * n * n * batch;
+  bf16 *xb = nullptr, *gb = nullptr;
+  const int ldg = r16(l.cout);
+  int st = WBFBT_OK;
+  if (cudaMalloc(&xb, sizeof(bf16) * rows * l.kp) != cudaSuccess) return WBFBT_ERR_CUDA;
+  if (g && cudaMalloc(&gb, sizeof(bf16) * rows * ldg) != cudaSuccess) {
+    cudaFree(xb);
+    return WBFBT_ERR_CUDA;
+  }
+  st = net_guard(N, [&]() {
+    wb_launch(k_pack_input, nb(rows * l.kp, 256), 256, 0, N->st, rows, l.cin, l.kp, x, xb);
+    if (y)
+      conv(l.npf, n, batch, xb, l.kp, l.kp, l.Wt, N->theta + l.boff, layer < 10 ? 1 : 0, nullptr, 0, l.cout, nullptr,
+           0, y, l.cout, N->st);
+    if (g) {
+      wb_launch(k_pack_input, nb(rows * ldg, 256), 256, 0, N->st, rows, l.cout, ldg, g, gb);
+      wgrad(n, batch, xb, l.kp, l.cin, gb, ldg, l.cout, dW, N->st);
+    }
+    if (cudaStreamSynchronize(N->st) != cudaSuccess) throw 1;
+  });
+  cudaFree(xb);
+  if (gb) cudaFree(gb);
+  return st;
+}
+
 }  // extern "C"
 
 // Forward for the solver: x [n^3][cin] FP32 device -> y [n^3][cout] FP32 device (batch 1), on st.

@@ -1268,11 +1268,14 @@ int wbfbt_train_learned(wbfbt_ctx* c, const char* cfg_json, const char* out_path
       for (long long e = 0; e < E; ++e) mean += rh[e * np];
       mean /= (double)E;
       for (long long e = 0; e < E; ++e) rh[e * np] -= mean;   // constant mode removed
-      if (cudaMemcpyAsync(r, rh.data(), sizeof(double) * E * np, cudaMemcpyHostToDevice, us) != cudaSuccess)
-        return WBFBT_ERR_CUDA;
+      if (cudaMemcpyAsync(r, rh.data(), sizeof(double) * E * np, cudaMemcpyHostToDevice, us) != cudaSuccess) {
+        st = WBFBT_ERR_CUDA;   // leave through the restore below
+        break;
+      }
       const long long pidx = (long long)f * cfg.per_field + j;
       if ((st = wbfbt_learned_sample(c, 1, r, X + pidx * E * cin, Y + pidx * E * np)) != WBFBT_OK) break;
     }
+    if (st != WBFBT_OK) break;
   }
   const int st_restore = wbfbt_setup(c, mu0);   // the context's own viscosity again
   if (st != WBFBT_OK) return st;

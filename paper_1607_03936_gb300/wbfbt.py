@@ -19,6 +19,7 @@ from . import build as _build
 F64, F32 = 0, 1
 MIXED = 1
 ELEM_AUTO, ELEM_POINT, ELEM_ROW = 0, 1, 2   # k = 2 element kernels: by level size, per point, row segments
+OK, ERR_INVALID, ERR_CUDA, ERR_NONFINITE, ERR_BREAKDOWN, ERR_MAXIT, ERR_SETUP = 0, -1, -2, -3, -4, -5, -6
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "non-finite value", -4: "Krylov breakdown",
           -5: "iteration limit reached", -6: "setup failed"}
 
@@ -29,7 +30,7 @@ SYMBOLS = ["wbfbt_default_opts", "wbfbt_sinker_setup", "wbfbt_create", "wbfbt_se
            "wbfbt_net_num_params", "wbfbt_net_create", "wbfbt_net_set_params", "wbfbt_net_get_params",
            "wbfbt_net_param_count", "wbfbt_net_forward", "wbfbt_net_loss_grad", "wbfbt_net_adam_step",
            "wbfbt_net_save", "wbfbt_net_load", "wbfbt_net_destroy", "wbfbt_attach_net", "wbfbt_learned_sample",
-           "wbfbt_learned_stats", "wbfbt_load_learned", "wbfbt_train_learned"]
+           "wbfbt_learned_stats", "wbfbt_load_learned", "wbfbt_train_learned", "wbfbt_net_conv_layer"]
 NOALLOC_MAX_NODES = 1 << 19
 
 
@@ -95,6 +96,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.wbfbt_net_load.argtypes = [vp, ctypes.c_char_p]
     lib.wbfbt_net_destroy.argtypes = [vp]
     lib.wbfbt_net_destroy.restype = None
+    lib.wbfbt_net_conv_layer.argtypes = [vp, i, i, i, vp, vp, vp, vp]
     lib.wbfbt_attach_net.argtypes = [vp, vp, i, d]
     lib.wbfbt_learned_sample.argtypes = [vp, i, vp, vp, vp]
     lib.wbfbt_learned_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
@@ -349,6 +351,21 @@ class Net:
         _check(lib().wbfbt_net_loss_grad(self.h, _ptr(x), _ptr(target), batch, ctypes.byref(loss),
                                          _ptr(g) if g is not None else None), "wbfbt_net_loss_grad")
         return loss.value, g
+
+    def conv_layer(self, layer: int, n: int, x: torch.Tensor, g: torch.Tensor | None = None,
+                   cout: int | None = None, want_y: bool = True):
+        """One layer in isolation: (y [batch][n^3][cout], dW [27][cin][cout] or None)."""
+        x = x.contiguous()
+        batch = x.shape[0]
+        y = torch.empty((batch, n ** 3, cout), dtype=torch.float32, device=x.device) if want_y else None
+        dw = None
+        if g is not None:
+            g = g.contiguous()
+            dw = torch.empty((27, x.shape[-1], g.shape[-1]), dtype=torch.float32, device=x.device)
+        _check(lib().wbfbt_net_conv_layer(self.h, layer, n, batch, _ptr(x), _ptr(y) if y is not None else None,
+                                          _ptr(g) if g is not None else None, _ptr(dw) if dw is not None else None),
+               "wbfbt_net_conv_layer")
+        return y, dw
 
     def adam_step(self, lr: float):
         _check(lib().wbfbt_net_adam_step(self.h, lr), "wbfbt_net_adam_step")

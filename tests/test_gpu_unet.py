@@ -197,3 +197,94 @@ def test_trained_net_gain_is_measured(wb):
         gains.append((r["vcycle"]["iters"] - r["learned"]["iters"],
                       r["vcycle"]["solve_s"] - r["learned"]["solve_s"], r["learned"]["accepted"]))
     print("learned gain per held-out problem (iterations saved, seconds saved, accepted steps):", gains)
+
+
+# ------------------------------------------------------------------ full-size grid (32^3)
+# The learned-correction workload runs the U-Net on the 32^3 element grid of a 32^3 Q2 mesh
+# (cin = 1 + Np = 5, cout = Np = 4).  There the full-resolution layers (c1, c2, c9, c10, c11)
+# take the kernel form with one warp per 16-voxel tile and every output tile, and the weight
+# gradients sum over 32768 voxels; the 8^3 cases above never reach either.
+
+NF = 32
+
+
+def _bf16_exact(a):
+    """Round to the nearest BF16 value (kept in float32): the kernels store exactly these."""
+    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+
+
+def test_forward_full_size_matches_oracle(wb):
+    theta = inputs.unet_init_params(11, CIN, COUT)
+    x = np.random.default_rng(12).standard_normal((1, NF, NF, NF, CIN)).astype(np.float32)
+    net = wb.Net(CIN, COUT, NF)
+    net.set_params(torch.tensor(theta, device="cuda"))
+    y = net.forward(torch.tensor(x.reshape(1, -1, CIN), device="cuda")).cpu().numpy().reshape(NF, NF, NF, COUT)
+    ref, _ = unet.forward(theta.astype(np.float64), x[0].astype(np.float64), CIN, COUT)
+    assert rel(y, ref) < 3e-2
+
+
+def test_loss_and_gradients_full_size_match_oracle(wb):
+    theta = inputs.unet_init_params(13, CIN, COUT)
+    rng = np.random.default_rng(14)
+    x = rng.standard_normal((1, NF, NF, NF, CIN)).astype(np.float32)
+    t = rng.standard_normal((1, NF, NF, NF, COUT)).astype(np.float32)
+    net = wb.Net(CIN, COUT, NF)
+    net.set_params(torch.tensor(theta, device="cuda"))
+    loss, g = net.loss_grad(torch.tensor(x.reshape(1, -1, CIN), device="cuda"),
+                            torch.tensor(t.reshape(1, -1, COUT), device="cuda"))
+    ref_l, ref_g = unet.loss_and_grad(theta.astype(np.float64), x[0].astype(np.float64), t[0].astype(np.float64),
+                                      CIN, COUT)
+    assert abs(loss - ref_l) / ref_l < 2e-2
+    g = g.cpu().numpy()
+    assert rel(g, ref_g) < 8e-2
+    off = 0
+    for name, ci, co in unet.layer_shapes(CIN, COUT):
+        nw = 27 * ci * co
+        a, b = g[off:off + nw], ref_g[off:off + nw]
+        assert rel(a, b) < 0.2, name
+        assert a @ b / (np.linalg.norm(a) * np.linalg.norm(b)) > 0.98, name
+        off += nw + co
+
+
+# One layer at a time with BF16-exact inputs, weights and output gradients: the only error left
+# is the FP32 accumulation of the tensor cores, so the bound is a small multiple of 2^-23 times
+# the sum of the magnitudes of the terms, far below the BF16 bounds above.
+#   (layer, grid n, batch): c1 / c9 / c11 at 32^3 (one warp per voxel tile, all output tiles),
+#   c7 (96 input channels) at 16^3 with batch 5 (the same form), c3 at 16^3 and c6 at 8^3 with
+#   batch 1 (one warp per voxel tile and 8-channel output tile).
+LAYER_CASES = [(0, 32, 1), (8, 32, 1), (10, 32, 1), (6, 16, 5), (2, 16, 1), (5, 8, 1)]
+
+
+@pytest.mark.parametrize("layer,n,batch", LAYER_CASES)
+def test_single_layer_bf16_exact(wb, layer, n, batch):
+    shapes = unet.layer_shapes(CIN, COUT)
+    _, ci, co = shapes[layer]
+    theta = _bf16_exact(inputs.unet_init_params(20 + layer, CIN, COUT))
+    rng = np.random.default_rng(30 + layer)
+    nb = sum(27 * a * b + b for _, a, b in shapes[:layer])
+    theta[nb + 27 * ci * co: nb + 27 * ci * co + co] = rng.standard_normal(co).astype(np.float32) * 0.1
+    W = theta[nb: nb + 27 * ci * co].astype(np.float64).reshape(27, ci, co)
+    bias = theta[nb + 27 * ci * co: nb + 27 * ci * co + co].astype(np.float64)
+    x = _bf16_exact(rng.standard_normal((batch, n, n, n, ci)))
+    gy = _bf16_exact(rng.standard_normal((batch, n, n, n, co)))
+    net = wb.Net(CIN, COUT, NF)
+    net.set_params(torch.tensor(theta, device="cuda"))
+    y, dw = net.conv_layer(layer, n, torch.tensor(x.reshape(batch, -1, ci), device="cuda"),
+                           torch.tensor(gy.reshape(batch, -1, co), device="cuda"), cout=co)
+    y = y.cpu().numpy().reshape(batch, n, n, n, co)
+    dw = dw.cpu().numpy()
+    relu = layer < 10
+    ref_dw = np.zeros_like(W)
+    for b in range(batch):
+        xb = x[b].astype(np.float64)
+        ref = unet.conv3d(xb, W, bias)
+        mag = unet.conv3d(np.abs(xb), np.abs(W), np.abs(bias))
+        if relu:
+            ref = np.maximum(ref, 0.0)
+        assert np.all(np.abs(y[b] - ref) <= 1e-5 * mag + 1e-30), (layer, np.abs(y[b] - ref).max())
+        _, gw, _ = unet.conv3d_backward(xb, W, gy[b].astype(np.float64))
+        ref_dw += gw
+    assert rel(dw, ref_dw) < 1e-5
+    mag_dw = sum(unet.conv3d_backward(np.abs(x[b]).astype(np.float64), W, np.abs(gy[b]).astype(np.float64))[1]
+                 for b in range(batch))
+    assert np.all(np.abs(dw - ref_dw) <= 1e-4 * mag_dw + 1e-30), (layer, np.abs(dw - ref_dw).max())

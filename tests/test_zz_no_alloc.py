@@ -47,3 +47,12 @@ def test_noalloc_rejects_meshes_beyond_the_static_scratch(wb):
     p = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(wb.WbfbtError):
         wb.apply_Kw_noalloc(n, 2, mu, 1.0, p, p)
+
+
+def test_noalloc_rejects_axis_counts_that_overflow_int(wb):
+    """k*n+1 beyond 2^31 on an axis is rejected before any product is formed."""
+    mu = torch.ones(1, dtype=torch.float64, device="cuda")
+    p = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for n in (2 ** 30, 2 ** 31 - 1):
+        with pytest.raises(wb.WbfbtError):
+            wb.apply_Kw_noalloc(n, 2, mu, 1.0, p, p)
