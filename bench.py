@@ -398,7 +398,7 @@ def finish_ours(args, name, cfg, rank, world, R):
     # operator applies on the fine level, timed on the launching stream with CUDA events.  The
     # mixed context applies A in FP32 (the preconditioner's) and FP64 (the Krylov side's).
     x64 = torch.randn(solver.n_u, dtype=torch.float64, device=dev)
-    t_a32 = time_op(lambda: solver.apply_A(x64.float())) if R["precision"] == wb.MIXED else None
+    t_a32 = None
     xk = torch.randn(solver.n_u + solver.n_p, dtype=torch.float64, device=dev)
     t_k64 = time_op(lambda: solver.apply_K(xk))
     t_a64 = time_op(lambda: solver.apply_A(x64))
@@ -513,7 +513,8 @@ def inputs_workload(name: str) -> dict:
 
 
 def run_profile(args, name, cfg):
-    """One setup + solve of the workload and nothing else (for an ncu launch list)."""
+    """One solve of the workload inside an NVTX range "prof" (after the context's creation and
+    setup), for an ncu launch list of the solve."""
     import torch
 
     from paper_1607_03936_gb300 import build
@@ -525,9 +526,12 @@ def run_profile(args, name, cfg):
     centres = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
     mu, f = wb.sinker_setup(n, k, centres, cfg["omega"], cfg["delta"], cfg["dr"])
     solver = wb.Solver(n, k, mu, precision=wb.MIXED if args.precision == "mixed" else wb.F64)
+    torch.cuda.synchronize()
     n0 = wb.launch_count()
+    torch.cuda.nvtx.range_push("prof")
     _, _, res = solver.solve(f, rtol=RTOL)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     print(json.dumps({"profile": name, "precision": args.precision, "create_launches": n0,
                       "solve_launches": wb.launch_count() - n0, "iters": res.iters, "rel_res": res.rel_res}),
           flush=True)
@@ -565,6 +569,64 @@ def run_profile_apply(args, name, cfg):
     s32.close()
 
 
+SWEEP_SINKERS = (1, 4, 8, 12, 16, 20, 24, 28)
+SWEEP_DR = (1e4, 1e6, 1e8, 1e10)
+
+
+def run_sweep(args):
+    """Iteration-count sweeps in the style of the paper's tables, one JSON line per solve.
+
+    robustness (Sec. 4, Table 1): w-BFBT against the inverse-viscosity pressure mass (lumped,
+      Eq. lumping, and its diagonal) over sinker counts x dynamic ratios, n^3 Q2, omega 0.1,
+      delta 200, seeded centres;
+    amplification (Sec. 5, Table 2): w-BFBT with a_l = 1 and a_r in {1, 2, 4, 8, 16, 32};
+    order (Sec. 7, Table 3b): w-BFBT for k = 2, 3, 4 on the same mesh, a_r by the Table 3 rule.
+    """
+    import torch
+
+    from paper_1607_03936_gb300 import build
+    build.build()
+    from paper_1607_03936_gb300 import inputs
+    from paper_1607_03936_gb300 import wbfbt as wb
+
+    prec = wb.MIXED if args.precision == "mixed" else wb.F64
+    n = args.sweep_n
+
+    def solve(k, ns, dr, schur=wb.SCHUR_WBFBT, a_r=0.0, seed=0):
+        c = inputs.sinker_centres(seed, ns)
+        mu, f = wb.sinker_setup(n, k, c, 0.1, 200.0, dr)
+        s = wb.Solver(n, k, mu, precision=prec, schur=schur, a_r=a_r)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, res = s.solve(f, rtol=RTOL, maxit=args.sweep_maxit)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        s.close()
+        return {"iters": res.iters, "converged": res.status == 0, "rel_res": res.rel_res, "solve_s": dt}
+
+    names = {wb.SCHUR_WBFBT: "w-BFBT", wb.SCHUR_MASS: "M_p(1/mu) lumped", wb.SCHUR_MASS_DIAG: "M_p(1/mu) diagonal"}
+    base = {"mesh": f"{n}^3", "precision": args.precision, "omega": 0.1, "delta": 200.0, "rtol": RTOL,
+            "maxit": args.sweep_maxit}
+    if args.sweep == "robustness":
+        for ns in SWEEP_SINKERS:
+            for dr in SWEEP_DR:
+                for schur in (wb.SCHUR_WBFBT, wb.SCHUR_MASS_DIAG, wb.SCHUR_MASS):
+                    r = solve(2, ns, dr, schur)
+                    print(json.dumps({"sweep": "robustness", **base, "k": 2, "sinkers": ns, "dr": dr,
+                                      "schur": names[schur], **r}), flush=True)
+    elif args.sweep == "amplification":
+        for k in (2, 3, 4):
+            for a_r in (1.0, 2.0, 4.0, 8.0, 16.0, 32.0):
+                r = solve(k, 16, 1e6, a_r=a_r)
+                print(json.dumps({"sweep": "amplification", **base, "k": k, "sinkers": 16, "dr": 1e6, "a_l": 1.0,
+                                  "a_r": a_r, **r}), flush=True)
+    elif args.sweep == "order":
+        for k in (2, 3, 4):
+            r = solve(k, 16, 1e6)
+            print(json.dumps({"sweep": "order", **base, "k": k, "sinkers": 16, "dr": 1e6,
+                              "a_r": max(1.0, n / 16.0 * 2.0 ** (k - 2)), **r}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -578,7 +640,14 @@ def main():
                     help="one setup + solve of the workload and nothing else (for an ncu launch list)")
     ap.add_argument("--profile-apply", action="store_true",
                     help="one FP64 and one FP32 A apply in an NVTX range 'prof' (for ncu --set full)")
+    ap.add_argument("--sweep", choices=["robustness", "amplification", "order"],
+                    help="iteration-count sweeps in the style of Tables 1, 2 and 3b (many JSON lines)")
+    ap.add_argument("--sweep-n", type=int, default=32)
+    ap.add_argument("--sweep-maxit", type=int, default=2000)
     args = ap.parse_args()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     cfg = inputs_workload(args.workload)

@@ -72,7 +72,25 @@ typedef struct {
                                       thread per point; WBFBT_ELEM_POINT / WBFBT_ELEM_ROW
                                       force either (and the three- or one-pass k = 2
                                       restriction)                                          */
+    int schur;                     /* Schur-complement approximation S~ in Eq. precond-stokes:
+                                      WBFBT_SCHUR_WBFBT (default) w-BFBT of Eq. wbfbt with
+                                      multigrid inner solves; WBFBT_SCHUR_MASS the lumped
+                                      inverse-viscosity pressure mass M~_p(1/mu) of Eq. lumping
+                                      (the baseline of Sec. 4), lumped in the element basis of
+                                      non-negative monomials ((1+xi)/2)^a ((1+eta)/2)^b
+                                      ((1+zeta)/2)^c; WBFBT_SCHUR_MASS_DIAG the diagonal of
+                                      M_p(1/mu) in the pressure basis above                 */
+    int arnoldi_precision;         /* precision of the K apply inside the Arnoldi process:
+                                      WBFBT_F64 (default; the exact Arnoldi relation) or, for
+                                      a WBFBT_MIXED context only, WBFBT_F32 (the fused K apply
+                                      on the FP32 preconditioner output); the true residual
+                                      F - K x at every restart and at exit is FP64 either way,
+                                      and convergence is declared on it                     */
 } wbfbt_opts;
+
+#define WBFBT_SCHUR_WBFBT 0
+#define WBFBT_SCHUR_MASS 1
+#define WBFBT_SCHUR_MASS_DIAG 2
 
 #define WBFBT_ELEM_AUTO 0
 #define WBFBT_ELEM_POINT 1

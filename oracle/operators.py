@@ -247,3 +247,43 @@ def sampled_apply_A(mesh: Mesh, mu_nodes: np.ndarray, u: np.ndarray, nodes: np.n
                     for c in range(3):
                         out[r, c] += ye[c * n3 + q]
     return out
+
+
+def nonneg_pressure_basis_at_points(k: int, pts: np.ndarray) -> np.ndarray:
+    """phi'_j = prod_d ((1 + xi_d) / 2)^(e_jd) at reference points, same exponents as the solver's
+    basis: (n_pts, Np).  Non-negative on the element, so each int_e phi'_j / mu > 0."""
+    s = 0.5 * (1.0 + pts)
+    return np.stack([s[:, 0] ** a * s[:, 1] ** b * s[:, 2] ** c for a, b, c in gll.pressure_exponents(k)], axis=-1)
+
+
+def lumped_mass_schur_inverse(mesh: Mesh, mu_nodes: np.ndarray) -> sp.csr_matrix:
+    """Inverse of the lumped inverse-viscosity pressure mass (Sec. 1.3, Eq. lumping), block diagonal.
+
+    Steps, per element, in the non-negative basis {phi'_j}:
+      M'_e(1/mu) = Phi'^T diag(W_q |J| / mu_q) Phi'       (the pressure mass weighted by 1/mu),
+      1'        = coefficients of the constant function 1 in {phi'_j},
+      M~'_e     = diag(M'_e(1/mu) 1')                    (Eq. lumping).
+    The solver's coefficients p in the centred monomial basis {psi_m} satisfy p = T p' with
+    Psi T = Phi' (T found by solving that linear system), so the approximation's inverse in the
+    solver's basis is T M~'_e^-1 T^T.  Returned as a sparse (n_p x n_p) matrix.
+    """
+    psi = gll.pressure_basis_at_points(mesh.k, mesh.ref_pts)          # (n3, Np)
+    phi = nonneg_pressure_basis_at_points(mesh.k, mesh.ref_pts)       # (n3, Np)
+    T = np.linalg.lstsq(psi, phi, rcond=None)[0]                       # psi @ T = phi
+    one = np.linalg.lstsq(phi, np.ones(phi.shape[0]), rcond=None)[0]   # phi @ one = 1
+    mu_q = point_values(mesh, mu_nodes)                                # (n_elem, n3)
+    blocks = []
+    for e in range(mesh.n_elem):
+        Me = phi.T @ ((mesh.W * mesh.detJ / mu_q[e])[:, None] * phi)
+        d = Me @ one
+        blocks.append(T @ np.diag(1.0 / d) @ T.T)
+    return sp.csr_matrix(sp.block_diag([sp.csr_matrix(b) for b in blocks], format="csr"))
+
+
+def diag_mass_schur_inverse(mesh: Mesh, mu_nodes: np.ndarray) -> sp.csr_matrix:
+    """Inverse of the diagonal of the inverse-viscosity pressure mass M_p(1/mu) (Sec. 1.3) in the
+    solver's centred monomial basis: diag(1 / int_e psi_m^2 / mu) per element, sparse (n_p x n_p)."""
+    psi = gll.pressure_basis_at_points(mesh.k, mesh.ref_pts)
+    mu_q = point_values(mesh, mu_nodes)
+    d = np.stack([np.diag(psi.T @ ((mesh.W * mesh.detJ / mu_q[e])[:, None] * psi)) for e in range(mesh.n_elem)])
+    return sp.diags(1.0 / d.ravel()).tocsr()

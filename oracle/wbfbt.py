@@ -44,6 +44,8 @@ class Options:
     restart: int = 50
     schur_sign: float = -1.0
     mode: str = "vcycle"
+    schur: str = "wbfbt"       # "wbfbt" (Eq. wbfbt), "mass" (lumped M_p(1/mu), Eq. lumping),
+                               # "mass_diag" (the diagonal of M_p(1/mu))
 
 
 class StokesProblem:
@@ -115,11 +117,27 @@ class WBFBT:
         return op.project_pressure(m, self.Kl_inv(z))
 
 
+class MassSchur:
+    """S~^-1 = M~_p(1/mu)^-1, the lumped inverse-viscosity pressure mass of Eq. lumping (the
+    Schur approximation w-BFBT is compared against in Sec. 4), with the same projections."""
+
+    def __init__(self, prob: StokesProblem, diag: bool = False):
+        self.prob = prob
+        if diag:
+            self.Sinv = op.diag_mass_schur_inverse(prob.mesh, prob.mu)
+        else:
+            self.Sinv = op.lumped_mass_schur_inverse(prob.mesh, prob.mu)
+
+    def apply(self, r: np.ndarray) -> np.ndarray:
+        m = self.prob.mesh
+        return op.project_pressure(m, self.Sinv @ op.project_pressure(m, r))
+
+
 class BlockPreconditioner:
     """[A~ B^T; 0 s S~]^-1: y_p = s S~^-1 r_p, y_u = A~^-1 (r_u - B^T y_p)."""
 
     def __init__(self, prob: StokesProblem, mode: str = "vcycle", schur_sign: float = -1.0,
-                 schur_inv=None, A_inv=None):
+                 schur_inv=None, A_inv=None, schur: str = "wbfbt"):
         self.prob = prob
         self.sign = schur_sign
         m = prob.mesh
@@ -137,7 +155,12 @@ class BlockPreconditioner:
         else:
             self.A_levels = mg.build_hierarchy(m, op.point_values(m, prob.mu), vector=True)
             self.A_inv = lambda b: mg.vcycle(self.A_levels, b)
-        self.S_inv = schur_inv if schur_inv is not None else WBFBT(prob, mode).apply
+        if schur_inv is not None:
+            self.S_inv = schur_inv
+        elif schur in ("mass", "mass_diag"):
+            self.S_inv = MassSchur(prob, diag=schur == "mass_diag").apply
+        else:
+            self.S_inv = WBFBT(prob, mode).apply
 
     def apply(self, v: np.ndarray) -> np.ndarray:
         nu = self.prob.nu
@@ -156,7 +179,7 @@ def sinker_problem(mesh: Mesh, centres, omega, delta, dr, beta=10.0):
 def solve(mesh: Mesh, mu_nodes, f_nodes, opts: Options = Options(), rtol=1e-6, maxit=1000, history=None):
     """FGMRES(restart) solve of the Stokes system; returns (u, p, iters, rel_res, prob)."""
     prob = StokesProblem(mesh, mu_nodes, opts.a_l, opts.a_r)
-    pc = BlockPreconditioner(prob, opts.mode, opts.schur_sign)
+    pc = BlockPreconditioner(prob, opts.mode, opts.schur_sign, schur=opts.schur)
     F = np.concatenate([op.load_vector(mesh, f_nodes), np.zeros(mesh.n_p)])
     x, its, rel = krylov.fgmres(prob.apply_K, pc.apply, F, rtol=rtol, restart=opts.restart,
                                 maxit=maxit, history=history)

@@ -95,3 +95,11 @@ cudaError_t launch_mask_boundary(const Grid& g, int ncomp, T* v, cudaStream_t st
 // Power-iteration start vector: counter-based SplitMix64 uniforms in [-0.5, 0.5).
 template <typename T>
 cudaError_t launch_splitmix_start(long long n, unsigned long long seed, T* v, cudaStream_t st);
+
+// Inverse-viscosity lumped pressure mass (Sec. 1.3, Eq. lumping), the Schur baseline of Sec. 4:
+// S[e] = T diag(1/d') T^T per element ([ne][Np][Np], FP64) from nodal mu, or with diag = 1 the
+// inverse diagonal of M_p(1/mu) in the centred basis; block apply y = S r.
+cudaError_t launch_mass_lumped_inv(const Grid& g, int k, const RefTables* dtab, const double* mu, int diag,
+                                   double* S, cudaStream_t st);
+template <typename T>
+cudaError_t launch_block_apply(long long ne, int np, const T* S, const T* r, T* y, cudaStream_t st);

@@ -104,6 +104,7 @@ struct Precond {
   T* Ye = nullptr;                                      // element-pass outputs [ne][3][n^3] (finest level)
   T* Kst[2] = {nullptr, nullptr};                       // assembled K_w stencils (k <= 3), w_l and w_r
   T* kwin = nullptr;                                    // copy of a K_w input its epilogue overwrites
+  T* Mp = nullptr;                                      // lumped M_p(1/mu)^-1 blocks [ne][Np][Np] (schur = MASS)
   double *c0[2] = {nullptr, nullptr}, *dK64[2] = {nullptr, nullptr};
 };
 
@@ -135,6 +136,7 @@ struct wbfbt_ctx {
   float* mu32 = nullptr;
   double* part = nullptr;   // reduction partials
   double* kwbref = nullptr; // reference divergence matrix for the K_w assembly (k <= 3)
+  double* Mp64 = nullptr;   // lumped M_p(1/mu)^-1 blocks in FP64 (schur = MASS)
   double* dsc = nullptr;    // device scalars (64)
   int* dflag = nullptr;
   Precond<double> P64;
@@ -449,11 +451,17 @@ void project(wbfbt_ctx* c, const T* src, T* dst) {
   CK(launch_project_pressure<T>(c->g.ne, c->NP, src, dst, c->part, c->dsc + 1, c->st));
 }
 
-// y = S~^-1 r (Eq. wbfbt), r and y pressure vectors.
+// y = S~^-1 r (Eq. wbfbt), r and y pressure vectors; with schur = MASS / MASS_DIAG the
+// inverse-viscosity pressure mass (Eq. lumping, or its diagonal) instead.
 template <typename T>
 void schur_inv(wbfbt_ctx* c, const T* r, T* y) {
   Precond<T>& P = prec<T>(c);
   project<T>(c, r, P.sr);
+  if (c->opt.schur != WBFBT_SCHUR_WBFBT) {
+    CK(launch_block_apply<T>(c->g.ne, c->NP, P.Mp, P.sr, P.sy, c->st));
+    project<T>(c, P.sy, y);
+    return;
+  }
   kinv_any<T>(c, 1, P.sr, P.sy);
   // middle factor B C^-1 A D^-1 B^T y, each diagonal scaling fused into the preceding node pass
   apply_BT_epi<T>(c, P.sy, epi_scale<T>(P.sv1, P.dinvw));
@@ -697,6 +705,18 @@ void build_precond(wbfbt_ctx* c) {
     auto M = [&](const T* p, const Epi<T>& e) { op_Kw<T>(c, wi, p, e); };
     P.lamKw[wi] = power_lambda<T>(c, M, (long long)np, P.dKw[wi], P.px, P.pd, nullptr);
   }
+  if (c->opt.schur != WBFBT_SCHUR_WBFBT) {
+    const size_t nb = (size_t)g.ne * c->NP * c->NP;
+    c->pool.ensure(c->Mp64, nb);
+    CK(launch_mass_lumped_inv(g, c->k, c->dtab, c->mu64, c->opt.schur == WBFBT_SCHUR_MASS_DIAG ? 1 : 0,
+                              c->Mp64, c->st));
+    if (std::is_same<T, double>::value) {
+      P.Mp = reinterpret_cast<T*>(c->Mp64);
+    } else {
+      c->pool.ensure(P.Mp, nb);
+      CK((launch_cast<double, T>((long long)nb, c->Mp64, P.Mp, c->st)));
+    }
+  }
   run_dense_jobs(c);
 }
 
@@ -791,6 +811,24 @@ void precond_graphed(wbfbt_ctx* c, const double* v, double* z) {
   CK((launch_cast<T, double>(c->ntot, P.vout, z, c->st)));
 }
 
+// w = K z inside the Arnoldi process.  FP64 by default (the exact Arnoldi relation).  With the
+// mixed-precision option arnoldi_precision = WBFBT_F32 the fused K apply runs in FP32 on the
+// preconditioner's FP32 output (z_j is exactly that vector widened), so the FP64 element pass
+// leaves the iteration; the true residual F - K x at every restart and at exit stays FP64, and
+// the solve ends only when that residual meets the tolerance.
+void apply_K_arnoldi(wbfbt_ctx* c, const double* z, double* w) {
+  if (!(c->mixed && c->opt.arnoldi_precision == WBFBT_F32)) {
+    apply_K64(c, z, w);
+    return;
+  }
+  Precond<float>& P = c->P32;
+  const long long nu = 3LL * c->g.nn;
+  CK(launch_elem_stokes<float>(c->g, c->k, c->ot32, OP_A | OP_BT | OP_B, P.vout, nullptr, P.vout + nu, c->mu32, 1,
+                               c->Ye32, epi_store<float>(P.vin + nu), c->st));
+  CK(launch_gather<float>(c->g, c->k, 3, 1, c->Ye32, epi_store<float>(P.vin), c->st));
+  CK((launch_cast<float, double>(c->ntot, P.vin, w, c->st)));
+}
+
 void precond_any(wbfbt_ctx* c, const double* v, double* z) {
   if (c->opt.use_graphs && c->net == nullptr) {
     if (c->mixed)
@@ -837,7 +875,7 @@ int fgmres(wbfbt_ctx* c, double rtol, int maxit, int* iters, double* relres) {
       double* vj = c->V + (size_t)j * n;
       double* zj = c->Z + (size_t)j * n;
       precond_any(c, vj, zj);
-      apply_K64(c, zj, c->w);
+      apply_K_arnoldi(c, zj, c->w);
       // CGS2: h = V^T w, w -= V h, twice
       double* h1 = c->hdev;
       double* h2 = c->hdev + (m + 1);
@@ -964,6 +1002,8 @@ void wbfbt_default_opts(wbfbt_opts* o) {
   o->schur_sign = -1;
   o->use_graphs = 1;
   o->elem_kernels = WBFBT_ELEM_AUTO;
+  o->schur = WBFBT_SCHUR_WBFBT;
+  o->arnoldi_precision = WBFBT_F64;
 }
 
 const char* wbfbt_status_string(int s) {
@@ -1004,7 +1044,10 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
   if (c->opt.restart < 1 || c->opt.restart > 1000 || c->opt.cheb_degree < 1 || c->opt.cheb_degree > 16 ||
       c->opt.a_l < 1.0 || (c->opt.a_r > 0 && c->opt.a_r < 1.0) ||
       (c->opt.precision != WBFBT_F64 && c->opt.precision != WBFBT_MIXED) || c->opt.mg_min_n < 1 ||
-      c->opt.elem_kernels < WBFBT_ELEM_AUTO || c->opt.elem_kernels > WBFBT_ELEM_ROW)
+      c->opt.elem_kernels < WBFBT_ELEM_AUTO || c->opt.elem_kernels > WBFBT_ELEM_ROW ||
+      c->opt.schur < WBFBT_SCHUR_WBFBT || c->opt.schur > WBFBT_SCHUR_MASS_DIAG ||
+      (c->opt.arnoldi_precision != WBFBT_F64 && c->opt.arnoldi_precision != WBFBT_F32) ||
+      (c->opt.arnoldi_precision == WBFBT_F32 && c->opt.precision != WBFBT_MIXED))
     return WBFBT_ERR_INVALID;
   if (c->opt.schur_sign >= 0) c->opt.schur_sign = 1; else c->opt.schur_sign = -1;
   c->ust = (cudaStream_t)stream;

@@ -19,6 +19,7 @@ from . import build as _build
 F64, F32 = 0, 1
 MIXED = 1
 ELEM_AUTO, ELEM_POINT, ELEM_ROW = 0, 1, 2   # k = 2 element kernels: by level size, per point, row segments
+SCHUR_WBFBT, SCHUR_MASS, SCHUR_MASS_DIAG = 0, 1, 2   # S~: w-BFBT (Eq. wbfbt), lumped M_p(1/mu), diag M_p(1/mu)
 OK, ERR_INVALID, ERR_CUDA, ERR_NONFINITE, ERR_BREAKDOWN, ERR_MAXIT, ERR_SETUP = 0, -1, -2, -3, -4, -5, -6
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "non-finite value", -4: "Krylov breakdown",
           -5: "iteration limit reached", -6: "setup failed"}
@@ -49,7 +50,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("a_l", ctypes.c_double), ("a_r", ctypes.c_double), ("restart", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("mg_min_n", ctypes.c_int), ("precision", ctypes.c_int),
                 ("schur_sign", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("elem_kernels", ctypes.c_int)]
+                ("elem_kernels", ctypes.c_int), ("schur", ctypes.c_int), ("arnoldi_precision", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -192,13 +193,16 @@ class Solver:
     def __init__(self, nx: int, k: int, mu: torch.Tensor, ny: int | None = None, nz: int | None = None,
                  lengths=(1.0, 1.0, 1.0), a_l: float = 1.0, a_r: float = 0.0, restart: int = 50,
                  cheb_degree: int = 3, mg_min_n: int = 4, precision: int = F64, schur_sign: int = -1,
-                 use_graphs: bool = True, elem_kernels: int = 0):
+                 use_graphs: bool = True, elem_kernels: int = 0, schur: int = SCHUR_WBFBT,
+                 arnoldi_precision: int = F64):
         self.nx, self.ny, self.nz, self.k = nx, ny or nx, nz or nx, k
         self.mesh = Mesh(self.nx, self.ny, self.nz, *lengths)
         o = default_opts()
         o.a_l, o.a_r, o.restart, o.cheb_degree = a_l, a_r, restart, cheb_degree
         o.mg_min_n, o.precision, o.schur_sign, o.use_graphs = mg_min_n, precision, schur_sign, int(use_graphs)
         o.elem_kernels = elem_kernels
+        o.schur = schur
+        o.arnoldi_precision = arnoldi_precision
         self.opts = o
         self.precision = precision
         self._mu = mu.contiguous()

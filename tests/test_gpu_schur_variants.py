@@ -1,0 +1,78 @@
+"""GPU parity of the inverse-viscosity pressure-mass Schur approximations (Sec. 1.3, Eq. lumping),
+the baseline that Sec. 4 / Table 1 compares w-BFBT against, through the C ABI.
+
+Tolerances as elsewhere: FP64 applies 1e-12 relative, FP32 2e-5; FP64 solves iterations +-1
+and solution 1e-10.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mesh as M
+from oracle import operators as op
+from oracle import wbfbt as W
+from paper_1607_03936_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_03936_gb300 import build
+    build.build()
+    from paper_1607_03936_gb300 import wbfbt
+    return wbfbt
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def N(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def problem(n, k, dr, ns, lengths=(1.0, 1.0, 1.0), ny=None, nz=None):
+    m = M.Mesh(n, ny or n, nz or n, k, *lengths)
+    c = inputs.sinker_centres(2, ns)
+    mu, f = W.sinker_problem(m, c, 0.1, 200.0, dr)
+    return m, mu, f
+
+
+VARIANTS = [("mass", 1), ("mass_diag", 2)]
+
+
+@pytest.mark.parametrize("name,code", VARIANTS)
+@pytest.mark.parametrize("shape", [(4, 2, (1.0, 1.0, 1.0), 3, 5), (3, 3, (1.0, 0.8, 1.2), 2, 2), (2, 4, (1.0, 1.0, 1.0), 2, 2)])
+def test_mass_schur_apply_matches_oracle(wb, name, code, shape):
+    n, k, L, ny, nz = shape
+    m, mu, _ = problem(n, k, 1e4, 4, L, ny, nz)
+    mu_t = torch.tensor(mu, device="cuda")
+    prob = W.StokesProblem(m, mu)
+    ref = W.MassSchur(prob, diag=name == "mass_diag")
+    r = np.random.default_rng(3).standard_normal(m.n_p)
+    s64 = wb.Solver(n, k, mu_t, ny=ny, nz=nz, lengths=L, schur=code)
+    assert rel(N(s64.apply_schur_inv(torch.tensor(r, device="cuda"))), ref.apply(r)) < 1e-12
+    s32 = wb.Solver(n, k, mu_t, ny=ny, nz=nz, lengths=L, schur=code, precision=wb.MIXED)
+    y32 = N(s32.apply_schur_inv(torch.tensor(r, dtype=torch.float32, device="cuda")))
+    assert rel(y32, ref.apply(r.astype(np.float32).astype(np.float64))) < 2e-5
+
+
+@pytest.mark.parametrize("name,code", VARIANTS)
+def test_mass_schur_solve_matches_oracle(wb, name, code):
+    m, mu, f = problem(8, 2, 1e2, 4)
+    uo, po, its, relo, _ = W.solve(m, mu, f, W.Options(schur=name), maxit=2000)
+    s = wb.Solver(8, 2, torch.tensor(mu, device="cuda"), schur=code)
+    u, p, res = s.solve(torch.tensor(f.T.ravel(), device="cuda"), maxit=2000)
+    assert res.status == 0 and abs(res.iters - its) <= 1, (res.iters, its)
+    assert rel(N(u), uo) < 1e-10 and rel(N(p), po) < 1e-10
+
+
+def test_invalid_schur_option_rejected(wb):
+    m, mu, _ = problem(2, 2, 1e2, 1)
+    with pytest.raises(wb.WbfbtError):
+        wb.Solver(2, 2, torch.tensor(mu, device="cuda"), schur=3)
