@@ -88,16 +88,40 @@ def test_config_b_mixed_solve_matches_oracle(wb, config_b):
     assert eu < 1e-6 and ep < 1e-6
 
 
+def test_config_b_mixed_fp32_arnoldi_matches_oracle(wb, config_b):
+    """Mixed precision with the K apply inside the Arnoldi process in FP32 as well: the FP64 true
+    residual decides convergence (<= 1e-6).  The FP32 error of the Arnoldi relation moves the
+    iterate within the set of vectors with that residual, so the solution is held to 1e-5 of the
+    oracle here (measured 1.5e-6), not to the 1e-6 of the default mixed form."""
+    cfg = inputs.WORKLOADS["32^3-Q2-S24-DR1e6"]
+    s, _, f_g = gpu_config(wb, cfg, config_b["centres"], precision=wb.MIXED, arnoldi_precision=wb.F32)
+    u, p, res = s.solve(f_g)
+    assert res.status == 0 and res.rel_res <= 1e-6
+    eu, ep = rel(N(u), config_b["u"]), rel(N(p), config_b["p"])
+    print(f"config B mixed, FP32 Arnoldi: its gpu {res.iters} oracle {config_b['its']}; rel err u {eu:.2e} p {ep:.2e}")
+    assert abs(res.iters - config_b["its"]) <= 3
+    assert eu < 1e-5 and ep < 1e-5
+
+
+def test_fp32_arnoldi_needs_a_mixed_context(wb):
+    s, mu_g, _ = small(wb)
+    with pytest.raises(wb.WbfbtError):
+        wb.Solver(4, 2, mu_g, arnoldi_precision=wb.F32)
+
+
 @pytest.mark.parametrize("n,k,dr,ns", [(8, 2, 1e6, 8), (6, 3, 1e4, 4)])
 def test_small_mixed_solve_matches_oracle(wb, n, k, dr, ns):
     """Mixed precision on 8^3 Q2 DR 1e6 and 6^3 Q3 DR 1e4 against the oracle's FP64 solve (on meshes this
     coarse, DR 1e8 sinkers of width 0.1 are unresolved and neither side converges in 1000 iterations)."""
     cfg = dict(n=n, k=k, n_sinkers=ns, omega=0.1, delta=200.0, dr=dr, seed=0)
     o = oracle_solve(cfg)
-    s, _, f_g = gpu_config(wb, cfg, o["centres"], precision=wb.MIXED)
-    u, p, res = s.solve(f_g)
-    assert res.status == 0 and abs(res.iters - o["its"]) <= 3, (res.iters, o["its"])
-    assert rel(N(u), o["u"]) < 1e-6 and rel(N(p), o["p"]) < 1e-6
+    for arn in (wb.F64, wb.F32):
+        s, _, f_g = gpu_config(wb, cfg, o["centres"], precision=wb.MIXED, arnoldi_precision=arn)
+        u, p, res = s.solve(f_g)
+        assert res.status == 0 and res.rel_res <= 1e-6
+        assert abs(res.iters - o["its"]) <= 3, (arn, res.iters, o["its"])
+        tol = 1e-6 if arn == wb.F64 else 1e-5
+        assert rel(N(u), o["u"]) < tol and rel(N(p), o["p"]) < tol
 
 
 # ------------------------------------------------------------------ failure statuses
