@@ -410,15 +410,17 @@ def finish_ours(args, name, cfg, rank, world, R):
     peak64 = fp64_alu_peak_tflops(clk["sm_mhz"] if clk else None)
     hbm, hbm_note = hbm_peak_gbs()
     flops_a = a_apply_flops_per_elem(k) * n_elem
-    # fused Stokes K apply: A (36n^4+30n^3) plus B and B^T (each 3 x 2 n^3 Np for the basis
-    # contractions after the 3 x 2n^4 derivative sums, which A shares)
+    # fused Stokes K apply: A (36n^4+30n^3) plus what B and B^T add at each of the n^3 points
+    # (their derivative sums are A's): B: the divergence (2 adds), its weight (1) and Np
+    # basis FMAs (2 Np); B^T: the pressure at the point (2 Np), its weight (1) and the
+    # three diagonal stress updates (3)
     np_e = k * (k + 1) * (k + 2) // 6
-    flops_k = flops_a + 2 * 3 * 2 * (k + 1) ** 3 * np_e * n_elem
+    flops_k = flops_a + (k + 1) ** 3 * (4 * np_e + 7) * n_elem
     roof64 = {"bound": "alu", "achieved": flops_k / t_k64 / 1e12, "peak": peak64, "unit": "TFLOP/s",
               "frac": flops_k / t_k64 / 1e12 / peak64, "traffic": traffic_for("apply_K_f64"),
               "kernel": "k_q2_elem64<OP_A|OP_BT|OP_B,iso> + k_q2_gather<double,3,STORE> (the FP64 Arnoldi K apply)",
-              "per_launch": ("one fine-level K = [A B^T; B 0] apply: (36n^4+30n^3 + 12 n^3 Np) flops per element "
-                             f"x {n_elem} elements"),
+              "per_launch": ("one fine-level K = [A B^T; B 0] apply: (36n^4 + 30n^3 + n^3 (4 Np + 7)) flops per "
+                             f"element x {n_elem} elements"),
               "peak_note": "FP64 ALU peak from 152 SMs x 2 DFMA/clk x 2 flop at the sampled SM clock"}
     bytes32 = a_apply_bytes_per_node(4) * n_nodes
     roof32 = None
@@ -539,8 +541,10 @@ def run_profile(args, name, cfg):
 
 
 def run_profile_apply(args, name, cfg):
-    """One fine-level A apply in FP64 and one in FP32 inside an NVTX range "prof" (after three
-    warm-up applies each), for ncu --nvtx --nvtx-include prof/ captures of the operator kernels."""
+    """One fine-level A apply in FP64, one in FP32 and one fused FP64 K apply inside an NVTX range
+    "prof" (after three warm-up applies each), for ncu --nvtx --nvtx-include prof/ captures of the
+    operator kernels (launch order: FP64 A element + node pass, FP32 A element + node pass, FP64 K
+    element + node pass)."""
     import torch
 
     from paper_1607_03936_gb300 import build
@@ -555,13 +559,17 @@ def run_profile_apply(args, name, cfg):
     s32 = wb.Solver(n, k, mu, precision=wb.MIXED, restart=5)
     u64 = torch.randn(s64.n_u, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
     u32 = u64.float()
+    x64 = torch.randn(s64.n_u + s64.n_p, dtype=torch.float64, device="cuda",
+                      generator=torch.Generator("cuda").manual_seed(1))
     for _ in range(3):
         s64.apply_A(u64)
         s32.apply_A(u32)
+        s64.apply_K(x64)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("prof")
     s64.apply_A(u64)
     s32.apply_A(u32)
+    s64.apply_K(x64)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     print(json.dumps({"profile_apply": name, "n_u": s64.n_u}), flush=True)
@@ -576,11 +584,15 @@ SWEEP_DR = (1e4, 1e6, 1e8, 1e10)
 def run_sweep(args):
     """Iteration-count sweeps in the style of the paper's tables, one JSON line per solve.
 
-    robustness (Sec. 4, Table 1): w-BFBT against the inverse-viscosity pressure mass (lumped,
-      Eq. lumping, and its diagonal) over sinker counts x dynamic ratios, n^3 Q2, omega 0.1,
-      delta 200, seeded centres;
+    robustness (Sec. 4, Table 1): w-BFBT (sqrt(mu) and viscosity-gradient weights) against the
+      inverse-viscosity pressure mass (lumped, Eq. lumping, and its diagonal) over sinker counts x
+      dynamic ratios, n^3 Q2, omega 0.1, delta 200, seeded centres;
     amplification (Sec. 5, Table 2): w-BFBT with a_l = 1 and a_r in {1, 2, 4, 8, 16, 32};
-    order (Sec. 7, Table 3b): w-BFBT for k = 2, 3, 4 on the same mesh, a_r by the Table 3 rule.
+    order (Sec. 7, Table 3b): w-BFBT for k = 2, 3, 4 on the same mesh, a_r by the Table 3 rule;
+    alone (Sec. 7, Table 3): the viscous block and K_{w_r} solved on their own with their V-cycles
+      beside the Stokes solve, over mesh size and order;
+    kcycles: Stokes iterations with 1-8 V-cycles per K~_w^-1, and the cost of one K_w V-cycle
+      against one U-Net forward pass (what a learned K~_w^-1 could at best save).
     """
     import torch
 
@@ -592,10 +604,10 @@ def run_sweep(args):
     prec = wb.MIXED if args.precision == "mixed" else wb.F64
     n = args.sweep_n
 
-    def solve(k, ns, dr, schur=wb.SCHUR_WBFBT, a_r=0.0, seed=0):
+    def solve(k, ns, dr, schur=wb.SCHUR_WBFBT, a_r=0.0, seed=0, weights=wb.WEIGHTS_SQRT_MU):
         c = inputs.sinker_centres(seed, ns)
         mu, f = wb.sinker_setup(n, k, c, 0.1, 200.0, dr)
-        s = wb.Solver(n, k, mu, precision=prec, schur=schur, a_r=a_r)
+        s = wb.Solver(n, k, mu, precision=prec, schur=schur, a_r=a_r, weights=weights)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, _, res = s.solve(f, rtol=RTOL, maxit=args.sweep_maxit)
@@ -614,12 +626,75 @@ def run_sweep(args):
                     r = solve(2, ns, dr, schur)
                     print(json.dumps({"sweep": "robustness", **base, "k": 2, "sinkers": ns, "dr": dr,
                                       "schur": names[schur], **r}), flush=True)
+                r = solve(2, ns, dr, weights=wb.WEIGHTS_GRAD)
+                print(json.dumps({"sweep": "robustness", **base, "k": 2, "sinkers": ns, "dr": dr,
+                                  "schur": "w-BFBT, gradient weights", **r}), flush=True)
     elif args.sweep == "amplification":
         for k in (2, 3, 4):
             for a_r in (1.0, 2.0, 4.0, 8.0, 16.0, 32.0):
                 r = solve(k, 16, 1e6, a_r=a_r)
                 print(json.dumps({"sweep": "amplification", **base, "k": k, "sinkers": 16, "dr": 1e6, "a_l": 1.0,
                                   "a_r": a_r, **r}), flush=True)
+    elif args.sweep == "alone":
+        # Table 3: the viscous block and the weighted pressure Poisson operator K_{w_r} solved on
+        # their own (FGMRES + their V-cycles, rhs: the load vector / a seeded mean-free vector)
+        # beside the full Stokes solve, S16 DR 1e6, over mesh size (k = 2) and order (n = 32)
+        for nn_, k in ((16, 2), (32, 2), (64, 2), (32, 3), (32, 4)):
+            c = inputs.sinker_centres(0, 16)
+            mu, f = wb.sinker_setup(nn_, k, c, 0.1, 200.0, 1e6)
+            s = wb.Solver(nn_, k, mu, precision=prec)
+            _, ra = s.solve_block(wb.BLOCK_A, f.clone(), rtol=RTOL, maxit=args.sweep_maxit)
+            gen = torch.Generator(device="cuda").manual_seed(9)
+            b = torch.randn(s.n_p, dtype=torch.float64, device="cuda", generator=gen)
+            _, rk = s.solve_block(wb.BLOCK_KR, b, rtol=RTOL, maxit=args.sweep_maxit)
+            _, _, rs = s.solve(f, rtol=RTOL, maxit=args.sweep_maxit)
+            print(json.dumps({"sweep": "alone", **base, "mesh": f"{nn_}^3", "k": k, "sinkers": 16, "dr": 1e6,
+                              "u_dof": s.n_u, "p_dof": s.n_p, "its_A_alone": ra.iters, "its_Kwr_alone": rk.iters,
+                              "its_stokes": rs.iters}), flush=True)
+            s.close()
+    elif args.sweep == "kcycles":
+        # how much a better K~_w^-1 could gain (the learned correction stands in for it): Stokes
+        # iterations and solve time with 1, 2, 4 and 8 V-cycles per K~_w^-1 application on the
+        # 32^3 and 64^3 workloads, beside the measured cost of one K_w V-cycle and of one U-Net
+        # forward pass on the same element grid
+        for wname in ("32^3-Q2-S24-DR1e6", "64^3-Q2-S64-DR1e10"):
+            cfg = inputs.WORKLOADS[wname]
+            c = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
+            mu, f = wb.sinker_setup(cfg["n"], cfg["k"], c, cfg["omega"], cfg["delta"], cfg["dr"])
+            for cyc in (1, 2, 4, 8):
+                s = wb.Solver(cfg["n"], cfg["k"], mu, precision=prec, kinv_cycles=cyc)
+                s.solve(f)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, _, res = s.solve(f, rtol=RTOL, maxit=args.sweep_maxit)
+                torch.cuda.synchronize()
+                row = {"sweep": "kcycles", "workload": wname, "precision": args.precision, "kinv_cycles": cyc,
+                       "iters": res.iters, "converged": res.status == 0, "solve_s": time.perf_counter() - t0}
+                if cyc == 1:
+                    r = torch.randn(s.n_p, device="cuda", dtype=s.pdtype)
+                    ev = _events(2)
+                    for _ in range(3):
+                        s.apply_Kinv(1, r)
+                    ev[0].record()
+                    for _ in range(20):
+                        s.apply_Kinv(1, r)
+                    ev[1].record()
+                    torch.cuda.synchronize()
+                    row["kw_vcycle_s"] = ev[0].elapsed_time(ev[1]) / 20 / 1e3
+                    net = wb.Net(1 + s.np, s.np, cfg["n"])
+                    net.set_params(torch.tensor(inputs.unet_init_params(3, 1 + s.np, s.np), device="cuda"))
+                    x = torch.randn(1, cfg["n"] ** 3, 1 + s.np, device="cuda")
+                    for _ in range(3):
+                        net.forward(x)
+                    ev[0].record()
+                    for _ in range(20):
+                        net.forward(x)
+                    ev[1].record()
+                    torch.cuda.synchronize()
+                    row["unet_forward_s"] = ev[0].elapsed_time(ev[1]) / 20 / 1e3
+                    net.close()
+                print(json.dumps(row), flush=True)
+                s.close()
     elif args.sweep == "order":
         for k in (2, 3, 4):
             r = solve(k, 16, 1e6)
@@ -639,8 +714,8 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="one setup + solve of the workload and nothing else (for an ncu launch list)")
     ap.add_argument("--profile-apply", action="store_true",
-                    help="one FP64 and one FP32 A apply in an NVTX range 'prof' (for ncu --set full)")
-    ap.add_argument("--sweep", choices=["robustness", "amplification", "order"],
+                    help="one FP64 A, one FP32 A and one FP64 K apply in an NVTX range 'prof' (for ncu)")
+    ap.add_argument("--sweep", choices=["robustness", "amplification", "order", "alone", "kcycles"],
                     help="iteration-count sweeps in the style of Tables 1, 2 and 3b (many JSON lines)")
     ap.add_argument("--sweep-n", type=int, default=32)
     ap.add_argument("--sweep-maxit", type=int, default=2000)

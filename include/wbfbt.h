@@ -86,11 +86,21 @@ typedef struct {
                                       on the FP32 preconditioner output); the true residual
                                       F - K x at every restart and at exit is FP64 either way,
                                       and convergence is declared on it                     */
+    int weights;                   /* w-BFBT weight function w in C = M~_u(a_l w),
+                                      D = M~_u(a_r w): WBFBT_WEIGHTS_SQRT_MU (default,
+                                      w = sqrt(mu), Eq. wbfbt) or WBFBT_WEIGHTS_GRAD
+                                      (w = (mu^2 + |grad mu|^2)^(1/4), the remark in Sec. 4;
+                                      grad mu of each element's Q_k interpolant, per point)  */
+    int kinv_cycles;               /* V-cycles per application of K~_l^-1 and K~_r^-1 inside
+                                      S~^-1 (default 1, Sec. 6; 1..64): each further cycle
+                                      corrects the residual, x += V(b - K_w x)             */
 } wbfbt_opts;
 
 #define WBFBT_SCHUR_WBFBT 0
 #define WBFBT_SCHUR_MASS 1
 #define WBFBT_SCHUR_MASS_DIAG 2
+#define WBFBT_WEIGHTS_SQRT_MU 0
+#define WBFBT_WEIGHTS_GRAD 1
 
 #define WBFBT_ELEM_AUTO 0
 #define WBFBT_ELEM_POINT 1
@@ -166,6 +176,21 @@ int wbfbt_apply_precond(wbfbt_ctx* ctx, const void* x, void* y, int dtype);
  * still written). */
 int wbfbt_solve(wbfbt_ctx* ctx, const double* f_nodes, double* u, double* p, double rtol, int maxit,
                 int* iters, double* final_rel_res);
+
+/* One block of the preconditioner solved on its own with FGMRES(m) to ||r|| <= rtol ||b||, x0 = 0,
+ * preconditioned by that block's V-cycle (the "alone" iteration counts of Table 3, Sec. 7):
+ *   WBFBT_BLOCK_A  : A x = b, velocity [3][nodes]; b's Dirichlet entries are ignored, x's are 0
+ *   WBFBT_BLOCK_KL : (B C^-1 B^T) x = b, pressure [E][Np]; b and x projected against 1_psi
+ *   WBFBT_BLOCK_KR : (B D^-1 B^T) x = b, as above
+ * The V-cycle runs in the context's preconditioner precision (FP32 in a mixed context), the
+ * Krylov vectors and the A operator in FP64, the K_w operator in the preconditioner precision.  b, x: FP64 device pointers.  iters / final_rel_res as in
+ * wbfbt_solve; WBFBT_ERR_MAXIT if maxit iterations did not reach rtol (x still written).  The
+ * context's Krylov workspace is reused: no allocation. */
+#define WBFBT_BLOCK_A 0
+#define WBFBT_BLOCK_KL 1
+#define WBFBT_BLOCK_KR 2
+int wbfbt_solve_block(wbfbt_ctx* ctx, int block, const double* b, double* x, double rtol, int maxit, int* iters,
+                      double* final_rel_res);
 
 /* Sizes of the context's vectors. */
 int wbfbt_sizes(const wbfbt_ctx* ctx, long long* n_nodes, long long* n_elem, int* np_per_elem,

@@ -257,7 +257,7 @@ def vcycle(levels: list[Level], b: np.ndarray, l: int = 0) -> np.ndarray:
 class PressurePoissonMG:
     """Approximate inverse of K_w = B C_w^-1 B^T by the two-space V-cycle of Sec. 6."""
 
-    def __init__(self, mesh: Mesh, B, cdiag: np.ndarray, mu_nodes: np.ndarray, a: float):
+    def __init__(self, mesh: Mesh, B, cdiag: np.ndarray, mu_nodes: np.ndarray, a: float, weights: str = "sqrt_mu"):
         self.mesh = mesh
         self.K = op.assemble_Kw(B, cdiag, mesh)
         diag = self.K.diagonal()
@@ -266,7 +266,7 @@ class PressurePoissonMG:
         self.dinv = np.where(diag > 0.0, 1.0 / np.where(diag > 0.0, diag, 1.0), 0.0)
         self.lam = power_lambda(self.K, self.dinv, splitmix64_uniform(START_SEED, self.K.shape[0]))
         amp = op.boundary_amplification(mesh, a)
-        c_pts = 1.0 / (amp[:, None] * np.sqrt(op.point_values(mesh, mu_nodes)))
+        c_pts = 1.0 / (amp[:, None] * op.weight_points(mesh, mu_nodes, weights))
         self.levels = build_hierarchy(mesh, c_pts, vector=False)
         Md = op.pressure_mass_element(mesh)
         self.Md_inv = np.linalg.inv(Md)

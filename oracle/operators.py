@@ -107,15 +107,33 @@ def boundary_amplification(mesh: Mesh, a: float) -> np.ndarray:
     return np.where(mesh.boundary_element_mask(), a, 1.0)
 
 
-def lumped_weight_diag(mesh: Mesh, mu_nodes: np.ndarray, a: float) -> np.ndarray:
-    """Diagonal of M~_u(w), w = a(e) sqrt(mu) (Eq. wbfbt, Eq. bdramp, lumping as Eq. lumping).
+def weight_points(mesh: Mesh, mu_nodes: np.ndarray, weights: str = "sqrt_mu") -> np.ndarray:
+    """The w-BFBT weight function at every element point, shape (n_elem, n^3).
+
+    "sqrt_mu": w = sqrt(mu) (Sec. 1.3, Eq. wbfbt).
+    "grad":    w = (mu^2 + |grad mu|^2)^(1/4), the viscosity-gradient weights of the remark in
+               Sec. 4, with grad mu the gradient of the element's Q_k interpolant of the nodal
+               viscosity at the point (discontinuous across elements, so the weight is per
+               element point).
+    """
+    mu_q = point_values(mesh, mu_nodes)
+    if weights == "sqrt_mu":
+        return np.sqrt(mu_q)
+    if weights == "grad":
+        g2 = sum((gradient_op(mesh, d) @ mu_nodes) ** 2 for d in range(3)).reshape(mu_q.shape)
+        return (mu_q ** 2 + g2) ** 0.25
+    raise ValueError(weights)
+
+
+def lumped_weight_diag(mesh: Mesh, mu_nodes: np.ndarray, a: float, weights: str = "sqrt_mu") -> np.ndarray:
+    """Diagonal of M~_u(w), w = a(e) w(x) (Eq. wbfbt, Eq. bdramp, lumping as Eq. lumping).
 
     With collocated GLL quadrature the weighted velocity mass matrix is already
-    diagonal, so its row sum is sum_{(e,q) -> node} W_q |J| a(e) sqrt(mu(node)).
-    Returned per node (n_nodes,); the three velocity components share it.
+    diagonal, so its row sum is sum_{(e,q) -> node} W_q |J| a(e) w_e(x_q), w = sqrt(mu) by default
+    (see weight_points).  Returned per node (n_nodes,); the three velocity components share it.
     """
     amp = boundary_amplification(mesh, a)
-    vals = (mesh.W * mesh.detJ)[None, :] * amp[:, None] * np.sqrt(point_values(mesh, mu_nodes))
+    vals = (mesh.W * mesh.detJ)[None, :] * amp[:, None] * weight_points(mesh, mu_nodes, weights)
     return incidence(mesh).T @ vals.ravel()
 
 

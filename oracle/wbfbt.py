@@ -46,21 +46,25 @@ class Options:
     mode: str = "vcycle"
     schur: str = "wbfbt"       # "wbfbt" (Eq. wbfbt), "mass" (lumped M_p(1/mu), Eq. lumping),
                                # "mass_diag" (the diagonal of M_p(1/mu))
+    weights: str = "sqrt_mu"   # w-BFBT weights: "sqrt_mu" (Eq. wbfbt) or "grad" (remark in Sec. 4)
+    kinv_cycles: int = 1       # V-cycles per K~_w^-1 application: x += V(b - K_w x) after the first
 
 
 class StokesProblem:
     """Assembled Stokes operators on a brick with per-node viscosity."""
 
-    def __init__(self, mesh: Mesh, mu_nodes: np.ndarray, a_l: float = 1.0, a_r: float | None = None):
+    def __init__(self, mesh: Mesh, mu_nodes: np.ndarray, a_l: float = 1.0, a_r: float | None = None,
+                 weights: str = "sqrt_mu"):
         self.mesh = mesh
         self.mu = np.asarray(mu_nodes, dtype=np.float64)
         self.a_l = a_l
         self.a_r = default_a_r(mesh) if a_r is None else a_r
+        self.weights = weights
         self.A = op.assemble_A(mesh, op.point_values(mesh, self.mu))
         self.B = op.assemble_B(mesh)
         self.BT = self.B.T.tocsr()
-        self.Cdiag = op.lumped_weight_diag(mesh, self.mu, self.a_l)
-        self.Ddiag = op.lumped_weight_diag(mesh, self.mu, self.a_r)
+        self.Cdiag = op.lumped_weight_diag(mesh, self.mu, self.a_l, weights)
+        self.Ddiag = op.lumped_weight_diag(mesh, self.mu, self.a_r, weights)
         interior = ~mesh.boundary_node_mask()
         self.Cinv = np.tile(np.where(interior, 1.0 / self.Cdiag, 0.0), 3)
         self.Dinv = np.tile(np.where(interior, 1.0 / self.Ddiag, 0.0), 3)
@@ -96,18 +100,28 @@ class _PinnedLU:
 class WBFBT:
     """S~^-1 of Eq. wbfbt with exact or multigrid inner inverses."""
 
-    def __init__(self, prob: StokesProblem, mode: str = "vcycle"):
+    def __init__(self, prob: StokesProblem, mode: str = "vcycle", kinv_cycles: int = 1):
         self.prob = prob
         m = prob.mesh
         if mode == "exact":
             self.Kl_inv = _PinnedLU(op.assemble_Kw(prob.B, prob.Cdiag, m), m)
             self.Kr_inv = _PinnedLU(op.assemble_Kw(prob.B, prob.Ddiag, m), m)
         elif mode == "vcycle":
-            self.Kl_mg = mg.PressurePoissonMG(m, prob.B, prob.Cdiag, prob.mu, prob.a_l)
-            self.Kr_mg = mg.PressurePoissonMG(m, prob.B, prob.Ddiag, prob.mu, prob.a_r)
-            self.Kl_inv, self.Kr_inv = self.Kl_mg.apply, self.Kr_mg.apply
+            self.Kl_mg = mg.PressurePoissonMG(m, prob.B, prob.Cdiag, prob.mu, prob.a_l, prob.weights)
+            self.Kr_mg = mg.PressurePoissonMG(m, prob.B, prob.Ddiag, prob.mu, prob.a_r, prob.weights)
+            self.Kl_inv, self.Kr_inv = self._cycles(self.Kl_mg, kinv_cycles), self._cycles(self.Kr_mg, kinv_cycles)
         else:
             raise ValueError(mode)
+
+    @staticmethod
+    def _cycles(pmg, cycles):
+        """cycles V-cycles of the two-space multigrid: x = V b, then x += V(b - K_w x)."""
+        def apply(b):
+            x = pmg.apply(b)
+            for _ in range(cycles - 1):
+                x = x + pmg.apply(b - pmg.K @ x)
+            return x
+        return apply
 
     def apply(self, r: np.ndarray) -> np.ndarray:
         m = self.prob.mesh
@@ -137,7 +151,7 @@ class BlockPreconditioner:
     """[A~ B^T; 0 s S~]^-1: y_p = s S~^-1 r_p, y_u = A~^-1 (r_u - B^T y_p)."""
 
     def __init__(self, prob: StokesProblem, mode: str = "vcycle", schur_sign: float = -1.0,
-                 schur_inv=None, A_inv=None, schur: str = "wbfbt"):
+                 schur_inv=None, A_inv=None, schur: str = "wbfbt", kinv_cycles: int = 1):
         self.prob = prob
         self.sign = schur_sign
         m = prob.mesh
@@ -160,7 +174,7 @@ class BlockPreconditioner:
         elif schur in ("mass", "mass_diag"):
             self.S_inv = MassSchur(prob, diag=schur == "mass_diag").apply
         else:
-            self.S_inv = WBFBT(prob, mode).apply
+            self.S_inv = WBFBT(prob, mode, kinv_cycles).apply
 
     def apply(self, v: np.ndarray) -> np.ndarray:
         nu = self.prob.nu
@@ -178,8 +192,8 @@ def sinker_problem(mesh: Mesh, centres, omega, delta, dr, beta=10.0):
 
 def solve(mesh: Mesh, mu_nodes, f_nodes, opts: Options = Options(), rtol=1e-6, maxit=1000, history=None):
     """FGMRES(restart) solve of the Stokes system; returns (u, p, iters, rel_res, prob)."""
-    prob = StokesProblem(mesh, mu_nodes, opts.a_l, opts.a_r)
-    pc = BlockPreconditioner(prob, opts.mode, opts.schur_sign, schur=opts.schur)
+    prob = StokesProblem(mesh, mu_nodes, opts.a_l, opts.a_r, opts.weights)
+    pc = BlockPreconditioner(prob, opts.mode, opts.schur_sign, schur=opts.schur, kinv_cycles=opts.kinv_cycles)
     F = np.concatenate([op.load_vector(mesh, f_nodes), np.zeros(mesh.n_p)])
     x, its, rel = krylov.fgmres(prob.apply_K, pc.apply, F, rtol=rtol, restart=opts.restart,
                                 maxit=maxit, history=history)

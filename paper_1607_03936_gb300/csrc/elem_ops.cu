@@ -413,6 +413,69 @@ __global__ void k_lumped(Grid g, int K, const RefTables* __restrict__ tab, const
   out[n] = mu ? acc * sqrt(mu[n]) : acc;
 }
 
+// The w-BFBT weight at every element point (FP64, [ne][N^3]): sqrt(mu) (grad = 0, Eq. wbfbt) or
+// (mu^2 + |grad mu_h|^2)^(1/4) (grad = 1, the viscosity-gradient weights of the remark in
+// Sec. 4), grad mu_h being the gradient of the element's Q_k interpolant of the nodal viscosity.
+template <int N>
+__global__ void k_weight_points(Grid g, const RefTables* __restrict__ tab, const double* __restrict__ mu, int grad,
+                                double* __restrict__ w) {
+  pdl_entry();
+  constexpr int N3 = Cfg<N>::N3, K = N - 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.ne * N3) return;
+  const int e = (int)(t / N3), q = (int)(t % N3);
+  const int i = q % N, j = (q / N) % N, l = q / (N * N);
+  const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
+  const long long base = (long long)K * ex + (long long)g.NX * (K * ey + (long long)g.NY * K * ez);
+  auto at = [&](int a, int b, int c) { return mu[base + a + (long long)g.NX * (b + (long long)g.NY * c)]; };
+  const double m0 = at(i, j, l);
+  if (!grad) {
+    w[t] = sqrt(m0);
+    return;
+  }
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  for (int a = 0; a < N; ++a) {
+    gx += tab->D[i][a] * at(a, j, l);
+    gy += tab->D[j][a] * at(i, a, l);
+    gz += tab->D[l][a] * at(i, j, a);
+  }
+  gx *= g.s[0];
+  gy *= g.s[1];
+  gz *= g.s[2];
+  w[t] = sqrt(sqrt(m0 * m0 + gx * gx + gy * gy + gz * gz));
+}
+
+// M~_u(a w) per node from the point weights: sum over the elements at the node of a(e) W_q |J| w_e(q).
+template <int N>
+__global__ void k_lumped_pts(Grid g, const RefTables* __restrict__ tab, const double* __restrict__ wp, double amp,
+                             double* __restrict__ out) {
+  pdl_entry();
+  constexpr int N3 = Cfg<N>::N3, K = N - 1;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nn) return;
+  const int ix = n % g.NX, iy = (n / g.NX) % g.NY, iz = n / (g.NX * g.NY);
+  double acc = 0.0;
+  for_elements_of_node(g, K, ix, iy, iz, [&](int e, int ex, int ey, int ez, int a0, int a1, int a2) {
+    const bool bnd_el = ex == 0 || ey == 0 || ez == 0 || ex == g.nx - 1 || ey == g.ny - 1 || ez == g.nz - 1;
+    acc += (bnd_el ? amp : 1.0) * tab->w[a0] * tab->w[a1] * tab->w[a2] * g.detJ *
+           wp[(size_t)e * N3 + a0 + N * (a1 + N * a2)];
+  });
+  out[n] = acc;
+}
+
+// Poisson coefficient c = 1 / (a(e) w) per element point from the point weights.
+template <typename T, int N>
+__global__ void k_poisson_coef_pts(Grid g, const double* __restrict__ wp, double amp, T* __restrict__ c) {
+  pdl_entry();
+  constexpr int N3 = Cfg<N>::N3;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.ne * N3) return;
+  const int e = (int)(t / N3);
+  const int ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / (g.nx * g.ny);
+  const bool bnd_el = ex == 0 || ey == 0 || ez == 0 || ex == g.nx - 1 || ey == g.ny - 1 || ez == g.nz - 1;
+  c[t] = T(1.0 / ((bnd_el ? amp : 1.0) * wp[t]));
+}
+
 // r_c(n) = sum_{e containing n} W_q sum_m psi_m(q) sum_m' minv[m][m'] r_d[e][m']   (|J| cancels)
 template <typename T, int N>
 __global__ void k_disc_to_cont(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ rd, T* __restrict__ rc) {
@@ -702,6 +765,27 @@ cudaError_t launch_lumped_mass(const Grid& g, int k, const RefTables* dtab, doub
   wb_launch(k_lumped, blocks_for(g.nn, 128), 128, 0, st, g, k, dtab, nullptr, 1.0, out);
   return cudaGetLastError();
 }
+
+cudaError_t launch_weight_points(const Grid& g, int k, const RefTables* dtab, const double* mu, int grad, double* w,
+                                 cudaStream_t st) {
+  WB_DISPATCH_N(k, ((wb_launch(k_weight_points<N>, blocks_for((long long)g.ne * Cfg<N>::N3, 128), 128, 0, st, g, dtab,
+                               mu, grad, w)),
+                    cudaGetLastError()));
+}
+
+cudaError_t launch_lumped_weight_pts(const Grid& g, int k, const RefTables* dtab, const double* wp, double a,
+                                     double* out, cudaStream_t st) {
+  WB_DISPATCH_N(k, ((wb_launch(k_lumped_pts<N>, blocks_for(g.nn, 128), 128, 0, st, g, dtab, wp, a, out)),
+                    cudaGetLastError()));
+}
+
+template <typename T>
+cudaError_t launch_poisson_coef_pts(const Grid& g, int k, const double* wp, double a, T* c, cudaStream_t st) {
+  WB_DISPATCH_N(k, ((wb_launch(k_poisson_coef_pts<T, N>, blocks_for((long long)g.ne * Cfg<N>::N3, 128), 128, 0, st, g,
+                               wp, a, c)),
+                    cudaGetLastError()));
+}
+template cudaError_t launch_poisson_coef_pts<double>(const Grid&, int, const double*, double, double*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_poisson_coef0(const Grid& g, int k, const double* mu, double a, T* c, cudaStream_t st) {

@@ -52,6 +52,15 @@ cudaError_t launch_lumped_weight(const Grid& g, int k, const RefTables* dtab, co
 // Lumped (unweighted) mass sum_{(e,q) at n} W_q |J| per node, used for the load vector.
 cudaError_t launch_lumped_mass(const Grid& g, int k, const RefTables* dtab, double* out, cudaStream_t st);
 
+// w-BFBT weights per element point (FP64 [ne][(k+1)^3]): sqrt(mu), or with grad = 1 the
+// viscosity-gradient weights (mu^2 + |grad mu|^2)^(1/4); the lumped mass M~_u(a w) per node and the
+// Poisson coefficient 1 / (a(e) w) per point from them.
+cudaError_t launch_weight_points(const Grid& g, int k, const RefTables* dtab, const double* mu, int grad, double* w,
+                                 cudaStream_t st);
+cudaError_t launch_lumped_weight_pts(const Grid& g, int k, const RefTables* dtab, const double* wp, double a,
+                                     double* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_poisson_coef_pts(const Grid& g, int k, const double* wp, double a, T* c, cudaStream_t st);
 // Coefficients: Poisson coefficient c = 1 / (a(e) sqrt(mu)) per element point; viscosity per
 // element point from nodes; coarsening fine -> coarse (normalised L^2-adjoint, Sec. 6).
 template <typename T>

@@ -137,6 +137,7 @@ struct wbfbt_ctx {
   double* part = nullptr;   // reduction partials
   double* kwbref = nullptr; // reference divergence matrix for the K_w assembly (k <= 3)
   double* Mp64 = nullptr;   // lumped M_p(1/mu)^-1 blocks in FP64 (schur = MASS)
+  double* wpts = nullptr;   // w-BFBT weights per element point (weights = GRAD)
   double* dsc = nullptr;    // device scalars (64)
   int* dflag = nullptr;
   Precond<double> P64;
@@ -438,12 +439,26 @@ void kinv_learned(wbfbt_ctx* c, int which, const T* bd, T* xd) {
   }
 }
 
+// K~_w^-1: the learned step when a net is attached for this operator, else kinv_cycles
+// V-cycles (default 1, Sec. 6); further cycles correct the residual of the current iterate,
+// x += V(b - K_w x), so many cycles approach the exact inverse.
 template <typename T>
 void kinv_any(wbfbt_ctx* c, int which, const T* bd, T* xd) {
-  if (c->net && ((c->net_mask >> which) & 1))
+  if (c->net && ((c->net_mask >> which) & 1)) {
     kinv_learned<T>(c, which, bd, xd);
-  else
-    kinv<T>(c, which, bd, xd);
+    return;
+  }
+  kinv<T>(c, which, bd, xd);
+  Precond<T>& P = prec<T>(c);
+  for (int cyc = 1; cyc < c->opt.kinv_cycles; ++cyc) {
+    Epi<T> e;
+    e.mode = EPI_BMINUS;
+    e.y = P.pb;
+    e.b = bd;
+    op_Kw<T>(c, which, xd, e);                       // pb = b - K_w x
+    kinv<T>(c, which, P.pb, P.px);
+    CK(launch_axpby<T>((long long)c->g.ne * c->NP, T(1), xd, T(1), P.px, xd, c->st));
+  }
 }
 
 template <typename T>
@@ -684,7 +699,10 @@ void build_precond(wbfbt_ctx* c) {
   const double amp[2] = {c->opt.a_l, c->opt.a_r};
   for (int wi = 0; wi < 2; ++wi) {
     c->pool.ensure(P.c0[wi], npts);
-    CK(launch_poisson_coef0<double>(g, c->k, c->mu64, amp[wi], P.c0[wi], c->st));
+    if (c->opt.weights == WBFBT_WEIGHTS_GRAD)
+      CK(launch_poisson_coef_pts<double>(g, c->k, c->wpts, amp[wi], P.c0[wi], c->st));
+    else
+      CK(launch_poisson_coef0<double>(g, c->k, c->mu64, amp[wi], P.c0[wi], c->st));
     build_hier<T>(c, P.HL[wi], false, P.c0[wi], 0);
     // disc level: Jacobi diagonal of K_w and lambda_hat
     c->pool.ensure(P.dK64[wi], np);
@@ -844,13 +862,16 @@ void precond_any(wbfbt_ctx* c, const double* v, double* z) {
   }
 }
 
-int fgmres(wbfbt_ctx* c, double rtol, int maxit, int* iters, double* relres) {
-  const long long n = c->ntot;
+// Right-preconditioned FGMRES(m) on vectors of length n <= ntot (Sec. 1.3): x0 = 0, CGS2
+// orthogonalisation and the Hessenberg/Givens recurrence in FP64, the true residual F - K x
+// recomputed in FP64 at every restart and at exit.  arn(z, w): w = K z inside the Arnoldi
+// process; tru(x, w): w = K x for the true residual; pc(v, z): z = P^-1 v.
+template <class Arn, class Tru, class Pc>
+int fgmres_core(wbfbt_ctx* c, long long n, const double* F, double* x, double* r, Arn arn, Tru tru, Pc pc,
+                double rtol, int maxit, int* iters, double* relres) {
   const int m = c->m;
-  double* x = c->x;
-  double* r = c->r;
   CK(cudaMemsetAsync(x, 0, sizeof(double) * n, c->st));
-  CK(cudaMemcpyAsync(r, c->F, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(r, F, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
   const double beta0 = norm<double>(c, r, n);
   if (!std::isfinite(beta0)) return WBFBT_ERR_NONFINITE;
   if (beta0 == 0.0) {
@@ -874,8 +895,8 @@ int fgmres(wbfbt_ctx* c, double rtol, int maxit, int* iters, double* relres) {
     for (int j = 0; j < m; ++j) {
       double* vj = c->V + (size_t)j * n;
       double* zj = c->Z + (size_t)j * n;
-      precond_any(c, vj, zj);
-      apply_K_arnoldi(c, zj, c->w);
+      pc(vj, zj);
+      arn(zj, c->w);
       // CGS2: h = V^T w, w -= V h, twice
       double* h1 = c->hdev;
       double* h2 = c->hdev + (m + 1);
@@ -924,8 +945,8 @@ int fgmres(wbfbt_ctx* c, double rtol, int maxit, int* iters, double* relres) {
     }
     CK(cudaMemcpyAsync(c->hdev, y.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, c->st));
     CK(launch_gemv_add(c->Z, n, jdone, c->hdev, x, n, c->st));
-    apply_K64(c, x, c->w);
-    CK(launch_axpby<double>(n, 1.0, c->F, -1.0, c->w, r, c->st));
+    tru(x, c->w);
+    CK(launch_axpby<double>(n, 1.0, F, -1.0, c->w, r, c->st));
     rel = norm<double>(c, r, n) / beta0;
     if (!std::isfinite(rel)) return WBFBT_ERR_NONFINITE;
     if ((converged && rel <= rtol) || its >= maxit) done = true;
@@ -934,6 +955,61 @@ int fgmres(wbfbt_ctx* c, double rtol, int maxit, int* iters, double* relres) {
   if (iters) *iters = its;
   if (relres) *relres = rel;
   return status;
+}
+
+// The Stokes solve: K = [A B^T; B 0], P = the block preconditioner of Eq. precond-stokes.
+int fgmres(wbfbt_ctx* c, double rtol, int maxit, int* iters, double* relres) {
+  return fgmres_core(
+      c, c->ntot, c->F, c->x, c->r, [&](const double* z, double* w) { apply_K_arnoldi(c, z, w); },
+      [&](const double* xx, double* w) { apply_K64(c, xx, w); }, [&](const double* v, double* z) { precond_any(c, v, z); },
+      rtol, maxit, iters, relres);
+}
+
+// One block of the preconditioner solved on its own (Table 3's "alone" counts): the viscous
+// block A with its V-cycle, or K_w = B C_w^-1 B^T (which 0: w_l, 1: w_r) with its two-space
+// V-cycle, both as right preconditioners of FGMRES.  The V-cycles run in the context's
+// preconditioner precision T (FP64, or FP32 in a mixed context), the Krylov vectors in FP64; the
+// operator is FP64 for A and in precision T for K_w.
+template <typename T>
+int block_solve(wbfbt_ctx* c, int block, long long n, double rtol, int maxit, int* iters, double* relres) {
+  Precond<T>& P = prec<T>(c);
+  T* tin = std::is_same<T, double>::value ? nullptr : P.vin;
+  T* tout = std::is_same<T, double>::value ? nullptr : P.vout;
+  // run f on T views of a (in) and b (out): direct for FP64, through casts for FP32
+  auto via = [&](const double* a, double* b, auto f) {
+    if (std::is_same<T, double>::value) {
+      f(reinterpret_cast<const T*>(a), reinterpret_cast<T*>(b));
+    } else {
+      CK((launch_cast<double, T>(n, a, tin, c->st)));
+      f(tin, tout);
+      CK((launch_cast<T, double>(n, tout, b, c->st)));
+    }
+  };
+  if (block == 0) {
+    // the operator in FP64 in every context: an FP32 A caps the attainable residual of the
+    // ill-conditioned viscous block near eps_32 kappa(A) (measured 3e-5 at 8^3, DR 1e4)
+    auto op = [&](const double* z, double* w) {
+      CK(launch_elem_stokes<double>(c->g, c->k, c->ot64, OP_A, z, nullptr, nullptr, c->mu64, 1, c->Ye64,
+                                    Epi<double>(), c->st));
+      CK(launch_gather<double>(c->g, c->k, 3, 1, c->Ye64, epi_store<double>(w), c->st));
+    };
+    auto pc = [&](const double* v, double* z) {
+      via(v, z, [&](const T* vi, T* zo) { vcycle<T>(c, P.HA, 0, vi, zo); });
+    };
+    return fgmres_core(c, n, c->F, c->x, c->r, op, op, pc, rtol, maxit, iters, relres);
+  }
+  const int which = block - 1;
+  auto op = [&](const double* z, double* w) {
+    via(z, w, [&](const T* zi, T* wo) { op_Kw<T>(c, which, zi, epi_store<T>(wo)); });
+  };
+  auto pc = [&](const double* v, double* z) {
+    via(v, z, [&](const T* vi, T* zo) {
+      project<T>(c, vi, P.sr);
+      kinv_any<T>(c, which, P.sr, P.sy);
+      project<T>(c, P.sy, zo);
+    });
+  };
+  return fgmres_core(c, n, c->F, c->x, c->r, op, op, pc, rtol, maxit, iters, relres);
 }
 
 }  // namespace
@@ -960,8 +1036,16 @@ void run_setup(wbfbt_ctx* cp, const double* mu_nodes) {
   CK(cudaStreamSynchronize(cp->st));
   if (bad) throw WbErr{WBFBT_ERR_INVALID};
   CK((launch_cast<double, float>((long long)nn, cp->mu64, cp->mu32, cp->st)));
-  CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_l, cp->C, cp->st));
-  CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_r, cp->D, cp->st));
+  if (cp->opt.weights == WBFBT_WEIGHTS_GRAD) {
+    // viscosity-gradient weights (remark in Sec. 4): per element point, then lumped per node
+    cp->pool.ensure(cp->wpts, (size_t)g.ne * cp->N3);
+    CK(launch_weight_points(g, cp->k, cp->dtab, cp->mu64, 1, cp->wpts, cp->st));
+    CK(launch_lumped_weight_pts(g, cp->k, cp->dtab, cp->wpts, cp->opt.a_l, cp->C, cp->st));
+    CK(launch_lumped_weight_pts(g, cp->k, cp->dtab, cp->wpts, cp->opt.a_r, cp->D, cp->st));
+  } else {
+    CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_l, cp->C, cp->st));
+    CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_r, cp->D, cp->st));
+  }
   wb_launch(k_inv_masked, (unsigned)((nn + 255) / 256), 256, 0, cp->st, g, cp->C, cp->cinv64);
   wb_launch(k_inv_masked, (unsigned)((nn + 255) / 256), 256, 0, cp->st, g, cp->D, cp->dinv64);
   CK(cudaGetLastError());
@@ -1004,6 +1088,8 @@ void wbfbt_default_opts(wbfbt_opts* o) {
   o->elem_kernels = WBFBT_ELEM_AUTO;
   o->schur = WBFBT_SCHUR_WBFBT;
   o->arnoldi_precision = WBFBT_F64;
+  o->weights = WBFBT_WEIGHTS_SQRT_MU;
+  o->kinv_cycles = 1;
 }
 
 const char* wbfbt_status_string(int s) {
@@ -1047,7 +1133,9 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
       c->opt.elem_kernels < WBFBT_ELEM_AUTO || c->opt.elem_kernels > WBFBT_ELEM_ROW ||
       c->opt.schur < WBFBT_SCHUR_WBFBT || c->opt.schur > WBFBT_SCHUR_MASS_DIAG ||
       (c->opt.arnoldi_precision != WBFBT_F64 && c->opt.arnoldi_precision != WBFBT_F32) ||
-      (c->opt.arnoldi_precision == WBFBT_F32 && c->opt.precision != WBFBT_MIXED))
+      (c->opt.arnoldi_precision == WBFBT_F32 && c->opt.precision != WBFBT_MIXED) ||
+      (c->opt.weights != WBFBT_WEIGHTS_SQRT_MU && c->opt.weights != WBFBT_WEIGHTS_GRAD) ||
+      c->opt.kinv_cycles < 1 || c->opt.kinv_cycles > 64)
     return WBFBT_ERR_INVALID;
   if (c->opt.schur_sign >= 0) c->opt.schur_sign = 1; else c->opt.schur_sign = -1;
   c->ust = (cudaStream_t)stream;
@@ -1479,6 +1567,31 @@ int wbfbt_solve(wbfbt_ctx* c, const double* f_nodes, double* u, double* p, doubl
       CK(cudaMemcpyAsync(u, c->stage_u, sizeof(double) * nu, cudaMemcpyDeviceToHost, c->st));
       CK(cudaMemcpyAsync(p, c->stage_p, sizeof(double) * np, cudaMemcpyDeviceToHost, c->st));
     }
+    CK(cudaStreamSynchronize(c->st));
+  });
+  return g != WBFBT_OK ? g : status;
+}
+
+int wbfbt_solve_block(wbfbt_ctx* c, int block, const double* b, double* x, double rtol, int maxit, int* iters,
+                      double* final_rel_res) {
+  if (!c || !b || !x || block < WBFBT_BLOCK_A || block > WBFBT_BLOCK_KR || !(rtol > 0.0) || maxit < 1)
+    return WBFBT_ERR_INVALID;
+  if (!is_device_ptr(b) || !is_device_ptr(x)) return WBFBT_ERR_INVALID;
+  int status = WBFBT_OK;
+  int g = guarded_ctx(c, [&]() {
+    const long long n = block == WBFBT_BLOCK_A ? 3LL * c->g.nn : (long long)c->g.ne * c->NP;
+    CK(cudaMemcpyAsync(c->F, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+    if (block == WBFBT_BLOCK_A)
+      CK(launch_mask_boundary<double>(c->g, 3, c->F, c->st));
+    else
+      project<double>(c, c->F, c->F);
+    status = c->mixed ? block_solve<float>(c, block, n, rtol, maxit, iters, final_rel_res)
+                      : block_solve<double>(c, block, n, rtol, maxit, iters, final_rel_res);
+    if (status != WBFBT_OK && status != WBFBT_ERR_MAXIT) return;
+    if (block == WBFBT_BLOCK_A)
+      CK(cudaMemcpyAsync(x, c->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+    else
+      project<double>(c, c->x, x);
     CK(cudaStreamSynchronize(c->st));
   });
   return g != WBFBT_OK ? g : status;

@@ -76,4 +76,6 @@ WORKLOADS = {
     "32^3-Q2-S24-DR1e6": dict(n=32, k=2, n_sinkers=24, omega=0.05, delta=200.0, dr=1e6, seed=0),
     "24^3-Q3-S32-DR1e8": dict(n=24, k=3, n_sinkers=32, omega=0.1, delta=200.0, dr=1e8, seed=0),
     "64^3-Q2-S64-DR1e10": dict(n=64, k=2, n_sinkers=64, omega=0.04, delta=400.0, dr=1e10, seed=0),
+    # the size of Table 3a's refinement level 7 (59.3M DOF) with its S16, DR 1e6 problem
+    "128^3-Q2-S16-DR1e6": dict(n=128, k=2, n_sinkers=16, omega=0.1, delta=200.0, dr=1e6, seed=0),
 }

@@ -20,6 +20,8 @@ F64, F32 = 0, 1
 MIXED = 1
 ELEM_AUTO, ELEM_POINT, ELEM_ROW = 0, 1, 2   # k = 2 element kernels: by level size, per point, row segments
 SCHUR_WBFBT, SCHUR_MASS, SCHUR_MASS_DIAG = 0, 1, 2   # S~: w-BFBT (Eq. wbfbt), lumped M_p(1/mu), diag M_p(1/mu)
+BLOCK_A, BLOCK_KL, BLOCK_KR = 0, 1, 2                # blocks for solve_block
+WEIGHTS_SQRT_MU, WEIGHTS_GRAD = 0, 1                 # w-BFBT weights: sqrt(mu), (mu^2 + |grad mu|^2)^(1/4)
 OK, ERR_INVALID, ERR_CUDA, ERR_NONFINITE, ERR_BREAKDOWN, ERR_MAXIT, ERR_SETUP = 0, -1, -2, -3, -4, -5, -6
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "non-finite value", -4: "Krylov breakdown",
           -5: "iteration limit reached", -6: "setup failed"}
@@ -31,7 +33,8 @@ SYMBOLS = ["wbfbt_default_opts", "wbfbt_sinker_setup", "wbfbt_create", "wbfbt_se
            "wbfbt_net_num_params", "wbfbt_net_create", "wbfbt_net_set_params", "wbfbt_net_get_params",
            "wbfbt_net_param_count", "wbfbt_net_forward", "wbfbt_net_loss_grad", "wbfbt_net_adam_step",
            "wbfbt_net_save", "wbfbt_net_load", "wbfbt_net_destroy", "wbfbt_attach_net", "wbfbt_learned_sample",
-           "wbfbt_learned_stats", "wbfbt_load_learned", "wbfbt_train_learned", "wbfbt_net_conv_layer"]
+           "wbfbt_learned_stats", "wbfbt_load_learned", "wbfbt_train_learned", "wbfbt_net_conv_layer",
+           "wbfbt_solve_block"]
 NOALLOC_MAX_NODES = 1 << 19
 
 
@@ -50,7 +53,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("a_l", ctypes.c_double), ("a_r", ctypes.c_double), ("restart", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("mg_min_n", ctypes.c_int), ("precision", ctypes.c_int),
                 ("schur_sign", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("elem_kernels", ctypes.c_int), ("schur", ctypes.c_int), ("arnoldi_precision", ctypes.c_int)]
+                ("elem_kernels", ctypes.c_int), ("schur", ctypes.c_int), ("arnoldi_precision", ctypes.c_int),
+                ("weights", ctypes.c_int), ("kinv_cycles", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -74,6 +78,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.wbfbt_apply_Kw.argtypes = [vp, i, vp, vp, i]
     lib.wbfbt_apply_Kinv.argtypes = [vp, i, vp, vp, i]
     lib.wbfbt_solve.argtypes = [vp, vp, vp, vp, d, i, ctypes.POINTER(i), ctypes.POINTER(d)]
+    lib.wbfbt_solve_block.argtypes = [vp, i, vp, vp, d, i, ctypes.POINTER(i), ctypes.POINTER(d)]
     lib.wbfbt_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.wbfbt_device_bytes.argtypes = [vp]
@@ -194,7 +199,7 @@ class Solver:
                  lengths=(1.0, 1.0, 1.0), a_l: float = 1.0, a_r: float = 0.0, restart: int = 50,
                  cheb_degree: int = 3, mg_min_n: int = 4, precision: int = F64, schur_sign: int = -1,
                  use_graphs: bool = True, elem_kernels: int = 0, schur: int = SCHUR_WBFBT,
-                 arnoldi_precision: int = F64):
+                 arnoldi_precision: int = F64, weights: int = WEIGHTS_SQRT_MU, kinv_cycles: int = 1):
         self.nx, self.ny, self.nz, self.k = nx, ny or nx, nz or nx, k
         self.mesh = Mesh(self.nx, self.ny, self.nz, *lengths)
         o = default_opts()
@@ -203,6 +208,8 @@ class Solver:
         o.elem_kernels = elem_kernels
         o.schur = schur
         o.arnoldi_precision = arnoldi_precision
+        o.weights = weights
+        o.kinv_cycles = kinv_cycles
         self.opts = o
         self.precision = precision
         self._mu = mu.contiguous()
@@ -303,6 +310,16 @@ class Solver:
 
     def apply_precond(self, x):
         return self._apply("wbfbt_apply_precond", x, self.n_u + self.n_p)
+
+    def solve_block(self, block: int, b: torch.Tensor, rtol: float = 1e-6, maxit: int = 1000, check=True):
+        """One preconditioner block alone (BLOCK_A, BLOCK_KL, BLOCK_KR) with FGMRES and its V-cycle."""
+        b = b.contiguous()
+        x = torch.empty_like(b)
+        its, rel = ctypes.c_int(), ctypes.c_double()
+        st = lib().wbfbt_solve_block(self.h, block, _ptr(b), _ptr(x), rtol, maxit, ctypes.byref(its), ctypes.byref(rel))
+        if check and st not in (0, -5):
+            _check(st, "wbfbt_solve_block")
+        return x, SolveResult(its.value, rel.value, st)
 
     def solve(self, f: torch.Tensor, rtol: float = 1e-6, maxit: int = 1000, u=None, p=None, check=True):
         """Solve with body force f [3][nodes] (device or pinned/pageable host float64 tensor)."""

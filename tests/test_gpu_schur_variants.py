@@ -76,3 +76,46 @@ def test_invalid_schur_option_rejected(wb):
     m, mu, _ = problem(2, 2, 1e2, 1)
     with pytest.raises(wb.WbfbtError):
         wb.Solver(2, 2, torch.tensor(mu, device="cuda"), schur=3)
+
+
+# ------------------------------------------------------------------ viscosity-gradient weights
+# w = (mu^2 + |grad mu|^2)^(1/4) in place of sqrt(mu) (remark in Sec. 4): the weighted lumped
+# masses C, D, the K_w operators, their V-cycles and the solve against the oracle.
+
+def test_gradient_weights_Kw_and_vcycle_match_oracle(wb):
+    from oracle import multigrid as mg
+    m, mu, _ = problem(8, 2, 1e4, 4)
+    prob = W.StokesProblem(m, mu, a_l=1.0, a_r=2.0, weights="grad")
+    r = op.project_pressure(m, np.random.default_rng(5).standard_normal(m.n_p))
+    s64 = wb.Solver(8, 2, torch.tensor(mu, device="cuda"), a_r=2.0, weights=wb.WEIGHTS_GRAD)
+    s32 = wb.Solver(8, 2, torch.tensor(mu, device="cuda"), a_r=2.0, weights=wb.WEIGHTS_GRAD, precision=wb.MIXED)
+    for which, cd, a in ((0, prob.Cdiag, 1.0), (1, prob.Ddiag, 2.0)):
+        K = op.assemble_Kw(prob.B, cd, m)
+        assert rel(N(s64.apply_Kw(which, torch.tensor(r, device="cuda"))), K @ r) < 1e-12
+        y32 = N(s32.apply_Kw(which, torch.tensor(r, dtype=torch.float32, device="cuda")))
+        assert rel(y32, K @ r.astype(np.float32).astype(np.float64)) < 5e-5
+        pp = mg.PressurePoissonMG(m, prob.B, cd, mu, a, "grad")
+        assert rel(N(s64.apply_Kinv(which, torch.tensor(r, device="cuda"))), pp.apply(r)) < 1e-10
+
+
+def test_gradient_weights_solve_matches_oracle(wb):
+    m, mu, f = problem(8, 2, 1e6, 8)
+    uo, po, its, relo, _ = W.solve(m, mu, f, W.Options(weights="grad"))
+    s = wb.Solver(8, 2, torch.tensor(mu, device="cuda"), weights=wb.WEIGHTS_GRAD)
+    u, p, res = s.solve(torch.tensor(f.T.ravel(), device="cuda"))
+    assert res.status == 0 and abs(res.iters - its) <= 1, (res.iters, its)
+    assert rel(N(u), uo) < 1e-10 and rel(N(p), po) < 1e-10
+
+
+def test_several_kinv_cycles_match_oracle(wb):
+    """kinv_cycles = 3: each K~_w^-1 runs three residual-correcting V-cycles, on both sides."""
+    m, mu, f = problem(8, 2, 1e6, 8)
+    uo, po, its, relo, _ = W.solve(m, mu, f, W.Options(kinv_cycles=3))
+    s = wb.Solver(8, 2, torch.tensor(mu, device="cuda"), kinv_cycles=3)
+    r = op.project_pressure(m, np.random.default_rng(6).standard_normal(m.n_p))
+    prob = W.StokesProblem(m, mu)
+    ref = W.WBFBT(prob, "vcycle", 3)
+    assert rel(N(s.apply_schur_inv(torch.tensor(r, device="cuda"))), ref.apply(r)) < 1e-10
+    u, p, res = s.solve(torch.tensor(f.T.ravel(), device="cuda"))
+    assert res.status == 0 and abs(res.iters - its) <= 1, (res.iters, its)
+    assert rel(N(u), uo) < 1e-10 and rel(N(p), po) < 1e-10

@@ -221,3 +221,23 @@ def test_schur_complement_positive_definite_on_mean_zero():
     S = B[:, free] @ spla.splu(Af).solve(B[:, free].T.toarray())
     ev = np.linalg.eigvalsh(0.5 * (S + S.T))
     assert ev[0] > -1e-12 and ev[1] > 1e-6   # S = B A^-1 B^T, kernel = constants only
+
+
+def test_gradient_weights_on_polynomial_viscosity():
+    """Viscosity-gradient w-BFBT weights (remark in Sec. 4): w = (mu^2 + |grad mu|^2)^(1/4).
+    Q2 interpolates mu = 1 + x^2 + 3y exactly, so at every element point grad mu = (2x, 3, 0)."""
+    from oracle import mesh as Mm
+    m = Mm.Mesh(3, 2, 2, 2, 1.5, 1.0, 0.5)
+    X = m.node_coords()
+    mu = 1.0 + X[:, 0] ** 2 + 3.0 * X[:, 1]
+    w = op.weight_points(m, mu, "grad")
+    Xq = X[m.point_to_node()]                              # (n_elem, n^3, 3)
+    mq = 1.0 + Xq[..., 0] ** 2 + 3.0 * Xq[..., 1]
+    np.testing.assert_allclose(w, (mq ** 2 + 4.0 * Xq[..., 0] ** 2 + 9.0) ** 0.25, rtol=1e-12)
+    np.testing.assert_allclose(op.weight_points(m, mu, "sqrt_mu"), np.sqrt(mq), rtol=1e-14)
+    # a constant viscosity has no gradient: both weights agree
+    c = np.full(m.n_nodes, 7.0)
+    np.testing.assert_allclose(op.weight_points(m, c, "grad"), op.weight_points(m, c, "sqrt_mu"), rtol=1e-14)
+    # the lumped weight sums W |J| a(e) w over the points at a node; the total is the integral
+    tot = op.lumped_weight_diag(m, mu, 1.0, "grad").sum()
+    np.testing.assert_allclose(tot, (w * (m.W * m.detJ)[None, :]).sum(), rtol=1e-13)
