@@ -241,13 +241,14 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
 
 # --------------------------------------------------------------------------- GPU arm
 
-def traffic_for(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+def traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, if the
+    kernel sources are unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     data = json.load(open(path))
-    ent = data.get(kernel)
+    ent = data.get(f"{kernel}@{workload}")
     if not ent:
         return None
     srcs = ent["source"] if isinstance(ent["source"], list) else [ent["source"]]
@@ -417,7 +418,7 @@ def finish_ours(args, name, cfg, rank, world, R):
     np_e = k * (k + 1) * (k + 2) // 6
     flops_k = flops_a + (k + 1) ** 3 * (4 * np_e + 7) * n_elem
     roof64 = {"bound": "alu", "achieved": flops_k / t_k64 / 1e12, "peak": peak64, "unit": "TFLOP/s",
-              "frac": flops_k / t_k64 / 1e12 / peak64, "traffic": traffic_for("apply_K_f64"),
+              "frac": flops_k / t_k64 / 1e12 / peak64, "traffic": traffic_for("apply_K_f64", name),
               "kernel": "k_q2_elem64<OP_A|OP_BT|OP_B,iso> + k_q2_gather<double,3,STORE> (the FP64 Arnoldi K apply)",
               "per_launch": ("one fine-level K = [A B^T; B 0] apply: (36n^4 + 30n^3 + n^3 (4 Np + 7)) flops per "
                              f"element x {n_elem} elements"),
@@ -426,11 +427,11 @@ def finish_ours(args, name, cfg, rank, world, R):
     roof32 = None
     if t_a32:
         roof32 = {"bound": "hbm", "achieved": bytes32 / t_a32 / 1e9, "peak": hbm, "unit": "GB/s",
-                  "frac": bytes32 / t_a32 / 1e9 / hbm, "traffic": traffic_for("apply_A_f32"),
+                  "frac": bytes32 / t_a32 / 1e9 / hbm, "traffic": traffic_for("apply_A_f32", name),
                   "kernel": "k_q2_elem<OP_A> + k_q2_gather<3,STORE> (one FP32 A apply)", "peak_note": hbm_note,
                   "per_launch": f"7 words x 4 B per node x {n_nodes} nodes (u, y, mu)"}
     roofA64 = {"bound": "alu", "achieved": flops_a / t_a64 / 1e12, "peak": peak64, "unit": "TFLOP/s",
-               "frac": flops_a / t_a64 / 1e12 / peak64, "traffic": traffic_for("apply_A_f64"),
+               "frac": flops_a / t_a64 / 1e12 / peak64, "traffic": traffic_for("apply_A_f64", name),
                "kernel": "k_q2_elem64<OP_A,iso> + k_q2_gather<double,3,STORE> (one FP64 A apply)"}
 
     # end to end through the C ABI, the call a user with host data makes: every step copies the
@@ -536,6 +537,31 @@ def run_profile(args, name, cfg):
     torch.cuda.nvtx.range_pop()
     print(json.dumps({"profile": name, "precision": args.precision, "create_launches": n0,
                       "solve_launches": wb.launch_count() - n0, "iters": res.iters, "rel_res": res.rel_res}),
+          flush=True)
+    solver.close()
+
+
+def run_profile_setup(args, name, cfg):
+    """One viscosity-dependent setup (wbfbt_setup) inside an NVTX range "prof", after the
+    context's creation, for an ncu launch list of the setup."""
+    import torch
+
+    from paper_1607_03936_gb300 import build
+    build.build()
+    from paper_1607_03936_gb300 import inputs
+    from paper_1607_03936_gb300 import wbfbt as wb
+
+    n, k = cfg["n"], cfg["k"]
+    centres = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
+    mu, _ = wb.sinker_setup(n, k, centres, cfg["omega"], cfg["delta"], cfg["dr"])
+    solver = wb.Solver(n, k, mu, precision=wb.MIXED if args.precision == "mixed" else wb.F64)
+    torch.cuda.synchronize()
+    n0 = wb.launch_count()
+    torch.cuda.nvtx.range_push("prof")
+    solver.setup(mu)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_setup": name, "precision": args.precision, "setup_launches": wb.launch_count() - n0}),
           flush=True)
     solver.close()
 
@@ -713,6 +739,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="one setup + solve of the workload and nothing else (for an ncu launch list)")
+    ap.add_argument("--profile-setup", action="store_true",
+                    help="one viscosity-dependent setup in an NVTX range 'prof' (for an ncu launch list)")
     ap.add_argument("--profile-apply", action="store_true",
                     help="one FP64 A, one FP32 A and one FP64 K apply in an NVTX range 'prof' (for ncu)")
     ap.add_argument("--sweep", choices=["robustness", "amplification", "order", "alone", "kcycles"],
@@ -737,6 +765,9 @@ def main():
         return
     if args.profile:
         run_profile(args, name, cfg)
+        return
+    if args.profile_setup:
+        run_profile_setup(args, name, cfg)
         return
     if world > 1:
         import torch
