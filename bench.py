@@ -610,9 +610,9 @@ SWEEP_DR = (1e4, 1e6, 1e8, 1e10)
 def run_sweep(args):
     """Iteration-count sweeps in the style of the paper's tables, one JSON line per solve.
 
-    robustness (Sec. 4, Table 1): w-BFBT (sqrt(mu) and viscosity-gradient weights) against the
-      inverse-viscosity pressure mass (lumped, Eq. lumping, and its diagonal) over sinker counts x
-      dynamic ratios, n^3 Q2, omega 0.1, delta 200, seeded centres;
+    robustness (Sec. 4, Table 1): w-BFBT (sqrt(mu) and viscosity-gradient weights) against
+      diag(A)-BFBT and the inverse-viscosity pressure mass (lumped, Eq. lumping, and its diagonal)
+      over sinker counts x dynamic ratios, n^3 Q2, omega 0.1, delta 200, seeded centres;
     amplification (Sec. 5, Table 2): w-BFBT with a_l = 1 and a_r in {1, 2, 4, 8, 16, 32};
     order (Sec. 7, Table 3b): w-BFBT for k = 2, 3, 4 on the same mesh, a_r by the Table 3 rule;
     alone (Sec. 7, Table 3): the viscous block and K_{w_r} solved on their own with their V-cycles
@@ -655,6 +655,9 @@ def run_sweep(args):
                 r = solve(2, ns, dr, weights=wb.WEIGHTS_GRAD)
                 print(json.dumps({"sweep": "robustness", **base, "k": 2, "sinkers": ns, "dr": dr,
                                   "schur": "w-BFBT, gradient weights", **r}), flush=True)
+                r = solve(2, ns, dr, weights=wb.WEIGHTS_DIAG_A)
+                print(json.dumps({"sweep": "robustness", **base, "k": 2, "sinkers": ns, "dr": dr,
+                                  "schur": "diag(A)-BFBT", **r}), flush=True)
     elif args.sweep == "amplification":
         for k in (2, 3, 4):
             for a_r in (1.0, 2.0, 4.0, 8.0, 16.0, 32.0):

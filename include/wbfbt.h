@@ -90,7 +90,10 @@ typedef struct {
                                       D = M~_u(a_r w): WBFBT_WEIGHTS_SQRT_MU (default,
                                       w = sqrt(mu), Eq. wbfbt) or WBFBT_WEIGHTS_GRAD
                                       (w = (mu^2 + |grad mu|^2)^(1/4), the remark in Sec. 4;
-                                      grad mu of each element's Q_k interpolant, per point)  */
+                                      grad mu of each element's Q_k interpolant, per point);
+                                      WBFBT_WEIGHTS_DIAG_A: C = D = diag(A) per DOF, the
+                                      diag(A)-BFBT of Sec. 1.3 (a_l, a_r unused; the Poisson
+                                      V-cycles use the coefficient 1/mu)                     */
     int kinv_cycles;               /* V-cycles per application of K~_l^-1 and K~_r^-1 inside
                                       S~^-1 (default 1, Sec. 6; 1..64): each further cycle
                                       corrects the residual, x += V(b - K_w x)             */
@@ -101,6 +104,7 @@ typedef struct {
 #define WBFBT_SCHUR_MASS_DIAG 2
 #define WBFBT_WEIGHTS_SQRT_MU 0
 #define WBFBT_WEIGHTS_GRAD 1
+#define WBFBT_WEIGHTS_DIAG_A 2
 
 #define WBFBT_ELEM_AUTO 0
 #define WBFBT_ELEM_POINT 1

@@ -122,6 +122,9 @@ def weight_points(mesh: Mesh, mu_nodes: np.ndarray, weights: str = "sqrt_mu") ->
     if weights == "grad":
         g2 = sum((gradient_op(mesh, d) @ mu_nodes) ** 2 for d in range(3)).reshape(mu_q.shape)
         return (mu_q ** 2 + g2) ** 0.25
+    if weights == "diag_a":
+        # diag(A)-BFBT scales like mu (diag(A) ~ mu); its Poisson surrogate uses the coefficient 1/mu
+        return mu_q
     raise ValueError(weights)
 
 
@@ -138,10 +141,14 @@ def lumped_weight_diag(mesh: Mesh, mu_nodes: np.ndarray, a: float, weights: str 
 
 
 def assemble_Kw(B: sp.csr_matrix, cdiag: np.ndarray, mesh: Mesh) -> sp.csr_matrix:
-    """Pressure Poisson matrix K_w = B C_w^-1 B^T (Sec. 6); C_w^-1 zeroed at Dirichlet nodes."""
-    inv = np.where(mesh.boundary_node_mask(), 0.0, 1.0 / cdiag)
-    Cinv = sp.diags(np.tile(inv, 3))
-    return (B @ Cinv @ B.T).tocsr()
+    """Pressure Poisson matrix K_w = B C_w^-1 B^T (Sec. 6); C_w^-1 zeroed at Dirichlet nodes.
+    cdiag per node (n_nodes,), shared by the three components, or per DOF (3 n_nodes,)."""
+    bmask = mesh.boundary_node_mask()
+    if cdiag.size == 3 * mesh.n_nodes:
+        inv = np.where(np.tile(bmask, 3), 0.0, 1.0 / np.where(np.tile(bmask, 3), 1.0, cdiag))
+    else:
+        inv = np.tile(np.where(bmask, 0.0, 1.0 / cdiag), 3)
+    return (B @ sp.diags(inv) @ B.T).tocsr()
 
 
 def assemble_Lc(mesh: Mesh, c_pts: np.ndarray) -> sp.csr_matrix:

@@ -46,7 +46,8 @@ class Options:
     mode: str = "vcycle"
     schur: str = "wbfbt"       # "wbfbt" (Eq. wbfbt), "mass" (lumped M_p(1/mu), Eq. lumping),
                                # "mass_diag" (the diagonal of M_p(1/mu))
-    weights: str = "sqrt_mu"   # w-BFBT weights: "sqrt_mu" (Eq. wbfbt) or "grad" (remark in Sec. 4)
+    weights: str = "sqrt_mu"   # w-BFBT weights: "sqrt_mu" (Eq. wbfbt), "grad" (remark in Sec. 4), or
+                               # "diag_a": C = D = diag(A), the diag(A)-BFBT of Sec. 1.3
     kinv_cycles: int = 1       # V-cycles per K~_w^-1 application: x += V(b - K_w x) after the first
 
 
@@ -63,11 +64,18 @@ class StokesProblem:
         self.A = op.assemble_A(mesh, op.point_values(mesh, self.mu))
         self.B = op.assemble_B(mesh)
         self.BT = self.B.T.tocsr()
-        self.Cdiag = op.lumped_weight_diag(mesh, self.mu, self.a_l, weights)
-        self.Ddiag = op.lumped_weight_diag(mesh, self.mu, self.a_r, weights)
         interior = ~mesh.boundary_node_mask()
-        self.Cinv = np.tile(np.where(interior, 1.0 / self.Cdiag, 0.0), 3)
-        self.Dinv = np.tile(np.where(interior, 1.0 / self.Ddiag, 0.0), 3)
+        if weights == "diag_a":
+            # diag(A)-BFBT (Sec. 1.3): C = D = diag(A), one entry per velocity DOF
+            dA = self.A.diagonal()
+            free = np.tile(interior, 3)
+            self.Cdiag = self.Ddiag = np.where(free, dA, 1.0)
+            self.Cinv = self.Dinv = np.where(free, 1.0 / self.Cdiag, 0.0)
+        else:
+            self.Cdiag = op.lumped_weight_diag(mesh, self.mu, self.a_l, weights)
+            self.Ddiag = op.lumped_weight_diag(mesh, self.mu, self.a_r, weights)
+            self.Cinv = np.tile(np.where(interior, 1.0 / self.Cdiag, 0.0), 3)
+            self.Dinv = np.tile(np.where(interior, 1.0 / self.Ddiag, 0.0), 3)
         self.nu, self.npr = mesh.n_u, mesh.n_p
 
     def apply_K(self, x: np.ndarray) -> np.ndarray:
@@ -107,8 +115,9 @@ class WBFBT:
             self.Kl_inv = _PinnedLU(op.assemble_Kw(prob.B, prob.Cdiag, m), m)
             self.Kr_inv = _PinnedLU(op.assemble_Kw(prob.B, prob.Ddiag, m), m)
         elif mode == "vcycle":
-            self.Kl_mg = mg.PressurePoissonMG(m, prob.B, prob.Cdiag, prob.mu, prob.a_l, prob.weights)
-            self.Kr_mg = mg.PressurePoissonMG(m, prob.B, prob.Ddiag, prob.mu, prob.a_r, prob.weights)
+            a_l, a_r = (1.0, 1.0) if prob.weights == "diag_a" else (prob.a_l, prob.a_r)
+            self.Kl_mg = mg.PressurePoissonMG(m, prob.B, prob.Cdiag, prob.mu, a_l, prob.weights)
+            self.Kr_mg = mg.PressurePoissonMG(m, prob.B, prob.Ddiag, prob.mu, a_r, prob.weights)
             self.Kl_inv, self.Kr_inv = self._cycles(self.Kl_mg, kinv_cycles), self._cycles(self.Kr_mg, kinv_cycles)
         else:
             raise ValueError(mode)

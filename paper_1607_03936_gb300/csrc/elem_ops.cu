@@ -369,7 +369,8 @@ __global__ void k_dinv_stiff(Grid g, const RefTables* __restrict__ tab, const T*
 
 // diag(B C^-1 B^T) per (element, mode): sum over element velocity DOFs of B_e[m][(c,a)]^2 cinv(a).
 template <typename T, int N>
-__global__ void k_dinv_Kw(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ cinv, T* __restrict__ dinv) {
+__global__ void k_dinv_Kw(Grid g, const RefTables* __restrict__ tab, const T* __restrict__ cinv, int per_dof,
+                          T* __restrict__ dinv) {
   pdl_entry();
   constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, K = N - 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -380,9 +381,9 @@ __global__ void k_dinv_Kw(Grid g, const RefTables* __restrict__ tab, const T* __
   for (int q = 0; q < N3; ++q) {
     const int a[3] = {q % N, (q / N) % N, q / (N * N)};
     const int node = (K * ex + a[0]) + g.NX * ((K * ey + a[1]) + g.NY * (K * ez + a[2]));
-    const double ci = (double)cinv[node];
-    if (ci == 0.0) continue;
     for (int c = 0; c < 3; ++c) {
+      const double ci = (double)cinv[(per_dof ? (size_t)c * g.nn : 0) + node];
+      if (ci == 0.0) continue;
       double b = 0.0;
       for (int ii = 0; ii < N; ++ii) {
         int qq[3] = {a[0], a[1], a[2]};
@@ -750,8 +751,10 @@ cudaError_t launch_dinv_L(const Grid& g, int k, const RefTables* dtab, const T* 
 }
 
 template <typename T>
-cudaError_t launch_dinv_Kw(const Grid& g, int k, const RefTables* dtab, const T* cinv, T* dinv, cudaStream_t st) {
-  WB_DISPATCH_N(k, ((wb_launch(k_dinv_Kw<T, N>, blocks_for((long long)g.ne * Cfg<N>::NP, 128), 128, 0, st, g, dtab, cinv, dinv)),
+cudaError_t launch_dinv_Kw(const Grid& g, int k, const RefTables* dtab, const T* cinv, int per_dof, T* dinv,
+                           cudaStream_t st) {
+  WB_DISPATCH_N(k, ((wb_launch(k_dinv_Kw<T, N>, blocks_for((long long)g.ne * Cfg<N>::NP, 128), 128, 0, st, g, dtab, cinv,
+                               per_dof, dinv)),
                     cudaGetLastError()));
 }
 
@@ -921,7 +924,7 @@ cudaError_t launch_load_vector(const Grid& g, const double* lm, const double* f,
   template cudaError_t launch_poisson<T>(const Grid&, int, const RefTables*, const T*, const T*, T*, cudaStream_t); \
   template cudaError_t launch_dinv_A<T>(const Grid&, int, const RefTables*, const T*, int, T*, cudaStream_t);       \
   template cudaError_t launch_dinv_L<T>(const Grid&, int, const RefTables*, const T*, T*, cudaStream_t);            \
-  template cudaError_t launch_dinv_Kw<T>(const Grid&, int, const RefTables*, const T*, T*, cudaStream_t);           \
+  template cudaError_t launch_dinv_Kw<T>(const Grid&, int, const RefTables*, const T*, int, T*, cudaStream_t);           \
   template cudaError_t launch_poisson_coef0<T>(const Grid&, int, const double*, double, T*, cudaStream_t);          \
   template cudaError_t launch_nodal_to_points<T>(const Grid&, int, const double*, T*, cudaStream_t);                \
   template cudaError_t launch_coarsen_coef<T>(const Grid&, int, const RefTables*, const T*, T*, cudaStream_t);      \

@@ -42,8 +42,10 @@ cudaError_t launch_dinv_A(const Grid& g, int k, const RefTables* dtab, const T* 
                           cudaStream_t st);
 template <typename T>
 cudaError_t launch_dinv_L(const Grid& g, int k, const RefTables* dtab, const T* coef, T* dinv, cudaStream_t st);
+// per_dof = 0: cinv per node [nn], shared by the three components; 1: per DOF [3][nn].
 template <typename T>
-cudaError_t launch_dinv_Kw(const Grid& g, int k, const RefTables* dtab, const T* cinv, T* dinv, cudaStream_t st);
+cudaError_t launch_dinv_Kw(const Grid& g, int k, const RefTables* dtab, const T* cinv, int per_dof, T* dinv,
+                           cudaStream_t st);
 
 // Lumped sqrt(mu)-weighted velocity mass M~_u(w), w = a(e) sqrt(mu), per node (FP64), and its
 // inverse in T with zeros on Dirichlet nodes.

@@ -11,6 +11,7 @@
 // order, so every result is reproducible.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -125,11 +126,13 @@ __global__ void __launch_bounds__(128) k_conv(int n, int batch, const bf16* __re
 }
 
 // dW[t][ci][co] = sum_{b,v} x[b][nbr(v,t)][ci] g[b][v][co]: block per (tap, 16-channel ci tile),
-// 8 warps split the voxels, partial tiles reduced in warp order.
+// 8 warps split the voxels, partial tiles reduced in warp order.  With gridDim.z = S > 1 the
+// voxel chunks are also split over S blocks (chunk kk goes to block kk / 8 mod S), each block
+// writing its partial tile to part[blockIdx.z]; k_wgrad_sum adds the S partials in order.
 template <int NT>
 __global__ void __launch_bounds__(256) k_wgrad(int n, int batch, const bf16* __restrict__ x, int ldx, int cin,
                                                const bf16* __restrict__ g, int ldg, int cout,
-                                               float* __restrict__ dW) {
+                                               float* __restrict__ dW, float* __restrict__ part) {
   pdl_entry();
   const int V = n * n * n, tot = V * batch;
   const int tap = blockIdx.x, ci0 = blockIdx.y * 16;
@@ -138,7 +141,9 @@ __global__ void __launch_bounds__(256) k_wgrad(int n, int batch, const bf16* __r
 #pragma unroll
   for (int t = 0; t < NT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
   const int ks = (tot + 15) / 16;
-  for (int kk = w; kk < ks; kk += 8) {
+  const int S = gridDim.z;
+  float* out = S > 1 ? part + (size_t)blockIdx.z * 27 * cin * cout : dW;
+  for (int kk = blockIdx.z * 8 + w; kk < ks; kk += 8 * S) {
     const int k0 = kk * 16;
     // A: 16 (ci) x 16 (voxels); B: 16 (voxels) x 8 (co)
     bf16 xa[4][2];
@@ -193,8 +198,18 @@ __global__ void __launch_bounds__(256) k_wgrad(int n, int batch, const bf16* __r
     float s = 0.f;
     for (int ww = 0; ww < 8; ++ww) s += red[ww][r][c];
     const int ci = ci0 + r;
-    if (ci < cin && c < cout) dW[((size_t)tap * cin + ci) * cout + c] = s;
+    if (ci < cin && c < cout) out[((size_t)tap * cin + ci) * cout + c] = s;
   }
+}
+
+// dW[i] = sum_{s < S} part[s][i], in the order of s (reproducible).
+__global__ void k_wgrad_sum(int S, long long n, const float* __restrict__ part, float* __restrict__ dW) {
+  pdl_entry();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float acc = 0.f;
+  for (int s2 = 0; s2 < S; ++s2) acc += part[(size_t)s2 * n + i];
+  dW[i] = acc;
 }
 
 // db[co] = sum over rows of g[row][co] (one block per channel, fixed tree)
@@ -398,15 +413,32 @@ void conv(int npad, int n, int batch, const bf16* x, int ldx, int kp, const bf16
   }
 }
 
+constexpr int WGRAD_MAX_SPLIT = 8;
+
+// Blocks in z (voxel-chunk split) for a weight gradient: fill about two blocks per SM, keep at
+// least four 16-voxel chunks per warp, at most WGRAD_MAX_SPLIT.
+int wgrad_split(int n, int batch, int cin) {
+  const long long ks = ((long long)n * n * n * batch + 15) / 16;
+  const int tiles = 27 * ((cin + 15) / 16);
+  int S = (2 * 152 + tiles - 1) / tiles;
+  while (S > 1 && ks < 8LL * 4 * S) --S;
+  return std::max(1, std::min(S, WGRAD_MAX_SPLIT));
+}
+
 void wgrad(int n, int batch, const bf16* x, int ldx, int cin, const bf16* g, int ldg, int cout, float* dW,
-           cudaStream_t st) {
-  dim3 grid(27, (cin + 15) / 16);
+           float* part, cudaStream_t st) {
+  const int S = part ? wgrad_split(n, batch, cin) : 1;
+  dim3 grid(27, (cin + 15) / 16, S);
   switch (r8(cout) / 8) {
-    case 1: wb_launch(k_wgrad<1>, grid, 256, 0, st, n, batch, x, ldx, cin, g, ldg, cout, dW); break;
-    case 2: wb_launch(k_wgrad<2>, grid, 256, 0, st, n, batch, x, ldx, cin, g, ldg, cout, dW); break;
-    case 4: wb_launch(k_wgrad<4>, grid, 256, 0, st, n, batch, x, ldx, cin, g, ldg, cout, dW); break;
-    case 8: wb_launch(k_wgrad<8>, grid, 256, 0, st, n, batch, x, ldx, cin, g, ldg, cout, dW); break;
+    case 1: wb_launch(k_wgrad<1>, grid, 256, 0, st, n, batch, x, ldx, cin, g, ldg, cout, dW, part); break;
+    case 2: wb_launch(k_wgrad<2>, grid, 256, 0, st, n, batch, x, ldx, cin, g, ldg, cout, dW, part); break;
+    case 4: wb_launch(k_wgrad<4>, grid, 256, 0, st, n, batch, x, ldx, cin, g, ldg, cout, dW, part); break;
+    case 8: wb_launch(k_wgrad<8>, grid, 256, 0, st, n, batch, x, ldx, cin, g, ldg, cout, dW, part); break;
     default: break;
+  }
+  if (S > 1) {
+    const long long cnt = 27LL * cin * cout;
+    wb_launch(k_wgrad_sum, nb(cnt, 256), 256, 0, st, S, cnt, (const float*)part, dW);
   }
 }
 
@@ -419,6 +451,7 @@ struct wbfbt_net {
   std::vector<Layer> L;
   std::vector<void*> allocs;
   float *theta = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
+  float* wpart = nullptr;   // split weight-gradient partials [WGRAD_MAX_SPLIT][largest 27 cin cout]
   double *part = nullptr, *dloss = nullptr;
   int adam_t = 0;
   // activations (BF16, [batch][voxels][ld])
@@ -482,7 +515,7 @@ void backward(wbfbt_net* N, int B) {
   auto& L = N->L;
   float* G = N->grad;
   auto layer_grads = [&](int i, int n, const bf16* xin, int ldx, const bf16* g, int ldg, long long rows) {
-    wgrad(n, B, xin, ldx, L[i].cin, g, ldg, L[i].cout, G + L[i].woff, st);
+    wgrad(n, B, xin, ldx, L[i].cin, g, ldg, L[i].cout, G + L[i].woff, N->wpart, st);
     wb_launch(k_colsum, L[i].cout, 256, 0, st, g, ldg, rows, G + L[i].boff);
   };
   // bwd data: input g (ld kpb), output (ld of the layer input), ReLU mask of the layer input
@@ -570,6 +603,9 @@ int wbfbt_net_create(int cin, int cout, int n, int max_batch, void* stream, wbfb
       N->L.push_back(l);
     }
     N->nparam = (long long)off;
+    size_t wmax = 0;
+    for (const auto& l : N->L) wmax = std::max(wmax, (size_t)27 * l.cin * l.cout);
+    N->wpart = N->get<float>((size_t)WGRAD_MAX_SPLIT * wmax);
     N->theta = N->get<float>(off);
     N->grad = N->get<float>(off);
     N->m1 = N->get<float>(off);
@@ -743,7 +779,7 @@ int wbfbt_net_conv_layer(wbfbt_net* N, int layer, int n, int batch, const float*
            0, y, l.cout, N->st);
     if (g) {
       wb_launch(k_pack_input, nb(rows * ldg, 256), 256, 0, N->st, rows, l.cout, ldg, g, gb);
-      wgrad(n, batch, xb, l.kp, l.cin, gb, ldg, l.cout, dW, N->st);
+      wgrad(n, batch, xb, l.kp, l.cin, gb, ldg, l.cout, dW, N->wpart, N->st);
     }
     if (cudaStreamSynchronize(N->st) != cudaSuccess) throw 1;
   });

@@ -105,6 +105,7 @@ struct Precond {
   T* Kst[2] = {nullptr, nullptr};                       // assembled K_w stencils (k <= 3), w_l and w_r
   T* kwin = nullptr;                                    // copy of a K_w input its epilogue overwrites
   T* Mp = nullptr;                                      // lumped M_p(1/mu)^-1 blocks [ne][Np][Np] (schur = MASS)
+  T* wdof = nullptr;                                    // diag(A)^-1 per DOF [3][nn] (weights = DIAG_A): C = D = diag(A)
   double *c0[2] = {nullptr, nullptr}, *dK64[2] = {nullptr, nullptr};
 };
 
@@ -137,7 +138,8 @@ struct wbfbt_ctx {
   double* part = nullptr;   // reduction partials
   double* kwbref = nullptr; // reference divergence matrix for the K_w assembly (k <= 3)
   double* Mp64 = nullptr;   // lumped M_p(1/mu)^-1 blocks in FP64 (schur = MASS)
-  double* wpts = nullptr;   // w-BFBT weights per element point (weights = GRAD)
+  double* wpts = nullptr;   // w-BFBT weights per element point (weights = GRAD), or mu per point (DIAG_A)
+  double* adinv64 = nullptr;// diag(A)^-1 per DOF, 0 on Dirichlet DOFs (weights = DIAG_A)
   double* dsc = nullptr;    // device scalars (64)
   int* dflag = nullptr;
   Precond<double> P64;
@@ -228,6 +230,16 @@ Epi<T> epi_scale(T* y, const T* sc) {
   return e;
 }
 
+// y[i] = dinv[i] v per entry (a per-DOF diagonal scaling)
+template <typename T>
+Epi<T> epi_dinv(T* y, const T* dinv) {
+  Epi<T> e;
+  e.mode = EPI_DINV;
+  e.y = y;
+  e.dinv = dinv;
+  return e;
+}
+
 // Level operator (A for the vector hierarchy, L_c for the scalar ones) with epilogue.
 template <typename T>
 void level_apply(wbfbt_ctx* c, const Hier<T>& H, const Level<T>& L, const T* u, const Epi<T>& e) {
@@ -265,7 +277,7 @@ void op_Kw(wbfbt_ctx* c, int which, const T* p, const Epi<T>& e) {
     return;
   }
   const T* winv = which == 0 ? P.cinv : P.dinvw;
-  apply_BT_epi<T>(c, p, epi_scale<T>(P.vtmp, winv));
+  apply_BT_epi<T>(c, p, P.wdof ? epi_dinv<T>(P.vtmp, P.wdof) : epi_scale<T>(P.vtmp, winv));
   CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_B, P.vtmp, nullptr, nullptr, nullptr, 0, nullptr, e, c->st));
 }
 
@@ -479,9 +491,10 @@ void schur_inv(wbfbt_ctx* c, const T* r, T* y) {
   }
   kinv_any<T>(c, 1, P.sr, P.sy);
   // middle factor B C^-1 A D^-1 B^T y, each diagonal scaling fused into the preceding node pass
-  apply_BT_epi<T>(c, P.sy, epi_scale<T>(P.sv1, P.dinvw));
+  apply_BT_epi<T>(c, P.sy, P.wdof ? epi_dinv<T>(P.sv1, P.wdof) : epi_scale<T>(P.sv1, P.dinvw));
   CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_A, P.sv1, nullptr, nullptr, P.mu, 1, P.Ye, Epi<T>(), c->st));
-  CK(launch_gather<T>(c->g, c->k, 3, 1, P.Ye, epi_scale<T>(P.sv2, P.cinv), c->st));
+  CK(launch_gather<T>(c->g, c->k, 3, 1, P.Ye, P.wdof ? epi_dinv<T>(P.sv2, P.wdof) : epi_scale<T>(P.sv2, P.cinv),
+                     c->st));
   CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_B, P.sv2, nullptr, nullptr, nullptr, 0, nullptr,
                            epi_store<T>(P.sz), c->st));
   kinv_any<T>(c, 0, P.sz, P.sy2);
@@ -679,6 +692,15 @@ void build_precond(wbfbt_ctx* c) {
     CK((launch_cast<double, T>((long long)nn, c->cinv64, P.cinv, c->st)));
     CK((launch_cast<double, T>((long long)nn, c->dinv64, P.dinvw, c->st)));
   }
+  const bool diag_a = c->opt.weights == WBFBT_WEIGHTS_DIAG_A;
+  if (diag_a) {   // diag(A)-BFBT: C = D = diag(A) per DOF (Sec. 1.3)
+    if (std::is_same<T, double>::value) {
+      P.wdof = reinterpret_cast<T*>(c->adinv64);
+    } else {
+      c->pool.ensure(P.wdof, nu);
+      CK((launch_cast<double, T>((long long)nu, c->adinv64, P.wdof, c->st)));
+    }
+  }
   for (T** q : {&P.pb, &P.px, &P.pr, &P.pd, &P.ptmp, &P.sr, &P.sy, &P.sz, &P.sy2}) c->pool.ensure(*q, np);
   for (T** q : {&P.vtmp, &P.sv1, &P.sv2, &P.urhs, &P.utmp}) c->pool.ensure(*q, nu);
   c->pool.ensure(P.vin, c->ntot);
@@ -701,21 +723,25 @@ void build_precond(wbfbt_ctx* c) {
     c->pool.ensure(P.c0[wi], npts);
     if (c->opt.weights == WBFBT_WEIGHTS_GRAD)
       CK(launch_poisson_coef_pts<double>(g, c->k, c->wpts, amp[wi], P.c0[wi], c->st));
+    else if (diag_a)   // the Poisson surrogate of B diag(A)^-1 B^T: coefficient 1/mu (weight mu)
+      CK(launch_poisson_coef_pts<double>(g, c->k, c->wpts, 1.0, P.c0[wi], c->st));
     else
       CK(launch_poisson_coef0<double>(g, c->k, c->mu64, amp[wi], P.c0[wi], c->st));
     build_hier<T>(c, P.HL[wi], false, P.c0[wi], 0);
     // disc level: Jacobi diagonal of K_w and lambda_hat
     c->pool.ensure(P.dK64[wi], np);
-    if (c->kwbref)
+    if (diag_a)
+      CK(launch_dinv_Kw<double>(g, c->k, c->dtab, c->adinv64, 1, P.dK64[wi], c->st));
+    else if (c->kwbref)
       CK(launch_kw_dinv<double>(g, c->k, c->kwbref, wi == 0 ? c->cinv64 : c->dinv64, P.dK64[wi], c->st));
     else
-      CK(launch_dinv_Kw<double>(g, c->k, c->dtab, wi == 0 ? c->cinv64 : c->dinv64, P.dK64[wi], c->st));
+      CK(launch_dinv_Kw<double>(g, c->k, c->dtab, wi == 0 ? c->cinv64 : c->dinv64, 0, P.dK64[wi], c->st));
     c->pool.ensure(P.dKw[wi], np);
     CK((launch_cast<double, T>((long long)np, P.dK64[wi], P.dKw[wi], c->st)));
     // FP64 preconditioners apply K_w as an assembled stencil (one memory-bound pass instead of
     // three FP64-bound element/node passes: 3x faster at 32^3 Q2); single precision keeps the
     // matrix-free row kernels, which move fewer bytes (the stencil is 27 Np^2 words per element)
-    if (c->kwbref && std::is_same<T, double>::value) {
+    if (c->kwbref && std::is_same<T, double>::value && !diag_a) {
       c->pool.ensure(P.Kst[wi], kw_stencil_entries(g, c->k));
       c->pool.ensure(P.kwin, np);
       CK(launch_kw_assemble<T>(g, c->k, c->kwbref, wi == 0 ? c->cinv64 : c->dinv64, P.Kst[wi], c->st));
@@ -897,7 +923,10 @@ int fgmres_core(wbfbt_ctx* c, long long n, const double* F, double* x, double* r
       double* zj = c->Z + (size_t)j * n;
       pc(vj, zj);
       arn(zj, c->w);
-      // CGS2: h = V^T w, w -= V h, twice
+      // CGS2: h = V^T w, w -= V h, twice.  (A second pass only when the first shrank w below
+      // 1/sqrt(2) of its norm was measured slower: with a good preconditioner K z_j is close to
+      // v_j, the first projection removes most of w, and the test asked for the second pass
+      // almost every step, at the cost of an extra host synchronisation.)
       double* h1 = c->hdev;
       double* h2 = c->hdev + (m + 1);
       double* hn = c->hdev + 2 * (m + 1);
@@ -1046,6 +1075,13 @@ void run_setup(wbfbt_ctx* cp, const double* mu_nodes) {
     CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_l, cp->C, cp->st));
     CK(launch_lumped_weight(g, cp->k, cp->dtab, cp->mu64, cp->opt.a_r, cp->D, cp->st));
   }
+  if (cp->opt.weights == WBFBT_WEIGHTS_DIAG_A) {
+    // diag(A)-BFBT: diag(A)^-1 per DOF in FP64, and mu per point for the Poisson surrogate
+    cp->pool.ensure(cp->adinv64, 3 * nn);
+    CK(launch_dinv_A<double>(g, cp->k, cp->dtab, cp->mu64, 1, cp->adinv64, cp->st));
+    cp->pool.ensure(cp->wpts, (size_t)g.ne * cp->N3);
+    CK(launch_nodal_to_points<double>(g, cp->k, cp->mu64, cp->wpts, cp->st));
+  }
   wb_launch(k_inv_masked, (unsigned)((nn + 255) / 256), 256, 0, cp->st, g, cp->C, cp->cinv64);
   wb_launch(k_inv_masked, (unsigned)((nn + 255) / 256), 256, 0, cp->st, g, cp->D, cp->dinv64);
   CK(cudaGetLastError());
@@ -1134,7 +1170,7 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
       c->opt.schur < WBFBT_SCHUR_WBFBT || c->opt.schur > WBFBT_SCHUR_MASS_DIAG ||
       (c->opt.arnoldi_precision != WBFBT_F64 && c->opt.arnoldi_precision != WBFBT_F32) ||
       (c->opt.arnoldi_precision == WBFBT_F32 && c->opt.precision != WBFBT_MIXED) ||
-      (c->opt.weights != WBFBT_WEIGHTS_SQRT_MU && c->opt.weights != WBFBT_WEIGHTS_GRAD) ||
+      c->opt.weights < WBFBT_WEIGHTS_SQRT_MU || c->opt.weights > WBFBT_WEIGHTS_DIAG_A ||
       c->opt.kinv_cycles < 1 || c->opt.kinv_cycles > 64)
     return WBFBT_ERR_INVALID;
   if (c->opt.schur_sign >= 0) c->opt.schur_sign = 1; else c->opt.schur_sign = -1;

@@ -21,7 +21,7 @@ MIXED = 1
 ELEM_AUTO, ELEM_POINT, ELEM_ROW = 0, 1, 2   # k = 2 element kernels: by level size, per point, row segments
 SCHUR_WBFBT, SCHUR_MASS, SCHUR_MASS_DIAG = 0, 1, 2   # S~: w-BFBT (Eq. wbfbt), lumped M_p(1/mu), diag M_p(1/mu)
 BLOCK_A, BLOCK_KL, BLOCK_KR = 0, 1, 2                # blocks for solve_block
-WEIGHTS_SQRT_MU, WEIGHTS_GRAD = 0, 1                 # w-BFBT weights: sqrt(mu), (mu^2 + |grad mu|^2)^(1/4)
+WEIGHTS_SQRT_MU, WEIGHTS_GRAD, WEIGHTS_DIAG_A = 0, 1, 2   # C, D: M~_u(sqrt(mu)), M~_u((mu^2+|grad mu|^2)^1/4), diag(A)
 OK, ERR_INVALID, ERR_CUDA, ERR_NONFINITE, ERR_BREAKDOWN, ERR_MAXIT, ERR_SETUP = 0, -1, -2, -3, -4, -5, -6
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "non-finite value", -4: "Krylov breakdown",
           -5: "iteration limit reached", -6: "setup failed"}

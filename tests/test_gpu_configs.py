@@ -173,3 +173,14 @@ def test_bad_viscosity_rejected_at_create_and_setup(wb, bad):
     s.setup(mu_g)      # a valid viscosity afterwards restores the context
     _, _, res = s.solve(small(wb)[2])
     assert res.status == 0
+
+
+def test_amplified_q3_solve_matches_oracle(wb):
+    """Boundary amplification a_r = 4 (Eq. bdramp, the Table 2 / 3b setting for k = 3) on 6^3 Q3:
+    iterations +-1 and solution 1e-10 against the oracle."""
+    cfg = dict(n=6, k=3, n_sinkers=4, omega=0.1, delta=200.0, dr=1e4, seed=0)
+    o = oracle_solve(cfg, opts=W.Options(a_r=4.0))
+    s, _, f_g = gpu_config(wb, cfg, o["centres"], a_r=4.0)
+    u, p, res = s.solve(f_g)
+    assert res.status == 0 and abs(res.iters - o["its"]) <= 1, (res.iters, o["its"])
+    assert rel(N(u), o["u"]) < 1e-10 and rel(N(p), o["p"]) < 1e-10

@@ -119,3 +119,27 @@ def test_several_kinv_cycles_match_oracle(wb):
     u, p, res = s.solve(torch.tensor(f.T.ravel(), device="cuda"))
     assert res.status == 0 and abs(res.iters - its) <= 1, (res.iters, its)
     assert rel(N(u), uo) < 1e-10 and rel(N(p), po) < 1e-10
+
+
+# ------------------------------------------------------------------ diag(A)-BFBT (Sec. 1.3)
+
+def test_diag_a_bfbt_matches_oracle(wb):
+    from oracle import multigrid as mg
+    m, mu, f = problem(8, 2, 1e4, 4)
+    prob = W.StokesProblem(m, mu, weights="diag_a")
+    r = op.project_pressure(m, np.random.default_rng(8).standard_normal(m.n_p))
+    s64 = wb.Solver(8, 2, torch.tensor(mu, device="cuda"), weights=wb.WEIGHTS_DIAG_A)
+    s32 = wb.Solver(8, 2, torch.tensor(mu, device="cuda"), weights=wb.WEIGHTS_DIAG_A, precision=wb.MIXED)
+    K = op.assemble_Kw(prob.B, prob.Cdiag, m)
+    for which in (0, 1):
+        assert rel(N(s64.apply_Kw(which, torch.tensor(r, device="cuda"))), K @ r) < 1e-12
+        y32 = N(s32.apply_Kw(which, torch.tensor(r, dtype=torch.float32, device="cuda")))
+        assert rel(y32, K @ r.astype(np.float32).astype(np.float64)) < 5e-5
+    pp = mg.PressurePoissonMG(m, prob.B, prob.Cdiag, mu, 1.0, "diag_a")
+    assert rel(N(s64.apply_Kinv(1, torch.tensor(r, device="cuda"))), pp.apply(r)) < 1e-10
+    ref = W.WBFBT(prob, "vcycle")
+    assert rel(N(s64.apply_schur_inv(torch.tensor(r, device="cuda"))), ref.apply(r)) < 1e-10
+    uo, po, its, relo, _ = W.solve(m, mu, f, W.Options(weights="diag_a"), maxit=2000)
+    u, p, res = s64.solve(torch.tensor(f.T.ravel(), device="cuda"), maxit=2000)
+    assert res.status == 0 and abs(res.iters - its) <= 1, (res.iters, its)
+    assert rel(N(u), uo) < 1e-10 and rel(N(p), po) < 1e-10

@@ -241,3 +241,21 @@ def test_gradient_weights_on_polynomial_viscosity():
     # the lumped weight sums W |J| a(e) w over the points at a node; the total is the integral
     tot = op.lumped_weight_diag(m, mu, 1.0, "grad").sum()
     np.testing.assert_allclose(tot, (w * (m.W * m.detJ)[None, :]).sum(), rtol=1e-13)
+
+
+def test_diag_a_bfbt_weights_are_the_viscous_diagonal():
+    """diag(A)-BFBT (Sec. 1.3): C = D = diag(A) per DOF; K_w = B diag(A)^-1 B^T equals the dense
+    product written out, and the constant pressure mode is in its null space (B^T 1_psi = 0)."""
+    from oracle import mesh as Mm
+    from oracle import wbfbt as Wb
+    m = Mm.Mesh(2, 2, 2, 2)
+    mu = 1.0 + m.node_coords()[:, 0]
+    prob = Wb.StokesProblem(m, mu, weights="diag_a")
+    A = prob.A.toarray()
+    free = m.interior_dof_mask()
+    np.testing.assert_allclose(prob.Cinv[free], 1.0 / np.diag(A)[free], rtol=1e-14)
+    assert np.all(prob.Cinv[~free] == 0.0)
+    K = op.assemble_Kw(prob.B, prob.Cdiag, m).toarray()
+    Bd = prob.B.toarray()
+    np.testing.assert_allclose(K, Bd @ np.diag(prob.Cinv) @ Bd.T, rtol=1e-13, atol=1e-13 * np.abs(K).max())
+    np.testing.assert_allclose(K @ op.constant_pressure(m), 0.0, atol=1e-12 * np.abs(K).max())
