@@ -97,6 +97,11 @@ typedef struct {
     int kinv_cycles;               /* V-cycles per application of K~_l^-1 and K~_r^-1 inside
                                       S~^-1 (default 1, Sec. 6; 1..64): each further cycle
                                       corrects the residual, x += V(b - K_w x)             */
+    int pmg;                       /* 1: p-coarsened multigrid for the viscous block A (Sec. 6,
+                                      Fig. 5): Q_k on the fine mesh, then trilinear Q1 on the
+                                      same mesh and on its h-coarsenings (coefficient moved to
+                                      Q1 by the normalised L^2-adjoint of trilinear
+                                      interpolation); 0 (default): Q_k on every level         */
 } wbfbt_opts;
 
 #define WBFBT_SCHUR_WBFBT 0

@@ -174,6 +174,47 @@ def coarsen_coefficient(mf: Mesh, c_fine: np.ndarray) -> np.ndarray:
     return out.reshape(mc.n_elem, n ** 3)
 
 
+# ------------------------------------------------------------------ p-coarsening (Q_k -> Q1)
+
+def p_prolongation_1d(n_el: int, k: int) -> sp.csr_matrix:
+    """Trilinear (Q1) functions on a line of n_el elements evaluated at the Q_k GLL nodes of the
+    same elements: (k n_el + 1) x (n_el + 1).  Node i of element e (i = k e + a) sits at reference
+    point xi_a, where the two Q1 vertex functions are (1 - xi_a)/2 and (1 + xi_a)/2."""
+    xi, _ = gll.gll_nodes_weights(k)
+    rows, cols, vals = [], [], []
+    for i in range(k * n_el + 1):
+        e = min(i // k, n_el - 1)
+        a = i - k * e
+        for v, val in ((e, 0.5 * (1.0 - xi[a])), (e + 1, 0.5 * (1.0 + xi[a]))):
+            if val != 0.0:
+                rows.append(i)
+                cols.append(v)
+                vals.append(val)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(k * n_el + 1, n_el + 1))
+
+
+def p_prolongation_vector(mf: Mesh) -> sp.csr_matrix:
+    """Q1 -> Q_k on the same mesh, three components: the embedding of trilinear functions."""
+    P = sp.kron(p_prolongation_1d(mf.nz, mf.k), sp.kron(p_prolongation_1d(mf.ny, mf.k),
+                                                          p_prolongation_1d(mf.nx, mf.k))).tocsr()
+    return sp.block_diag([P, P, P], format="csr")
+
+
+def p_coarsen_coefficient(mf: Mesh, c_fine: np.ndarray) -> np.ndarray:
+    """Coefficient at the Q1 points (vertices) of each element from its Q_k point values: the
+    normalised L^2-adjoint of element-wise trilinear interpolation (the h-coarsening rule of Sec. 6
+    applied within the element), c1(v) = sum_q W_q phi_v(x_q) c(x_q) / sum_q W_q phi_v(x_q) with
+    phi_v the trilinear vertex functions and W_q the Q_k GLL weights.  Returns (n_elem, 8)."""
+    xi, w = mf.xi, mf.w1
+    lin = np.stack([0.5 * (1.0 - xi), 0.5 * (1.0 + xi)])          # (2, n): phi_v at the GLL points
+    T = lin * w[None, :]
+    T = T / T.sum(axis=1, keepdims=True)
+    n = mf.n
+    cf = c_fine.reshape(mf.n_elem, n, n, n)                          # (e, l, j, i)
+    out = np.einsum("vc,ub,ta,ecba->evut", T, T, T, cf)              # (e, v_z, v_y, v_x)
+    return out.reshape(mf.n_elem, 8)
+
+
 # ------------------------------------------------------------------ levels
 
 def n_levels(m: Mesh) -> int:
@@ -225,11 +266,22 @@ class Level:
         return x - x.mean()
 
 
-def build_hierarchy(mesh: Mesh, coef_pts: np.ndarray, vector: bool) -> list[Level]:
-    """Levels for A (vector, Dirichlet; coef = mu) or L_c (scalar, Neumann; coef = 1/w)."""
-    L = n_levels(mesh)
+def build_hierarchy(mesh: Mesh, coef_pts: np.ndarray, vector: bool, pmg: bool = False) -> list[Level]:
+    """Levels for A (vector, Dirichlet; coef = mu) or L_c (scalar, Neumann; coef = 1/w).
+
+    pmg (vector, k > 1): the p-coarsened hierarchy of Sec. 6 / Fig. 5 -- the Q_k fine level, then
+    trilinear Q1 on the same mesh (coefficient by p_coarsen_coefficient, transfer by the Q1 -> Q_k
+    embedding), then Q1 h-levels as below."""
     levels = []
     m, c = mesh, coef_pts
+    if pmg and vector and mesh.k > 1:
+        M = op.assemble_A(m, c)
+        lev = Level(m, M, vector, coarsest=False)
+        levels.append(lev)
+        lev.P = p_prolongation_vector(m)
+        c = p_coarsen_coefficient(m, c)
+        m = Mesh(m.nx, m.ny, m.nz, 1, m.lx, m.ly, m.lz)
+    L = n_levels(m)
     for l in range(L):
         M = op.assemble_A(m, c) if vector else op.assemble_Lc(m, c)
         lev = Level(m, M, vector, coarsest=(l == L - 1))

@@ -414,6 +414,110 @@ __global__ void k_lumped(Grid g, int K, const RefTables* __restrict__ tab, const
   out[n] = mu ? acc * sqrt(mu[n]) : acc;
 }
 
+// p-coarsening of a per-point coefficient from Q_k (N = k + 1 points per axis) to Q1 on the same
+// element: the normalised L^2-adjoint of element-wise trilinear interpolation, per axis
+// T[v][a] = W_a l1_v(x_a) / sum_a' W_a' l1_v(x_a'), l1_0 = (1 - x)/2, l1_1 = (1 + x)/2 on the
+// Q_k GLL points x_a with weights W_a; c1(v) = sum_{a,b,c} T[v0][a] T[v1][b] T[v2][c] c(a, b, c).
+// Non-negative weights, constants preserved (Sec. 6, as the h-coarsening of the coefficient).
+template <int N>
+__global__ void k_pcoarsen_coef(Grid g, const RefTables* __restrict__ tab, const double* __restrict__ cf,
+                                double* __restrict__ cc) {
+  pdl_entry();
+  constexpr int N3 = Cfg<N>::N3;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.ne * 8) return;
+  const int e = (int)(t >> 3), v = (int)(t & 7);
+  const int vi[3] = {v & 1, (v >> 1) & 1, v >> 2};
+  double T[3][N];
+  for (int d = 0; d < 3; ++d) {
+    double den = 0.0;
+    for (int a = 0; a < N; ++a) {
+      const double l1 = vi[d] ? 0.5 * (1.0 + tab->x[a]) : 0.5 * (1.0 - tab->x[a]);
+      T[d][a] = tab->w[a] * l1;
+      den += T[d][a];
+    }
+    for (int a = 0; a < N; ++a) T[d][a] /= den;
+  }
+  const double* ce = cf + (size_t)e * N3;
+  double acc = 0.0;
+  for (int c = 0; c < N; ++c)
+    for (int b = 0; b < N; ++b)
+      for (int a = 0; a < N; ++a) acc += T[0][a] * T[1][b] * T[2][c] * ce[a + N * (b + N * c)];
+  cc[t] = acc;
+}
+
+// p-transfers between Q1 on grid g1 (vertices, (n+1)^3 per axis counts) and Q_k on the same
+// mesh (node grid k n + 1 per axis), for k >= 3 (at k = 2 the Q_k node grid is that of Q1 on the
+// refined mesh, and the nested h-transfer kernels serve).  Per axis the Q1 vertex function v takes
+// the value (1 + x_a)/2 at local GLL node a of element v - 1 and (1 - x_a)/2 at node a of element v.
+__device__ inline double p_weight(int i, int v, int k, const double* x) {
+  if (i < k * v) {
+    const int a = i - k * (v - 1);
+    return (a >= 0 && a <= k) ? 0.5 * (1.0 + x[a]) : 0.0;
+  }
+  const int a = i - k * v;
+  return a <= k ? 0.5 * (1.0 - x[a]) : 0.0;
+}
+
+// out_f (+)= P in_c: one thread per Q_k node, the 2 x 2 x 2 vertices of its element
+template <typename T>
+__global__ void k_p_prolong(Grid g1, int k, const RefTables* __restrict__ tab, int ncomp, const T* __restrict__ in_c,
+                            T* __restrict__ out_f, int add) {
+  pdl_entry();
+  const int NXf = k * g1.nx + 1, NYf = k * g1.ny + 1, NZf = k * g1.nz + 1;
+  const long long nnf = (long long)NXf * NYf * NZf;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnf) return;
+  const int ix = (int)(t % NXf), iy = (int)((t / NXf) % NYf), iz = (int)(t / ((long long)NXf * NYf));
+  const int ex = min(ix / k, g1.nx - 1), ey = min(iy / k, g1.ny - 1), ez = min(iz / k, g1.nz - 1);
+  double wx[2], wy[2], wz[2];
+  for (int s = 0; s < 2; ++s) {
+    wx[s] = p_weight(ix, ex + s, k, tab->x);
+    wy[s] = p_weight(iy, ey + s, k, tab->x);
+    wz[s] = p_weight(iz, ez + s, k, tab->x);
+  }
+  for (int c = 0; c < ncomp; ++c) {
+    double acc = 0.0;
+    for (int sz = 0; sz < 2; ++sz)
+      for (int sy = 0; sy < 2; ++sy)
+        for (int sx = 0; sx < 2; ++sx)
+          acc += wx[sx] * wy[sy] * wz[sz] *
+                 (double)in_c[(size_t)c * g1.nn + (ex + sx) + g1.NX * ((ey + sy) + (size_t)g1.NY * (ez + sz))];
+    T* o = out_f + (size_t)c * nnf + t;
+    *o = add ? *o + T(acc) : T(acc);
+  }
+}
+
+// out_c = P^T in_f: one thread per Q1 vertex, the Q_k nodes of the up to 2 x 2 x 2 elements around
+// it; Dirichlet vertices zeroed when mask_dirichlet
+template <typename T>
+__global__ void k_p_restrict(Grid g1, int k, const RefTables* __restrict__ tab, int ncomp, const T* __restrict__ in_f,
+                             T* __restrict__ out_c, int mask_dirichlet) {
+  pdl_entry();
+  const int NXf = k * g1.nx + 1, NYf = k * g1.ny + 1, NZf = k * g1.nz + 1;
+  const long long nnf = (long long)NXf * NYf * NZf;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g1.nn) return;
+  const int vx = t % g1.NX, vy = (t / g1.NX) % g1.NY, vz = t / (g1.NX * g1.NY);
+  const bool bnd = mask_dirichlet && on_boundary(g1, vx, vy, vz);
+  const int x0 = max(0, k * (vx - 1)), x1 = min(NXf - 1, k * (vx + 1));
+  const int y0 = max(0, k * (vy - 1)), y1 = min(NYf - 1, k * (vy + 1));
+  const int z0 = max(0, k * (vz - 1)), z1 = min(NZf - 1, k * (vz + 1));
+  for (int c = 0; c < ncomp; ++c) {
+    double acc = 0.0;
+    if (!bnd)
+      for (int iz = z0; iz <= z1; ++iz) {
+        const double wz = p_weight(iz, vz, k, tab->x);
+        for (int iy = y0; iy <= y1; ++iy) {
+          const double wy = wz * p_weight(iy, vy, k, tab->x);
+          const T* row = in_f + (size_t)c * nnf + (size_t)NXf * (iy + (size_t)NYf * iz);
+          for (int ix = x0; ix <= x1; ++ix) acc += wy * p_weight(ix, vx, k, tab->x) * (double)row[ix];
+        }
+      }
+    out_c[(size_t)c * g1.nn + t] = T(acc);
+  }
+}
+
 // The w-BFBT weight at every element point (FP64, [ne][N^3]): sqrt(mu) (grad = 0, Eq. wbfbt) or
 // (mu^2 + |grad mu_h|^2)^(1/4) (grad = 1, the viscosity-gradient weights of the remark in
 // Sec. 4), grad mu_h being the gradient of the element's Q_k interpolant of the nodal viscosity.
@@ -681,6 +785,7 @@ inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1)
 
 #define WB_DISPATCH_N(k, CALL) \
   switch (k) {                 \
+    case 1: { constexpr int N = 2; return CALL; } \
     case 2: { constexpr int N = 3; return CALL; } \
     case 3: { constexpr int N = 4; return CALL; } \
     case 4: { constexpr int N = 5; return CALL; } \
@@ -767,6 +872,35 @@ cudaError_t launch_lumped_weight(const Grid& g, int k, const RefTables* dtab, co
 cudaError_t launch_lumped_mass(const Grid& g, int k, const RefTables* dtab, double* out, cudaStream_t st) {
   wb_launch(k_lumped, blocks_for(g.nn, 128), 128, 0, st, g, k, dtab, nullptr, 1.0, out);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_p_prolong(const Grid& g1, int k, const RefTables* dtab, int ncomp, const T* in_c, T* out_f, int add,
+                             cudaStream_t st) {
+  const long long nnf = (long long)(k * g1.nx + 1) * (k * g1.ny + 1) * (k * g1.nz + 1);
+  wb_launch(k_p_prolong<T>, blocks_for(nnf, 128), 128, 0, st, g1, k, dtab, ncomp, in_c, out_f, add);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_p_restrict(const Grid& g1, int k, const RefTables* dtab, int ncomp, const T* in_f, T* out_c,
+                              int mask_dirichlet, cudaStream_t st) {
+  wb_launch(k_p_restrict<T>, blocks_for(g1.nn, 128), 128, 0, st, g1, k, dtab, ncomp, in_f, out_c, mask_dirichlet);
+  return cudaGetLastError();
+}
+template cudaError_t launch_p_prolong<double>(const Grid&, int, const RefTables*, int, const double*, double*, int,
+                                              cudaStream_t);
+template cudaError_t launch_p_prolong<float>(const Grid&, int, const RefTables*, int, const float*, float*, int,
+                                             cudaStream_t);
+template cudaError_t launch_p_restrict<double>(const Grid&, int, const RefTables*, int, const double*, double*, int,
+                                               cudaStream_t);
+template cudaError_t launch_p_restrict<float>(const Grid&, int, const RefTables*, int, const float*, float*, int,
+                                              cudaStream_t);
+
+cudaError_t launch_pcoarsen_coef(const Grid& g, int k, const RefTables* dtab, const double* cf, double* cc,
+                                 cudaStream_t st) {
+  WB_DISPATCH_N(k, ((wb_launch(k_pcoarsen_coef<N>, blocks_for((long long)g.ne * 8, 128), 128, 0, st, g, dtab, cf, cc)),
+                    cudaGetLastError()));
 }
 
 cudaError_t launch_weight_points(const Grid& g, int k, const RefTables* dtab, const double* mu, int grad, double* w,

@@ -537,6 +537,7 @@ cudaError_t run_elem(const Grid& g, const void* otab_v, int ops, const T* u, con
 
 #define WB_FUSED_DISPATCH(k, CALL) \
   switch (k) {                     \
+    case 1: { constexpr int N = 2; return CALL; } \
     case 2: { constexpr int N = 3; return CALL; } \
     case 3: { constexpr int N = 4; return CALL; } \
     case 4: { constexpr int N = 5; return CALL; } \
@@ -712,6 +713,7 @@ cudaError_t launch_restrict_batched(const Grid& gc, int k, const void* otab, int
 template <typename T>
 size_t optab_bytes(int k) {
   switch (k) {
+    case 1: return sizeof(OpTab<T, 2>);
     case 2: return sizeof(OpTab<T, 3>);
     case 3: return sizeof(OpTab<T, 4>);
     case 4: return sizeof(OpTab<T, 5>);
@@ -722,6 +724,7 @@ size_t optab_bytes(int k) {
 template <typename T>
 void build_optab_host(const RefTables& t, const Grid& g, int k, void* out) {
   switch (k) {
+    case 1: make_optab<T, 2>(t, g, static_cast<OpTab<T, 2>*>(out)); break;
     case 2: make_optab<T, 3>(t, g, static_cast<OpTab<T, 3>*>(out)); break;
     case 3: make_optab<T, 4>(t, g, static_cast<OpTab<T, 4>*>(out)); break;
     case 4: make_optab<T, 5>(t, g, static_cast<OpTab<T, 5>*>(out)); break;

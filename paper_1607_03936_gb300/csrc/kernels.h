@@ -54,6 +54,19 @@ cudaError_t launch_lumped_weight(const Grid& g, int k, const RefTables* dtab, co
 // Lumped (unweighted) mass sum_{(e,q) at n} W_q |J| per node, used for the load vector.
 cudaError_t launch_lumped_mass(const Grid& g, int k, const RefTables* dtab, double* out, cudaStream_t st);
 
+// p-transfers (k >= 3) between Q1 on g1 and Q_k on the same mesh: prolong out_f (+)= P in_c,
+// restrict out_c = P^T in_f (mask_dirichlet zeroes the Dirichlet vertices); ncomp stacked fields;
+// dtab: the order-k tables (GLL nodes).
+template <typename T>
+cudaError_t launch_p_prolong(const Grid& g1, int k, const RefTables* dtab, int ncomp, const T* in_c, T* out_f, int add,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_p_restrict(const Grid& g1, int k, const RefTables* dtab, int ncomp, const T* in_f, T* out_c,
+                              int mask_dirichlet, cudaStream_t st);
+// p-coarsening of a per-point FP64 coefficient from Q_k ([ne][(k+1)^3], tables of order k) to Q1
+// on the same mesh ([ne][8]): normalised L^2-adjoint of element-wise trilinear interpolation.
+cudaError_t launch_pcoarsen_coef(const Grid& g, int k, const RefTables* dtab, const double* cf, double* cc,
+                                 cudaStream_t st);
 // w-BFBT weights per element point (FP64 [ne][(k+1)^3]): sqrt(mu), or with grad = 1 the
 // viscosity-gradient weights (mu^2 + |grad mu|^2)^(1/4); the lumped mass M~_u(a w) per node and the
 // Poisson coefficient 1 / (a(e) w) per point from them.

@@ -70,7 +70,7 @@ bool invert(int n, double a[WB_MAXNP][WB_MAXNP], double inv[WB_MAXNP][WB_MAXNP])
 }  // namespace
 
 bool build_ref_tables(int k, RefTables* t) {
-  if (k < 2 || k > 4) return false;
+  if (k < 1 || k > 4) return false;
   std::memset(t, 0, sizeof(*t));
   const int n = k + 1;
   t->k = k;

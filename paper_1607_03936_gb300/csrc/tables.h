@@ -16,5 +16,6 @@ struct RefTables {
   double Tc[2][WB_MAXN][WB_MAXN];    // coefficient coarsening weights per axis, Tc[s][i][i']
 };
 
-// Fill t for order k in {2, 3, 4}; returns false for other k.
+// Fill t for order k in {1, 2, 3, 4} (k = 1: the trilinear levels of the p-coarsened viscous
+// multigrid; the solver itself takes k >= 2); returns false for other k.
 bool build_ref_tables(int k, RefTables* t);

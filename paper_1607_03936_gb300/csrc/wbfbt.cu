@@ -67,6 +67,8 @@ struct Pool {
 template <typename T>
 struct Level {
   Grid g;
+  int k = 2;                       // element order of this level (1 on the p-coarsened levels)
+  const RefTables* dtab = nullptr; // reference tables of that order (device)
   const T* coef = nullptr;     // level 0 of A: nodal viscosity; otherwise per element point
   int coef_nodal = 0;
   double* coef64 = nullptr;    // FP64 copy used by the setup (per point; nodal on A level 0)
@@ -131,6 +133,8 @@ struct wbfbt_ctx {
   int nlev = 1;
   RefTables htab;
   RefTables* dtab = nullptr;
+  RefTables htab1;                // order-1 tables for the p-coarsened viscous multigrid (pmg)
+  RefTables* dtab1 = nullptr;
   Pool pool;
   // FP64 fine data
   double *mu64 = nullptr, *lm = nullptr, *C = nullptr, *D = nullptr, *cinv64 = nullptr, *dinv64 = nullptr;
@@ -186,10 +190,10 @@ const void* fine_tab(wbfbt_ctx* c) {
 
 // Device copy of the operator tables of grid g in precision T (built once; tables depend only on g).
 template <typename T>
-void* make_device_optab(wbfbt_ctx* c, const Grid& g) {
-  const size_t nb = optab_bytes<T>(c->k);
+void* make_device_optab(wbfbt_ctx* c, const Grid& g, int k) {
+  const size_t nb = optab_bytes<T>(k);
   std::vector<unsigned char> h(nb);
-  build_optab_host<T>(c->htab, g, c->k, h.data());
+  build_optab_host<T>(k == 1 ? c->htab1 : c->htab, g, k, h.data());
   unsigned char* d = c->pool.get<unsigned char>(nb);
   CK(cudaMemcpy(d, h.data(), nb, cudaMemcpyHostToDevice));
   return d;
@@ -245,11 +249,11 @@ template <typename T>
 void level_apply(wbfbt_ctx* c, const Hier<T>& H, const Level<T>& L, const T* u, const Epi<T>& e) {
   T* Ye = prec<T>(c).Ye;
   if (H.vec)
-    CK(launch_elem_stokes<T>(L.g, c->k, L.optab, OP_A, u, nullptr, nullptr, L.coef, L.coef_nodal, Ye, Epi<T>(),
+    CK(launch_elem_stokes<T>(L.g, L.k, L.optab, OP_A, u, nullptr, nullptr, L.coef, L.coef_nodal, Ye, Epi<T>(),
                              c->st));
   else
-    CK(launch_elem_poisson<T>(L.g, c->k, L.optab, u, L.coef, Ye, c->st));
-  CK(launch_gather<T>(L.g, c->k, H.ncomp, H.vec ? 1 : 0, Ye, e, c->st));
+    CK(launch_elem_poisson<T>(L.g, L.k, L.optab, u, L.coef, Ye, c->st));
+  CK(launch_gather<T>(L.g, L.k, H.ncomp, H.vec ? 1 : 0, Ye, e, c->st));
 }
 
 // epilogue(B^T p) on the fine velocity nodes (Dirichlet nodes 0): element pass + node pass.
@@ -332,9 +336,20 @@ void vcycle(wbfbt_ctx* c, Hier<T>& H, int l, const T* b, T* x) {
   auto M = [&](const T* u, const Epi<T>& e) { level_apply<T>(c, H, L, u, e); };
   chebyshev<T>(c, M, n, L.dinv, L.lam, b, x, true, true, L.r, L.d);
   Level<T>& Lc = H.lv[l + 1];
-  CK(launch_restrict_batched<T>(Lc.g, c->k, Lc.optab, H.ncomp, L.r, Lc.b, H.vec ? 1 : 0, L.w1, L.w2, c->st));
+  // Lc.g refined with Lc.k has the node grid of level l: for the p-step (Q_k on N^3 -> Q1 on N^3,
+  // k = 2) that is the Q1 grid on (2N)^3, whose nodes are exactly the Q2 nodes, and trilinear
+  // interpolation from the N^3 vertices to them is the Q1 -> Q2 embedding
+  // (k >= 3: the p-step has its own transfer kernels)
+  const bool pstep = Lc.k != L.k && L.k > 2;
+  if (pstep)
+    CK(launch_p_restrict<T>(Lc.g, L.k, L.dtab, H.ncomp, L.r, Lc.b, H.vec ? 1 : 0, c->st));
+  else
+    CK(launch_restrict_batched<T>(Lc.g, Lc.k, Lc.optab, H.ncomp, L.r, Lc.b, H.vec ? 1 : 0, L.w1, L.w2, c->st));
   vcycle<T>(c, H, l + 1, Lc.b, Lc.x);
-  CK(launch_prolong_fused<T>(Lc.g, c->k, Lc.optab, H.ncomp, Lc.x, x, 1, c->st));
+  if (pstep)
+    CK(launch_p_prolong<T>(Lc.g, L.k, L.dtab, H.ncomp, Lc.x, x, 1, c->st));
+  else
+    CK(launch_prolong_fused<T>(Lc.g, Lc.k, Lc.optab, H.ncomp, Lc.x, x, 1, c->st));
   chebyshev<T>(c, M, n, L.dinv, L.lam, b, x, false, false, L.r, L.d);
 }
 
@@ -564,14 +579,21 @@ template <typename T>
 void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int coef0_nodal) {
   H.vec = vec;
   H.ncomp = vec ? 3 : 1;
-  H.lv.resize(c->nlev);
+  // p-coarsened viscous multigrid (Sec. 6, Fig. 5: p- before h-coarsening): Q_k on the fine mesh,
+  // then Q1 on the same mesh and on its h-coarsenings; otherwise fixed-order Q_k h-levels
+  const bool pmg = vec && c->opt.pmg && c->k > 1;
+  const int nl = c->nlev + (pmg ? 1 : 0);
+  H.lv.resize(nl);
   Grid g = c->g;
+  int kl = c->k;
   const double* prev_pts = nullptr;   // FP64 per-point coefficient of the previous level
-  for (int l = 0; l < c->nlev; ++l) {
+  for (int l = 0; l < nl; ++l) {
     Level<T>& L = H.lv[l];
     L.g = g;
-    L.coarsest = (l == c->nlev - 1);
-    const size_t npts = (size_t)g.ne * c->N3;
+    L.k = kl;
+    L.dtab = kl == 1 ? c->dtab1 : c->dtab;
+    L.coarsest = (l == nl - 1);
+    const size_t npts = (size_t)g.ne * (kl + 1) * (kl + 1) * (kl + 1);
     const size_t nv = (size_t)H.ncomp * g.nn;
     if (l == 0) {
       L.coef64 = const_cast<double*>(coef0_64);
@@ -585,7 +607,11 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
       }
     } else {
       c->pool.ensure(L.pts64, npts);
-      CK(launch_coarsen_coef<double>(H.lv[l - 1].g, c->k, c->dtab, prev_pts, L.pts64, c->st));
+      const Level<T>& Lf = H.lv[l - 1];
+      if (Lf.k != L.k)   // the p-step: Q_k points -> Q1 points on the same elements
+        CK(launch_pcoarsen_coef(Lf.g, Lf.k, Lf.dtab, prev_pts, L.pts64, c->st));
+      else
+        CK(launch_coarsen_coef<double>(Lf.g, L.k, L.dtab, prev_pts, L.pts64, c->st));
       L.coef64 = L.pts64;
       L.coef_nodal = 0;
       prev_pts = L.pts64;
@@ -601,7 +627,7 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
     }
     c->pool.ensure(L.b, nv);
     c->pool.ensure(L.x, nv);
-    if (!L.optab) L.optab = make_device_optab<T>(c, g);
+    if (!L.optab) L.optab = make_device_optab<T>(c, g, kl);
     if (!L.coarsest) {
       c->pool.ensure(L.r, nv);
       c->pool.ensure(L.d, nv);
@@ -609,12 +635,17 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
       c->pool.ensure(L.dinv, nv);
       c->pool.ensure(L.d64, nv);
       if (vec)
-        CK(launch_dinv_A<double>(g, c->k, c->dtab, L.coef64, L.coef_nodal, L.d64, c->st));
+        CK(launch_dinv_A<double>(g, L.k, L.dtab, L.coef64, L.coef_nodal, L.d64, c->st));
       else
-        CK(launch_dinv_L<double>(g, c->k, c->dtab, L.coef64, L.d64, c->st));
+        CK(launch_dinv_L<double>(g, L.k, L.dtab, L.coef64, L.d64, c->st));
       CK((launch_cast<double, T>((long long)nv, L.d64, L.dinv, c->st)));
-      Grid gc = with_kernels(c, coarser(g, c->k));
-      size_t ws = transfer_work_size(gc, c->k);
+      // the next level: Q1 on this mesh after the fine level of a p-coarsened hierarchy, else the
+      // h-coarsening of this mesh at this level's order
+      const int kc = (pmg && l == 0) ? 1 : kl;
+      Grid gc = (pmg && l == 0) ? make_grid(g.nx, g.ny, g.nz, 1, g.h[0] * g.nx, g.h[1] * g.ny, g.h[2] * g.nz)
+                                : coarser(g, kc);
+      gc = with_kernels(c, gc);
+      size_t ws = transfer_work_size(gc, kc);
       c->pool.ensure(L.w1, ws * H.ncomp);   // restriction passes run all components at once
       c->pool.ensure(L.w2, ws * H.ncomp);
       c->pool.ensure(L.pv, nv);
@@ -622,6 +653,7 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
       auto M = [&](const T* u, const Epi<T>& e) { level_apply<T>(c, H, L, u, e); };
       L.lam = power_lambda<T>(c, M, (long long)nv, L.dinv, L.pv, L.pw, vec ? &L.g : nullptr);
       g = gc;
+      kl = kc;
     } else {
       // coarsest: dense FP64 matrix over the free DOFs, explicit inverse
       std::vector<int> hmap(g.nn);
@@ -644,9 +676,9 @@ void build_hier(wbfbt_ctx* c, Hier<T>& H, bool vec, const double* coef0_64, int 
       c->pool.ensure(L.xf, nd);
       CK(cudaMemsetAsync(L.Md, 0, sizeof(double) * (size_t)nd * nd, c->st));
       if (vec)
-        CK(launch_assemble_dense_A(g, c->k, c->dtab, L.coef64, L.coef_nodal, L.map, nfree, L.Md, nd, c->st));
+        CK(launch_assemble_dense_A(g, L.k, L.dtab, L.coef64, L.coef_nodal, L.map, nfree, L.Md, nd, c->st));
       else
-        CK(launch_assemble_dense_L_mapped(g, c->k, c->dtab, L.coef64, L.map, L.Md, nd, c->st));
+        CK(launch_assemble_dense_L_mapped(g, L.k, L.dtab, L.coef64, L.map, L.Md, nd, c->st));
       L.Ainv = L.Md;   // inverted in place by run_dense_jobs once every hierarchy is assembled
       c->dense_jobs.push_back({L.Md, nd, vec ? 0 : 1});
     }
@@ -1126,6 +1158,7 @@ void wbfbt_default_opts(wbfbt_opts* o) {
   o->arnoldi_precision = WBFBT_F64;
   o->weights = WBFBT_WEIGHTS_SQRT_MU;
   o->kinv_cycles = 1;
+  o->pmg = 0;
 }
 
 const char* wbfbt_status_string(int s) {
@@ -1171,7 +1204,7 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
       (c->opt.arnoldi_precision != WBFBT_F64 && c->opt.arnoldi_precision != WBFBT_F32) ||
       (c->opt.arnoldi_precision == WBFBT_F32 && c->opt.precision != WBFBT_MIXED) ||
       c->opt.weights < WBFBT_WEIGHTS_SQRT_MU || c->opt.weights > WBFBT_WEIGHTS_DIAG_A ||
-      c->opt.kinv_cycles < 1 || c->opt.kinv_cycles > 64)
+      c->opt.kinv_cycles < 1 || c->opt.kinv_cycles > 64 || (c->opt.pmg != 0 && c->opt.pmg != 1))
     return WBFBT_ERR_INVALID;
   if (c->opt.schur_sign >= 0) c->opt.schur_sign = 1; else c->opt.schur_sign = -1;
   c->ust = (cudaStream_t)stream;
@@ -1192,12 +1225,17 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
   c->mixed = c->opt.precision == WBFBT_MIXED;
   c->m = c->opt.restart;
   if (!build_ref_tables(k, &c->htab)) return WBFBT_ERR_INVALID;
+  if (c->opt.pmg && !build_ref_tables(1, &c->htab1)) return WBFBT_ERR_INVALID;
   wbfbt_ctx* cp = c.get();
   int status = guarded_ctx(cp, [&]() {
     const Grid& g = cp->g;
     const size_t nn = g.nn;
     cp->dtab = cp->pool.get<RefTables>(1);
     CK(cudaMemcpyAsync(cp->dtab, &cp->htab, sizeof(RefTables), cudaMemcpyHostToDevice, cp->st));
+    if (cp->opt.pmg) {
+      cp->dtab1 = cp->pool.get<RefTables>(1);
+      CK(cudaMemcpyAsync(cp->dtab1, &cp->htab1, sizeof(RefTables), cudaMemcpyHostToDevice, cp->st));
+    }
     if (k == 2) CK(q2_elem64_prepare());
     if (k <= 3) {
       cp->kwbref = cp->pool.get<double>(kw_bref_entries(k));
@@ -1216,8 +1254,8 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
     cp->ntot = 3LL * nn + (long long)g.ne * cp->NP;
     cp->Ye64 = cp->pool.get<double>(elem_scratch_size<double>(g, k));
     cp->Ye32 = cp->pool.get<float>(elem_scratch_size<float>(g, k));
-    cp->ot64 = make_device_optab<double>(cp, g);
-    cp->ot32 = make_device_optab<float>(cp, g);
+    cp->ot64 = make_device_optab<double>(cp, g, cp->k);
+    cp->ot32 = make_device_optab<float>(cp, g, cp->k);
     cp->lx = cp->pool.get<float>((size_t)g.ne * (cp->NP + 1));
     cp->ly = cp->pool.get<float>((size_t)g.ne * cp->NP);
     cp->lq = cp->pool.get<float>((size_t)g.ne * cp->NP);

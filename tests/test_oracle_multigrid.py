@@ -183,3 +183,44 @@ def test_single_element_mesh_pressure_poisson_is_finite():
     assert pp.dinv[0] == 0.0 and np.all(pp.dinv[1:] > 0)
     y = pp.apply(op.project_pressure(m, np.arange(m.n_p, dtype=float)))
     assert np.all(np.isfinite(y))
+
+
+def test_p_prolongation_embeds_trilinear_functions():
+    """Q1 vertex values of a trilinear function, carried to the Q2 (and Q3) nodes of the same mesh,
+    equal that function at those nodes (the embedding Q1 in Q_k is exact)."""
+    from oracle import mesh as Mm
+    for k in (2, 3):
+        mf = Mm.Mesh(3, 2, 2, k, 1.5, 1.0, 0.5)
+        m1 = Mm.Mesh(3, 2, 2, 1, 1.5, 1.0, 0.5)
+        f = lambda X: 1.0 + 2.0 * X[:, 0] - X[:, 1] + 0.5 * X[:, 2] + 3.0 * X[:, 0] * X[:, 1] * X[:, 2]
+        P = mg.p_prolongation_vector(mf)
+        u1 = np.concatenate([f(m1.node_coords())] * 3)
+        np.testing.assert_allclose(P @ u1, np.concatenate([f(mf.node_coords())] * 3), rtol=1e-13, atol=1e-13)
+
+
+def test_p_coarsen_coefficient_weights():
+    """k = 2: per axis the vertex weights are W_a phi_v(x_a) normalised, W = (1/3, 4/3, 1/3), phi_0 =
+    (1, 1/2, 0): (1/3, 2/3, 0) -- a coefficient equal to the reference coordinate xi along x gives
+    -1/3 at the left vertices and +1/3 at the right; constants are kept."""
+    from oracle import mesh as Mm
+    m = Mm.Mesh(1, 1, 1, 2)
+    xi = m.ref_pts[:, 0]
+    c1 = mg.p_coarsen_coefficient(m, xi[None, :]).reshape(2, 2, 2)    # (vz, vy, vx)
+    np.testing.assert_allclose(c1[..., 0], -1.0 / 3.0, rtol=1e-14)
+    np.testing.assert_allclose(c1[..., 1], 1.0 / 3.0, rtol=1e-14)
+    const = mg.p_coarsen_coefficient(m, np.full((1, 27), 2.5))
+    np.testing.assert_allclose(const, 2.5, rtol=1e-14)
+
+
+def test_p_coarsened_hierarchy_levels():
+    """pmg: Q2 on 8^3, Q1 on 8^3, Q1 on 4^3 (coarsest); the Q1 operator on the same mesh equals the
+    Galerkin-free re-discretisation with the p-coarsened coefficient (symmetric, SPD on free DOFs)."""
+    from oracle import mesh as Mm
+    from oracle import operators as opx
+    m = Mm.Mesh(8, 8, 8, 2)
+    mu = 1.0 + m.node_coords()[:, 0] ** 2
+    lv = mg.build_hierarchy(m, opx.point_values(m, mu), True, pmg=True)
+    assert [(l.mesh.nx, l.mesh.k) for l in lv] == [(8, 2), (8, 1), (4, 1)]
+    M1 = lv[1].M
+    assert abs(M1 - M1.T).max() < 1e-12 * abs(M1).max()
+    assert lv[0].P.shape == (3 * 17 ** 3, 3 * 9 ** 3)
