@@ -1,0 +1,172 @@
+"""Element slabs for a partitioned operator apply over several ranks (one GPU each).
+
+The structured brick is cut along z into slabs of whole element layers, one per rank.  Rank r
+owns elements ez in [z0, z1) and the node planes iz in [k z0, k z1) (the last rank also the top
+plane k nz); pressure is element-local, so it owns the coefficients of its elements.  Its local
+problem is the sub-mesh of elements [e0, e1) = [max(0, z0 - 2), min(nz, z1 + 2)): two ghost
+element layers on each interior side.  The library treats every face of a mesh as Dirichlet, so
+the sub-mesh's outer ghost planes read and write zero; two layers keep them away from every
+element that touches an owned node, and the apply on the sub-mesh is then exact on all owned
+nodes and elements without any change to the element kernels.
+
+One apply is: a halo exchange (the neighbour's owned node planes and pressure layers that are this
+rank's ghosts, copied into the local vector), the local apply, and the owned part of the result.
+Dot products sum over owned entries and reduce over ranks.  The exchange uses torch.distributed
+point-to-point messages of contiguous plane blocks (node index ix + NX (iy + NY iz): a z-plane is
+contiguous), so it runs on NCCL with device tensors and on gloo with host tensors.
+
+This module holds the index bookkeeping and the exchange only; the local applies are the
+library's (wbfbt.Solver on the sub-mesh).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+
+@dataclass
+class SlabPartition:
+    nx: int
+    ny: int
+    nz: int
+    k: int
+    world: int
+    rank: int
+
+    def __post_init__(self):
+        if self.nz < 2 * self.world:
+            raise ValueError("each rank needs at least two element layers")
+        base, extra = divmod(self.nz, self.world)
+        bounds = [0]
+        for r in range(self.world):
+            bounds.append(bounds[-1] + base + (1 if r < extra else 0))
+        self.bounds = bounds
+        self.z0, self.z1 = bounds[self.rank], bounds[self.rank + 1]
+        self.e0, self.e1 = max(0, self.z0 - 2), min(self.nz, self.z1 + 2)
+        self.NX, self.NY = self.k * self.nx + 1, self.k * self.ny + 1
+        self.plane = self.NX * self.NY                      # nodes per z-plane
+        self.np_layer = self.nx * self.ny                   # elements per layer
+
+    # ---------------------------------------------------------------- sizes
+    @property
+    def ext_nz(self) -> int:
+        """Element layers of the local (extended) sub-mesh."""
+        return self.e1 - self.e0
+
+    @property
+    def ext_planes(self) -> int:
+        return self.k * self.ext_nz + 1
+
+    def owned_planes(self, r: int | None = None) -> tuple[int, int]:
+        """Global node planes [lo, hi) owned by rank r (default: this rank)."""
+        r = self.rank if r is None else r
+        lo, hi = self.k * self.bounds[r], self.k * self.bounds[r + 1]
+        if r == self.world - 1:
+            hi += 1
+        return lo, hi
+
+    def owned_local_planes(self) -> tuple[int, int]:
+        lo, hi = self.owned_planes()
+        return lo - self.k * self.e0, hi - self.k * self.e0
+
+    # ---------------------------------------------------------------- vectors
+    def local_from_global(self, g: torch.Tensor, ncomp: int) -> torch.Tensor:
+        """The sub-mesh part of a global nodal vector [ncomp][NZ][NY][NX] (flat)."""
+        NZ = self.k * self.nz + 1
+        v = g.reshape(ncomp, NZ, self.plane)
+        return v[:, self.k * self.e0: self.k * self.e1 + 1].contiguous().reshape(-1)
+
+    def local_pressure_from_global(self, p: torch.Tensor, npe: int) -> torch.Tensor:
+        v = p.reshape(self.nz, self.np_layer * npe)
+        return v[self.e0: self.e1].contiguous().reshape(-1)
+
+    def owned_nodes(self, loc: torch.Tensor, ncomp: int) -> torch.Tensor:
+        """The owned node planes of a local nodal vector: [ncomp][owned planes][NY][NX]."""
+        lo, hi = self.owned_local_planes()
+        return loc.reshape(ncomp, self.ext_planes, self.plane)[:, lo:hi]
+
+    def owned_elements(self, loc_p: torch.Tensor, npe: int) -> torch.Tensor:
+        v = loc_p.reshape(self.ext_nz, self.np_layer * npe)
+        return v[self.z0 - self.e0: self.z1 - self.e0]
+
+    # ---------------------------------------------------------------- exchange
+    def halo_exchange(self, loc: torch.Tensor, ncomp: int, loc_p: torch.Tensor | None = None, npe: int = 0):
+        """Fill this rank's ghost node planes (and ghost pressure layers) from the neighbours' owned
+        data, in place.  Every rank calls it; messages go to r - 1 and r + 1."""
+        import torch.distributed as dist
+
+        v = loc.reshape(ncomp, self.ext_planes, self.plane)
+        k, e0 = self.k, self.e0
+        reqs = []
+        recv = []
+        for nb in (self.rank - 1, self.rank + 1):
+            if nb < 0 or nb >= self.world:
+                continue
+            # what nb needs from me: my owned planes inside nb's sub-mesh
+            nb_e0 = max(0, self.bounds[nb] - 2)
+            nb_e1 = min(self.nz, self.bounds[nb + 1] + 2)
+            lo, hi = self.owned_planes()
+            s_lo, s_hi = max(lo, k * nb_e0), min(hi, k * nb_e1 + 1)
+            send = v[:, s_lo - k * e0: s_hi - k * e0].contiguous()
+            reqs.append(dist.isend(send, nb))
+            # what I need from nb: nb's owned planes inside my sub-mesh
+            nlo, nhi = self.owned_planes(nb)
+            r_lo, r_hi = max(nlo, k * e0), min(nhi, k * self.e1 + 1)
+            buf = torch.empty((ncomp, r_hi - r_lo, self.plane), dtype=loc.dtype, device=loc.device)
+            reqs.append(dist.irecv(buf, nb))
+            recv.append((buf, r_lo - k * e0, r_hi - k * e0))
+            if loc_p is not None:
+                pv = loc_p.reshape(self.ext_nz, self.np_layer * npe)
+                sl, sh = max(self.z0, nb_e0), min(self.z1, nb_e1)
+                reqs.append(dist.isend(pv[sl - e0: sh - e0].contiguous(), nb))
+                rl, rh = max(self.bounds[nb], e0), min(self.bounds[nb + 1], self.e1)
+                pbuf = torch.empty((rh - rl, self.np_layer * npe), dtype=loc_p.dtype, device=loc_p.device)
+                reqs.append(dist.irecv(pbuf, nb))
+                recv.append((pbuf, rl - e0, rh - e0, "p"))
+        for q in reqs:
+            q.wait()
+        for item in recv:
+            if len(item) == 4:
+                buf, a, b, _ = item
+                loc_p.reshape(self.ext_nz, -1)[a:b] = buf
+            else:
+                buf, a, b = item
+                v[:, a:b] = buf
+
+    def dot(self, a: torch.Tensor, b: torch.Tensor, ncomp: int) -> torch.Tensor:
+        """Sum over owned nodes of a * b, reduced over all ranks (FP64)."""
+        import torch.distributed as dist
+
+        s = (self.owned_nodes(a, ncomp).double() * self.owned_nodes(b, ncomp).double()).sum().reshape(1)
+        if self.world > 1:
+            dist.all_reduce(s)
+        return s[0]
+
+
+def partitioned_apply(part: SlabPartition, u_loc: torch.Tensor, p_loc: torch.Tensor | None, local_apply,
+                      npe: int = 0):
+    """One partitioned operator apply: halo exchange, the local apply on the sub-mesh, and the owned
+    part of the result.  u_loc [3][ext planes][NY][NX] flat (ghost planes overwritten), p_loc the
+    sub-mesh pressure or None; local_apply(u_loc, p_loc) -> (yu_loc, yp_loc or None).  Returns the
+    owned node planes of yu and the owned element layers of yp."""
+    part.halo_exchange(u_loc, 3, p_loc, npe)
+    yu, yp = local_apply(u_loc, p_loc)
+    return part.owned_nodes(yu, 3), (part.owned_elements(yp, npe) if yp is not None else None)
+
+
+def library_local_apply(part: SlabPartition, mu_loc: torch.Tensor, lengths, **opts):
+    """local_apply backed by the CUDA library: a wbfbt.Solver on this rank's sub-mesh (its own GPU),
+    applying K = [A B^T; B 0] in FP64.  mu_loc: the sub-mesh's nodal viscosity (device)."""
+    from . import wbfbt as wb
+
+    h = (lengths[0] / part.nx, lengths[1] / part.ny, lengths[2] / part.nz)
+    s = wb.Solver(part.nx, part.k, mu_loc, ny=part.ny, nz=part.ext_nz,
+                  lengths=(lengths[0], lengths[1], h[2] * part.ext_nz), **opts)
+
+    def apply(u_loc, p_loc):
+        y = s.apply_K(torch.cat([u_loc, p_loc]))
+        return y[: s.n_u], y[s.n_u:]
+
+    apply.solver = s
+    return apply

@@ -1,0 +1,110 @@
+"""The slab partition of the operator apply on 2 gloo ranks (CPU): halo exchange of node planes and
+pressure layers, the local apply on each rank's sub-mesh with its two ghost element layers, and
+the owned parts of the result, against the global apply (1e-12).  The local applies here are the
+oracle's assembled matrices on the sub-meshes (the same matrices the CUDA kernels apply); dot
+products over owned nodes reduce to the global ones."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+NX, NY, NZ, K = 3, 2, 6, 2
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from oracle import mesh as M
+    from oracle import operators as op
+    from paper_1607_03936_gb300 import partition
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        mg = M.Mesh(NX, NY, NZ, K)
+        X = mg.node_coords()
+        mu = 1.0 + X[:, 0] + 2.0 * X[:, 2] ** 2
+        rng = np.random.default_rng(5)
+        u = rng.standard_normal(mg.n_u)
+        p = rng.standard_normal(mg.n_p)
+        part = partition.SlabPartition(NX, NY, NZ, K, world, rank)
+        u_loc = part.local_from_global(torch.tensor(u), 3).clone()
+        p_loc = part.local_pressure_from_global(torch.tensor(p), mg.Np).clone()
+        # ghosts start as garbage: the halo exchange must overwrite them
+        lo, hi = part.owned_local_planes()
+        v = u_loc.reshape(3, part.ext_planes, part.plane)
+        v[:, :lo] = 1e3
+        v[:, hi:] = 1e3
+        pv = p_loc.reshape(part.ext_nz, -1)
+        pv[: part.z0 - part.e0] = 1e3
+        pv[part.z1 - part.e0:] = 1e3
+        ms = M.Mesh(NX, NY, part.ext_nz, K, 1.0, 1.0, part.ext_nz / NZ)
+        mu_loc = part.local_from_global(torch.tensor(mu), 1).numpy()
+        A = op.assemble_A(ms, op.point_values(ms, mu_loc))
+        B = op.assemble_B(ms)
+
+        def local_apply(ul, pl):
+            a, b = ul.numpy(), pl.numpy()
+            return torch.tensor(A @ a + B.T @ b), torch.tensor(B @ a)
+
+        yu, yp = partition.partitioned_apply(part, u_loc, p_loc, local_apply, mg.Np)
+        d = part.dot(u_loc, u_loc, 3).item()
+        out.put((rank, part.owned_planes(), yu.numpy().copy(), (part.z0, part.z1), yp.numpy().copy(), d))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_partitioned_K_apply_matches_global_on_two_gloo_ranks():
+    from oracle import mesh as M
+    from oracle import operators as op
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    res = sorted([out.get(timeout=180) for _ in range(2)], key=lambda t: t[0])
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    mg = M.Mesh(NX, NY, NZ, K)
+    X = mg.node_coords()
+    mu = 1.0 + X[:, 0] + 2.0 * X[:, 2] ** 2
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal(mg.n_u)
+    p = rng.standard_normal(mg.n_p)
+    A = op.assemble_A(mg, op.point_values(mg, mu))
+    B = op.assemble_B(mg)
+    yu = (A @ u + B.T @ p).reshape(3, mg.NZ, mg.NX * mg.NY)
+    yp = (B @ u).reshape(NZ, NX * NY * mg.Np)
+    got_u = np.concatenate([r[2] for r in res], axis=1)
+    got_p = np.concatenate([r[4] for r in res], axis=0)
+    assert [r[1] for r in res] == [(0, 6), (6, 13)]
+    np.testing.assert_allclose(got_u, yu, rtol=0, atol=1e-12 * np.abs(yu).max())
+    np.testing.assert_allclose(got_p, yp, rtol=0, atol=1e-12 * np.abs(yp).max())
+    for r in res:
+        np.testing.assert_allclose(r[5], u @ u, rtol=1e-13)
+
+
+def test_slab_bounds_and_ghost_layers():
+    sys.path.insert(0, ROOT)
+    from paper_1607_03936_gb300 import partition
+    parts = [partition.SlabPartition(4, 4, 10, 2, 3, r) for r in range(3)]
+    assert [(q.z0, q.z1) for q in parts] == [(0, 4), (4, 7), (7, 10)]
+    assert [(q.e0, q.e1) for q in parts] == [(0, 6), (2, 9), (5, 10)]
+    # owned planes tile the global planes 0..k nz exactly once
+    planes = [q.owned_planes() for q in parts]
+    assert planes == [(0, 8), (8, 14), (14, 21)]
+    with pytest.raises(ValueError):
+        partition.SlabPartition(4, 4, 5, 2, 3, 0)
