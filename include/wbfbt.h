@@ -69,9 +69,11 @@ typedef struct {
                                       WBFBT_ELEM_AUTO (default) row-segment kernels (FP32:
                                       a thread per element, FP64: a warp per element
                                       point) on levels of >= 20000 elements, else one
-                                      thread per point; WBFBT_ELEM_POINT / WBFBT_ELEM_ROW
-                                      force either (and the three- or one-pass k = 2
-                                      restriction)                                          */
+                                      thread per point, and the single-kernel FP32 A apply
+                                      on levels of >= 32768 elements with nx >= 32;
+                                      WBFBT_ELEM_POINT / WBFBT_ELEM_ROW force the two-pass
+                                      per-point or row kernels everywhere (and the three-
+                                      or one-pass k = 2 restriction)                        */
     int schur;                     /* Schur-complement approximation S~ in Eq. precond-stokes:
                                       WBFBT_SCHUR_WBFBT (default) w-BFBT of Eq. wbfbt with
                                       multigrid inner solves; WBFBT_SCHUR_MASS the lumped

@@ -174,6 +174,40 @@ cudaError_t launch_q2_d2c(const Grid& g, const T* rd, T* rc, T* R, cudaStream_t 
 template <typename T>
 cudaError_t launch_q2_c2d(const Grid& g, const T* ec, T* ed, int add, cudaStream_t st);
 
+// ---- Single-kernel FP32 Q2 A apply (q2_fused.cu) on large row-segment levels: tiles of 32 x 4
+// element columns and zc element layers; the element kernel applies the epilogue to the nodes
+// inside each tile's node box and stores the box-surface parts in a shell array [tile][3][ss],
+// which a second kernel sums per surface node (1, 2, 4 or 8 tiles) before the epilogue.
+struct Q2Tiles {
+  int zc;                  // element layers per tile (each thread marches its column through them)
+  int nseg, nyt, nzc;      // tiles along x, y and z
+  int ss;                  // shell entries per tile and component (full tile)
+  int n1, n2, n3;          // surface nodes: on a z face; on a y face only; on an x face only
+  FastDiv fNX, fNY, fnyf, fnxf, fnyo, fpz;   // NX, NY, y faces, x faces, NY - y faces, 2 zc - 1
+};
+constexpr int Q2_FUSED_POISSON = 8;   // ops value of launch_q2_fused: the scalar Poisson operator
+// Once per process, outside stream capture: the fused kernels' resident blocks per device.
+cudaError_t q2_fused_prepare();
+bool q2_fused_eligible(const Grid& g);
+Q2Tiles q2_fused_tiles(const Grid& g, int ops);
+// Shell entries (floats) the fused apply writes on grid g.
+size_t q2_fused_scratch(const Grid& g);
+// epilogue(A u) (ops OP_A) or epilogue(B^T p) (ops OP_BT) on every velocity entry (Dirichlet
+// nodes: v = 0 when mask_boundary), or epilogue(L_c u) (ops Q2_FUSED_POISSON, scalar, coefficient
+// per element point) on every node.
+cudaError_t launch_q2_fused(const Grid& g, int ops, const float* u, const float* p, const float* coef,
+                            int coef_nodal, float* shell, int mask_boundary, const Epi<float>& e, cudaStream_t st);
+// A apply (ops OP_A: input u, coefficient coef) or B^T apply (OP_BT: input p) with epilogue on a
+// vector level of order k: the fused form where it applies, else the element pass and the node pass.
+// L_c u with epilogue on a scalar Poisson level of order k (no boundary mask): the same choice.
+template <typename T>
+cudaError_t launch_apply_poisson_epi(const Grid& g, int k, const void* optab, const T* u, const T* coef, T* Ye,
+                                     const Epi<T>& e, cudaStream_t st);
+template <typename T>
+cudaError_t launch_apply_vec_epi(const Grid& g, int k, const void* optab, int ops, const T* u, const T* p,
+                                 const T* coef, int coef_nodal, T* Ye, int mask_boundary, const Epi<T>& e,
+                                 cudaStream_t st);
+
 // ---- Assembled K_w = B C_w^-1 B^T (kw_ops.cu), k = 2 and 3: a 27-neighbour block stencil of
 // Np x Np blocks per element, stored [o][m][m'][e] in the preconditioner precision.
 size_t kw_stencil_entries(const Grid& g, int k);

@@ -569,9 +569,15 @@ bool flat_path(const Grid& g, int k) {
 }
 
 template <typename T>
+bool fused_path(const Grid& g, int k) {
+  return std::is_same<T, float>::value && k == 2 && q2_fused_eligible(g);
+}
+
+template <typename T>
 size_t elem_scratch_size(const Grid& g, int k) {
   const size_t n = (size_t)(k + 1);
   const size_t elem = 3 * (size_t)g.ne * n * n * n;
+  if (fused_path<T>(g, k)) return std::max({elem, q2_row_scratch(g, 3), q2_fused_scratch(g)});
   if (row_path_vector<T>(g, k)) return std::max(elem, q2_row_scratch(g, 3));
   if (row_path_scalar<T>(g, k)) return std::max(elem, q2_row_scratch(g, 1));
   return elem;
@@ -589,6 +595,32 @@ cudaError_t launch_elem_stokes(const Grid& g, int k, const void* otab, int ops, 
     if (flat_path<T>(g, k) && ops == OP_A && us == nullptr) return launch_q2_elem64_flat(g, u, coef, cn, Ye, st);
   }
   WB_FUSED_DISPATCH(k, (run_elem<T, N>(g, otab, ops, u, us, p, coef, cn, Ye, pe, st)));
+}
+
+template <typename T>
+cudaError_t launch_apply_vec_epi(const Grid& g, int k, const void* otab, int ops, const T* u, const T* p,
+                                 const T* coef, int cn, T* Ye, int mask, const Epi<T>& e, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (fused_path<T>(g, k)) return launch_q2_fused(g, ops, u, p, coef, cn, Ye, mask, e, st);
+  }
+  const cudaError_t err = launch_elem_stokes<T>(g, k, otab, ops, u, nullptr, p, coef, cn, Ye, Epi<T>(), st);
+  if (err != cudaSuccess) return err;
+  return launch_gather<T>(g, k, 3, mask, Ye, e, st);
+}
+
+template <typename T>
+cudaError_t launch_elem_poisson(const Grid& g, int k, const void* otab, const T* u, const T* coef, T* Ye,
+                                cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_apply_poisson_epi(const Grid& g, int k, const void* otab, const T* u, const T* coef, T* Ye,
+                                     const Epi<T>& e, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (fused_path<T>(g, k)) return launch_q2_fused(g, Q2_FUSED_POISSON, u, nullptr, coef, 0, Ye, 0, e, st);
+  }
+  const cudaError_t err = launch_elem_poisson<T>(g, k, otab, u, coef, Ye, st);
+  if (err != cudaSuccess) return err;
+  return launch_gather<T>(g, k, 1, 0, Ye, e, st);
 }
 
 template <typename T>
@@ -736,6 +768,10 @@ void build_optab_host(const RefTables& t, const Grid& g, int k, void* out) {
   template cudaError_t launch_elem_stokes<T>(const Grid&, int, const void*, int, const T*, const T*, const T*,        \
                                              const T*, int, T*, const Epi<T>&, cudaStream_t);                         \
   template cudaError_t launch_elem_poisson<T>(const Grid&, int, const void*, const T*, const T*, T*, cudaStream_t);  \
+  template cudaError_t launch_apply_poisson_epi<T>(const Grid&, int, const void*, const T*, const T*, T*,          \
+                                                   const Epi<T>&, cudaStream_t);                                     \
+  template cudaError_t launch_apply_vec_epi<T>(const Grid&, int, const void*, int, const T*, const T*, const T*, int, \
+                                               T*, int, const Epi<T>&, cudaStream_t);                                \
   template cudaError_t launch_gather<T>(const Grid&, int, int, int, const T*, const Epi<T>&, cudaStream_t);           \
   template cudaError_t launch_prolong_fused<T>(const Grid&, int, const void*, int, const T*, T*, int, cudaStream_t);  \
   template cudaError_t launch_restrict_batched<T>(const Grid&, int, const void*, int, const T*, T*, int, T*, T*,      \

@@ -3,14 +3,11 @@
 // two-space cycle and the node pass that all row-segment producers share.
 //
 // Element pass: a warp owns a row segment of up to 32 consecutive elements along x (fixed ey,
-// ez), one thread per element.  The thread loads its element's 27 nodal values per component
-// into registers, forms the gradient at each of the 27 GLL points by 1-D derivative sums along
-// the three axes (sum factorisation with the 3 x 3 derivative matrix), the quadrature-weighted
-// stress, and accumulates the transposed derivative sums into 27 register outputs per component
-// (Sec. 1.2: a(u,v) = int 2 mu eps(u):eps(v), b(v,q) = -int q div v; the scalar Poisson operator
-// of the two-space pressure cycle, Sec. 6, is int c grad u . grad v).  The operator tables
-// (derivatives scaled by 2/h, weights times |J|, pressure basis) are a kernel parameter, so every
-// table entry is a constant-bank operand of the FMAs that use it.
+// ez), one thread per element, with the element arithmetic of q2_body.cuh (Sec. 1.2: the viscous
+// stress a(u,v) = int 2 mu eps(u):eps(v), b(v,q) = -int q div v) and, for the scalar Poisson
+// operator of the two-space pressure cycle (Sec. 6, int c grad u . grad v), the same sums on one
+// component.  The operator tables (derivatives scaled by 2/h, weights times |J|, pressure basis)
+// are a kernel parameter, so every table entry is a constant-bank operand of the FMAs using it.
 // Row assembly: neighbouring threads share an x-face; each thread passes its right face to the
 // next lane (one warp shuffle per value) and adds it to its own left face, so the lane holding
 // element ex owns the x-nodes 2 ex and 2 ex + 1 of the segment (the last lane also 2 ex + 2).
@@ -21,6 +18,7 @@
 // result is bitwise reproducible.
 #include "elem_common.cuh"
 #include "epi.cuh"
+#include "q2_body.cuh"
 #include "fused.h"
 #include "kernels.h"
 
@@ -101,31 +99,14 @@ k_q2_elem(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restr
   const bool lo_y = rp.ey == 0, hi_y = rp.ey == g.ny - 1;
   const bool lo_z = rp.ez == 0, hi_z = rp.ez == g.nz - 1;
 
-  float ur[GRAD ? 3 : 1][27];
-  if (GRAD) {
-#pragma unroll
-    for (int l = 0; l < 3; ++l)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int roff = n0 + g.NX * (j + g.NY * l);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const bool bnd = (i == 0 && lo_x) || (i == 2 && hi_x) || (j == 0 && lo_y) || (j == 2 && hi_y) ||
-                           (l == 0 && lo_z) || (l == 2 && hi_z);
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            ur[c][q3(i, j, l)] = (rp.act && !bnd) ? __ldg(u + c * nn + roff + i) : 0.f;
-        }
-      }
-  }
+  float ur[3][27], mur[27], out[3][27];
+  if (GRAD) q2_load_u(u, nn, g.NX, g.NY, n0, rp.act, lo_x, hi_x, lo_y, hi_y, lo_z, hi_z, ur);
+  if (DA) q2_load_coef(coef_nodal ? coef + n0 : coef + (size_t)rp.e * 27, coef_nodal, g.NX, g.NY, rp.act, mur);
   float pm[4] = {0.f, 0.f, 0.f, 0.f};
   if (DBT && rp.act) {
 #pragma unroll
     for (int m = 0; m < 4; ++m) pm[m] = __ldg(p + (size_t)rp.e * 4 + m);
   }
-  const float* mu_base = coef_nodal ? coef + n0 : coef + (size_t)rp.e * 27;
-
-  float out[SCAT ? 3 : 1][27];
   if (SCAT) {
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -133,76 +114,7 @@ k_q2_elem(Grid g, Rows rw, const __grid_constant__ Tab2 tb, const float* __restr
       for (int q = 0; q < 27; ++q) out[c][q] = 0.f;
   }
   float bacc[4] = {0.f, 0.f, 0.f, 0.f};
-
-#pragma unroll
-  for (int l = 0; l < 3; ++l)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const int q = q3(i, j, l);
-        const float W = tb.W3[q];
-        float G[3][3];
-        if (GRAD) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              a0 += tb.Ds[0][i][a] * ur[c][q3(a, j, l)];
-              a1 += tb.Ds[1][j][a] * ur[c][q3(i, a, l)];
-              a2 += tb.Ds[2][l][a] * ur[c][q3(i, j, a)];
-            }
-            G[c][0] = a0;
-            G[c][1] = a1;
-            G[c][2] = a2;
-          }
-        }
-        if (DB) {
-          const float dv = W * (G[0][0] + G[1][1] + G[2][2]);
-#pragma unroll
-          for (int m = 0; m < 4; ++m) bacc[m] -= tb.Psi[q][m] * dv;
-        }
-        if (SCAT) {
-          float sd[3] = {0.f, 0.f, 0.f};   // diagonal stress entries
-          float sxy = 0.f, sxz = 0.f, syz = 0.f;
-          if (DA) {
-            const int mo = coef_nodal ? i + g.NX * (j + g.NY * l) : q;
-            const float mu = rp.act ? __ldg(mu_base + mo) : 0.f;
-            const float f = 2.f * W * mu, hf = W * mu;
-            sd[0] = f * G[0][0];
-            sd[1] = f * G[1][1];
-            sd[2] = f * G[2][2];
-            sxy = hf * (G[0][1] + G[1][0]);
-            sxz = hf * (G[0][2] + G[2][0]);
-            syz = hf * (G[1][2] + G[2][1]);
-          }
-          if (DBT) {
-            float pq = 0.f;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) pq += tb.Psi[q][m] * pm[m];
-            const float tq = W * pq;
-            sd[0] -= tq;
-            sd[1] -= tq;
-            sd[2] -= tq;
-          }
-          // output component c, derivative direction d: out_c(node on the d-line) += Ds[d] S_cd
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            out[0][q3(a, j, l)] += tb.Ds[0][i][a] * sd[0];
-            out[1][q3(i, a, l)] += tb.Ds[1][j][a] * sd[1];
-            out[2][q3(i, j, a)] += tb.Ds[2][l][a] * sd[2];
-            if (DA) {
-              out[0][q3(i, a, l)] += tb.Ds[1][j][a] * sxy;
-              out[0][q3(i, j, a)] += tb.Ds[2][l][a] * sxz;
-              out[1][q3(a, j, l)] += tb.Ds[0][i][a] * sxy;
-              out[1][q3(i, j, a)] += tb.Ds[2][l][a] * syz;
-              out[2][q3(a, j, l)] += tb.Ds[0][i][a] * sxz;
-              out[2][q3(i, a, l)] += tb.Ds[1][j][a] * syz;
-            }
-          }
-        }
-      }
+  q2_stokes_points<DA, DBT, DB>(tb, ur, mur, pm, out, bacc);
 
   if (DB && rp.act) {
 #pragma unroll
@@ -220,44 +132,14 @@ k_q2_poisson(Grid g, Rows rw, const __grid_constant__ OpTab<T, 3> tb, const T* _
   const RowPos rp = row_pos(g, rw);
   if (!rp.warp_live) return;
   const int n0 = 2 * rp.ex + g.NX * (2 * rp.ey + g.NY * 2 * rp.ez);
-  T ur[27], out[1][27];
+  T ur[27], cf[27], out[1][27];
+  q2_load_scalar(u, g.NX, g.NY, n0, rp.act, ur);
 #pragma unroll
-  for (int l = 0; l < 3; ++l)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int roff = n0 + g.NX * (j + g.NY * l);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        ur[q3(i, j, l)] = rp.act ? __ldg(u + roff + i) : T(0);
-        out[0][q3(i, j, l)] = T(0);
-      }
-    }
-  const T* cf = coef + (size_t)rp.e * 27;
-#pragma unroll
-  for (int l = 0; l < 3; ++l)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const int q = q3(i, j, l);
-        T a0 = T(0), a1 = T(0), a2 = T(0);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          a0 += tb.Ds[0][i][a] * ur[q3(a, j, l)];
-          a1 += tb.Ds[1][j][a] * ur[q3(i, a, l)];
-          a2 += tb.Ds[2][l][a] * ur[q3(i, j, a)];
-        }
-        const T f = rp.act ? tb.W3[q] * __ldg(cf + q) : T(0);
-        a0 *= f;
-        a1 *= f;
-        a2 *= f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          out[0][q3(a, j, l)] += tb.Ds[0][i][a] * a0;
-          out[0][q3(i, a, l)] += tb.Ds[1][j][a] * a1;
-          out[0][q3(i, j, a)] += tb.Ds[2][l][a] * a2;
-        }
-      }
+  for (int q = 0; q < 27; ++q) {
+    cf[q] = rp.act ? __ldg(coef + (size_t)rp.e * 27 + q) : T(0);
+    out[0][q] = T(0);
+  }
+  q2_poisson_points<T>(tb, ur, cf, out[0]);
   row_store<1, T>(g, rp, out, R);
 }
 

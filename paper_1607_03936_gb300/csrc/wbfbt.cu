@@ -248,21 +248,20 @@ Epi<T> epi_dinv(T* y, const T* dinv) {
 template <typename T>
 void level_apply(wbfbt_ctx* c, const Hier<T>& H, const Level<T>& L, const T* u, const Epi<T>& e) {
   T* Ye = prec<T>(c).Ye;
-  if (H.vec)
-    CK(launch_elem_stokes<T>(L.g, L.k, L.optab, OP_A, u, nullptr, nullptr, L.coef, L.coef_nodal, Ye, Epi<T>(),
-                             c->st));
-  else
-    CK(launch_elem_poisson<T>(L.g, L.k, L.optab, u, L.coef, Ye, c->st));
-  CK(launch_gather<T>(L.g, L.k, H.ncomp, H.vec ? 1 : 0, Ye, e, c->st));
+  if (H.vec) {
+    CK(launch_apply_vec_epi<T>(L.g, L.k, L.optab, OP_A, u, nullptr, L.coef, L.coef_nodal, Ye, 1, e, c->st));
+    return;
+  }
+  CK(launch_apply_poisson_epi<T>(L.g, L.k, L.optab, u, L.coef, Ye, e, c->st));
 }
 
-// epilogue(B^T p) on the fine velocity nodes (Dirichlet nodes 0): element pass + node pass.
-// (A node-by-node variant summing the pressure side per node was measured slower in the solve.)
+// epilogue(B^T p) on the fine velocity nodes (Dirichlet nodes 0): element pass + node pass, or the
+// single-kernel form on large FP32 levels.  (A node-by-node variant summing the pressure side per
+// node was measured slower in the solve.)
 template <typename T>
 void apply_BT_epi(wbfbt_ctx* c, const T* p, const Epi<T>& e) {
-  T* Ye = prec<T>(c).Ye;
-  CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_BT, nullptr, nullptr, p, nullptr, 0, Ye, Epi<T>(), c->st));
-  CK(launch_gather<T>(c->g, c->k, 3, 1, Ye, e, c->st));
+  CK(launch_apply_vec_epi<T>(c->g, c->k, fine_tab<T>(c), OP_BT, nullptr, p, nullptr, 0, prec<T>(c).Ye, 1, e,
+                             c->st));
 }
 
 // K_w p = B C_w^-1 B^T p with epilogue on the pressure output (which: 0 -> C (w_l), 1 -> D (w_r)).
@@ -507,9 +506,8 @@ void schur_inv(wbfbt_ctx* c, const T* r, T* y) {
   kinv_any<T>(c, 1, P.sr, P.sy);
   // middle factor B C^-1 A D^-1 B^T y, each diagonal scaling fused into the preceding node pass
   apply_BT_epi<T>(c, P.sy, P.wdof ? epi_dinv<T>(P.sv1, P.wdof) : epi_scale<T>(P.sv1, P.dinvw));
-  CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_A, P.sv1, nullptr, nullptr, P.mu, 1, P.Ye, Epi<T>(), c->st));
-  CK(launch_gather<T>(c->g, c->k, 3, 1, P.Ye, P.wdof ? epi_dinv<T>(P.sv2, P.wdof) : epi_scale<T>(P.sv2, P.cinv),
-                     c->st));
+  CK(launch_apply_vec_epi<T>(c->g, c->k, fine_tab<T>(c), OP_A, P.sv1, nullptr, P.mu, 1, P.Ye, 1,
+                             P.wdof ? epi_dinv<T>(P.sv2, P.wdof) : epi_scale<T>(P.sv2, P.cinv), c->st));
   CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), OP_B, P.sv2, nullptr, nullptr, nullptr, 0, nullptr,
                            epi_store<T>(P.sz), c->st));
   kinv_any<T>(c, 0, P.sz, P.sy2);
@@ -1132,6 +1130,10 @@ namespace {
 
 template <typename T>
 void stokes_apply_t(wbfbt_ctx* c, int ops, const T* u, const T* p, T* yu, T* yp, const T* mu, T* Ye) {
+  if (ops == OP_A || ops == OP_BT) {
+    CK(launch_apply_vec_epi<T>(c->g, c->k, fine_tab<T>(c), ops, u, p, mu, 1, Ye, 1, epi_store<T>(yu), c->st));
+    return;
+  }
   const bool scat = (ops & OP_A) || (ops & OP_BT);
   CK(launch_elem_stokes<T>(c->g, c->k, fine_tab<T>(c), ops, u, nullptr, p, mu, 1, Ye, epi_store<T>(yp), c->st));
   if (scat) CK(launch_gather<T>(c->g, c->k, 3, 1, Ye, epi_store<T>(yu), c->st));
@@ -1236,7 +1238,10 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
       cp->dtab1 = cp->pool.get<RefTables>(1);
       CK(cudaMemcpyAsync(cp->dtab1, &cp->htab1, sizeof(RefTables), cudaMemcpyHostToDevice, cp->st));
     }
-    if (k == 2) CK(q2_elem64_prepare());
+    if (k == 2) {
+      CK(q2_elem64_prepare());
+      CK(q2_fused_prepare());
+    }
     if (k <= 3) {
       cp->kwbref = cp->pool.get<double>(kw_bref_entries(k));
       CK(launch_kw_bref(g, k, cp->dtab, cp->kwbref, cp->st));
