@@ -428,7 +428,9 @@ def finish_ours(args, name, cfg, rank, world, R):
     if t_a32:
         roof32 = {"bound": "hbm", "achieved": bytes32 / t_a32 / 1e9, "peak": hbm, "unit": "GB/s",
                   "frac": bytes32 / t_a32 / 1e9 / hbm, "traffic": traffic_for("apply_A_f32", name),
-                  "kernel": "k_q2_elem<OP_A> + k_q2_gather<3,STORE> (one FP32 A apply)", "peak_note": hbm_note,
+                  "kernel": ("k_q2_fused<OP_A,STORE> + k_q2_fused_fix<3,STORE> (one FP32 A apply, single-kernel "
+                             "form)" if solver.n_elem >= (1 << 17) else
+                             "k_q2_elem<OP_A> + k_q2_gather<3,STORE> (one FP32 A apply)"), "peak_note": hbm_note,
                   "per_launch": f"7 words x 4 B per node x {n_nodes} nodes (u, y, mu)"}
     roofA64 = {"bound": "alu", "achieved": flops_a / t_a64 / 1e12, "peak": peak64, "unit": "TFLOP/s",
                "frac": flops_a / t_a64 / 1e12 / peak64, "traffic": traffic_for("apply_A_f64", name),

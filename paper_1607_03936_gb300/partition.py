@@ -15,8 +15,16 @@ Dot products sum over owned entries and reduce over ranks.  The exchange uses to
 point-to-point messages of contiguous plane blocks (node index ix + NX (iy + NY iz): a z-plane is
 contiguous), so it runs on NCCL with device tensors and on gloo with host tensors.
 
-This module holds the index bookkeeping and the exchange only; the local applies are the
-library's (wbfbt.Solver on the sub-mesh).
+A partitioned solve (SlabOperator, fgmres): the Krylov vectors hold owned entries only; every
+operator apply scatters them into the sub-mesh vectors, exchanges the halo and applies locally;
+the Arnoldi step orthogonalises by classical Gram-Schmidt applied twice, each pass one batched
+all-reduce of the local V^T w, and norms reduce the same way.  With an identical preconditioner
+on every rank count (the identity, or any owned-entry-wise map) the iterates equal the one-rank
+iterates up to the reduction order.
+
+This module holds the index bookkeeping, the exchange and the distributed Krylov loop (vector
+algebra in torch on the ranks' own tensors); the local applies are the library's (wbfbt.Solver
+on the sub-mesh) or, in CPU tests, any callable with the same signature.
 """
 from __future__ import annotations
 
@@ -170,3 +178,94 @@ def library_local_apply(part: SlabPartition, mu_loc: torch.Tensor, lengths, **op
 
     apply.solver = s
     return apply
+
+
+class SlabOperator:
+    """K = [A B^T; B 0] on the owned entries of a slab partition.  An owned vector is the owned
+    velocity node planes [3][owned planes][NY][NX] followed by the owned pressure layers
+    [owned layers][nx ny][npe], flattened; local_apply(u_loc, p_loc) -> (yu_loc, yp_loc) applies
+    the sub-mesh operator."""
+
+    def __init__(self, part: SlabPartition, local_apply, npe: int, dtype=torch.float64, device="cpu"):
+        self.part, self.local_apply, self.npe = part, local_apply, npe
+        self.dtype, self.device = dtype, device
+        lo, hi = part.owned_local_planes()
+        self.n_u = 3 * (hi - lo) * part.plane
+        self.n_p = (part.z1 - part.z0) * part.np_layer * npe
+        self.n = self.n_u + self.n_p
+
+    def apply(self, x: torch.Tensor) -> torch.Tensor:
+        part = self.part
+        lo, hi = part.owned_local_planes()
+        u_loc = torch.zeros((3, part.ext_planes, part.plane), dtype=self.dtype, device=self.device)
+        p_loc = torch.zeros((part.ext_nz, part.np_layer * self.npe), dtype=self.dtype, device=self.device)
+        u_loc[:, lo:hi] = x[: self.n_u].reshape(3, hi - lo, part.plane)
+        p_loc[part.z0 - part.e0: part.z1 - part.e0] = x[self.n_u:].reshape(part.z1 - part.z0, -1)
+        yu, yp = partitioned_apply(part, u_loc.reshape(-1), p_loc.reshape(-1), self.local_apply, self.npe)
+        return torch.cat([yu.reshape(-1), yp.reshape(-1)])
+
+    def allreduce(self, t: torch.Tensor) -> torch.Tensor:
+        import torch.distributed as dist
+
+        if self.part.world > 1:
+            dist.all_reduce(t)
+        return t
+
+    def norm(self, v: torch.Tensor) -> float:
+        return float(torch.sqrt(self.allreduce((v * v).sum().reshape(1)))[0])
+
+
+def fgmres(op: SlabOperator, b: torch.Tensor, precond=None, restart: int = 50, maxit: int = 1000,
+           rtol: float = 1e-6):
+    """Right-preconditioned FGMRES(restart) on a SlabOperator, every rank calling it with its owned
+    part of b.  precond(v) -> z on owned vectors (identity when None).  Orthogonalisation: classical
+    Gram-Schmidt twice (one batched all-reduce per pass), Givens rotations; at a restart the
+    residual is recomputed as b - K x.  Returns (x, iterations, relative true residual)."""
+    x = torch.zeros_like(b)
+    r = b.clone()
+    beta0 = op.norm(r)
+    if beta0 == 0.0:
+        return x, 0, 0.0
+    its = 0
+    while True:
+        beta = op.norm(r)
+        m = restart
+        V = torch.zeros((m + 1, b.numel()), dtype=b.dtype, device=b.device)
+        Z = torch.zeros((m, b.numel()), dtype=b.dtype, device=b.device)
+        H = torch.zeros((m + 1, m), dtype=torch.float64)
+        cs, sn = torch.zeros(m, dtype=torch.float64), torch.zeros(m, dtype=torch.float64)
+        g = torch.zeros(m + 1, dtype=torch.float64)
+        g[0] = beta
+        V[0] = r / beta
+        j_done, converged = 0, False
+        for j in range(m):
+            Z[j] = V[j] if precond is None else precond(V[j])
+            w = op.apply(Z[j])
+            for _ in range(2):
+                h = op.allreduce(V[: j + 1] @ w)
+                w = w - h @ V[: j + 1]
+                H[: j + 1, j] += h.cpu().double()
+            H[j + 1, j] = op.norm(w)
+            if H[j + 1, j] > 0:
+                V[j + 1] = w / H[j + 1, j].item()
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = torch.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            j_done = j + 1
+            if abs(float(g[j + 1])) <= rtol * beta0 or its >= maxit:
+                converged = abs(float(g[j + 1])) <= rtol * beta0
+                break
+        y = torch.linalg.solve_triangular(H[:j_done, :j_done], g[:j_done].reshape(-1, 1), upper=True).reshape(-1)
+        x = x + y.to(b.dtype).to(b.device) @ Z[:j_done]
+        r = b - op.apply(x)
+        if converged or its >= maxit:
+            return x, its, op.norm(r) / beta0
+

@@ -108,3 +108,89 @@ def test_slab_bounds_and_ghost_layers():
     assert planes == [(0, 8), (8, 14), (14, 21)]
     with pytest.raises(ValueError):
         partition.SlabPartition(4, 4, 5, 2, 3, 0)
+
+
+def _solve_worker(rank, world, port, out):
+    """The distributed FGMRES of partition.py on `world` gloo ranks (world 1: no process group)."""
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from oracle import mesh as M
+    from oracle import operators as op
+    from paper_1607_03936_gb300 import partition
+    if world > 1:
+        os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        mg = M.Mesh(NX, NY, NZ, K)
+        X = mg.node_coords()
+        mu = 1.0 + X[:, 0] + 2.0 * X[:, 2] ** 2
+        part = partition.SlabPartition(NX, NY, NZ, K, world, rank)
+        ms = M.Mesh(NX, NY, part.ext_nz, K, 1.0, 1.0, part.ext_nz / NZ)
+        mu_loc = part.local_from_global(torch.tensor(mu), 1).numpy()
+        A = op.assemble_A(ms, op.point_values(ms, mu_loc))
+        B = op.assemble_B(ms)
+
+        def local_apply(ul, pl):
+            a, b = ul.numpy(), pl.numpy()
+            return torch.tensor(A @ a + B.T @ b), torch.tensor(B @ a)
+
+        K_op = partition.SlabOperator(part, local_apply, mg.Np)
+        b_glob = _consistent_rhs(mg, mu)
+        lo, hi = part.owned_planes()
+        bu = torch.tensor(b_glob[: mg.n_u]).reshape(3, mg.NZ, mg.NX * mg.NY)[:, lo:hi].reshape(-1)
+        bp = torch.tensor(b_glob[mg.n_u:]).reshape(NZ, -1)[part.z0: part.z1].reshape(-1)
+        x, its, rel = partition.fgmres(K_op, torch.cat([bu, bp]), restart=20, maxit=40, rtol=1e-14)
+        out.put((rank, x[: K_op.n_u].numpy().copy(), x[K_op.n_u:].numpy().copy(), its, rel))
+    finally:
+        if world > 1:
+            dist.destroy_process_group()
+
+
+def _consistent_rhs(mg, mu):
+    from oracle import operators as op
+    A = op.assemble_A(mg, op.point_values(mg, mu))
+    B = op.assemble_B(mg)
+    rng = np.random.default_rng(9)
+    u = rng.standard_normal(mg.n_u) * np.tile(~mg.boundary_node_mask(), 3)
+    p = rng.standard_normal(mg.n_p)
+    return np.concatenate([A @ u + B.T @ p, B @ u])
+
+
+def _gather(res, mg):
+    u = np.concatenate([r[1].reshape(3, -1, mg.NX * mg.NY) for r in res], axis=1).reshape(-1)
+    p = np.concatenate([r[2] for r in res])
+    return np.concatenate([u, p])
+
+
+def test_partitioned_fgmres_matches_one_rank_and_oracle():
+    """40 FGMRES iterations (restart 20, identity preconditioner) of the Stokes system on 2 gloo ranks
+    against the same code on 1 rank and against the oracle's FGMRES on the assembled global matrices."""
+    import queue
+    from oracle import krylov
+    from oracle import mesh as M
+    from oracle import operators as op
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_solve_worker, args=(r, 2, port, out)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    res2 = sorted([out.get(timeout=300) for _ in range(2)], key=lambda t: t[0])
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    q1 = queue.Queue()
+    _solve_worker(0, 1, 0, q1)
+    res1 = [q1.get()]
+    mg = M.Mesh(NX, NY, NZ, K)
+    X = mg.node_coords()
+    mu = 1.0 + X[:, 0] + 2.0 * X[:, 2] ** 2
+    x2, x1 = _gather(res2, mg), _gather(res1, mg)
+    assert res2[0][3] == res1[0][3] == 40
+    assert np.linalg.norm(x2 - x1) <= 1e-10 * np.linalg.norm(x1)
+    A = op.assemble_A(mg, op.point_values(mg, mu))
+    B = op.assemble_B(mg)
+    Kg = lambda v: np.concatenate([A @ v[: mg.n_u] + B.T @ v[mg.n_u:], B @ v[: mg.n_u]])
+    xo, its, _ = krylov.fgmres(Kg, lambda v: v, _consistent_rhs(mg, mu), rtol=1e-14, restart=20, maxit=40)
+    assert its == 40
+    assert np.linalg.norm(x1 - xo) <= 1e-8 * np.linalg.norm(xo)
