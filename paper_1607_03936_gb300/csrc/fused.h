@@ -79,6 +79,8 @@ cudaError_t launch_gather(const Grid& g, int k, int ncomp, int mask_boundary, co
 template <typename T>
 cudaError_t launch_prolong_fused(const Grid& gc, int k, const void* optab, int ncomp, const T* in_c, T* out_f, int add,
                                  cudaStream_t st);
+// Once per process, outside stream capture: shared-memory opt-in of the tiled transfers.
+cudaError_t transfer_prepare();
 template <typename T>
 cudaError_t launch_restrict_batched(const Grid& gc, int k, const void* optab, int ncomp, const T* in_f, T* out_c,
                                     int mask_dirichlet, T* w1, T* w2, cudaStream_t st);

@@ -442,6 +442,175 @@ __global__ void __launch_bounds__(256, 2) k_restrict_q2(Grid gc, const OpTab<T, 
     }
 }
 
+// Q2 transfers on large grids, tiled through shared memory: the tensor-product weights are applied
+// one axis at a time on a tile, so each fine value is read from memory about once instead of once
+// per coarse node (restriction, 125 taps) or per fine node (prolongation, 27 taps).
+constexpr int TR_C = 8;                 // restriction: coarse nodes per tile edge
+constexpr int TR_F = 2 * TR_C + 5;      // fine nodes per tile edge (taps reach 3 beyond each end)
+constexpr int TP_F = 16;                // prolongation: fine nodes per tile edge
+constexpr int TP_C = TP_F / 2 + 1;      // coarse nodes per tile edge
+constexpr int TT_THREADS = 256;
+
+// Asynchronous copy of one entry into shared memory; src_bytes = 0 writes zeros (the source is not
+// read).
+template <typename T>
+__device__ __forceinline__ void cp_async_entry(T* dst, const T* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(sizeof(T)),
+               "r"(valid ? (int)sizeof(T) : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <typename T>
+constexpr size_t restrict_tiled_smem() {
+  return sizeof(T) * ((size_t)TR_F * TR_F * TR_F + (size_t)TR_F * TR_F * TR_C + (size_t)TR_F * TR_C * TR_C);
+}
+
+// out_c = P^T in_f: the taps of k_restrict_q2 along x, then y, then z, on a TR_C^3 coarse tile.
+template <typename T>
+__global__ void __launch_bounds__(TT_THREADS) k_restrict_q2_tiled(Grid gc, const OpTab<T, 3>* __restrict__ otab,
+                                                                  int ncomp, const T* __restrict__ in,
+                                                                  T* __restrict__ out, int mask) {
+  pdl_entry();
+  extern __shared__ __align__(16) unsigned char tr_smem[];
+  T* F = reinterpret_cast<T*>(tr_smem);        // [TR_F z][TR_F y][TR_F x]
+  T* T1 = F + TR_F * TR_F * TR_F;              // [TR_F z][TR_F y][TR_C x]
+  T* T2 = T1 + TR_F * TR_F * TR_C;             // [TR_F z][TR_C y][TR_C x]
+  const int NXf = 2 * gc.NX - 1, NYf = 2 * gc.NY - 1, NZf = 2 * gc.NZ - 1;
+  const size_t nf = (size_t)NXf * NYf * NZf;
+  const T(*P1)[3][3] = otab->P1;
+  const int c = blockIdx.z % ncomp;   // one component per block: grid.z = tiles along z x ncomp
+  const int cx0 = blockIdx.x * TR_C, cy0 = blockIdx.y * TR_C, cz0 = (blockIdx.z / ncomp) * TR_C;
+  const int fx0 = 2 * cx0 - 3, fy0 = 2 * cy0 - 3, fz0 = 2 * cz0 - 3;
+  {
+    const T* src = in + (size_t)c * nf;
+    for (int t = threadIdx.x; t < TR_F * TR_F * TR_F; t += TT_THREADS) {
+      const int x = t % TR_F, y = (t / TR_F) % TR_F, z = t / (TR_F * TR_F);
+      const int gx = fx0 + x, gy = fy0 + y, gz = fz0 + z;
+      const bool in_range = gx >= 0 && gx < NXf && gy >= 0 && gy < NYf && gz >= 0 && gz < NZf;
+      cp_async_entry(F + t, in_range ? src + (size_t)gx + (size_t)NXf * (gy + (size_t)NYf * gz) : src, in_range);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int t = threadIdx.x; t < TR_F * TR_F * TR_C; t += TT_THREADS) {
+      const int cx = t % TR_C, yz = t / TR_C;
+      const Q2Taps<T> tx = q2_taps<T>(cx0 + cx, NXf, P1);
+      const T* row = F + yz * TR_F - fx0;
+      T r = T(0);
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        if (tx.ok[k]) r += tx.w[k] * row[tx.off[k]];
+      T1[t] = r;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < TR_F * TR_C * TR_C; t += TT_THREADS) {
+      const int cx = t % TR_C, cy = (t / TR_C) % TR_C, z = t / (TR_C * TR_C);
+      const Q2Taps<T> ty = q2_taps<T>(cy0 + cy, NYf, P1);
+      T r = T(0);
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        if (ty.ok[k]) r += ty.w[k] * T1[(z * TR_F + (ty.off[k] - fy0)) * TR_C + cx];
+      T2[t] = r;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < TR_C * TR_C * TR_C; t += TT_THREADS) {
+      const int cx = t % TR_C, cy = (t / TR_C) % TR_C, cz = t / (TR_C * TR_C);
+      const int ix = cx0 + cx, iy = cy0 + cy, iz = cz0 + cz;
+      if (ix >= gc.NX || iy >= gc.NY || iz >= gc.NZ) continue;
+      T r = T(0);
+      if (!(mask && on_boundary(gc, ix, iy, iz))) {
+        const Q2Taps<T> tz = q2_taps<T>(iz, NZf, P1);
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          if (tz.ok[k]) r += tz.w[k] * T2[((tz.off[k] - fz0) * TR_C + cy) * TR_C + cx];
+      }
+      out[(size_t)c * gc.nn + (size_t)ix + (size_t)gc.NX * (iy + (size_t)gc.NY * iz)] = r;
+    }
+  }
+}
+
+// out_f (+)= P in_c: the nodal interpolation weights of k_prolong3d along z, then y, then x, on a
+// TP_F^3 fine tile (its coarse nodes: a TP_C^3 block).
+template <typename T>
+__global__ void __launch_bounds__(TT_THREADS) k_prolong_q2_tiled(Grid gc, const OpTab<T, 3>* __restrict__ otab,
+                                                                 int ncomp, const T* __restrict__ in_c,
+                                                                 T* __restrict__ out_f, int add) {
+  pdl_entry();
+  __shared__ T C[TP_C][TP_C][TP_C];
+  __shared__ T Z1[TP_F][TP_C][TP_C];
+  __shared__ T Y1[TP_F][TP_F][TP_C];
+  __shared__ T P1[2][3][3];
+  for (int t = threadIdx.x; t < 18; t += TT_THREADS) (&P1[0][0][0])[t] = (&otab->P1[0][0][0])[t];
+  const int NXf = 4 * gc.nx + 1, NYf = 4 * gc.ny + 1, NZf = 4 * gc.nz + 1;
+  const size_t nf = (size_t)NXf * NYf * NZf;
+  const int c = blockIdx.z % ncomp;   // one component per block: grid.z = tiles along z x ncomp
+  const int fx0 = blockIdx.x * TP_F, fy0 = blockIdx.y * TP_F, fz0 = (blockIdx.z / ncomp) * TP_F;
+  const int nfe[3] = {2 * gc.nx, 2 * gc.ny, 2 * gc.nz};
+  // fine node f along an axis: its fine element ef (the last one for the end node), child s of
+  // the coarse element ef / 2, local node a; coarse nodes 2 (ef / 2) + b, b = 0, 1, 2
+  auto split = [&](int f, int d, int& s, int& a, int& cb) {
+    int ef = f / 2;
+    if (ef > nfe[d] - 1) ef = nfe[d] - 1;
+    s = ef % 2;
+    a = f - 2 * ef;
+    cb = 2 * (ef / 2);
+  };
+  // the tile's first coarse node per axis: that of its first fine node (a tile holding only the
+  // end node starts two coarse nodes before it); every fine node of the tile then reads coarse
+  // nodes c0 .. c0 + TP_C - 1
+  int c0x, c0y, c0z, s_, a_;
+  split(fx0, 0, s_, a_, c0x);
+  split(fy0, 1, s_, a_, c0y);
+  split(fz0, 2, s_, a_, c0z);
+  {
+    const T* src = in_c + (size_t)c * gc.nn;
+    __syncthreads();   // P1 is in shared memory
+    for (int t = threadIdx.x; t < TP_C * TP_C * TP_C; t += TT_THREADS) {
+      const int x = t % TP_C, y = (t / TP_C) % TP_C, z = t / (TP_C * TP_C);
+      const int gx = c0x + x, gy = c0y + y, gz = c0z + z;
+      const bool in_range = gx < gc.NX && gy < gc.NY && gz < gc.NZ;
+      cp_async_entry(&C[0][0][0] + t, in_range ? src + (size_t)gx + (size_t)gc.NX * (gy + (size_t)gc.NY * gz) : src,
+                     in_range);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int t = threadIdx.x; t < TP_F * TP_C * TP_C; t += TT_THREADS) {
+      const int x = t % TP_C, y = (t / TP_C) % TP_C, fz = t / (TP_C * TP_C);
+      int s, a, cb;
+      split(min(fz0 + fz, NZf - 1), 2, s, a, cb);
+      T r = T(0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) r += P1[s][a][b] * C[cb + b - c0z][y][x];
+      Z1[fz][y][x] = r;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < TP_F * TP_F * TP_C; t += TT_THREADS) {
+      const int x = t % TP_C, fy = (t / TP_C) % TP_F, fz = t / (TP_C * TP_F);
+      int s, a, cb;
+      split(min(fy0 + fy, NYf - 1), 1, s, a, cb);
+      T r = T(0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) r += P1[s][a][b] * Z1[fz][cb + b - c0y][x];
+      Y1[fz][fy][x] = r;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int t = threadIdx.x; t < TP_F * TP_F * TP_F; t += TT_THREADS) {
+      const int fx = t % TP_F, fy = (t / TP_F) % TP_F, fz = t / (TP_F * TP_F);
+      const int gx = fx0 + fx, gy = fy0 + fy, gz = fz0 + fz;
+      if (gx >= NXf || gy >= NYf || gz >= NZf) continue;
+      int s, a, cb;
+      split(gx, 0, s, a, cb);
+      T r = T(0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) r += P1[s][a][b] * Y1[fz][fy][cb + b - c0x];
+      T* dst = out_f + (size_t)c * nf + (size_t)gx + (size_t)NXf * (gy + (size_t)NYf * gz);
+      *dst = add ? *dst + r : r;
+    }
+  }
+}
+
 // Pressure transfers of the two-space Poisson cycle (|J| cancels between M_d^-1 and the masses):
 //   element pass of r_c = M_cd M_d^-1 r_d: Ye[e][q] = W_q sum_m psi_m(q) (Minv r_e)_m
 template <typename T, int N>
@@ -696,9 +865,30 @@ cudaError_t launch_gather(const Grid& g, int k, int ncomp, int mask, const T* Ye
   return launch_gather_elem<T>(g, k, ncomp, mask, Ye, e, st);
 }
 
+// The tiled Q2 transfers on grids of at least this many coarse nodes, under the automatic kernel
+// choice (the forced choices keep the per-node kernels).
+constexpr long long TILED_MIN_NODES = 100000;
+bool tiled_transfers(const Grid& gc, int k) { return k == 2 && gc.kern == 0 && gc.nn >= TILED_MIN_NODES; }
+
+cudaError_t transfer_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(k_restrict_q2_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)restrict_tiled_smem<float>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_restrict_q2_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)restrict_tiled_smem<double>());
+  return e;
+}
+
 template <typename T>
 cudaError_t launch_prolong_fused(const Grid& gc, int k, const void* otab, int ncomp, const T* in_c, T* out_f, int add,
                                  cudaStream_t st) {
+  if (tiled_transfers(gc, k)) {
+    const dim3 grid((unsigned)((4 * gc.nx + TP_F) / TP_F), (unsigned)((4 * gc.ny + TP_F) / TP_F),
+                    (unsigned)((4 * gc.nz + TP_F) / TP_F * ncomp));
+    wb_launch(k_prolong_q2_tiled<T>, grid, TT_THREADS, 0, st, gc, static_cast<const OpTab<T, 3>*>(otab), ncomp, in_c,
+              out_f, add);
+    return cudaGetLastError();
+  }
   const long long nf = (long long)(2 * k * gc.nx + 1) * (2 * k * gc.ny + 1) * (2 * k * gc.nz + 1);
   WB_FUSED_DISPATCH(k, ((wb_launch(k_prolong3d<T, N>, nb(nf, 128), 128, 0, st, gc, WB_TAB(T), ncomp, in_c,
                                                                                             out_f, add)),
@@ -730,7 +920,14 @@ cudaError_t launch_restrict_batched(const Grid& gc, int k, const void* otab, int
   // One pass (one thread per coarse node) pays off on large coarse grids; small ones keep three
   // short separable passes, which have more threads per node (the element-kernel option forces
   // either: per element -> one pass, per point -> three passes).
-  const bool one_pass = gc.kern == 2 || (gc.kern == 0 && gc.nn >= 100000);
+  if (tiled_transfers(gc, k)) {
+    const dim3 grid((unsigned)((gc.NX + TR_C - 1) / TR_C), (unsigned)((gc.NY + TR_C - 1) / TR_C),
+                    (unsigned)((gc.NZ + TR_C - 1) / TR_C * ncomp));
+    wb_launch(k_restrict_q2_tiled<T>, grid, TT_THREADS, restrict_tiled_smem<T>(), st, gc,
+              static_cast<const OpTab<T, 3>*>(otab), ncomp, in_f, out_c, mask);
+    return cudaGetLastError();
+  }
+  const bool one_pass = gc.kern == 2 || (gc.kern == 0 && gc.nn >= TILED_MIN_NODES);
   if (k == 2 && one_pass) {
     dim3 grid;
     int bs;

@@ -1241,6 +1241,7 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
     if (k == 2) {
       CK(q2_elem64_prepare());
       CK(q2_fused_prepare());
+      CK(transfer_prepare());
     }
     if (k <= 3) {
       cp->kwbref = cp->pool.get<double>(kw_bref_entries(k));

@@ -138,3 +138,24 @@ def test_fused_BT_and_Kw_match_two_pass(wb, shape):
     z = N(s.apply_Kinv(1, r32))   # fused B^T and fused Poisson smoothing on the fine levels
     assert rel(z, z64) < 1e-4
     assert rel(z, N(s_row.apply_Kinv(1, r32))) < 1e-4
+
+
+@pytest.mark.parametrize("shape", SHAPES[:2])
+def test_tiled_transfers_fp64_match_per_node(wb, shape):
+    """The tiled Q2 restriction and prolongation (coarse grids of >= 100000 nodes under the automatic
+    kernel choice) against the per-node kernels, through FP64 V-cycles of both hierarchies: the two
+    differ only in summation order."""
+    nx, ny, nz = shape
+    m = M.Mesh(nx, ny, nz, 2, 1.0, ny / nx, nz / nx)
+    mu = sinker.viscosity(m.node_coords(), inputs.sinker_centres(3, 6), 0.1, 200.0, 1e6)
+    kw = dict(ny=ny, nz=nz, lengths=(1.0, ny / nx, nz / nx), restart=5)
+    s = wb.Solver(nx, 2, torch.tensor(mu, device="cuda"), **kw)
+    s_row = wb.Solver(nx, 2, torch.tensor(mu, device="cuda"), elem_kernels=ELEM_ROW, **kw)
+    rng = np.random.default_rng(11)
+    r = rng.standard_normal(m.n_u)
+    r[np.tile(m.boundary_node_mask(), 3)] = 0.0
+    rt = torch.tensor(r, device="cuda")
+    assert rel(N(s.apply_Ainv(rt)), N(s_row.apply_Ainv(rt))) < 1e-11
+    q = torch.tensor(op.project_pressure(m, rng.standard_normal(m.n_p)), device="cuda")
+    for which in (0, 1):
+        assert rel(N(s.apply_Kinv(which, q)), N(s_row.apply_Kinv(which, q))) < 1e-11
