@@ -621,7 +621,8 @@ def run_sweep(args):
       beside the Stokes solve, over mesh size and order;
     kcycles: Stokes iterations with 1-8 V-cycles per K~_w^-1, and the cost of one K_w V-cycle
       against one U-Net forward pass (what a learned K~_w^-1 could at best save);
-    cheb: Stokes iterations and solve time against the Chebyshev smoothing degree.
+    cheb: Stokes iterations and solve time against the Chebyshev smoothing degree;
+    restart: the same against the FGMRES restart length.
     """
     import torch
 
@@ -748,6 +749,26 @@ def run_sweep(args):
                                   "cheb_degree": deg, "iters": res.iters, "converged": res.status == 0,
                                   "solve_s": min(ts)}), flush=True)
                 s.close()
+    elif args.sweep == "restart":
+        # FGMRES restart length: iterations against the per-iteration cost of the Arnoldi basis
+        # (CGS2 is 4 (j + 1) n FP64 multiply-adds at step j)
+        for wname in ("32^3-Q2-S24-DR1e6", "64^3-Q2-S64-DR1e10"):
+            cfg = inputs.WORKLOADS[wname]
+            c = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
+            mu, f = wb.sinker_setup(cfg["n"], cfg["k"], c, cfg["omega"], cfg["delta"], cfg["dr"])
+            for m in (10, 20, 30, 50, 100):
+                s = wb.Solver(cfg["n"], cfg["k"], mu, precision=prec, restart=m)
+                s.solve(f)
+                ts = []
+                for _ in range(2):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    _, _, res = s.solve(f, rtol=RTOL, maxit=args.sweep_maxit)
+                    torch.cuda.synchronize()
+                    ts.append(time.perf_counter() - t0)
+                print(json.dumps({"sweep": "restart", "workload": wname, "precision": args.precision, "restart": m,
+                                  "iters": res.iters, "converged": res.status == 0, "solve_s": min(ts)}), flush=True)
+                s.close()
     elif args.sweep == "order":
         for k in (2, 3, 4):
             r = solve(k, 16, 1e6)
@@ -770,7 +791,7 @@ def main():
                     help="one viscosity-dependent setup in an NVTX range 'prof' (for an ncu launch list)")
     ap.add_argument("--profile-apply", action="store_true",
                     help="one FP64 A, one FP32 A and one FP64 K apply in an NVTX range 'prof' (for ncu)")
-    ap.add_argument("--sweep", choices=["robustness", "amplification", "order", "alone", "kcycles", "cheb"],
+    ap.add_argument("--sweep", choices=["robustness", "amplification", "order", "alone", "kcycles", "cheb", "restart"],
                     help="iteration-count sweeps in the style of Tables 1, 2 and 3b (many JSON lines)")
     ap.add_argument("--sweep-n", type=int, default=32)
     ap.add_argument("--sweep-maxit", type=int, default=2000)
