@@ -464,10 +464,19 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 template <typename T>
 constexpr size_t restrict_tiled_smem() {
-  return sizeof(T) * ((size_t)TR_F * TR_F * TR_F + (size_t)TR_F * TR_F * TR_C + (size_t)TR_F * TR_C * TR_C);
+  return sizeof(T) * ((size_t)TR_F * TR_F * TR_F + (size_t)TR_F * TR_F * TR_C + (size_t)TR_F * TR_C * TR_C +
+                      3 * TR_C * 5) +
+         sizeof(int) * 3 * TR_C * 5;
+}
+template <typename T>
+constexpr size_t prolong_tiled_smem() {
+  return sizeof(T) * ((size_t)TP_C * TP_C * TP_C + (size_t)TP_F * TP_C * TP_C + (size_t)TP_F * TP_F * TP_C +
+                      (size_t)TP_F * TP_F * TP_F + 18);
 }
 
 // out_c = P^T in_f: the taps of k_restrict_q2 along x, then y, then z, on a TR_C^3 coarse tile.
+// The taps of the tile's coarse nodes per axis are formed once (an absent tap has weight 0 and
+// reads an entry of the tile: adding the exact zero leaves the sums unchanged).
 template <typename T>
 __global__ void __launch_bounds__(TT_THREADS) k_restrict_q2_tiled(Grid gc, const OpTab<T, 3>* __restrict__ otab,
                                                                   int ncomp, const T* __restrict__ in,
@@ -477,71 +486,100 @@ __global__ void __launch_bounds__(TT_THREADS) k_restrict_q2_tiled(Grid gc, const
   T* F = reinterpret_cast<T*>(tr_smem);        // [TR_F z][TR_F y][TR_F x]
   T* T1 = F + TR_F * TR_F * TR_F;              // [TR_F z][TR_F y][TR_C x]
   T* T2 = T1 + TR_F * TR_F * TR_C;             // [TR_F z][TR_C y][TR_C x]
+  T* tw = T2 + TR_F * TR_C * TR_C;             // [axis][coarse node][tap]: weight
+  int* to = reinterpret_cast<int*>(tw + 3 * TR_C * 5);   // tile-local fine index of the tap
   const int NXf = 2 * gc.NX - 1, NYf = 2 * gc.NY - 1, NZf = 2 * gc.NZ - 1;
   const size_t nf = (size_t)NXf * NYf * NZf;
-  const T(*P1)[3][3] = otab->P1;
   const int c = blockIdx.z % ncomp;   // one component per block: grid.z = tiles along z x ncomp
   const int cx0 = blockIdx.x * TR_C, cy0 = blockIdx.y * TR_C, cz0 = (blockIdx.z / ncomp) * TR_C;
   const int fx0 = 2 * cx0 - 3, fy0 = 2 * cy0 - 3, fz0 = 2 * cz0 - 3;
-  {
-    const T* src = in + (size_t)c * nf;
-    for (int t = threadIdx.x; t < TR_F * TR_F * TR_F; t += TT_THREADS) {
-      const int x = t % TR_F, y = (t / TR_F) % TR_F, z = t / (TR_F * TR_F);
-      const int gx = fx0 + x, gy = fy0 + y, gz = fz0 + z;
-      const bool in_range = gx >= 0 && gx < NXf && gy >= 0 && gy < NYf && gz >= 0 && gz < NZf;
-      cp_async_entry(F + t, in_range ? src + (size_t)gx + (size_t)NXf * (gy + (size_t)NYf * gz) : src, in_range);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    for (int t = threadIdx.x; t < TR_F * TR_F * TR_C; t += TT_THREADS) {
-      const int cx = t % TR_C, yz = t / TR_C;
-      const Q2Taps<T> tx = q2_taps<T>(cx0 + cx, NXf, P1);
-      const T* row = F + yz * TR_F - fx0;
-      T r = T(0);
+  const T* src = in + (size_t)c * nf;
+  for (int t = threadIdx.x; t < TR_F * TR_F * TR_F; t += TT_THREADS) {
+    const int gx = fx0 + t % TR_F, gy = fy0 + (t / TR_F) % TR_F, gz = fz0 + t / (TR_F * TR_F);
+    const bool ok = gx >= 0 && gx < NXf && gy >= 0 && gy < NYf && gz >= 0 && gz < NZf;
+    cp_async_entry(F + t, ok ? src + (size_t)gx + (size_t)NXf * (gy + (size_t)NYf * gz) : src, ok);
+  }
+  if (threadIdx.x < 3 * TR_C) {
+    const int axis = threadIdx.x / TR_C, kk = threadIdx.x % TR_C;
+    const int c0 = axis == 0 ? cx0 : (axis == 1 ? cy0 : cz0), f0 = 2 * c0 - 3;
+    const int nfa = axis == 0 ? NXf : (axis == 1 ? NYf : NZf);
+    const Q2Taps<T> tp = q2_taps<T>(c0 + kk, nfa, otab->P1);
 #pragma unroll
-      for (int k = 0; k < 5; ++k)
-        if (tx.ok[k]) r += tx.w[k] * row[tx.off[k]];
-      T1[t] = r;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < TR_F * TR_C * TR_C; t += TT_THREADS) {
-      const int cx = t % TR_C, cy = (t / TR_C) % TR_C, z = t / (TR_C * TR_C);
-      const Q2Taps<T> ty = q2_taps<T>(cy0 + cy, NYf, P1);
-      T r = T(0);
-#pragma unroll
-      for (int k = 0; k < 5; ++k)
-        if (ty.ok[k]) r += ty.w[k] * T1[(z * TR_F + (ty.off[k] - fy0)) * TR_C + cx];
-      T2[t] = r;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < TR_C * TR_C * TR_C; t += TT_THREADS) {
-      const int cx = t % TR_C, cy = (t / TR_C) % TR_C, cz = t / (TR_C * TR_C);
-      const int ix = cx0 + cx, iy = cy0 + cy, iz = cz0 + cz;
-      if (ix >= gc.NX || iy >= gc.NY || iz >= gc.NZ) continue;
-      T r = T(0);
-      if (!(mask && on_boundary(gc, ix, iy, iz))) {
-        const Q2Taps<T> tz = q2_taps<T>(iz, NZf, P1);
-#pragma unroll
-        for (int k = 0; k < 5; ++k)
-          if (tz.ok[k]) r += tz.w[k] * T2[((tz.off[k] - fz0) * TR_C + cy) * TR_C + cx];
-      }
-      out[(size_t)c * gc.nn + (size_t)ix + (size_t)gc.NX * (iy + (size_t)gc.NY * iz)] = r;
+    for (int t = 0; t < 5; ++t) {
+      tw[threadIdx.x * 5 + t] = tp.ok[t] ? tp.w[t] : T(0);
+      to[threadIdx.x * 5 + t] = tp.ok[t] ? tp.off[t] - f0 : 0;
     }
   }
+  cp_async_wait_all();
+  __syncthreads();
+  {
+    // a thread's coarse x node (t mod 8) is the same in every step: its taps stay in registers
+    const int kx = threadIdx.x & (TR_C - 1);
+    T w[5];
+    int o[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      w[k] = tw[kx * 5 + k];
+      o[k] = to[kx * 5 + k];
+    }
+    for (int t = threadIdx.x; t < TR_F * TR_F * TR_C; t += TT_THREADS) {
+      const T* fr = F + (t >> 3) * TR_F;
+      T r = T(0);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) r += w[k] * fr[o[k]];
+      T1[t] = r;
+    }
+  }
+  __syncthreads();
+  {
+    // likewise the coarse y node ((t / 8) mod 8)
+    const int kx = threadIdx.x & (TR_C - 1), ky = (threadIdx.x >> 3) & (TR_C - 1);
+    T w[5];
+    int o[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      w[k] = tw[(TR_C + ky) * 5 + k];
+      o[k] = to[(TR_C + ky) * 5 + k] * TR_C + kx;
+    }
+    for (int t = threadIdx.x; t < TR_F * TR_C * TR_C; t += TT_THREADS) {
+      const T* tz = T1 + (t >> 6) * TR_F * TR_C;
+      T r = T(0);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) r += w[k] * tz[o[k]];
+      T2[t] = r;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < TR_C * TR_C * TR_C; t += TT_THREADS) {
+    const int kx = t & (TR_C - 1), ky = (t >> 3) & (TR_C - 1), kz = t >> 6;
+    const int ix = cx0 + kx, iy = cy0 + ky, iz = cz0 + kz;
+    if (ix >= gc.NX || iy >= gc.NY || iz >= gc.NZ) continue;
+    T r = T(0);
+    if (!(mask && on_boundary(gc, ix, iy, iz))) {
+      const T* w = tw + (2 * TR_C + kz) * 5;
+      const int* o = to + (2 * TR_C + kz) * 5;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) r += w[k] * T2[(o[k] * TR_C + ky) * TR_C + kx];
+    }
+    out[(size_t)c * gc.nn + (size_t)ix + (size_t)gc.NX * (iy + (size_t)gc.NY * iz)] = r;
+  }
 }
+static_assert(TR_C == 8 && TT_THREADS % 64 == 0, "the pass index arithmetic assumes 8 coarse nodes per tile edge");
 
 // out_f (+)= P in_c: the nodal interpolation weights of k_prolong3d along z, then y, then x, on a
-// TP_F^3 fine tile (its coarse nodes: a TP_C^3 block).
+// TP_F^3 fine tile (its coarse nodes: a TP_C^3 block).  The target tile is fetched asynchronously
+// with the coarse block, so the final pass reads it from shared memory.
 template <typename T>
 __global__ void __launch_bounds__(TT_THREADS) k_prolong_q2_tiled(Grid gc, const OpTab<T, 3>* __restrict__ otab,
                                                                  int ncomp, const T* __restrict__ in_c,
                                                                  T* __restrict__ out_f, int add) {
   pdl_entry();
-  __shared__ T C[TP_C][TP_C][TP_C];
-  __shared__ T Z1[TP_F][TP_C][TP_C];
-  __shared__ T Y1[TP_F][TP_F][TP_C];
-  __shared__ T P1[2][3][3];
-  for (int t = threadIdx.x; t < 18; t += TT_THREADS) (&P1[0][0][0])[t] = (&otab->P1[0][0][0])[t];
+  extern __shared__ __align__(16) unsigned char tp_smem[];
+  T* C = reinterpret_cast<T*>(tp_smem);       // [TP_C z][TP_C y][TP_C x]
+  T* Z1 = C + TP_C * TP_C * TP_C;             // [TP_F z][TP_C y][TP_C x]
+  T* Y1 = Z1 + TP_F * TP_C * TP_C;            // [TP_F z][TP_F y][TP_C x]
+  T* O = Y1 + TP_F * TP_F * TP_C;             // [TP_F z][TP_F y][TP_F x]: the target tile
+  T* P1 = O + TP_F * TP_F * TP_F;             // [2][3][3]
   const int NXf = 4 * gc.nx + 1, NYf = 4 * gc.ny + 1, NZf = 4 * gc.nz + 1;
   const size_t nf = (size_t)NXf * NYf * NZf;
   const int c = blockIdx.z % ncomp;   // one component per block: grid.z = tiles along z x ncomp
@@ -563,53 +601,57 @@ __global__ void __launch_bounds__(TT_THREADS) k_prolong_q2_tiled(Grid gc, const 
   split(fx0, 0, s_, a_, c0x);
   split(fy0, 1, s_, a_, c0y);
   split(fz0, 2, s_, a_, c0z);
-  {
-    const T* src = in_c + (size_t)c * gc.nn;
-    __syncthreads();   // P1 is in shared memory
-    for (int t = threadIdx.x; t < TP_C * TP_C * TP_C; t += TT_THREADS) {
-      const int x = t % TP_C, y = (t / TP_C) % TP_C, z = t / (TP_C * TP_C);
-      const int gx = c0x + x, gy = c0y + y, gz = c0z + z;
-      const bool in_range = gx < gc.NX && gy < gc.NY && gz < gc.NZ;
-      cp_async_entry(&C[0][0][0] + t, in_range ? src + (size_t)gx + (size_t)gc.NX * (gy + (size_t)gc.NY * gz) : src,
-                     in_range);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    for (int t = threadIdx.x; t < TP_F * TP_C * TP_C; t += TT_THREADS) {
-      const int x = t % TP_C, y = (t / TP_C) % TP_C, fz = t / (TP_C * TP_C);
-      int s, a, cb;
-      split(min(fz0 + fz, NZf - 1), 2, s, a, cb);
-      T r = T(0);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) r += P1[s][a][b] * C[cb + b - c0z][y][x];
-      Z1[fz][y][x] = r;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < TP_F * TP_F * TP_C; t += TT_THREADS) {
-      const int x = t % TP_C, fy = (t / TP_C) % TP_F, fz = t / (TP_C * TP_F);
-      int s, a, cb;
-      split(min(fy0 + fy, NYf - 1), 1, s, a, cb);
-      T r = T(0);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) r += P1[s][a][b] * Z1[fz][cb + b - c0y][x];
-      Y1[fz][fy][x] = r;
-    }
-    __syncthreads();
-#pragma unroll 4
+  const T* src = in_c + (size_t)c * gc.nn;
+  T* dst = out_f + (size_t)c * nf;
+  for (int t = threadIdx.x; t < TP_C * TP_C * TP_C; t += TT_THREADS) {
+    const int x = t % TP_C, y = (t / TP_C) % TP_C, z = t / (TP_C * TP_C);
+    const int gx = c0x + x, gy = c0y + y, gz = c0z + z;
+    const bool ok = gx < gc.NX && gy < gc.NY && gz < gc.NZ;
+    cp_async_entry(C + t, ok ? src + (size_t)gx + (size_t)gc.NX * (gy + (size_t)gc.NY * gz) : src, ok);
+  }
+  if (add) {
     for (int t = threadIdx.x; t < TP_F * TP_F * TP_F; t += TT_THREADS) {
-      const int fx = t % TP_F, fy = (t / TP_F) % TP_F, fz = t / (TP_F * TP_F);
-      const int gx = fx0 + fx, gy = fy0 + fy, gz = fz0 + fz;
-      if (gx >= NXf || gy >= NYf || gz >= NZf) continue;
-      int s, a, cb;
-      split(gx, 0, s, a, cb);
-      T r = T(0);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) r += P1[s][a][b] * Y1[fz][fy][cb + b - c0x];
-      T* dst = out_f + (size_t)c * nf + (size_t)gx + (size_t)NXf * (gy + (size_t)NYf * gz);
-      *dst = add ? *dst + r : r;
+      const int gx = fx0 + (t & (TP_F - 1)), gy = fy0 + ((t >> 4) & (TP_F - 1)), gz = fz0 + (t >> 8);
+      const bool ok = gx < NXf && gy < NYf && gz < NZf;
+      cp_async_entry(O + t, ok ? dst + (size_t)gx + (size_t)NXf * (gy + (size_t)NYf * gz) : dst, ok);
     }
   }
+  for (int t = threadIdx.x; t < 18; t += TT_THREADS) P1[t] = (&otab->P1[0][0][0])[t];
+  cp_async_wait_all();
+  __syncthreads();
+  for (int t = threadIdx.x; t < TP_F * TP_C * TP_C; t += TT_THREADS) {
+    const int x = t % TP_C, y = (t / TP_C) % TP_C, fz = t / (TP_C * TP_C);
+    int s, a, cb;
+    split(min(fz0 + fz, NZf - 1), 2, s, a, cb);
+    T r = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) r += P1[(s * 3 + a) * 3 + b] * C[((cb + b - c0z) * TP_C + y) * TP_C + x];
+    Z1[t] = r;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < TP_F * TP_F * TP_C; t += TT_THREADS) {
+    const int x = t % TP_C, fy = (t / TP_C) % TP_F, fz = t / (TP_C * TP_F);
+    int s, a, cb;
+    split(min(fy0 + fy, NYf - 1), 1, s, a, cb);
+    T r = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) r += P1[(s * 3 + a) * 3 + b] * Z1[(fz * TP_C + (cb + b - c0y)) * TP_C + x];
+    Y1[t] = r;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < TP_F * TP_F * TP_F; t += TT_THREADS) {
+    const int fx = t & (TP_F - 1), fy = (t >> 4) & (TP_F - 1), fz = t >> 8;
+    const int gx = fx0 + fx, gy = fy0 + fy, gz = fz0 + fz;
+    if (gx >= NXf || gy >= NYf || gz >= NZf) continue;
+    int s, a, cb;
+    split(gx, 0, s, a, cb);
+    T r = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) r += P1[(s * 3 + a) * 3 + b] * Y1[(fz * TP_F + fy) * TP_C + (cb + b - c0x)];
+    dst[(size_t)gx + (size_t)NXf * (gy + (size_t)NYf * gz)] = add ? O[t] + r : r;
+  }
 }
+static_assert(TP_F == 16, "the pass index arithmetic assumes 16 fine nodes per tile edge");
 
 // Pressure transfers of the two-space Poisson cycle (|J| cancels between M_d^-1 and the masses):
 //   element pass of r_c = M_cd M_d^-1 r_d: Ye[e][q] = W_q sum_m psi_m(q) (Minv r_e)_m
@@ -876,6 +918,12 @@ cudaError_t transfer_prepare() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_restrict_q2_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)restrict_tiled_smem<double>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_prolong_q2_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)prolong_tiled_smem<float>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_prolong_q2_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)prolong_tiled_smem<double>());
   return e;
 }
 
@@ -885,8 +933,8 @@ cudaError_t launch_prolong_fused(const Grid& gc, int k, const void* otab, int nc
   if (tiled_transfers(gc, k)) {
     const dim3 grid((unsigned)((4 * gc.nx + TP_F) / TP_F), (unsigned)((4 * gc.ny + TP_F) / TP_F),
                     (unsigned)((4 * gc.nz + TP_F) / TP_F * ncomp));
-    wb_launch(k_prolong_q2_tiled<T>, grid, TT_THREADS, 0, st, gc, static_cast<const OpTab<T, 3>*>(otab), ncomp, in_c,
-              out_f, add);
+    wb_launch(k_prolong_q2_tiled<T>, grid, TT_THREADS, prolong_tiled_smem<T>(), st, gc,
+              static_cast<const OpTab<T, 3>*>(otab), ncomp, in_c, out_f, add);
     return cudaGetLastError();
   }
   const long long nf = (long long)(2 * k * gc.nx + 1) * (2 * k * gc.ny + 1) * (2 * k * gc.nz + 1);

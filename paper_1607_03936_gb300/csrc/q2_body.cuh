@@ -15,6 +15,12 @@ namespace wb {
 
 __host__ __device__ constexpr int q2i(int i, int j, int l) { return i + 3 * (j + 3 * l); }
 
+// Entries of the Q2 GLL derivative matrix D[i][a] = l_a'(x_i) that can be nonzero: the middle basis
+// function is even about the middle node, so D[1][1] = 0 exactly (for every element size, since
+// the table holds D scaled by 2/h).  The sums below skip that term at compile time; adding the exact
+// zero would not change the result.
+__host__ __device__ constexpr bool q2d(int i, int a) { return !(i == 1 && a == 1); }
+
 // The element's nodal values of 3 components starting at node n0 (its lowest corner), with the
 // nodes on Dirichlet faces of the domain read as zero; lo_*/hi_*: the element touches that face.
 __device__ __forceinline__ void q2_load_u(const float* __restrict__ u, size_t nn, int NX, int NY, int n0, bool act,
@@ -69,9 +75,9 @@ __device__ __forceinline__ void q2_stokes_points(const OpTab<float, 3>& tb, cons
             float a0 = 0.f, a1 = 0.f, a2 = 0.f;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-              a0 += tb.Ds[0][i][a] * ur[c][q2i(a, j, l)];
-              a1 += tb.Ds[1][j][a] * ur[c][q2i(i, a, l)];
-              a2 += tb.Ds[2][l][a] * ur[c][q2i(i, j, a)];
+              if (q2d(i, a)) a0 += tb.Ds[0][i][a] * ur[c][q2i(a, j, l)];
+              if (q2d(j, a)) a1 += tb.Ds[1][j][a] * ur[c][q2i(i, a, l)];
+              if (q2d(l, a)) a2 += tb.Ds[2][l][a] * ur[c][q2i(i, j, a)];
             }
             G[c][0] = a0;
             G[c][1] = a1;
@@ -107,16 +113,16 @@ __device__ __forceinline__ void q2_stokes_points(const OpTab<float, 3>& tb, cons
           // output component c, derivative direction d: out_c(node on the d-line) += Ds[d] S_cd
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
-            out[0][q2i(a, j, l)] += tb.Ds[0][i][a] * sd[0];
-            out[1][q2i(i, a, l)] += tb.Ds[1][j][a] * sd[1];
-            out[2][q2i(i, j, a)] += tb.Ds[2][l][a] * sd[2];
+            if (q2d(i, a)) out[0][q2i(a, j, l)] += tb.Ds[0][i][a] * sd[0];
+            if (q2d(j, a)) out[1][q2i(i, a, l)] += tb.Ds[1][j][a] * sd[1];
+            if (q2d(l, a)) out[2][q2i(i, j, a)] += tb.Ds[2][l][a] * sd[2];
             if (DA) {
-              out[0][q2i(i, a, l)] += tb.Ds[1][j][a] * sxy;
-              out[0][q2i(i, j, a)] += tb.Ds[2][l][a] * sxz;
-              out[1][q2i(a, j, l)] += tb.Ds[0][i][a] * sxy;
-              out[1][q2i(i, j, a)] += tb.Ds[2][l][a] * syz;
-              out[2][q2i(a, j, l)] += tb.Ds[0][i][a] * sxz;
-              out[2][q2i(i, a, l)] += tb.Ds[1][j][a] * syz;
+              if (q2d(j, a)) out[0][q2i(i, a, l)] += tb.Ds[1][j][a] * sxy;
+              if (q2d(l, a)) out[0][q2i(i, j, a)] += tb.Ds[2][l][a] * sxz;
+              if (q2d(i, a)) out[1][q2i(a, j, l)] += tb.Ds[0][i][a] * sxy;
+              if (q2d(l, a)) out[1][q2i(i, j, a)] += tb.Ds[2][l][a] * syz;
+              if (q2d(i, a)) out[2][q2i(a, j, l)] += tb.Ds[0][i][a] * sxz;
+              if (q2d(j, a)) out[2][q2i(i, a, l)] += tb.Ds[1][j][a] * syz;
             }
           }
         }
@@ -151,9 +157,9 @@ __device__ __forceinline__ void q2_poisson_points(const OpTab<T, 3>& tb, const T
         T a0 = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          a0 += tb.Ds[0][i][a] * ur[q2i(a, j, l)];
-          a1 += tb.Ds[1][j][a] * ur[q2i(i, a, l)];
-          a2 += tb.Ds[2][l][a] * ur[q2i(i, j, a)];
+          if (q2d(i, a)) a0 += tb.Ds[0][i][a] * ur[q2i(a, j, l)];
+          if (q2d(j, a)) a1 += tb.Ds[1][j][a] * ur[q2i(i, a, l)];
+          if (q2d(l, a)) a2 += tb.Ds[2][l][a] * ur[q2i(i, j, a)];
         }
         const T f = tb.W3[q] * cf[q];
         a0 *= f;
@@ -161,9 +167,9 @@ __device__ __forceinline__ void q2_poisson_points(const OpTab<T, 3>& tb, const T
         a2 *= f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          out[q2i(a, j, l)] += tb.Ds[0][i][a] * a0;
-          out[q2i(i, a, l)] += tb.Ds[1][j][a] * a1;
-          out[q2i(i, j, a)] += tb.Ds[2][l][a] * a2;
+          if (q2d(i, a)) out[q2i(a, j, l)] += tb.Ds[0][i][a] * a0;
+          if (q2d(j, a)) out[q2i(i, a, l)] += tb.Ds[1][j][a] * a1;
+          if (q2d(l, a)) out[q2i(i, j, a)] += tb.Ds[2][l][a] * a2;
         }
       }
 }

@@ -159,3 +159,24 @@ def test_tiled_transfers_fp64_match_per_node(wb, shape):
     q = torch.tensor(op.project_pressure(m, rng.standard_normal(m.n_p)), device="cuda")
     for which in (0, 1):
         assert rel(N(s.apply_Kinv(which, q)), N(s_row.apply_Kinv(which, q))) < 1e-11
+
+
+def test_fused_apply_on_a_coarse_level_128cubed(wb):
+    """128^3 Q2 (the paper's level-7 size): the second level of the viscous hierarchy (64^3) also
+    takes the single-kernel A apply, there with the viscosity per element point; the FP32 A and
+    K_w V-cycles against the two-pass kernels (1e-4, as for every FP32 V-cycle)."""
+    cfg = inputs.WORKLOADS["128^3-Q2-S16-DR1e6"]
+    n, k = cfg["n"], cfg["k"]
+    c = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
+    mu, _ = wb.sinker_setup(n, k, c, cfg["omega"], cfg["delta"], cfg["dr"])
+    s = wb.Solver(n, k, mu, precision=wb.MIXED, restart=5)
+    rng = torch.Generator(device="cuda").manual_seed(4)
+    r = torch.randn(s.n_u, device="cuda", generator=rng).float()
+    q = torch.randn(s.n_p, device="cuda", generator=rng).float()
+    z = N(s.apply_Ainv(r))
+    zk = N(s.apply_Kinv(1, q))
+    s.close()
+    s_row = wb.Solver(n, k, mu, precision=wb.MIXED, restart=5, elem_kernels=ELEM_ROW)
+    assert rel(z, N(s_row.apply_Ainv(r))) < 1e-4
+    assert rel(zk, N(s_row.apply_Kinv(1, q))) < 1e-4
+    s_row.close()
