@@ -119,14 +119,17 @@ def test_fused_mixed_solve_matches_two_pass(wb):
 
 @pytest.mark.parametrize("shape", SHAPES[:2])
 def test_fused_BT_and_Kw_match_two_pass(wb, shape):
-    """B^T p (the fused gradient pass) and K_w p = B C^-1 B^T p (its C^-1 node epilogue feeding the
-    element-local B pass) against the two-pass row kernels; the K_w V-cycle (fused K_w and Poisson
+    """B^T p (the fused gradient pass), B u and K_w p = B C^-1 B^T p against the two-pass row
+    kernels; the K_w V-cycle (fused K_w and Poisson
     smoothing steps) against FP64 and the two-pass V-cycle."""
     m, mu, s = setup(wb, shape)
     _, _, s_row = setup(wb, shape, elem_kernels=ELEM_ROW)
     rng = np.random.default_rng(7)
     p = torch.tensor(rng.standard_normal(m.n_p), dtype=torch.float32, device="cuda")
     assert rel(N(s.apply_BT(p)), N(s_row.apply_BT(p))) < 1e-6
+    # B u (the element-local pass both contexts share) on the same shapes
+    u = torch.tensor(rng.standard_normal(m.n_u), dtype=torch.float32, device="cuda")
+    assert rel(N(s.apply_B(u)), N(s_row.apply_B(u))) < 1e-6
     for which in (0, 1):
         assert rel(N(s.apply_Kw(which, p)), N(s_row.apply_Kw(which, p))) < 1e-5
     nx, ny, nz = shape
