@@ -16,6 +16,7 @@ operators  assembled A, B, B^T, lumped weights C/D, K_w, Q_k Poisson L_c
 multigrid  nested transfers, coefficient coarsening, Chebyshev-Jacobi, V-cycles
 krylov     right-preconditioned flexible GMRES(m)
 wbfbt      w-BFBT (Eq. wbfbt), block preconditioner (Eq. precond-stokes), solve
+mapped     A, B and the load vector on mapped (isoparametric) hexahedra; the mapped solve
 
 Parity status: every function is pinned by a CPU test against closed forms,
 symbolic integrals, invariants or brute force, except the upper spectral bound

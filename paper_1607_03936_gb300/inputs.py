@@ -79,3 +79,44 @@ WORKLOADS = {
     # the size of Table 3a's refinement level 7 (59.3M DOF) with its S16, DR 1e6 problem
     "128^3-Q2-S16-DR1e6": dict(n=128, k=2, n_sinkers=16, omega=0.1, delta=200.0, dr=1e6, seed=0),
 }
+
+
+# Mapped (non-affine) hexahedral meshes.  Both generators move the nodes of a brick mesh: they take
+# the brick's nodal coordinates X0 (n_nodes, 3) and return the moved coordinates, which then define
+# each element's isoparametric map.  Nodes on the brick's faces stay where they are, so the domain
+# stays the brick.
+
+def deform_vertices(X0: np.ndarray, n_el: tuple[int, int, int], lengths: tuple[float, float, float],
+                    amp: float, seed: int) -> np.ndarray:
+    """Straight-edged, non-affine elements: every interior element vertex moves by a seeded uniform
+    offset in [-amp, amp] h per axis (vertices on the boundary stay), and every node moves by the
+    trilinear interpolant of its brick element's vertex offsets.  amp < 1/6 keeps det J > 0
+    everywhere: every entry of (2/h) J - I is an average of edge-offset differences, at most 2 amp
+    in magnitude, so its norm stays below 1."""
+    nx, ny, nz = n_el
+    h = np.array(lengths, dtype=np.float64) / np.array([nx, ny, nz])
+    rng = np.random.default_rng(seed)
+    off = rng.uniform(-amp, amp, size=(nz + 1, ny + 1, nx + 1, 3)) * h
+    off[0, :, :] = off[-1, :, :] = 0.0
+    off[:, 0, :] = off[:, -1, :] = 0.0
+    off[:, :, 0] = off[:, :, -1] = 0.0
+    t = X0 / h                                           # brick coordinates in element units
+    e = np.minimum(np.floor(t + 1e-12).astype(np.int64), np.array([nx, ny, nz]) - 1)
+    s = np.clip(t - e, 0.0, 1.0)
+    out = X0.astype(np.float64).copy()
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                wgt = ((s[:, 0] if cx else 1 - s[:, 0]) * (s[:, 1] if cy else 1 - s[:, 1])
+                       * (s[:, 2] if cz else 1 - s[:, 2]))
+                out += wgt[:, None] * off[e[:, 2] + cz, e[:, 1] + cy, e[:, 0] + cx]
+    return out
+
+
+def deform_smooth(X0: np.ndarray, lengths: tuple[float, float, float], amp: float) -> np.ndarray:
+    """Curved elements: x -> x + amp L b(x) v, b(x) = prod_d sin(pi x_d / L_d), v = (1, -1, 1) / 2
+    scaled per axis by L_d; b vanishes on the boundary.  The Jacobian of the move is I plus a rank-one
+    term, det = 1 + amp L v . grad b >= 1 - 1.5 pi amp, so amp < 0.2 keeps it positive."""
+    L = np.array(lengths, dtype=np.float64)
+    b = np.prod(np.sin(np.pi * X0 / L), axis=1)
+    return X0 + amp * b[:, None] * (L * np.array([0.5, -0.5, 0.5]))[None, :]
