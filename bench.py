@@ -622,8 +622,10 @@ def run_sweep(args):
     kcycles: Stokes iterations with 1-8 V-cycles per K~_w^-1, and the cost of one K_w V-cycle
       against one U-Net forward pass (what a learned K~_w^-1 could at best save);
     cheb: Stokes iterations and solve time against the Chebyshev smoothing degree;
-    restart: the same against the FGMRES restart length.
+    restart: the same against the FGMRES restart length;
+    mapped: mapped-hexahedron applies beside the brick's, and iterations against the distortion.
     """
+    import numpy as np
     import torch
 
     from paper_1607_03936_gb300 import build
@@ -769,6 +771,61 @@ def run_sweep(args):
                 print(json.dumps({"sweep": "restart", "workload": wname, "precision": args.precision, "restart": m,
                                   "iters": res.iters, "converged": res.status == 0, "solve_s": min(ts)}), flush=True)
                 s.close()
+    elif args.sweep == "mapped":
+        # mapped hexahedra (isoparametric Q2 from moved nodes, the fields of Sec. 2.1 at the moved
+        # nodes): the mapped operator applies beside the brick's on the same mesh (CUDA events),
+        # and Stokes iterations and solve time against the distortion, the preconditioner staying
+        # the brick's
+        k = 2
+        c = inputs.sinker_centres(0, 16)
+        X0 = wb.node_coords(n, k).view(3, -1).T.cpu().numpy()
+        geoms = (("brick", 0.0), ("trilinear", 0.05), ("trilinear", 0.1), ("trilinear", 0.15), ("smooth", 0.05),
+                 ("smooth", 0.1), ("smooth", 0.15))
+
+        def apply_s(fn, x, reps=20):
+            for _ in range(3):
+                fn(x)
+            ev = _events(2)
+            ev[0].record()
+            for _ in range(reps):
+                fn(x)
+            ev[1].record()
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]) / reps / 1e3
+
+        for kind, amp in geoms:
+            if kind == "brick":
+                X = X0
+            elif kind == "trilinear":
+                X = inputs.deform_vertices(X0, (n, n, n), (1.0, 1.0, 1.0), amp, 7)
+            else:
+                X = inputs.deform_smooth(X0, (1.0, 1.0, 1.0), amp)
+            Xt = torch.tensor(np.ascontiguousarray(X.T).ravel(), device="cuda")
+            mu, f = wb.sinker_setup_at(Xt, n, k, c, 0.1, 200.0, 1e6)
+            s = wb.Solver(n, k, mu, precision=prec)
+            s.set_geometry(Xt)
+            gen = torch.Generator(device="cuda").manual_seed(5)
+            x64 = torch.randn(s.n_u + s.n_p, dtype=torch.float64, device="cuda", generator=gen)
+            u32 = x64[: s.n_u].float()
+            row = {"sweep": "mapped", **base, "k": k, "sinkers": 16, "dr": 1e6, "geometry": kind, "amp": amp,
+                   "A64_mapped_s": apply_s(s.apply_A, x64[: s.n_u]), "K64_mapped_s": apply_s(s.apply_K, x64),
+                   "A32_mapped_s": apply_s(s.apply_A, u32)}
+            s.set_geometry(None)
+            row.update({"A64_brick_s": apply_s(s.apply_A, x64[: s.n_u]), "K64_brick_s": apply_s(s.apply_K, x64),
+                        "A32_brick_s": apply_s(s.apply_A, u32)})
+            if kind == "brick":
+                _, _, rb = s.solve(f, rtol=RTOL, maxit=args.sweep_maxit)
+                row["iters_brick_path"] = rb.iters
+            s.set_geometry(Xt)
+            s.solve(f, rtol=RTOL, maxit=args.sweep_maxit)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, res = s.solve(f, rtol=RTOL, maxit=args.sweep_maxit)
+            torch.cuda.synchronize()
+            row.update({"iters": res.iters, "converged": res.status == 0, "rel_res": res.rel_res,
+                        "solve_s": time.perf_counter() - t0})
+            print(json.dumps(row), flush=True)
+            s.close()
     elif args.sweep == "order":
         for k in (2, 3, 4):
             r = solve(k, 16, 1e6)
@@ -791,7 +848,8 @@ def main():
                     help="one viscosity-dependent setup in an NVTX range 'prof' (for an ncu launch list)")
     ap.add_argument("--profile-apply", action="store_true",
                     help="one FP64 A, one FP32 A and one FP64 K apply in an NVTX range 'prof' (for ncu)")
-    ap.add_argument("--sweep", choices=["robustness", "amplification", "order", "alone", "kcycles", "cheb", "restart"],
+    ap.add_argument("--sweep", choices=["robustness", "amplification", "order", "alone", "kcycles", "cheb", "restart",
+                                        "mapped"],
                     help="iteration-count sweeps in the style of Tables 1, 2 and 3b (many JSON lines)")
     ap.add_argument("--sweep-n", type=int, default=32)
     ap.add_argument("--sweep-maxit", type=int, default=2000)

@@ -18,8 +18,9 @@
  * storage: operator inputs there are ignored and outputs there are zero.
  *
  * Ownership: the caller owns every input and output buffer; the context owns
- * the multigrid hierarchy and all workspaces, allocated in wbfbt_create and
- * freed in wbfbt_destroy.  No other call allocates device memory.  Work is
+ * the multigrid hierarchy and all workspaces, allocated in wbfbt_create (and
+ * the geometry buffers, in the first wbfbt_set_geometry) and freed in
+ * wbfbt_destroy.  No other call allocates device memory.  Work is
  * stream-ordered with the stream given to wbfbt_create: each call runs after
  * all work issued on that stream before it, on an internal stream of the
  * context, and work issued on the caller's stream after the call runs after
@@ -132,6 +133,17 @@ int wbfbt_sinker_setup(const wbfbt_mesh* mesh, int k, const double* centres, int
                        double omega, double delta, double dr, double beta,
                        double* mu_out, double* f_out, void* stream);
 
+/* The same fields at given node positions: X_nodes is a device array [3][nodes] (component-major,
+ * the coordinates of a mapped mesh, see wbfbt_set_geometry); mesh and k give the node count.
+ * Other arguments as in wbfbt_sinker_setup. */
+int wbfbt_sinker_setup_at(const wbfbt_mesh* mesh, int k, const double* X_nodes, const double* centres,
+                          int n_sinkers, double omega, double delta, double dr, double beta,
+                          double* mu_out, double* f_out, void* stream);
+
+/* The brick's node positions (GLL nodes of every element, Sec. 1.2) into the device array
+ * X_out [3][nodes], component-major: the starting point of a mapped mesh. */
+int wbfbt_node_coords(const wbfbt_mesh* mesh, int k, double* X_out, void* stream);
+
 /* Build a solver context: the fine operators, the sqrt(mu) lumped weights
  * C = M~_u(w_l), D = M~_u(w_r) (Eq. wbfbt, Eq. bdramp), and three multigrid
  * hierarchies (A; continuous Q_k Poisson for K_l and K_r, Sec. 6) with
@@ -202,6 +214,24 @@ int wbfbt_solve(wbfbt_ctx* ctx, const double* f_nodes, double* u, double* p, dou
 #define WBFBT_BLOCK_KR 2
 int wbfbt_solve_block(wbfbt_ctx* ctx, int block, const double* b, double* x, double rtol, int maxit, int* iters,
                       double* final_rel_res);
+
+/* Mapped (non-affine) hexahedral geometry.  X_nodes: the physical coordinates of every node,
+ * component-major [3][nodes] (x of all nodes, then y, z), FP64, device or host pointer (copied).
+ * Each element becomes the image of the reference cube under its isoparametric Q_k map
+ * x(xi) = sum_a X_a l_a(xi) over its (k+1)^3 nodes, and the forms of Sec. 1.2 are integrated on
+ * it: at GLL point q, du/dx = J_q^-T du/dxi with J_q = dx/dxi, weights W_q det J_q; the pressure
+ * space is P_{k-1} in each element's reference coordinates.  The node numbering, the Dirichlet set
+ * (the nodes on the boundary of the node grid) and the vector layouts stay those of the brick.
+ * From this call on, wbfbt_apply_A / _B / _BT / _K (both dtypes), the Krylov operator and the load
+ * vector of wbfbt_solve are the mapped ones; the preconditioner (every wbfbt_apply_* below
+ * wbfbt_apply_K, and the block preconditioner inside wbfbt_solve) stays the brick's with the
+ * context's nodal viscosity, and wbfbt_solve_block returns WBFBT_ERR_INVALID.  mu_nodes given to
+ * wbfbt_create / wbfbt_setup are the viscosity at the mapped nodes.  X_nodes = NULL returns to the
+ * brick.  Returns WBFBT_ERR_INVALID (and keeps the brick) if det J <= 0 or is not finite at some
+ * point.  The first call allocates the geometry buffers (coordinates in FP64 and FP32, the mapped
+ * lumped mass, reference tables: 36 bytes per node) in the context; later calls reuse them.
+ * Synchronises. */
+int wbfbt_set_geometry(wbfbt_ctx* ctx, const double* X_nodes);
 
 /* Sizes of the context's vectors. */
 int wbfbt_sizes(const wbfbt_ctx* ctx, long long* n_nodes, long long* n_elem, int* np_per_elem,

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build", platform.machine())
 LIB = os.path.join(BUILD, "libwbfbt.so")
-SOURCES = ["tables.cpp", "elem_ops.cu", "fused_ops.cu", "q2_ops.cu", "q2_fused.cu", "q2_fp64.cu", "kw_ops.cu", "vec_ops.cu", "wbfbt.cu", "noalloc.cu", "unet.cu", "schur_mass.cu"]
+SOURCES = ["tables.cpp", "elem_ops.cu", "fused_ops.cu", "q2_ops.cu", "q2_fused.cu", "q2_fp64.cu", "kw_ops.cu", "vec_ops.cu", "wbfbt.cu", "noalloc.cu", "unet.cu", "schur_mass.cu", "mapped.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -743,20 +743,20 @@ struct Centres {
   double x[WB_MAXN];   // GLL nodes
 };
 
-__global__ void k_sinker(Grid g, int K, Centres cs, int ns, double omega,
-                         double delta, double dr, double beta, double* __restrict__ mu, double* __restrict__ f) {
-  pdl_entry();
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= g.nn) return;
-  const int idx[3] = {n % g.NX, (n / g.NX) % g.NY, n / (g.NX * g.NY)};
+// Brick coordinate of node index idx along axis d: element e = idx / K (the last node belongs to the
+// last element), local GLL node a = idx - K e.
+__device__ inline double brick_coord(const Grid& g, int K, const Centres& cs, int d, int idx) {
   const int ne[3] = {g.nx, g.ny, g.nz};
-  double x[3];
-  for (int d = 0; d < 3; ++d) {
-    int e = idx[d] / K;
-    if (e > ne[d] - 1) e = ne[d] - 1;
-    const int a = idx[d] - K * e;
-    x[d] = e * g.h[d] + (cs.x[a] + 1.0) * 0.5 * g.h[d];
-  }
+  int e = idx / K;
+  if (e > ne[d] - 1) e = ne[d] - 1;
+  const int a = idx - K * e;
+  return e * g.h[d] + (cs.x[a] + 1.0) * 0.5 * g.h[d];
+}
+
+// mu and f_z of Sec. 2.1 at point x: chi = prod_s (1 - exp(-delta max(0, |x - c_s| - omega/2)^2)),
+// mu = (mu_max - mu_min)(1 - chi) + mu_min with mu_max/min = dr^(+-1/2), f = (0, 0, beta (chi - 1)).
+__device__ inline void sinker_point(const double (&x)[3], const Centres& cs, int ns, double omega, double delta,
+                                    double dr, double beta, double& mu, double& fz) {
   double chi = 1.0;
   for (int s = 0; s < ns; ++s) {
     const double dx = x[0] - cs.c[s][0], dy = x[1] - cs.c[s][1], dz = x[2] - cs.c[s][2];
@@ -769,12 +769,36 @@ __global__ void k_sinker(Grid g, int K, Centres cs, int ns, double omega,
     chi *= 1.0 - exp(-t);
   }
   const double mu_min = 1.0 / sqrt(dr), mu_max = sqrt(dr);
-  mu[n] = (mu_max - mu_min) * (1.0 - chi) + mu_min;
+  mu = (mu_max - mu_min) * (1.0 - chi) + mu_min;
+  fz = beta * (chi - 1.0);
+}
+
+// X: given nodal coordinates [3][nn] (the mapped form), or null for the brick's GLL nodes.
+__global__ void k_sinker(Grid g, int K, Centres cs, const double* __restrict__ X, int ns, double omega,
+                         double delta, double dr, double beta, double* __restrict__ mu, double* __restrict__ f) {
+  pdl_entry();
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nn) return;
+  const int idx[3] = {n % g.NX, (n / g.NX) % g.NY, n / (g.NX * g.NY)};
+  double x[3];
+  for (int d = 0; d < 3; ++d) x[d] = X ? X[(size_t)d * g.nn + n] : brick_coord(g, K, cs, d, idx[d]);
+  double m, fz;
+  sinker_point(x, cs, ns, omega, delta, dr, beta, m, fz);
+  mu[n] = m;
   if (f) {
     f[n] = 0.0;
     f[(size_t)g.nn + n] = 0.0;
-    f[2 * (size_t)g.nn + n] = beta * (chi - 1.0);
+    f[2 * (size_t)g.nn + n] = fz;
   }
+}
+
+// The brick's nodal coordinates [3][nn].
+__global__ void k_node_coords(Grid g, int K, Centres cs, double* __restrict__ X) {
+  pdl_entry();
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nn) return;
+  const int idx[3] = {n % g.NX, (n / g.NX) % g.NY, n / (g.NX * g.NY)};
+  for (int d = 0; d < 3; ++d) X[(size_t)d * g.nn + n] = brick_coord(g, K, cs, d, idx[d]);
 }
 
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -998,13 +1022,21 @@ cudaError_t launch_restrict(const Grid& gc, int k, const RefTables* dtab, int nc
 }
 
 cudaError_t launch_sinker(const Grid& g, int k, const RefTables& htab, const double* centres, int ns, double omega,
-                          double delta, double dr, double beta, double* mu, double* f, cudaStream_t st) {
+                          double delta, double dr, double beta, double* mu, double* f, cudaStream_t st,
+                          const double* X) {
   if (ns < 0 || ns > 128) return cudaErrorInvalidValue;
   Centres cs;
   for (int s = 0; s < ns; ++s)
     for (int d = 0; d < 3; ++d) cs.c[s][d] = centres[3 * s + d];
   for (int a = 0; a < WB_MAXN; ++a) cs.x[a] = htab.x[a];
-  wb_launch(k_sinker, blocks_for(g.nn, 128), 128, 0, st, g, k, cs, ns, omega, delta, dr, beta, mu, f);
+  wb_launch(k_sinker, blocks_for(g.nn, 128), 128, 0, st, g, k, cs, X, ns, omega, delta, dr, beta, mu, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_node_coords(const Grid& g, int k, const RefTables& htab, double* X, cudaStream_t st) {
+  Centres cs;
+  for (int a = 0; a < WB_MAXN; ++a) cs.x[a] = htab.x[a];
+  wb_launch(k_node_coords, blocks_for(g.nn, 128), 128, 0, st, g, k, cs, X);
   return cudaGetLastError();
 }
 

@@ -71,6 +71,26 @@ template <typename T>
 cudaError_t launch_gather(const Grid& g, int k, int ncomp, int mask_boundary, const T* Ye, const Epi<T>& e,
                           cudaStream_t st);
 
+// The same node pass over the element-major scratch [ne][ncomp][n^3] on any grid (launch_gather
+// reads the row-segment layout on grids whose k = 2 element passes take the row kernels).
+template <typename T>
+cudaError_t launch_gather_elem(const Grid& g, int k, int ncomp, int mask_boundary, const T* Ye, const Epi<T>& e,
+                               cudaStream_t st);
+
+// ---- Mapped (non-affine) hexahedra (mapped.cu): isoparametric Q_k geometry from the nodal
+// coordinates X [3][nn] (precision T); reftab: the operator tables of the reference element
+// (derivatives unscaled, weights without |J|).  Ye: element-major scratch [ne][3][n^3].
+// ops OP_A, OP_BT, OP_B or all three: yu = epilogue of the velocity output (Dirichlet rows 0),
+// yp = epilogue of the B output per (e, m).  bad: set to 1 where det J <= 0.
+template <typename T>
+cudaError_t launch_mapped_stokes(const Grid& g, int k, const void* reftab, const T* X, int ops, const T* u,
+                                 const T* p, const T* coef, int coef_nodal, T* Ye, const Epi<T>& yu, const Epi<T>& yp,
+                                 int* bad, cudaStream_t st);
+// lm(node) = sum over the points at that node of W_q det J_q (the mapped lumped mass, no mask).
+template <typename T>
+cudaError_t launch_mapped_mass(const Grid& g, int k, const void* reftab, const T* X, T* Ye, T* lm, int* bad,
+                               cudaStream_t st);
+
 // Fused transfers between coarse grid gc and its refinement, ncomp components.
 //   prolong : out_f (+)= P in_c in one pass (N^3 coarse values per fine node)
 //   restrict: out_c = P^T in_f in three separable passes, all components per launch

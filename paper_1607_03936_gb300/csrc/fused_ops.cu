@@ -1018,6 +1018,7 @@ void build_optab_host(const RefTables& t, const Grid& g, int k, void* out) {
   template cudaError_t launch_apply_vec_epi<T>(const Grid&, int, const void*, int, const T*, const T*, const T*, int, \
                                                T*, int, const Epi<T>&, cudaStream_t);                                \
   template cudaError_t launch_gather<T>(const Grid&, int, int, int, const T*, const Epi<T>&, cudaStream_t);           \
+  template cudaError_t launch_gather_elem<T>(const Grid&, int, int, int, const T*, const Epi<T>&, cudaStream_t);      \
   template cudaError_t launch_prolong_fused<T>(const Grid&, int, const void*, int, const T*, T*, int, cudaStream_t);  \
   template cudaError_t launch_restrict_batched<T>(const Grid&, int, const void*, int, const T*, T*, int, T*, T*,      \
                                                   cudaStream_t);                                                      \

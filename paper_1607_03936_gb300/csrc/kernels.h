@@ -106,10 +106,13 @@ template <typename T>
 cudaError_t launch_restrict(const Grid& gc, int k, const RefTables* dtab, int ncomp, const T* in_f, T* out_c,
                             int mask_dirichlet, T* w1, T* w2, cudaStream_t st);
 
-// Multi-sinker viscosity / forcing (Sec. 2.1) and the load vector F = lumped_mass * f (masked).
+// Multi-sinker viscosity / forcing (Sec. 2.1) at the brick's nodes, or at the given nodal
+// coordinates X [3][nn] (mapped meshes); the brick's nodal coordinates; the load vector
+// F = lumped_mass * f (masked).
 cudaError_t launch_sinker(const Grid& g, int k, const RefTables& htab, const double* centres, int ns,
                           double omega, double delta, double dr, double beta, double* mu, double* f,
-                          cudaStream_t st);
+                          cudaStream_t st, const double* X = nullptr);
+cudaError_t launch_node_coords(const Grid& g, int k, const RefTables& htab, double* X, cudaStream_t st);
 cudaError_t launch_load_vector(const Grid& g, const double* lm, const double* f, double* F, cudaStream_t st);
 
 // Zero the boundary-node entries of ncomp stacked nodal fields.

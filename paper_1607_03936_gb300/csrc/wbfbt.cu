@@ -158,6 +158,14 @@ struct wbfbt_ctx {
   float* Ye32 = nullptr;    // element-pass scratch for the FP32 applies
   void* ot64 = nullptr;     // fine-level operator tables, FP64
   void* ot32 = nullptr;     // fine-level operator tables, FP32
+  // mapped geometry (wbfbt_set_geometry): the Krylov operator, the entry-point applies and the
+  // load vector take the isoparametric map of these nodal coordinates
+  bool mapped = false;
+  double* X64 = nullptr;    // coordinates [3][nn]
+  float* X32 = nullptr;
+  void* rt64 = nullptr;     // reference-element operator tables (unscaled derivatives, weights)
+  void* rt32 = nullptr;
+  double* lm_map = nullptr; // mapped lumped mass per node
   struct DenseJob {
     double* M;
     int n;
@@ -848,6 +856,11 @@ int guarded_ctx(wbfbt_ctx* c, F f) {
 
 void apply_K64(wbfbt_ctx* c, const double* x, double* y) {
   const long long nu = 3LL * c->g.nn;
+  if (c->mapped) {
+    CK(launch_mapped_stokes<double>(c->g, c->k, c->rt64, c->X64, OP_A | OP_BT | OP_B, x, x + nu, c->mu64, 1, c->Ye64,
+                                    epi_store<double>(y), epi_store<double>(y + nu), c->dflag, c->st));
+    return;
+  }
   CK(launch_elem_stokes<double>(c->g, c->k, c->ot64, OP_A | OP_BT | OP_B, x, nullptr, x + nu, c->mu64, 1, c->Ye64,
                                 epi_store<double>(y + nu), c->st));
   CK(launch_gather<double>(c->g, c->k, 3, 1, c->Ye64, epi_store<double>(y), c->st));
@@ -897,9 +910,14 @@ void apply_K_arnoldi(wbfbt_ctx* c, const double* z, double* w) {
   }
   Precond<float>& P = c->P32;
   const long long nu = 3LL * c->g.nn;
-  CK(launch_elem_stokes<float>(c->g, c->k, c->ot32, OP_A | OP_BT | OP_B, P.vout, nullptr, P.vout + nu, c->mu32, 1,
-                               c->Ye32, epi_store<float>(P.vin + nu), c->st));
-  CK(launch_gather<float>(c->g, c->k, 3, 1, c->Ye32, epi_store<float>(P.vin), c->st));
+  if (c->mapped) {
+    CK(launch_mapped_stokes<float>(c->g, c->k, c->rt32, c->X32, OP_A | OP_BT | OP_B, P.vout, P.vout + nu, c->mu32, 1,
+                                   c->Ye32, epi_store<float>(P.vin), epi_store<float>(P.vin + nu), c->dflag, c->st));
+  } else {
+    CK(launch_elem_stokes<float>(c->g, c->k, c->ot32, OP_A | OP_BT | OP_B, P.vout, nullptr, P.vout + nu, c->mu32, 1,
+                                 c->Ye32, epi_store<float>(P.vin + nu), c->st));
+    CK(launch_gather<float>(c->g, c->k, 3, 1, c->Ye32, epi_store<float>(P.vin), c->st));
+  }
   CK((launch_cast<float, double>(c->ntot, P.vin, w, c->st)));
 }
 
@@ -1130,6 +1148,13 @@ namespace {
 
 template <typename T>
 void stokes_apply_t(wbfbt_ctx* c, int ops, const T* u, const T* p, T* yu, T* yp, const T* mu, T* Ye) {
+  if (c->mapped) {
+    const bool dbl = std::is_same<T, double>::value;
+    CK(launch_mapped_stokes<T>(c->g, c->k, dbl ? c->rt64 : c->rt32,
+                               dbl ? (const T*)(const void*)c->X64 : (const T*)(const void*)c->X32, ops, u, p, mu, 1,
+                               Ye, epi_store<T>(yu), epi_store<T>(yp), c->dflag, c->st));
+    return;
+  }
   if (ops == OP_A || ops == OP_BT) {
     CK(launch_apply_vec_epi<T>(c->g, c->k, fine_tab<T>(c), ops, u, p, mu, 1, Ye, 1, epi_store<T>(yu), c->st));
     return;
@@ -1188,6 +1213,28 @@ int wbfbt_sinker_setup(const wbfbt_mesh* mesh, int k, const double* centres, int
   if (!build_ref_tables(k, &t)) return WBFBT_ERR_INVALID;
   Grid g = make_grid(mesh->nx, mesh->ny, mesh->nz, k, mesh->lx, mesh->ly, mesh->lz);
   cudaError_t e = launch_sinker(g, k, t, centres, ns, omega, delta, dr, beta, mu_out, f_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? WBFBT_OK : WBFBT_ERR_CUDA;
+}
+
+int wbfbt_sinker_setup_at(const wbfbt_mesh* mesh, int k, const double* X_nodes, const double* centres, int ns,
+                          double omega, double delta, double dr, double beta, double* mu_out, double* f_out,
+                          void* stream) {
+  if (!mesh_ok(mesh, k) || !X_nodes || (!centres && ns > 0) || ns < 0 || ns > 128 || !mu_out || !(dr >= 1.0))
+    return WBFBT_ERR_INVALID;
+  RefTables t;
+  if (!build_ref_tables(k, &t)) return WBFBT_ERR_INVALID;
+  Grid g = make_grid(mesh->nx, mesh->ny, mesh->nz, k, mesh->lx, mesh->ly, mesh->lz);
+  cudaError_t e = launch_sinker(g, k, t, centres, ns, omega, delta, dr, beta, mu_out, f_out, (cudaStream_t)stream,
+                                X_nodes);
+  return e == cudaSuccess ? WBFBT_OK : WBFBT_ERR_CUDA;
+}
+
+int wbfbt_node_coords(const wbfbt_mesh* mesh, int k, double* X_out, void* stream) {
+  if (!mesh_ok(mesh, k) || !X_out) return WBFBT_ERR_INVALID;
+  RefTables t;
+  if (!build_ref_tables(k, &t)) return WBFBT_ERR_INVALID;
+  Grid g = make_grid(mesh->nx, mesh->ny, mesh->nz, k, mesh->lx, mesh->ly, mesh->lz);
+  cudaError_t e = launch_node_coords(g, k, t, X_out, (cudaStream_t)stream);
   return e == cudaSuccess ? WBFBT_OK : WBFBT_ERR_CUDA;
 }
 
@@ -1622,6 +1669,40 @@ int wbfbt_apply_precond(wbfbt_ctx* c, const void* x, void* y, int dtype) {
   });
 }
 
+int wbfbt_set_geometry(wbfbt_ctx* c, const double* X_nodes) {
+  if (!c) return WBFBT_ERR_INVALID;
+  if (!X_nodes) {
+    c->mapped = false;
+    return WBFBT_OK;
+  }
+  const bool dev = is_device_ptr(X_nodes);
+  int bad = 0;
+  int g = guarded_ctx(c, [&]() {
+    const size_t nn = c->g.nn;
+    if (c->X64 == nullptr) {
+      c->X64 = c->pool.get<double>(3 * nn);
+      c->X32 = c->pool.get<float>(3 * nn);
+      c->lm_map = c->pool.get<double>(nn);
+      Grid gr = c->g;   // the reference element: unit derivative scale, |J| = 1
+      gr.s[0] = gr.s[1] = gr.s[2] = 1.0;
+      gr.detJ = 1.0;
+      c->rt64 = make_device_optab<double>(c, gr, c->k);
+      c->rt32 = make_device_optab<float>(c, gr, c->k);
+    }
+    c->mapped = false;
+    CK(cudaMemcpyAsync(c->X64, X_nodes, sizeof(double) * 3 * nn, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->st));
+    CK((launch_cast<double, float>(3LL * (long long)nn, c->X64, c->X32, c->st)));
+    CK(cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st));
+    CK(launch_mapped_mass<double>(c->g, c->k, c->rt64, c->X64, c->Ye64, c->lm_map, c->dflag, c->st));
+    CK(cudaMemcpyAsync(&bad, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->mapped = bad == 0;
+  });
+  if (g != WBFBT_OK) return g;
+  return bad ? WBFBT_ERR_INVALID : WBFBT_OK;
+}
+
 int wbfbt_solve(wbfbt_ctx* c, const double* f_nodes, double* u, double* p, double rtol, int maxit, int* iters,
                 double* final_rel_res) {
   if (!c || !f_nodes || !u || !p || !(rtol > 0.0) || maxit < 1) return WBFBT_ERR_INVALID;
@@ -1636,7 +1717,7 @@ int wbfbt_solve(wbfbt_ctx* c, const double* f_nodes, double* u, double* p, doubl
       fd = c->stage_f;
     }
     CK(cudaMemsetAsync(c->F + nu, 0, sizeof(double) * np, c->st));
-    CK(launch_load_vector(c->g, c->lm, fd, c->F, c->st));
+    CK(launch_load_vector(c->g, c->mapped ? c->lm_map : c->lm, fd, c->F, c->st));
     status = fgmres(c, rtol, maxit, iters, final_rel_res);
     if (status != WBFBT_OK && status != WBFBT_ERR_MAXIT) return;
     double* ud = dev_u ? u : c->stage_u;
@@ -1654,7 +1735,7 @@ int wbfbt_solve(wbfbt_ctx* c, const double* f_nodes, double* u, double* p, doubl
 
 int wbfbt_solve_block(wbfbt_ctx* c, int block, const double* b, double* x, double rtol, int maxit, int* iters,
                       double* final_rel_res) {
-  if (!c || !b || !x || block < WBFBT_BLOCK_A || block > WBFBT_BLOCK_KR || !(rtol > 0.0) || maxit < 1)
+  if (!c || !b || !x || block < WBFBT_BLOCK_A || block > WBFBT_BLOCK_KR || !(rtol > 0.0) || maxit < 1 || c->mapped)
     return WBFBT_ERR_INVALID;
   if (!is_device_ptr(b) || !is_device_ptr(x)) return WBFBT_ERR_INVALID;
   int status = WBFBT_OK;

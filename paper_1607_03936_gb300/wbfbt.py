@@ -34,7 +34,7 @@ SYMBOLS = ["wbfbt_default_opts", "wbfbt_sinker_setup", "wbfbt_create", "wbfbt_se
            "wbfbt_net_param_count", "wbfbt_net_forward", "wbfbt_net_loss_grad", "wbfbt_net_adam_step",
            "wbfbt_net_save", "wbfbt_net_load", "wbfbt_net_destroy", "wbfbt_attach_net", "wbfbt_learned_sample",
            "wbfbt_learned_stats", "wbfbt_load_learned", "wbfbt_train_learned", "wbfbt_net_conv_layer",
-           "wbfbt_solve_block"]
+           "wbfbt_solve_block", "wbfbt_set_geometry", "wbfbt_sinker_setup_at", "wbfbt_node_coords"]
 NOALLOC_MAX_NODES = 1 << 19
 
 
@@ -79,6 +79,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.wbfbt_apply_Kinv.argtypes = [vp, i, vp, vp, i]
     lib.wbfbt_solve.argtypes = [vp, vp, vp, vp, d, i, ctypes.POINTER(i), ctypes.POINTER(d)]
     lib.wbfbt_solve_block.argtypes = [vp, i, vp, vp, d, i, ctypes.POINTER(i), ctypes.POINTER(d)]
+    lib.wbfbt_set_geometry.argtypes = [vp, vp]
+    lib.wbfbt_sinker_setup_at.argtypes = [ctypes.POINTER(Mesh), i, vp, vp, i, d, d, d, d, vp, vp, vp]
+    lib.wbfbt_node_coords.argtypes = [ctypes.POINTER(Mesh), i, vp, vp]
     lib.wbfbt_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.wbfbt_device_bytes.argtypes = [vp]
@@ -166,6 +169,34 @@ def sinker_setup(nx: int, k: int, centres, omega: float, delta: float, dr: float
     return mu, f
 
 
+def sinker_setup_at(X: torch.Tensor, nx: int, k: int, centres, omega: float, delta: float, dr: float,
+                    beta: float = 10.0, ny: int | None = None, nz: int | None = None, lengths=(1.0, 1.0, 1.0)):
+    """The fields of Sec. 2.1 at the node positions X (float64 device tensor [3][nodes])."""
+    ny, nz = ny or nx, nz or nx
+    mesh = Mesh(nx, ny, nz, *lengths)
+    nn = (k * nx + 1) * (k * ny + 1) * (k * nz + 1)
+    if X.dtype != torch.float64 or X.numel() != 3 * nn or not X.is_cuda:
+        raise ValueError("X must be a float64 device tensor with 3 * n_nodes entries")
+    X = X.contiguous()
+    mu = torch.empty(nn, dtype=torch.float64, device=X.device)
+    f = torch.empty(3 * nn, dtype=torch.float64, device=X.device)
+    c = torch.as_tensor(centres, dtype=torch.float64).contiguous().cpu()
+    _check(lib().wbfbt_sinker_setup_at(ctypes.byref(mesh), k, _ptr(X), ctypes.c_void_p(c.data_ptr()),
+                                       int(c.shape[0]), omega, delta, dr, beta, _ptr(mu), _ptr(f), _stream()),
+           "wbfbt_sinker_setup_at")
+    return mu, f
+
+
+def node_coords(nx: int, k: int, ny: int | None = None, nz: int | None = None, lengths=(1.0, 1.0, 1.0),
+                device="cuda") -> torch.Tensor:
+    """The brick's node positions, float64 device tensor [3][nodes] (component-major)."""
+    ny, nz = ny or nx, nz or nx
+    mesh = Mesh(nx, ny, nz, *lengths)
+    X = torch.empty(3 * (k * nx + 1) * (k * ny + 1) * (k * nz + 1), dtype=torch.float64, device=device)
+    _check(lib().wbfbt_node_coords(ctypes.byref(mesh), k, _ptr(X), _stream()), "wbfbt_node_coords")
+    return X
+
+
 def launch_count() -> int:
     """Kernels launched by libwbfbt.so so far in this process."""
     return lib().wbfbt_launch_count()
@@ -230,6 +261,19 @@ class Solver:
         """Re-run the viscosity-dependent setup for a new mu (no allocation)."""
         self._mu = mu.contiguous()
         _check(lib().wbfbt_setup(self.h, _ptr(self._mu)), "wbfbt_setup")
+
+    def set_geometry(self, X: "torch.Tensor | None"):
+        """Mapped hexahedra: X holds the nodal coordinates, component-major [3][nodes] float64
+        (device or host), or None for the brick.  The operator applies, the Krylov operator and the
+        load vector of solve() take the mapped geometry; the preconditioner stays the brick's."""
+        if X is None:
+            _check(lib().wbfbt_set_geometry(self.h, None), "wbfbt_set_geometry")
+            self._X = None
+            return
+        if X.dtype != torch.float64 or X.numel() != self.n_u:
+            raise ValueError("X must be float64 with 3 * n_nodes entries, component-major")
+        self._X = X.contiguous()
+        _check(lib().wbfbt_set_geometry(self.h, _ptr(self._X)), "wbfbt_set_geometry")
 
     def attach_net(self, net: "Net | None", which_mask: int = 2, accept_ratio: float = 1.0):
         """Use `net` for K_r (bit 1) and/or K_l (bit 0) inside S~^-1, V-cycle as fallback.
