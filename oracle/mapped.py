@@ -20,7 +20,8 @@ node grid, as on the brick.
 The solve: FGMRES on the mapped Stokes system, right-preconditioned by the w-BFBT block
 preconditioner of the undeformed brick with the same nodal viscosity (Eq. precond-stokes,
 Eq. wbfbt): the preconditioner's operators stay those of the brick; only the Krylov operator and
-the right-hand side carry the geometry.
+the right-hand side carry the geometry.  A second form takes the preconditioner's finest level
+from the mapped mesh (its A, B and lumped weights), for comparison.
 """
 from __future__ import annotations
 
@@ -28,6 +29,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import krylov
+from . import multigrid as mg
 from . import operators as op
 from . import wbfbt
 from .mesh import Mesh
@@ -133,14 +135,44 @@ class MappedStokes:
         return np.concatenate([self.A @ u + self.BT @ p, self.B @ u])
 
 
+def lumped_weight_diag(mesh: Mesh, X: np.ndarray, mu_nodes: np.ndarray, a: float) -> np.ndarray:
+    """The sqrt(mu) lumped weight of Eq. wbfbt / Eq. bdramp on the mapped mesh: per node, the sum over
+    the element points at it of W_q det J_q a(e) sqrt(mu)."""
+    _, wq = geometry(mesh, X)
+    w = np.sqrt(op.point_values(mesh, np.asarray(mu_nodes, dtype=np.float64))).ravel()
+    amp = np.repeat(op.boundary_amplification(mesh, a), mesh.n ** 3)
+    return op.incidence(mesh).T @ (wq * amp * w)
+
+
 def solve(mesh: Mesh, X: np.ndarray, mu_nodes, f_nodes, opts: wbfbt.Options = wbfbt.Options(), rtol=1e-6,
-          maxit=1000, history=None):
-    """FGMRES on the mapped system, preconditioned by the brick's w-BFBT block preconditioner.
-    Returns (u, p, iters, rel_res) with p projected against 1_psi."""
+          maxit=1000, history=None, preconditioner: str = "brick"):
+    """FGMRES on the mapped system.  Returns (u, p, iters, rel_res) with p projected against 1_psi.
+
+    preconditioner "brick": the brick's w-BFBT block preconditioner (the GPU path's);
+    "mapped_fine" (sqrt(mu) weights only): the same with its finest level taken from the mapped
+    mesh: A, B, B^T and the lumped weights C, D in the Schur approximation, and the mapped A
+    (its Jacobi diagonal and spectral bound) on the finest level of the viscous V-cycle; the coarser
+    levels and the pressure-Poisson hierarchies stay the brick's."""
     sysm = MappedStokes(mesh, X, mu_nodes)
     prob = wbfbt.StokesProblem(mesh, mu_nodes, opts.a_l, opts.a_r, opts.weights)
+    if preconditioner == "mapped_fine":
+        if opts.weights != "sqrt_mu" or opts.mode != "vcycle" or opts.pmg:
+            raise ValueError("mapped_fine takes the sqrt(mu) weights and the fixed-order V-cycles")
+        interior = ~mesh.boundary_node_mask()
+        prob.A, prob.B, prob.BT = sysm.A, sysm.B, sysm.BT
+        prob.Cdiag = lumped_weight_diag(mesh, X, mu_nodes, prob.a_l)
+        prob.Ddiag = lumped_weight_diag(mesh, X, mu_nodes, prob.a_r)
+        prob.Cinv = np.tile(np.where(interior, 1.0 / prob.Cdiag, 0.0), 3)
+        prob.Dinv = np.tile(np.where(interior, 1.0 / prob.Ddiag, 0.0), 3)
+    elif preconditioner != "brick":
+        raise ValueError(preconditioner)
     pc = wbfbt.BlockPreconditioner(prob, opts.mode, opts.schur_sign, schur=opts.schur,
                                    kinv_cycles=opts.kinv_cycles, pmg=opts.pmg)
+    if preconditioner == "mapped_fine":
+        fine = pc.A_levels[0]
+        lev = mg.Level(mesh, sysm.A, True, coarsest=fine.coarsest)
+        lev.P = fine.P
+        pc.A_levels[0] = lev
     F = np.concatenate([load_vector(mesh, X, f_nodes), np.zeros(mesh.n_p)])
     x, its, rel = krylov.fgmres(sysm.apply_K, pc.apply, F, rtol=rtol, restart=opts.restart, maxit=maxit,
                                 history=history)
