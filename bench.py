@@ -265,6 +265,12 @@ def fp64_alu_peak_tflops(sm_mhz: float | None) -> float:
     return 152 * 2 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
 
 
+def fp32_alu_peak_tflops(sm_mhz: float | None) -> float:
+    """FP32 ALU peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop (one FMA per lane and
+    clock), at the given SM clock (2070 MHz by default)."""
+    return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
 def hbm_peak_gbs() -> tuple[float, str]:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -605,6 +611,39 @@ def run_profile_apply(args, name, cfg):
     s32.close()
 
 
+def run_profile_mapped(args, name, cfg):
+    """One fused FP64 K apply on a mapped mesh of the workload's size (vertex offsets of amp 0.1,
+    seed 7) inside an NVTX range "prof" (after three warm-up applies), for ncu captures of the mapped
+    element pass (launch order: mapped K element pass, node pass)."""
+    import numpy as np
+    import torch
+
+    from paper_1607_03936_gb300 import build
+    build.build()
+    from paper_1607_03936_gb300 import inputs
+    from paper_1607_03936_gb300 import wbfbt as wb
+
+    n, k = cfg["n"], cfg["k"]
+    centres = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
+    X0 = wb.node_coords(n, k).view(3, -1).T.cpu().numpy()
+    X = torch.tensor(np.ascontiguousarray(inputs.deform_vertices(X0, (n, n, n), (1.0, 1.0, 1.0), 0.1, 7).T).ravel(),
+                     device="cuda")
+    mu, _ = wb.sinker_setup_at(X, n, k, centres, cfg["omega"], cfg["delta"], cfg["dr"])
+    s = wb.Solver(n, k, mu, precision=wb.F64, restart=5)
+    s.set_geometry(X)
+    x64 = torch.randn(s.n_u + s.n_p, dtype=torch.float64, device="cuda",
+                      generator=torch.Generator("cuda").manual_seed(1))
+    for _ in range(3):
+        s.apply_K(x64)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("prof")
+    s.apply_K(x64)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_mapped": name, "n_u": s.n_u}), flush=True)
+    s.close()
+
+
 SWEEP_SINKERS = (1, 4, 8, 12, 16, 20, 24, 28)
 SWEEP_DR = (1e4, 1e6, 1e8, 1e10)
 
@@ -623,7 +662,8 @@ def run_sweep(args):
       against one U-Net forward pass (what a learned K~_w^-1 could at best save);
     cheb: Stokes iterations and solve time against the Chebyshev smoothing degree;
     restart: the same against the FGMRES restart length;
-    mapped: mapped-hexahedron applies beside the brick's, and iterations against the distortion.
+    mapped: mapped-hexahedron applies beside the brick's, and iterations against the distortion;
+    applies: every fine-level operator apply of --workload against its HBM and ALU rooflines.
     """
     import numpy as np
     import torch
@@ -771,6 +811,62 @@ def run_sweep(args):
                 print(json.dumps({"sweep": "restart", "workload": wname, "precision": args.precision, "restart": m,
                                   "iters": res.iters, "converged": res.status == 0, "solve_s": min(ts)}), flush=True)
                 s.close()
+    elif args.sweep == "applies":
+        # every fine-level operator apply of the workload against its own roofline: algorithmic
+        # bytes (each vector word moved once) and flops per apply, the time each would take at the
+        # HBM and the ALU peak, and the fraction of the larger of the two that the apply reaches
+        # (CUDA events around each apply, warm, a 256 MiB write before each so L2 starts cold; median
+        # of 20)
+        cfg = inputs.WORKLOADS[args.workload]
+        nn_, k = cfg["n"], cfg["k"]
+        if k != 2:
+            raise SystemExit("--sweep applies counts Q2 operators")
+        c = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
+        mu, f = wb.sinker_setup(nn_, k, c, cfg["omega"], cfg["delta"], cfg["dr"])
+        hbm, hbm_note = hbm_peak_gbs()
+        E, NN, NP = nn_ ** 3, (2 * nn_ + 1) ** 3, 4
+        nq = 3                                            # points per axis
+        fl_A = 36 * nq ** 4 + 30 * nq ** 3                # per element (sum factorisation)
+        fl_B = 6 * nq ** 4 + 2 * nq ** 3 * NP
+        rows = []
+        for prec_name, sprec, es in (("fp32", wb.MIXED, 4), ("fp64", wb.F64, 8)):
+            s = wb.Solver(nn_, k, mu, precision=sprec)
+            dt = torch.float32 if es == 4 else torch.float64
+            gen = torch.Generator(device="cuda").manual_seed(3)
+            u = torch.randn(s.n_u, device="cuda", generator=gen).to(dt)
+            p = torch.randn(s.n_p, device="cuda", generator=gen).to(dt)
+            x = torch.cat([u, p])
+            peak_alu = fp32_alu_peak_tflops(None) if es == 4 else fp64_alu_peak_tflops(None)
+            cases = [("A", lambda: s.apply_A(u), 7 * NN, fl_A * E),
+                     ("B", lambda: s.apply_B(u), 3 * NN + NP * E, fl_B * E),
+                     ("BT", lambda: s.apply_BT(p), NP * E + 3 * NN, fl_B * E),
+                     ("K", lambda: s.apply_K(x), 7 * NN + 2 * NP * E, (fl_A + 2 * fl_B) * E),
+                     ("Kw", lambda: s.apply_Kw(1, p), 2 * NP * E + NN, 2 * fl_B * E + 3 * NN)]
+            flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+            for name, fn, words, flops in cases:
+                for _ in range(3):
+                    fn()
+                ts = []
+                for _ in range(20):
+                    flush.zero_()                        # L2 (129 MB) holds none of the apply's data
+                    ev = _events(2)
+                    ev[0].record()
+                    fn()
+                    ev[1].record()
+                    ts.append(ev)
+                torch.cuda.synchronize()
+                t = statistics.median(e0.elapsed_time(e1) for e0, e1 in ts) / 1e3
+                t_mem = words * es / (hbm * 1e9)
+                t_alu = flops / (peak_alu * 1e12)
+                bound = "hbm" if t_mem >= t_alu else "alu"
+                rows.append({"sweep": "applies", "workload": args.workload, "precision": prec_name, "apply": name,
+                             "t_us": t * 1e6, "alg_bytes": words * es, "alg_flops": flops,
+                             "flop_per_byte": flops / (words * es), "bound": bound,
+                             "hbm_frac": words * es / t / (hbm * 1e9), "alu_frac": flops / t / (peak_alu * 1e12),
+                             "bound_frac": max(t_mem, t_alu) / t, "hbm_peak_gbs": hbm, "hbm_note": hbm_note,
+                             "alu_peak_tflops": peak_alu})
+                print(json.dumps(rows[-1]), flush=True)
+            s.close()
     elif args.sweep == "mapped":
         # mapped hexahedra (isoparametric Q2 from moved nodes, the fields of Sec. 2.1 at the moved
         # nodes): the mapped operator applies beside the brick's on the same mesh (CUDA events),
@@ -846,10 +942,12 @@ def main():
                     help="one setup + solve of the workload and nothing else (for an ncu launch list)")
     ap.add_argument("--profile-setup", action="store_true",
                     help="one viscosity-dependent setup in an NVTX range 'prof' (for an ncu launch list)")
+    ap.add_argument("--profile-mapped", action="store_true",
+                    help="one FP64 K apply on a mapped mesh in an NVTX range 'prof' (for ncu)")
     ap.add_argument("--profile-apply", action="store_true",
                     help="one FP64 A, one FP32 A and one FP64 K apply in an NVTX range 'prof' (for ncu)")
     ap.add_argument("--sweep", choices=["robustness", "amplification", "order", "alone", "kcycles", "cheb", "restart",
-                                        "mapped"],
+                                        "mapped", "applies"],
                     help="iteration-count sweeps in the style of Tables 1, 2 and 3b (many JSON lines)")
     ap.add_argument("--sweep-n", type=int, default=32)
     ap.add_argument("--sweep-maxit", type=int, default=2000)
@@ -865,6 +963,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, name, cfg, rank, world)
+        return
+    if args.profile_mapped:
+        run_profile_mapped(args, name, cfg)
         return
     if args.profile_apply:
         run_profile_apply(args, name, cfg)
