@@ -167,7 +167,7 @@ def solve(mesh: Mesh, X: np.ndarray, mu_nodes, f_nodes, opts: wbfbt.Options = wb
     elif preconditioner != "brick":
         raise ValueError(preconditioner)
     pc = wbfbt.BlockPreconditioner(prob, opts.mode, opts.schur_sign, schur=opts.schur,
-                                   kinv_cycles=opts.kinv_cycles, pmg=opts.pmg)
+                                   kinv_cycles=opts.kinv_cycles, pmg=opts.pmg, ainv_cycles=opts.ainv_cycles)
     if preconditioner == "mapped_fine":
         fine = pc.A_levels[0]
         lev = mg.Level(mesh, sysm.A, True, coarsest=fine.coarsest)

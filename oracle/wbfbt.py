@@ -49,6 +49,7 @@ class Options:
     weights: str = "sqrt_mu"   # w-BFBT weights: "sqrt_mu" (Eq. wbfbt), "grad" (remark in Sec. 4), or
                                # "diag_a": C = D = diag(A), the diag(A)-BFBT of Sec. 1.3
     kinv_cycles: int = 1       # V-cycles per K~_w^-1 application: x += V(b - K_w x) after the first
+    ainv_cycles: int = 1       # V-cycles per A~^-1 application: x += V(b - A x) after the first
     pmg: bool = False          # p-coarsened multigrid (Q_k -> Q1 -> h-levels) for the viscous block
 
 
@@ -161,7 +162,8 @@ class BlockPreconditioner:
     """[A~ B^T; 0 s S~]^-1: y_p = s S~^-1 r_p, y_u = A~^-1 (r_u - B^T y_p)."""
 
     def __init__(self, prob: StokesProblem, mode: str = "vcycle", schur_sign: float = -1.0,
-                 schur_inv=None, A_inv=None, schur: str = "wbfbt", kinv_cycles: int = 1, pmg: bool = False):
+                 schur_inv=None, A_inv=None, schur: str = "wbfbt", kinv_cycles: int = 1, pmg: bool = False,
+                 ainv_cycles: int = 1):
         self.prob = prob
         self.sign = schur_sign
         m = prob.mesh
@@ -178,7 +180,14 @@ class BlockPreconditioner:
             self.A_inv = _ainv
         else:
             self.A_levels = mg.build_hierarchy(m, op.point_values(m, prob.mu), vector=True, pmg=pmg)
-            self.A_inv = lambda b: mg.vcycle(self.A_levels, b)
+
+            def _vcycles(b):
+                # ainv_cycles V-cycles: x = V b, then x += V(b - A x) with the finest level's operator
+                x = mg.vcycle(self.A_levels, b)
+                for _ in range(ainv_cycles - 1):
+                    x = x + mg.vcycle(self.A_levels, b - self.A_levels[0].M @ x)
+                return x
+            self.A_inv = _vcycles
         if schur_inv is not None:
             self.S_inv = schur_inv
         elif schur in ("mass", "mass_diag"):
@@ -204,6 +213,7 @@ def solve(mesh: Mesh, mu_nodes, f_nodes, opts: Options = Options(), rtol=1e-6, m
     """FGMRES(restart) solve of the Stokes system; returns (u, p, iters, rel_res, prob)."""
     prob = StokesProblem(mesh, mu_nodes, opts.a_l, opts.a_r, opts.weights)
     pc = BlockPreconditioner(prob, opts.mode, opts.schur_sign, schur=opts.schur, kinv_cycles=opts.kinv_cycles,
+                             ainv_cycles=opts.ainv_cycles,
                              pmg=opts.pmg)
     F = np.concatenate([op.load_vector(mesh, f_nodes), np.zeros(mesh.n_p)])
     x, its, rel = krylov.fgmres(prob.apply_K, pc.apply, F, rtol=rtol, restart=opts.restart,

@@ -203,3 +203,28 @@ def test_manufactured_solution_rates_q2():
     rp = np.log2(e[1][1] / e[2][1])
     assert ru > 2.7, e
     assert rp > 1.8, e
+
+
+def test_more_A_vcycles_approach_the_exact_viscous_block():
+    """ainv_cycles V-cycles per A~^-1 (x += V(b - A x)): the error against the exact inverse falls
+    with every cycle (the V-cycle is a contraction), and the preconditioned solve needs no more
+    iterations with three cycles than with one."""
+    import scipy.sparse.linalg as spla
+    from oracle import operators as op
+    from oracle import wbfbt as W
+    from oracle.mesh import Mesh
+    from paper_1607_03936_gb300 import inputs
+    m = Mesh(8, 8, 8, 2)
+    mu, f = W.sinker_problem(m, inputs.sinker_centres(0, 8), 0.1, 200.0, 1e6)
+    prob = W.StokesProblem(m, mu)
+    free = np.flatnonzero(m.interior_dof_mask())
+    b = np.random.default_rng(3).standard_normal(m.n_u) * m.interior_dof_mask()
+    xe = np.zeros(m.n_u)
+    xe[free] = spla.spsolve(prob.A[free][:, free].tocsc(), b[free])
+    errs = []
+    for cyc in (1, 2, 3):
+        pc = W.BlockPreconditioner(prob, "vcycle", -1.0, ainv_cycles=cyc)
+        errs.append(np.linalg.norm(pc.A_inv(b) - xe) / np.linalg.norm(xe))
+    assert errs[0] > errs[1] > errs[2]
+    its = [W.solve(m, mu, f, W.Options(ainv_cycles=c))[2] for c in (1, 3)]
+    assert its[1] <= its[0]
