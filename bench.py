@@ -661,6 +661,7 @@ def run_sweep(args):
     kcycles: Stokes iterations with 1-8 V-cycles per K~_w^-1, and the cost of one K_w V-cycle
       against one U-Net forward pass (what a learned K~_w^-1 could at best save);
     cheb: Stokes iterations and solve time against the Chebyshev smoothing degree;
+    acycles: the same against the number of V-cycles per A~^-1 application;
     restart: the same against the FGMRES restart length;
     mapped: mapped-hexahedron applies beside the brick's, and iterations against the distortion;
     applies: every fine-level operator apply of --workload against its HBM and ALU rooflines.
@@ -769,6 +770,27 @@ def run_sweep(args):
                     row["unet_forward_s"] = ev[0].elapsed_time(ev[1]) / 20 / 1e3
                     net.close()
                 print(json.dumps(row), flush=True)
+                s.close()
+    elif args.sweep == "acycles":
+        # V-cycles per A~^-1 application (Sec. 6 approximates A^-1 by V-cycles without fixing their
+        # number): Stokes iterations and solve time on the bench workloads
+        for wname in ("32^3-Q2-S24-DR1e6", "64^3-Q2-S64-DR1e10"):
+            cfg = inputs.WORKLOADS[wname]
+            c = inputs.sinker_centres(cfg["seed"], cfg["n_sinkers"])
+            mu, f = wb.sinker_setup(cfg["n"], cfg["k"], c, cfg["omega"], cfg["delta"], cfg["dr"])
+            for cyc in (1, 2, 3, 4):
+                s = wb.Solver(cfg["n"], cfg["k"], mu, precision=prec, ainv_cycles=cyc)
+                s.solve(f)
+                ts = []
+                for _ in range(2):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    _, _, res = s.solve(f, rtol=RTOL, maxit=args.sweep_maxit)
+                    torch.cuda.synchronize()
+                    ts.append(time.perf_counter() - t0)
+                print(json.dumps({"sweep": "acycles", "workload": wname, "precision": args.precision,
+                                  "ainv_cycles": cyc, "iters": res.iters, "converged": res.status == 0,
+                                  "solve_s": min(ts)}), flush=True)
                 s.close()
     elif args.sweep == "cheb":
         # Chebyshev smoothing degree of every V-cycle (Sec. 6 fixes the smoother family, not its
@@ -947,7 +969,7 @@ def main():
     ap.add_argument("--profile-apply", action="store_true",
                     help="one FP64 A, one FP32 A and one FP64 K apply in an NVTX range 'prof' (for ncu)")
     ap.add_argument("--sweep", choices=["robustness", "amplification", "order", "alone", "kcycles", "cheb", "restart",
-                                        "mapped", "applies"],
+                                        "mapped", "applies", "acycles"],
                     help="iteration-count sweeps in the style of Tables 1, 2 and 3b (many JSON lines)")
     ap.add_argument("--sweep-n", type=int, default=32)
     ap.add_argument("--sweep-maxit", type=int, default=2000)

@@ -105,6 +105,10 @@ typedef struct {
                                       same mesh and on its h-coarsenings (coefficient moved to
                                       Q1 by the normalised L^2-adjoint of trilinear
                                       interpolation); 0 (default): Q_k on every level         */
+    int ainv_cycles;               /* V-cycles per application of A~^-1 in Eq. precond-stokes
+                                      (default 1; 1..64; Sec. 6 approximates A^-1 by V-cycles
+                                      without fixing their number): each further cycle corrects
+                                      the residual, x += V(b - A x)                          */
 } wbfbt_opts;
 
 #define WBFBT_SCHUR_WBFBT 0

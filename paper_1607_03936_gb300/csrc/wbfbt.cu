@@ -102,6 +102,7 @@ struct Precond {
   T *pb = nullptr, *px = nullptr, *pr = nullptr, *pd = nullptr, *ptmp = nullptr, *vtmp = nullptr;
   T *sr = nullptr, *sy = nullptr, *sz = nullptr, *sy2 = nullptr, *sv1 = nullptr, *sv2 = nullptr;
   T *urhs = nullptr, *utmp = nullptr;                   // Schur / block workspaces
+  T *ares = nullptr, *acor = nullptr;                   // A~^-1 residual and correction (ainv_cycles > 1)
   T *vin = nullptr, *vout = nullptr;                    // mixed-precision Krylov <-> preconditioner
   T* Ye = nullptr;                                      // element-pass outputs [ne][3][n^3] (finest level)
   T* Kst[2] = {nullptr, nullptr};                       // assembled K_w stencils (k <= 3), w_l and w_r
@@ -540,6 +541,17 @@ void precond(wbfbt_ctx* c, const T* x, T* y) {
   e.b = xu;
   apply_BT_epi<T>(c, yp, e);
   vcycle<T>(c, P.HA, 0, P.urhs, yu);
+  // further V-cycles on the residual of the current iterate: y_u += V(b - A y_u)
+  Level<T>& L0 = P.HA.lv[0];
+  for (int cyc = 1; cyc < c->opt.ainv_cycles && !L0.coarsest; ++cyc) {
+    Epi<T> er;
+    er.mode = EPI_BMINUS;
+    er.y = P.ares;
+    er.b = P.urhs;
+    level_apply<T>(c, P.HA, L0, yu, er);
+    vcycle<T>(c, P.HA, 0, P.ares, P.acor);
+    CK(launch_axpby<T>(nu, T(1), yu, T(1), P.acor, yu, c->st));
+  }
 }
 
 // ------------------------------------------------------------------ setup
@@ -741,6 +753,8 @@ void build_precond(wbfbt_ctx* c) {
   }
   for (T** q : {&P.pb, &P.px, &P.pr, &P.pd, &P.ptmp, &P.sr, &P.sy, &P.sz, &P.sy2}) c->pool.ensure(*q, np);
   for (T** q : {&P.vtmp, &P.sv1, &P.sv2, &P.urhs, &P.utmp}) c->pool.ensure(*q, nu);
+  if (c->opt.ainv_cycles > 1)
+    for (T** q : {&P.ares, &P.acor}) c->pool.ensure(*q, nu);
   c->pool.ensure(P.vin, c->ntot);
   c->pool.ensure(P.vout, c->ntot);
   {
@@ -1185,6 +1199,7 @@ void wbfbt_default_opts(wbfbt_opts* o) {
   o->arnoldi_precision = WBFBT_F64;
   o->weights = WBFBT_WEIGHTS_SQRT_MU;
   o->kinv_cycles = 1;
+  o->ainv_cycles = 1;
   o->pmg = 0;
 }
 
@@ -1253,7 +1268,8 @@ int wbfbt_create(const wbfbt_mesh* mesh, int k, const double* mu_nodes, const wb
       (c->opt.arnoldi_precision != WBFBT_F64 && c->opt.arnoldi_precision != WBFBT_F32) ||
       (c->opt.arnoldi_precision == WBFBT_F32 && c->opt.precision != WBFBT_MIXED) ||
       c->opt.weights < WBFBT_WEIGHTS_SQRT_MU || c->opt.weights > WBFBT_WEIGHTS_DIAG_A ||
-      c->opt.kinv_cycles < 1 || c->opt.kinv_cycles > 64 || (c->opt.pmg != 0 && c->opt.pmg != 1))
+      c->opt.kinv_cycles < 1 || c->opt.kinv_cycles > 64 || (c->opt.pmg != 0 && c->opt.pmg != 1) ||
+      c->opt.ainv_cycles < 1 || c->opt.ainv_cycles > 64)
     return WBFBT_ERR_INVALID;
   if (c->opt.schur_sign >= 0) c->opt.schur_sign = 1; else c->opt.schur_sign = -1;
   c->ust = (cudaStream_t)stream;

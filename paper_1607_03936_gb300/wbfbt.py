@@ -54,7 +54,8 @@ class Opts(ctypes.Structure):
                 ("cheb_degree", ctypes.c_int), ("mg_min_n", ctypes.c_int), ("precision", ctypes.c_int),
                 ("schur_sign", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("elem_kernels", ctypes.c_int), ("schur", ctypes.c_int), ("arnoldi_precision", ctypes.c_int),
-                ("weights", ctypes.c_int), ("kinv_cycles", ctypes.c_int), ("pmg", ctypes.c_int)]
+                ("weights", ctypes.c_int), ("kinv_cycles", ctypes.c_int), ("pmg", ctypes.c_int),
+                ("ainv_cycles", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -231,6 +232,7 @@ class Solver:
                  cheb_degree: int = 3, mg_min_n: int = 4, precision: int = F64, schur_sign: int = -1,
                  use_graphs: bool = True, elem_kernels: int = 0, schur: int = SCHUR_WBFBT,
                  arnoldi_precision: int = F64, weights: int = WEIGHTS_SQRT_MU, kinv_cycles: int = 1,
+                 ainv_cycles: int = 1,
                  pmg: bool = False):
         self.nx, self.ny, self.nz, self.k = nx, ny or nx, nz or nx, k
         self.mesh = Mesh(self.nx, self.ny, self.nz, *lengths)
@@ -242,6 +244,7 @@ class Solver:
         o.arnoldi_precision = arnoldi_precision
         o.weights = weights
         o.kinv_cycles = kinv_cycles
+        o.ainv_cycles = ainv_cycles
         o.pmg = int(pmg)
         self.opts = o
         self.precision = precision

@@ -121,6 +121,27 @@ def test_several_kinv_cycles_match_oracle(wb):
     assert rel(N(u), uo) < 1e-10 and rel(N(p), po) < 1e-10
 
 
+def test_several_ainv_cycles_match_oracle(wb):
+    """ainv_cycles = 3: each A~^-1 of the block preconditioner runs three residual-correcting
+    V-cycles, on both sides: the block preconditioner at 1e-10 (FP64), the FP64 solve +-1 its and
+    1e-10, the mixed solve within 1e-6 of the oracle's."""
+    m, mu, f = problem(8, 2, 1e6, 8)
+    uo, po, its, relo, _ = W.solve(m, mu, f, W.Options(ainv_cycles=3))
+    s = wb.Solver(8, 2, torch.tensor(mu, device="cuda"), ainv_cycles=3)
+    prob = W.StokesProblem(m, mu)
+    pc = W.BlockPreconditioner(prob, "vcycle", -1.0, ainv_cycles=3)
+    rng = np.random.default_rng(9)
+    x = np.concatenate([rng.standard_normal(m.n_u) * m.interior_dof_mask(), rng.standard_normal(m.n_p)])
+    assert rel(N(s.apply_precond(torch.tensor(x, device="cuda"))), pc.apply(x)) < 1e-10
+    u, p, res = s.solve(torch.tensor(f.T.ravel(), device="cuda"))
+    assert res.status == 0 and abs(res.iters - its) <= 1, (res.iters, its)
+    assert rel(N(u), uo) < 1e-10 and rel(N(p), po) < 1e-10
+    s32 = wb.Solver(8, 2, torch.tensor(mu, device="cuda"), ainv_cycles=3, precision=wb.MIXED)
+    u, p, res = s32.solve(torch.tensor(f.T.ravel(), device="cuda"))
+    assert res.status == 0 and abs(res.iters - its) <= 3, (res.iters, its)
+    assert rel(N(u), uo) < 1e-6 and rel(N(p), po) < 1e-6
+
+
 # ------------------------------------------------------------------ diag(A)-BFBT (Sec. 1.3)
 
 def test_diag_a_bfbt_matches_oracle(wb):
