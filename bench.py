@@ -575,10 +575,10 @@ def run_profile_setup(args, name, cfg):
 
 
 def run_profile_apply(args, name, cfg):
-    """One fine-level A apply in FP64, one in FP32 and one fused FP64 K apply inside an NVTX range
-    "prof" (after three warm-up applies each), for ncu --nvtx --nvtx-include prof/ captures of the
-    operator kernels (launch order: FP64 A element + node pass, FP32 A element + node pass, FP64 K
-    element + node pass)."""
+    """One fine-level A apply in FP64, one in FP32, one fused FP64 K apply and one FP32 B^T apply
+    inside an NVTX range "prof" (after three warm-up applies each), for ncu --nvtx --nvtx-include
+    prof/ captures of the operator kernels (launch order: FP64 A element + node pass, FP32 A element
+    + node pass, FP64 K element + node pass, FP32 B^T element + node pass)."""
     import torch
 
     from paper_1607_03936_gb300 import build
@@ -595,15 +595,18 @@ def run_profile_apply(args, name, cfg):
     u32 = u64.float()
     x64 = torch.randn(s64.n_u + s64.n_p, dtype=torch.float64, device="cuda",
                       generator=torch.Generator("cuda").manual_seed(1))
+    p32 = x64[s64.n_u:].float()
     for _ in range(3):
         s64.apply_A(u64)
         s32.apply_A(u32)
         s64.apply_K(x64)
+        s32.apply_BT(p32)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("prof")
     s64.apply_A(u64)
     s32.apply_A(u32)
     s64.apply_K(x64)
+    s32.apply_BT(p32)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     print(json.dumps({"profile_apply": name, "n_u": s64.n_u}), flush=True)
