@@ -86,6 +86,8 @@ template <typename T>
 cudaError_t launch_mapped_stokes(const Grid& g, int k, const void* reftab, const T* X, int ops, const T* u,
                                  const T* p, const T* coef, int coef_nodal, T* Ye, const Epi<T>& yu, const Epi<T>& yp,
                                  int* bad, cudaStream_t st);
+// Once per process, outside stream capture: shared-memory opt-in of the mapped element passes.
+cudaError_t mapped_prepare();
 // lm(node) = sum over the points at that node of W_q det J_q (the mapped lumped mass, no mask).
 template <typename T>
 cudaError_t launch_mapped_mass(const Grid& g, int k, const void* reftab, const T* X, T* Ye, T* lm, int* bad,

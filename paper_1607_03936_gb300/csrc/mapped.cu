@@ -28,6 +28,26 @@ using namespace wb;
 
 constexpr int OPM_MASS = 16;   // this file only: the point weights W_q det J_q, one component
 
+// Elements per block: in FP64 at k = 2, 32, so the 27 x 32 threads fill 27 warps (four elements
+// would leave a quarter of the last warp idle; the FP64 pass is bound by the FP64 pipe, 2469 against
+// 2767 us for the A apply at 64^3); otherwise the per-point layout's count (FP32 k = 2: 4 x 27
+// threads, measured faster there; k = 3: 2 x 64; k = 4: 125).
+template <typename T, int N>
+struct MCfg {
+  static constexpr int N3 = N * N * N;
+  static constexpr int EPB = (N == 3 && sizeof(T) == 8) ? 32 : Cfg<N>::EPB;
+  static constexpr int THREADS = EPB * N3;
+};
+
+// Dynamic shared memory of one block: the operator tables, then the staged coordinates, velocities,
+// pulled-back stresses and weighted divergences of its elements.
+template <typename T, int N, int OPS>
+constexpr size_t mapped_smem() {
+  constexpr bool GRAD = (OPS & OP_A) || (OPS & OP_B), SCAT = (OPS & OP_A) || (OPS & OP_BT), DB = OPS & OP_B;
+  constexpr size_t tab = (sizeof(OpTab<T, N>) + 15) / 16 * 16;
+  return tab + sizeof(T) * MCfg<T, N>::EPB * MCfg<T, N>::N3 * (3 + (GRAD ? 3 : 0) + (SCAT ? 9 : 0) + (DB ? 1 : 0));
+}
+
 template <typename T>
 struct Jac {
   T inv[3][3];   // inv[r][d] = dxi_r / dx_d
@@ -75,19 +95,24 @@ __device__ __forceinline__ Jac<T> invert(const T (&M)[3][3]) {
 // outputs [ne][3][N^3] (A, B^T), or [ne][N^3] point weights (OPM_MASS).  pe: epilogue of the
 // pressure output (B).  bad: set to 1 where det J <= 0 (the outputs there are not meaningful).
 template <typename T, int N, int OPS>
-__global__ void __launch_bounds__(Cfg<N>::THREADS)
+__global__ void __launch_bounds__(MCfg<T, N>::THREADS)
 k_mapped_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict__ X, const T* __restrict__ u,
               const T* __restrict__ p, const T* __restrict__ coef, int coef_nodal, T* __restrict__ Ye, Epi<T> pe,
               int* __restrict__ bad) {
   pdl_entry();
-  constexpr int N3 = Cfg<N>::N3, NP = Cfg<N>::NP, EPB = Cfg<N>::EPB, K = N - 1;
+  constexpr int N3 = MCfg<T, N>::N3, NP = Cfg<N>::NP, EPB = MCfg<T, N>::EPB, K = N - 1;
   constexpr bool DA = OPS & OP_A, DBT = OPS & OP_BT, DB = OPS & OP_B, MASS = OPS & OPM_MASS;
   constexpr bool GRAD = DA || DB, SCAT = DA || DBT;
-  __shared__ OpTab<T, N> st;
-  __shared__ T sX[EPB][3][N3];
-  __shared__ T su[GRAD ? EPB : 1][3][N3];
-  __shared__ T sT[SCAT ? EPB : 1][9][N3];
-  __shared__ T sdiv[DB ? EPB : 1][N3];
+  extern __shared__ __align__(16) unsigned char msm[];
+  OpTab<T, N>& st = *reinterpret_cast<OpTab<T, N>*>(msm);
+  T* base = reinterpret_cast<T*>(msm + (sizeof(OpTab<T, N>) + 15) / 16 * 16);
+  T(*sX)[3][N3] = reinterpret_cast<T(*)[3][N3]>(base);
+  base += (size_t)EPB * 3 * N3;
+  T(*su)[3][N3] = reinterpret_cast<T(*)[3][N3]>(base);
+  base += GRAD ? (size_t)EPB * 3 * N3 : 0;
+  T(*sT)[9][N3] = reinterpret_cast<T(*)[9][N3]>(base);
+  base += SCAT ? (size_t)EPB * 9 * N3 : 0;
+  T(*sdiv)[N3] = reinterpret_cast<T(*)[N3]>(base);
   copy_tab(st, otab);
   const int tid = threadIdx.x;
   const int le = tid / N3, q = tid - le * N3;
@@ -189,26 +214,46 @@ k_mapped_elem(Grid g, const OpTab<T, N>* __restrict__ otab, const T* __restrict_
   }
 }
 
+template <typename T, int N, int OPS>
+cudaError_t launch_one(const Grid& g, const OpTab<T, N>* tab, const T* X, const T* u, const T* p, const T* coef,
+                       int cn, T* Ye, const Epi<T>& pe, int* bad, cudaStream_t st) {
+  constexpr int EPB = MCfg<T, N>::EPB, TH = MCfg<T, N>::THREADS;
+  const long long nb = ((long long)g.ne + EPB - 1) / EPB;
+  const long long cap = 152LL * 16 * Cfg<N>::EPB / EPB;   // about 16 blocks' worth of elements per SM
+  const unsigned blocks = (unsigned)(nb < cap ? nb : cap);
+  wb_launch(k_mapped_elem<T, N, OPS>, blocks, TH, mapped_smem<T, N, OPS>(), st, g, tab, X, u, p, coef, cn, Ye, pe,
+            bad);
+  return cudaGetLastError();
+}
+
 template <typename T, int N>
 cudaError_t run_mapped(const Grid& g, const void* reftab, const T* X, int ops, const T* u, const T* p, const T* coef,
                        int cn, T* Ye, const Epi<T>& pe, int* bad, cudaStream_t st) {
-  constexpr int EPB = Cfg<N>::EPB, TH = Cfg<N>::THREADS;
   const OpTab<T, N>* tab = static_cast<const OpTab<T, N>*>(reftab);
-  const long long nb = ((long long)g.ne + EPB - 1) / EPB;
-  const unsigned blocks = (unsigned)(nb < 152LL * 16 ? nb : 152LL * 16);
   switch (ops) {
-    case OP_A: wb_launch(k_mapped_elem<T, N, OP_A>, blocks, TH, 0, st, g, tab, X, u, p, coef, cn, Ye, pe, bad); break;
-    case OP_BT: wb_launch(k_mapped_elem<T, N, OP_BT>, blocks, TH, 0, st, g, tab, X, u, p, coef, cn, Ye, pe, bad); break;
-    case OP_B: wb_launch(k_mapped_elem<T, N, OP_B>, blocks, TH, 0, st, g, tab, X, u, p, coef, cn, Ye, pe, bad); break;
-    case OP_A | OP_BT | OP_B:
-      wb_launch(k_mapped_elem<T, N, OP_A | OP_BT | OP_B>, blocks, TH, 0, st, g, tab, X, u, p, coef, cn, Ye, pe, bad);
-      break;
-    case OPM_MASS:
-      wb_launch(k_mapped_elem<T, N, OPM_MASS>, blocks, TH, 0, st, g, tab, X, u, p, coef, cn, Ye, pe, bad);
-      break;
+    case OP_A: return launch_one<T, N, OP_A>(g, tab, X, u, p, coef, cn, Ye, pe, bad, st);
+    case OP_BT: return launch_one<T, N, OP_BT>(g, tab, X, u, p, coef, cn, Ye, pe, bad, st);
+    case OP_B: return launch_one<T, N, OP_B>(g, tab, X, u, p, coef, cn, Ye, pe, bad, st);
+    case OP_A | OP_BT | OP_B: return launch_one<T, N, OP_A | OP_BT | OP_B>(g, tab, X, u, p, coef, cn, Ye, pe, bad, st);
+    case OPM_MASS: return launch_one<T, N, OPM_MASS>(g, tab, X, u, p, coef, cn, Ye, pe, bad, st);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+}
+
+template <typename T, int N, int OPS>
+cudaError_t smem_attr() {
+  return cudaFuncSetAttribute(k_mapped_elem<T, N, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)mapped_smem<T, N, OPS>());
+}
+
+template <typename T, int N>
+cudaError_t smem_attrs() {
+  cudaError_t e = smem_attr<T, N, OP_A>();
+  if (e == cudaSuccess) e = smem_attr<T, N, OP_BT>();
+  if (e == cudaSuccess) e = smem_attr<T, N, OP_B>();
+  if (e == cudaSuccess) e = smem_attr<T, N, OP_A | OP_BT | OP_B>();
+  if (e == cudaSuccess) e = smem_attr<T, N, OPM_MASS>();
+  return e;
 }
 
 template <typename T>
@@ -223,6 +268,19 @@ cudaError_t run_mapped_k(const Grid& g, int k, const void* reftab, const T* X, i
 }
 
 }  // namespace
+
+cudaError_t mapped_prepare() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = smem_attrs<double, 3>();
+  if (e == cudaSuccess) e = smem_attrs<double, 4>();
+  if (e == cudaSuccess) e = smem_attrs<double, 5>();
+  if (e == cudaSuccess) e = smem_attrs<float, 3>();
+  if (e == cudaSuccess) e = smem_attrs<float, 4>();
+  if (e == cudaSuccess) e = smem_attrs<float, 5>();
+  done = e == cudaSuccess;
+  return e;
+}
 
 template <typename T>
 cudaError_t launch_mapped_stokes(const Grid& g, int k, const void* reftab, const T* X, int ops, const T* u,

@@ -1696,6 +1696,7 @@ int wbfbt_set_geometry(wbfbt_ctx* c, const double* X_nodes) {
   int g = guarded_ctx(c, [&]() {
     const size_t nn = c->g.nn;
     if (c->X64 == nullptr) {
+      CK(mapped_prepare());
       c->X64 = c->pool.get<double>(3 * nn);
       c->X32 = c->pool.get<float>(3 * nn);
       c->lm_map = c->pool.get<double>(nn);
