@@ -139,13 +139,15 @@ int wbfbt_sinker_setup(const wbfbt_mesh* mesh, int k, const double* centres, int
 
 /* The same fields at given node positions: X_nodes is a device array [3][nodes] (component-major,
  * the coordinates of a mapped mesh, see wbfbt_set_geometry); mesh and k give the node count.
- * Other arguments as in wbfbt_sinker_setup. */
+ * Other arguments as in wbfbt_sinker_setup.  Returns WBFBT_ERR_INVALID (before any device work) if
+ * X_nodes, mu_out or a non-NULL f_out is not device memory. */
 int wbfbt_sinker_setup_at(const wbfbt_mesh* mesh, int k, const double* X_nodes, const double* centres,
                           int n_sinkers, double omega, double delta, double dr, double beta,
                           double* mu_out, double* f_out, void* stream);
 
 /* The brick's node positions (GLL nodes of every element, Sec. 1.2) into the device array
- * X_out [3][nodes], component-major: the starting point of a mapped mesh. */
+ * X_out [3][nodes], component-major: the starting point of a mapped mesh.  Returns
+ * WBFBT_ERR_INVALID if X_out is not device memory. */
 int wbfbt_node_coords(const wbfbt_mesh* mesh, int k, double* X_out, void* stream);
 
 /* Build a solver context: the fine operators, the sqrt(mu) lumped weights

@@ -1236,6 +1236,7 @@ int wbfbt_sinker_setup_at(const wbfbt_mesh* mesh, int k, const double* X_nodes, 
                           void* stream) {
   if (!mesh_ok(mesh, k) || !X_nodes || (!centres && ns > 0) || ns < 0 || ns > 128 || !mu_out || !(dr >= 1.0))
     return WBFBT_ERR_INVALID;
+  if (!is_device_ptr(X_nodes) || !is_device_ptr(mu_out) || (f_out && !is_device_ptr(f_out))) return WBFBT_ERR_INVALID;
   RefTables t;
   if (!build_ref_tables(k, &t)) return WBFBT_ERR_INVALID;
   Grid g = make_grid(mesh->nx, mesh->ny, mesh->nz, k, mesh->lx, mesh->ly, mesh->lz);
@@ -1245,7 +1246,7 @@ int wbfbt_sinker_setup_at(const wbfbt_mesh* mesh, int k, const double* X_nodes, 
 }
 
 int wbfbt_node_coords(const wbfbt_mesh* mesh, int k, double* X_out, void* stream) {
-  if (!mesh_ok(mesh, k) || !X_out) return WBFBT_ERR_INVALID;
+  if (!mesh_ok(mesh, k) || !X_out || !is_device_ptr(X_out)) return WBFBT_ERR_INVALID;
   RefTables t;
   if (!build_ref_tables(k, &t)) return WBFBT_ERR_INVALID;
   Grid g = make_grid(mesh->nx, mesh->ny, mesh->nz, k, mesh->lx, mesh->ly, mesh->lz);

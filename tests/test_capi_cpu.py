@@ -41,6 +41,9 @@ def test_status_strings_and_defaults_without_gpu():
     assert lib.wbfbt_create(ctypes.byref(m), 9, ctypes.c_void_p(1), None, None, ctypes.byref(h)) == -1
     assert lib.wbfbt_apply_A(None, None, None, 0) == -1
     assert lib.wbfbt_set_geometry(None, None) == -1
+    assert lib.wbfbt_node_coords(ctypes.byref(m), 2, None, None) == -1
+    assert lib.wbfbt_sinker_setup_at(ctypes.byref(m), 2, None, None, 0, 0.1, 200.0, 1e4, 10.0, None, None,
+                                     None) == -1
     assert lib.wbfbt_load_learned(None, b"net.bin") == -1
     assert lib.wbfbt_train_learned(None, None, b"net.bin") == -1
     # options out of range are rejected before any device call

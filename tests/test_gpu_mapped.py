@@ -205,6 +205,20 @@ def test_mapped_solve_mixed_precision(wb):
         assert rel(N(u), uo) < tol and rel(N(p), po) < tol
 
 
+def test_setup_entry_points_reject_host_buffers(wb):
+    """Host memory where device arrays are required is refused before any device work."""
+    import ctypes
+    lib = wb.lib()
+    mesh = wb.Mesh(2, 2, 2, 1.0, 1.0, 1.0)
+    host = torch.zeros(3 * 125, dtype=torch.float64)
+    dev = torch.zeros(125, dtype=torch.float64, device="cuda")
+    c = torch.tensor([[0.5, 0.5, 0.5]], dtype=torch.float64)
+    assert lib.wbfbt_node_coords(ctypes.byref(mesh), 2, ctypes.c_void_p(host.data_ptr()), None) == -1
+    assert lib.wbfbt_sinker_setup_at(ctypes.byref(mesh), 2, ctypes.c_void_p(host.data_ptr()),
+                                     ctypes.c_void_p(c.data_ptr()), 1, 0.1, 200.0, 1e4, 10.0,
+                                     ctypes.c_void_p(dev.data_ptr()), None, None) == -1
+
+
 def test_node_coords_and_sinker_fields_at_mapped_nodes(wb):
     """The library's brick node positions against the oracle mesh's (k = 3: GLL nodes that are not
     evenly spaced), and the fields of Sec. 2.1 evaluated at moved nodes against the oracle's."""
