@@ -38,7 +38,7 @@ def relmax(a, b):
     return abs(a - b).max() / abs(b).max()
 
 
-@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("k", [2, 3, 4])
 def test_axis_aligned_nodes_give_the_brick_operators(k):
     m, X = mesh_and_coords("brick", k=k)
     mu = np.random.default_rng(0).uniform(1.0, 5.0, m.n_nodes)
@@ -50,7 +50,7 @@ def test_axis_aligned_nodes_give_the_brick_operators(k):
     assert relmax(mp.lumped_weight_diag(m, X, mu, 2.0), op.lumped_weight_diag(m, mu, 2.0)) < 1e-13
 
 
-@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("k", [2, 3, 4])
 def test_affine_fields_patch_test_on_trilinear_elements(k):
     m, X = mesh_and_coords("trilinear", k=k)
     vol = LEN[0] * LEN[1] * LEN[2]
