@@ -163,14 +163,20 @@ def partitioned_apply(part: SlabPartition, u_loc: torch.Tensor, p_loc: torch.Ten
     return part.owned_nodes(yu, 3), (part.owned_elements(yp, npe) if yp is not None else None)
 
 
-def library_local_apply(part: SlabPartition, mu_loc: torch.Tensor, lengths, **opts):
+def library_local_apply(part: SlabPartition, mu_loc: torch.Tensor, lengths, X_loc: torch.Tensor | None = None,
+                        **opts):
     """local_apply backed by the CUDA library: a wbfbt.Solver on this rank's sub-mesh (its own GPU),
-    applying K = [A B^T; B 0] in FP64.  mu_loc: the sub-mesh's nodal viscosity (device)."""
+    applying K = [A B^T; B 0] in FP64.  mu_loc: the sub-mesh's nodal viscosity (device).  X_loc: on
+    a mapped mesh, the sub-mesh's node coordinates [3][nodes] (the global coordinates' local planes,
+    as for a velocity); the ghost-layer argument is unchanged, since the mapped operators keep the
+    node grid's boundary as their Dirichlet set."""
     from . import wbfbt as wb
 
     h = (lengths[0] / part.nx, lengths[1] / part.ny, lengths[2] / part.nz)
     s = wb.Solver(part.nx, part.k, mu_loc, ny=part.ny, nz=part.ext_nz,
                   lengths=(lengths[0], lengths[1], h[2] * part.ext_nz), **opts)
+    if X_loc is not None:
+        s.set_geometry(X_loc)
 
     def apply(u_loc, p_loc):
         y = s.apply_K(torch.cat([u_loc, p_loc]))
