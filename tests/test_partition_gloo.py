@@ -1,7 +1,8 @@
 """The slab partition of the operator apply on 2 gloo ranks (CPU): halo exchange of node planes and
 pressure layers, the local apply on each rank's sub-mesh with its two ghost element layers, and
-the owned parts of the result, against the global apply (1e-12).  The local applies here are the
-oracle's assembled matrices on the sub-meshes (the same matrices the CUDA kernels apply); dot
+the owned parts of the result, against the global apply (1e-12), on the brick and on a mapped mesh
+(each rank assembling from its local planes of the node coordinates).  The local applies here are
+the oracle's assembled matrices on the sub-meshes (the same matrices the CUDA kernels apply); dot
 products over owned nodes reduce to the global ones."""
 import os
 import socket
@@ -23,21 +24,37 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _worker(rank, world, port, out):
+def _problem(mapped):
+    """Global mesh, node coordinates (moved interior vertices when mapped), viscosity, inputs."""
+    from oracle import mesh as M
+    from paper_1607_03936_gb300 import inputs
+    mg = M.Mesh(NX, NY, NZ, K)
+    X = mg.node_coords()
+    if mapped:
+        X = inputs.deform_vertices(X, (NX, NY, NZ), (1.0, 1.0, 1.0), 0.12, 9)
+    mu = 1.0 + X[:, 0] + 2.0 * X[:, 2] ** 2
+    rng = np.random.default_rng(5)
+    return mg, X, mu, rng.standard_normal(mg.n_u), rng.standard_normal(mg.n_p)
+
+
+def _operators(mesh, X, mu, mapped):
+    """A and B of the oracle: the brick's, or the mapped mesh's with nodal coordinates X."""
+    from oracle import mapped as mpd
+    from oracle import operators as op
+    if mapped:
+        return mpd.assemble_A(mesh, X, op.point_values(mesh, mu)), mpd.assemble_B(mesh, X)
+    return op.assemble_A(mesh, op.point_values(mesh, mu)), op.assemble_B(mesh)
+
+
+def _worker(rank, world, port, out, mapped=False):
     import torch.distributed as dist
     sys.path.insert(0, ROOT)
     from oracle import mesh as M
-    from oracle import operators as op
     from paper_1607_03936_gb300 import partition
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        mg = M.Mesh(NX, NY, NZ, K)
-        X = mg.node_coords()
-        mu = 1.0 + X[:, 0] + 2.0 * X[:, 2] ** 2
-        rng = np.random.default_rng(5)
-        u = rng.standard_normal(mg.n_u)
-        p = rng.standard_normal(mg.n_p)
+        mg, X, mu, u, p = _problem(mapped)
         part = partition.SlabPartition(NX, NY, NZ, K, world, rank)
         u_loc = part.local_from_global(torch.tensor(u), 3).clone()
         p_loc = part.local_pressure_from_global(torch.tensor(p), mg.Np).clone()
@@ -51,8 +68,8 @@ def _worker(rank, world, port, out):
         pv[part.z1 - part.e0:] = 1e3
         ms = M.Mesh(NX, NY, part.ext_nz, K, 1.0, 1.0, part.ext_nz / NZ)
         mu_loc = part.local_from_global(torch.tensor(mu), 1).numpy()
-        A = op.assemble_A(ms, op.point_values(ms, mu_loc))
-        B = op.assemble_B(ms)
+        X_loc = part.local_from_global(torch.tensor(np.ascontiguousarray(X.T).ravel()), 3).reshape(3, -1).T.numpy()
+        A, B = _operators(ms, X_loc, mu_loc, mapped)
 
         def local_apply(ul, pl):
             a, b = ul.numpy(), pl.numpy()
@@ -65,27 +82,23 @@ def _worker(rank, world, port, out):
         dist.destroy_process_group()
 
 
-def test_partitioned_K_apply_matches_global_on_two_gloo_ranks():
-    from oracle import mesh as M
-    from oracle import operators as op
+@pytest.mark.parametrize("mapped", [False, True])
+def test_partitioned_K_apply_matches_global_on_two_gloo_ranks(mapped):
+    """Brick, and a mapped mesh whose ranks assemble their sub-mesh operators from their local
+    planes of the global node coordinates."""
     ctx = mp.get_context("spawn")
     out = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, out, mapped)) for r in range(2)]
     for pr in procs:
         pr.start()
     res = sorted([out.get(timeout=180) for _ in range(2)], key=lambda t: t[0])
     for pr in procs:
         pr.join(timeout=60)
         assert pr.exitcode == 0
-    mg = M.Mesh(NX, NY, NZ, K)
-    X = mg.node_coords()
-    mu = 1.0 + X[:, 0] + 2.0 * X[:, 2] ** 2
-    rng = np.random.default_rng(5)
-    u = rng.standard_normal(mg.n_u)
-    p = rng.standard_normal(mg.n_p)
-    A = op.assemble_A(mg, op.point_values(mg, mu))
-    B = op.assemble_B(mg)
+    sys.path.insert(0, ROOT)
+    mg, X, mu, u, p = _problem(mapped)
+    A, B = _operators(mg, X, mu, mapped)
     yu = (A @ u + B.T @ p).reshape(3, mg.NZ, mg.NX * mg.NY)
     yp = (B @ u).reshape(NZ, NX * NY * mg.Np)
     got_u = np.concatenate([r[2] for r in res], axis=1)
