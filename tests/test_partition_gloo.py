@@ -123,32 +123,29 @@ def test_slab_bounds_and_ghost_layers():
         partition.SlabPartition(4, 4, 5, 2, 3, 0)
 
 
-def _solve_worker(rank, world, port, out):
+def _solve_worker(rank, world, port, out, mapped=False):
     """The distributed FGMRES of partition.py on `world` gloo ranks (world 1: no process group)."""
     import torch.distributed as dist
     sys.path.insert(0, ROOT)
     from oracle import mesh as M
-    from oracle import operators as op
     from paper_1607_03936_gb300 import partition
     if world > 1:
         os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
         dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        mg = M.Mesh(NX, NY, NZ, K)
-        X = mg.node_coords()
-        mu = 1.0 + X[:, 0] + 2.0 * X[:, 2] ** 2
+        mg, X, mu, _, _ = _problem(mapped)
         part = partition.SlabPartition(NX, NY, NZ, K, world, rank)
         ms = M.Mesh(NX, NY, part.ext_nz, K, 1.0, 1.0, part.ext_nz / NZ)
         mu_loc = part.local_from_global(torch.tensor(mu), 1).numpy()
-        A = op.assemble_A(ms, op.point_values(ms, mu_loc))
-        B = op.assemble_B(ms)
+        X_loc = part.local_from_global(torch.tensor(np.ascontiguousarray(X.T).ravel()), 3).reshape(3, -1).T.numpy()
+        A, B = _operators(ms, X_loc, mu_loc, mapped)
 
         def local_apply(ul, pl):
             a, b = ul.numpy(), pl.numpy()
             return torch.tensor(A @ a + B.T @ b), torch.tensor(B @ a)
 
         K_op = partition.SlabOperator(part, local_apply, mg.Np)
-        b_glob = _consistent_rhs(mg, mu)
+        b_glob = _consistent_rhs(mg, X, mu, mapped)
         lo, hi = part.owned_planes()
         bu = torch.tensor(b_glob[: mg.n_u]).reshape(3, mg.NZ, mg.NX * mg.NY)[:, lo:hi].reshape(-1)
         bp = torch.tensor(b_glob[mg.n_u:]).reshape(NZ, -1)[part.z0: part.z1].reshape(-1)
@@ -159,10 +156,8 @@ def _solve_worker(rank, world, port, out):
             dist.destroy_process_group()
 
 
-def _consistent_rhs(mg, mu):
-    from oracle import operators as op
-    A = op.assemble_A(mg, op.point_values(mg, mu))
-    B = op.assemble_B(mg)
+def _consistent_rhs(mg, X, mu, mapped):
+    A, B = _operators(mg, X, mu, mapped)
     rng = np.random.default_rng(9)
     u = rng.standard_normal(mg.n_u) * np.tile(~mg.boundary_node_mask(), 3)
     p = rng.standard_normal(mg.n_p)
@@ -175,17 +170,17 @@ def _gather(res, mg):
     return np.concatenate([u, p])
 
 
-def test_partitioned_fgmres_matches_one_rank_and_oracle():
+@pytest.mark.parametrize("mapped", [False, True])
+def test_partitioned_fgmres_matches_one_rank_and_oracle(mapped):
     """40 FGMRES iterations (restart 20, identity preconditioner) of the Stokes system on 2 gloo ranks
-    against the same code on 1 rank and against the oracle's FGMRES on the assembled global matrices."""
+    against the same code on 1 rank and against the oracle's FGMRES on the assembled global matrices
+    (brick, and a mapped mesh)."""
     import queue
     from oracle import krylov
-    from oracle import mesh as M
-    from oracle import operators as op
     ctx = mp.get_context("spawn")
     out = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_solve_worker, args=(r, 2, port, out)) for r in range(2)]
+    procs = [ctx.Process(target=_solve_worker, args=(r, 2, port, out, mapped)) for r in range(2)]
     for pr in procs:
         pr.start()
     res2 = sorted([out.get(timeout=300) for _ in range(2)], key=lambda t: t[0])
@@ -193,17 +188,15 @@ def test_partitioned_fgmres_matches_one_rank_and_oracle():
         pr.join(timeout=60)
         assert pr.exitcode == 0
     q1 = queue.Queue()
-    _solve_worker(0, 1, 0, q1)
+    _solve_worker(0, 1, 0, q1, mapped)
     res1 = [q1.get()]
-    mg = M.Mesh(NX, NY, NZ, K)
-    X = mg.node_coords()
-    mu = 1.0 + X[:, 0] + 2.0 * X[:, 2] ** 2
+    mg, X, mu, _, _ = _problem(mapped)
     x2, x1 = _gather(res2, mg), _gather(res1, mg)
     assert res2[0][3] == res1[0][3] == 40
     assert np.linalg.norm(x2 - x1) <= 1e-10 * np.linalg.norm(x1)
-    A = op.assemble_A(mg, op.point_values(mg, mu))
-    B = op.assemble_B(mg)
+    A, B = _operators(mg, X, mu, mapped)
     Kg = lambda v: np.concatenate([A @ v[: mg.n_u] + B.T @ v[mg.n_u:], B @ v[: mg.n_u]])
-    xo, its, _ = krylov.fgmres(Kg, lambda v: v, _consistent_rhs(mg, mu), rtol=1e-14, restart=20, maxit=40)
+    xo, its, _ = krylov.fgmres(Kg, lambda v: v, _consistent_rhs(mg, X, mu, mapped), rtol=1e-14, restart=20,
+                               maxit=40)
     assert its == 40
     assert np.linalg.norm(x1 - xo) <= 1e-8 * np.linalg.norm(xo)
