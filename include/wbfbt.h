@@ -235,7 +235,7 @@ int wbfbt_solve_block(wbfbt_ctx* ctx, int block, const double* b, double* x, dou
  * wbfbt_create / wbfbt_setup are the viscosity at the mapped nodes.  X_nodes = NULL returns to the
  * brick.  Returns WBFBT_ERR_INVALID (and keeps the brick) if det J <= 0 or is not finite at some
  * point.  The first call allocates the geometry buffers (coordinates in FP64 and FP32, the mapped
- * lumped mass, reference tables: 36 bytes per node) in the context; later calls reuse them.
+ * lumped mass, reference tables: 44 bytes per node) in the context; later calls reuse them.
  * Synchronises. */
 int wbfbt_set_geometry(wbfbt_ctx* ctx, const double* X_nodes);
 
